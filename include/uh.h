@@ -1,0 +1,222 @@
+/*
+ * uh.h - C ABI of the GB300 uniform H-matrix (UH) and H-matrix matrix-vector library.
+ *
+ * The operator is the uniform hierarchical matrix of Def. 2.4 of Bruyninckx, Huybrechs and
+ * Meerbergen, "Uniform H-matrix compression with applications to boundary integral equations":
+ *
+ *     A|_b = U_tau S_b V_sigma^*   for every admissible leaf b = tau x sigma in P^+,
+ *     A|_b  stored dense           for every inadmissible leaf b in P^-,
+ *
+ * with one row basis U_tau per row cluster and one column basis V_sigma per column cluster
+ * (Section 2.2, eq. (2.1)). uh_matvec computes w = A v in the four steps of Algorithm 6
+ * (Section 4.4): forward transform xhat_sigma = V_sigma^* x|_sigma, coupling
+ * yhat_tau = sum_{sigma in row(tau)} S_b xhat_sigma, backward transform y|_tau += U_tau yhat_tau,
+ * and the dense near field y|_tau += A|_b x|_sigma. h_* is the ordinary H-matrix of Def. 2.3,
+ * A|_b = X_b Y_b^* per admissible block, applied as in Algorithm 5, kept beside it as the plain
+ * form to compare with.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an int status: UH_OK (0) or one of the UH_E* codes below. No C++
+ *    exception crosses this boundary. uh_last_error() gives a message for the calling thread's
+ *    most recent failure.
+ *  - Complex numbers are stored interleaved (re, im), as C99 complex / std::complex.
+ *  - Matrices are column-major with the leading dimension equal to the row count unless a
+ *    leading dimension argument says otherwise.
+ *  - Index sets: points carry two orderings. "Original" indices are the caller's; "positions"
+ *    are the cluster ordering in which every cluster is a contiguous range [begin, begin+size).
+ *    perm[p] is the original index stored at position p. Vectors passed to the products are in
+ *    ORIGINAL ordering; the permutation is applied inside the kernels.
+ *  - uh_create / h_create read HOST memory only, copy what they need to device memory that the
+ *    op owns, and return; the caller keeps ownership of its arrays and may free them afterwards.
+ *  - Product calls take DEVICE pointers owned by the caller and are asynchronous on the given
+ *    cudaStream_t (passed as void*, NULL = legacy default stream). Scratch memory belongs to the
+ *    op; calls on one op must be ordered (same stream, or synchronised between streams), since
+ *    they share that scratch.
+ */
+#ifndef UH_H
+#define UH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+  UH_OK = 0,
+  UH_EINVAL = 1,     /* invalid argument or descriptor (message in uh_last_error) */
+  UH_ENOMEM = 2,     /* a host or device allocation failed */
+  UH_ECUDA = 3,      /* a CUDA call failed (message names it) */
+  UH_ENOTREADY = 4,  /* result not available yet */
+  UH_ETIMEOUT = 5,   /* a bounded device-side wait ran out */
+  UH_EBUSY = 6       /* resource limit reached */
+};
+
+/* Message for the calling thread's most recent failed call ("" if none). Never NULL. */
+const char* uh_last_error(void);
+
+/* Library version string. */
+const char* uh_version(void);
+
+/* ---------------------------------------------------------------- element types */
+/* Element type of the arrays a descriptor points to. */
+enum { UH_DATA_C128 = 0, /* complex double, 16 bytes */
+       UH_DATA_C64 = 1   /* complex float, 8 bytes */ };
+
+/* Storage and arithmetic of a created op.
+ *  UH_PREC_C128: operator stored complex128, products in FP64; x and y are complex128.
+ *  UH_PREC_C64:  operator stored complex64, products accumulated in FP32; x and y complex64. */
+enum { UH_PREC_C128 = 0, UH_PREC_C64 = 1 };
+
+/* ---------------------------------------------------------------- shared structure */
+/*
+ * Cluster table (Def. 2.1). Cluster c covers positions [cl_begin[c], cl_begin[c]+cl_size[c]).
+ * Only clusters named by a block need to be meaningful; the tree structure itself is not
+ * needed, because the blocks must tile the index square exactly (checked by uh_create).
+ */
+typedef struct {
+  int64_t n;               /* |I| = |J| = number of points, >= 1 */
+  const int64_t* perm;     /* [n] position -> original index, a permutation; NULL = identity */
+  int32_t n_clusters;      /* >= 1 */
+  const int64_t* cl_begin; /* [n_clusters] first position of each cluster */
+  const int64_t* cl_size;  /* [n_clusters] number of positions, >= 1 */
+} uh_tree_desc;
+
+/* Near field P^- (Def. 2.3): dense blocks A|_b, |tau| x |sigma| column-major at D_data+D_off[i]. */
+typedef struct {
+  int64_t n_dense;
+  const int32_t* row_cl;   /* [n_dense] tau */
+  const int32_t* col_cl;   /* [n_dense] sigma */
+  const int64_t* off;      /* [n_dense] element offset into data */
+  const void* data;        /* complex elements of type data_type */
+  int64_t len;             /* number of complex elements in data (bounds check) */
+} uh_dense_desc;
+
+/* ---------------------------------------------------------------- UH operator */
+/*
+ * Uniform H-matrix (Def. 2.4):
+ *  row bases  U_tau   = U_data + row_off[tau],   |tau| x row_rank[tau] column-major;
+ *  col bases  V_sigma = V_data + col_off[sigma], |sigma| x col_rank[sigma] column-major;
+ *  coupling   S_b     = S_data + S_off[i], row_rank[tau] x col_rank[sigma] column-major, for the
+ *             admissible block b = (adm_row[i], adm_col[i]);
+ *  near field as in uh_dense_desc.
+ * Ranks may be 0 (the block then contributes nothing). A cluster that is not the row cluster of
+ * an admissible block may carry row_rank 0 and any offset (likewise for columns).
+ */
+typedef struct {
+  uh_tree_desc tree;
+  int32_t data_type;        /* UH_DATA_C128 or UH_DATA_C64, for every *_data array */
+  const int32_t* row_rank;  /* [n_clusters] */
+  const int64_t* row_off;   /* [n_clusters] */
+  const void* U_data;
+  int64_t U_len;
+  const int32_t* col_rank;  /* [n_clusters] */
+  const int64_t* col_off;   /* [n_clusters] */
+  const void* V_data;
+  int64_t V_len;
+  int64_t n_adm;
+  const int32_t* adm_row;   /* [n_adm] tau */
+  const int32_t* adm_col;   /* [n_adm] sigma */
+  const int64_t* S_off;     /* [n_adm] */
+  const void* S_data;
+  int64_t S_len;
+  uh_dense_desc dense;
+} uh_desc;
+
+typedef struct uh_op uh_op;
+
+/*
+ * Validate the descriptor and create a device-resident op with storage `precision`
+ * (UH_PREC_*). Checks: perm is a permutation; every cluster lies in [0, n); the admissible and
+ * dense blocks together cover the n x n index square exactly once (Def. 2.2); ranks lie in
+ * [0, cluster size]; every matrix lies inside its data array. Fails with UH_EINVAL (nothing
+ * allocated) on the first violation, UH_ENOMEM / UH_ECUDA on allocation or copy failure.
+ * Uses the current CUDA device; the op must be used and destroyed with that device current.
+ */
+int uh_create(const uh_desc* desc, int32_t precision, uh_op** out);
+
+/* Free all device and host memory of the op. NULL is accepted. Synchronises the device. */
+int uh_destroy(uh_op* op);
+
+/*
+ * y = A^UH x (overwrites y). x and y: device arrays of n complex values in ORIGINAL ordering,
+ * complex128 for UH_PREC_C128 ops and complex64 for UH_PREC_C64 ops; they must not overlap.
+ * Asynchronous on `stream` (cudaStream_t as void*). Algorithm 6 (Section 4.4).
+ */
+int uh_matvec(uh_op* op, const void* x, void* y, void* stream);
+
+/*
+ * Y = A^UH X for nrhs right-hand sides: X is n x nrhs column-major with leading dimension ldx
+ * (>= n), Y likewise with ldy; types as for uh_matvec. nrhs >= 1. The first call with a given
+ * nrhs may allocate scratch (call uh_reserve beforehand to avoid that).
+ */
+int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy,
+              void* stream);
+
+/* Allocate the scratch that uh_matmat needs for up to max_nrhs right-hand sides. */
+int uh_reserve(uh_op* op, int32_t max_nrhs);
+
+/* Sizes of the stored operator and of one product (Lemma 2.6, Def. 2.5). */
+typedef struct {
+  int64_t n;
+  int32_t precision;
+  int32_t elem_bytes;         /* 16 (C128) or 8 (C64) */
+  int64_t n_row_bases, n_col_bases, n_adm, n_dense;
+  int64_t E_U, E_V, E_S, E_D; /* stored complex element counts */
+  int64_t sum_row_rank, sum_col_rank;
+  int32_t rank_min, rank_max; /* over all row and column bases with rank > 0 */
+  double rank_mean;
+  int32_t csp;                /* sparsity constant c_sp (Def. 2.5) */
+  int64_t algo_bytes_matvec;  /* elem_bytes*(E_U+E_V+E_S+E_D + 2n + 2(sum ranks)) */
+  int64_t device_bytes;       /* device memory held by the op (packed operator, indices, scratch) */
+  int64_t packed_bytes;       /* bytes streamed per matvec: packed matrices + column indices */
+  int32_t n_launches;         /* kernel launches per uh_matvec */
+  int64_t n_items;            /* work items per matvec, all launches */
+} uh_stats_t;
+
+int uh_stats(const uh_op* op, uh_stats_t* out);
+
+/* ---------------------------------------------------------------- H operator (plain form) */
+/*
+ * H-matrix (Def. 2.3): admissible block i = (adm_row[i], adm_col[i]) with rank adm_rank[i] = k_b
+ * holds X_b = X_data + X_off[i] (|tau| x k_b) and Y_b = Y_data + Y_off[i] (|sigma| x k_b), both
+ * column-major, A|_b = X_b Y_b^*. Near field as for the UH operator.
+ */
+typedef struct {
+  uh_tree_desc tree;
+  int32_t data_type;
+  int64_t n_adm;
+  const int32_t* adm_row;
+  const int32_t* adm_col;
+  const int32_t* adm_rank;
+  const int64_t* X_off;
+  const void* X_data;
+  int64_t X_len;
+  const int64_t* Y_off;
+  const void* Y_data;
+  int64_t Y_len;
+  uh_dense_desc dense;
+} h_desc;
+
+typedef struct h_op h_op;
+
+/* Same conventions, checks and errors as uh_create. */
+int h_create(const h_desc* desc, int32_t precision, h_op** out);
+int h_destroy(h_op* op);
+/* y = A^H x, Algorithm 5 (Section 4.4); arguments as for uh_matvec. */
+int h_matvec(h_op* op, const void* x, void* y, void* stream);
+/* Y = A^H X; arguments as for uh_matmat. */
+int h_matmat(h_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy,
+             void* stream);
+int h_reserve(h_op* op, int32_t max_nrhs);
+/* Fills the fields that apply: E_D, n_adm, n_dense, algo_bytes_matvec (elem_bytes*(E_H+2n+2 sum k_b)),
+ * E_U = sum_b k_b |tau|, E_V = sum_b k_b |sigma|, E_S = 0. */
+int h_stats(const h_op* op, uh_stats_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UH_H */

@@ -1,0 +1,298 @@
+"""ctypes binding of libuh.so (include/uh.h): argument marshalling only.
+
+Every product runs in the library's CUDA kernels; this module only builds the C descriptors
+from numpy arrays (or takes them from the host-side builder), passes device pointers of torch
+tensors, and maps status codes to exceptions. There is no CPU fallback: if the library has not
+been built, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libuh.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+lib = C.CDLL(_LIB_PATH)
+
+UH_OK, UH_EINVAL, UH_ENOMEM, UH_ECUDA, UH_ENOTREADY, UH_ETIMEOUT, UH_EBUSY = range(7)
+UH_DATA_C128, UH_DATA_C64 = 0, 1
+UH_PREC_C128, UH_PREC_C64 = 0, 1
+_PREC = {"c128": UH_PREC_C128, "c64": UH_PREC_C64}
+
+_p = C.c_void_p
+_i32 = C.c_int32
+_i64 = C.c_int64
+
+
+class TreeDesc(C.Structure):
+    _fields_ = [("n", _i64), ("perm", _p), ("n_clusters", _i32), ("cl_begin", _p), ("cl_size", _p)]
+
+
+class DenseDesc(C.Structure):
+    _fields_ = [("n_dense", _i64), ("row_cl", _p), ("col_cl", _p), ("off", _p), ("data", _p),
+                ("len", _i64)]
+
+
+class UHDesc(C.Structure):
+    _fields_ = [("tree", TreeDesc), ("data_type", _i32),
+                ("row_rank", _p), ("row_off", _p), ("U_data", _p), ("U_len", _i64),
+                ("col_rank", _p), ("col_off", _p), ("V_data", _p), ("V_len", _i64),
+                ("n_adm", _i64), ("adm_row", _p), ("adm_col", _p), ("S_off", _p), ("S_data", _p),
+                ("S_len", _i64), ("dense", DenseDesc)]
+
+
+class HDesc(C.Structure):
+    _fields_ = [("tree", TreeDesc), ("data_type", _i32), ("n_adm", _i64),
+                ("adm_row", _p), ("adm_col", _p), ("adm_rank", _p),
+                ("X_off", _p), ("X_data", _p), ("X_len", _i64),
+                ("Y_off", _p), ("Y_data", _p), ("Y_len", _i64), ("dense", DenseDesc)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", _i64), ("precision", _i32), ("elem_bytes", _i32),
+                ("n_row_bases", _i64), ("n_col_bases", _i64), ("n_adm", _i64), ("n_dense", _i64),
+                ("E_U", _i64), ("E_V", _i64), ("E_S", _i64), ("E_D", _i64),
+                ("sum_row_rank", _i64), ("sum_col_rank", _i64),
+                ("rank_min", _i32), ("rank_max", _i32), ("rank_mean", C.c_double), ("csp", _i32),
+                ("algo_bytes_matvec", _i64), ("device_bytes", _i64), ("packed_bytes", _i64),
+                ("n_launches", _i32), ("n_items", _i64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+lib.uh_last_error.restype = C.c_char_p
+lib.uh_version.restype = C.c_char_p
+for _name, _args in [
+    ("uh_create", [C.POINTER(UHDesc), _i32, C.POINTER(_p)]),
+    ("uh_destroy", [_p]),
+    ("uh_matvec", [_p, _p, _p, _p]),
+    ("uh_matmat", [_p, _i32, _p, _i64, _p, _i64, _p]),
+    ("uh_reserve", [_p, _i32]),
+    ("uh_stats", [_p, C.POINTER(Stats)]),
+    ("h_create", [C.POINTER(HDesc), _i32, C.POINTER(_p)]),
+    ("h_destroy", [_p]),
+    ("h_matvec", [_p, _p, _p, _p]),
+    ("h_matmat", [_p, _i32, _p, _i64, _p, _i64, _p]),
+    ("h_reserve", [_p, _i32]),
+    ("h_stats", [_p, C.POINTER(Stats)]),
+]:
+    getattr(lib, _name).argtypes = _args
+    getattr(lib, _name).restype = C.c_int
+
+
+class UHError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where} failed ({code}): {lib.uh_last_error().decode()}")
+
+
+def check(code: int, where: str) -> None:
+    if code != UH_OK:
+        raise UHError(code, where)
+
+
+def version() -> str:
+    return lib.uh_version().decode()
+
+
+def _ptr(a) -> int | None:
+    return None if a is None else a.ctypes.data
+
+
+class _Keep:
+    """Holds the numpy arrays a descriptor points into."""
+
+    def __init__(self):
+        self.arrays = []
+
+    def __call__(self, a, dtype):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dtype)
+        self.arrays.append(a)
+        return a
+
+
+def _tree(keep, d, arrays):
+    d.tree.n = int(arrays["n"])
+    d.tree.perm = _ptr(keep(arrays.get("perm"), np.int64))
+    cb = keep(arrays["cl_begin"], np.int64)
+    d.tree.n_clusters = len(cb)
+    d.tree.cl_begin = _ptr(cb)
+    d.tree.cl_size = _ptr(keep(arrays["cl_size"], np.int64))
+
+
+def _data(keep, a, c128):
+    return keep(a, np.complex128 if c128 else np.complex64)
+
+
+def _dense(keep, d, arrays, c128):
+    row = keep(arrays["dense_row"], np.int32)
+    d.dense.n_dense = len(row)
+    d.dense.row_cl = _ptr(row)
+    d.dense.col_cl = _ptr(keep(arrays["dense_col"], np.int32))
+    d.dense.off = _ptr(keep(arrays["D_off"], np.int64))
+    D = _data(keep, arrays["D_data"], c128)
+    d.dense.data = _ptr(D)
+    d.dense.len = len(D)
+
+
+def uh_desc_from_arrays(arrays: dict):
+    """Build a uh_desc from numpy arrays named like the descriptor fields (plus dense_row,
+    dense_col, D_off, D_data). Returns (desc, keepalive)."""
+    keep = _Keep()
+    c128 = np.asarray(arrays["U_data"]).dtype != np.complex64
+    d = UHDesc()
+    _tree(keep, d, arrays)
+    d.data_type = UH_DATA_C128 if c128 else UH_DATA_C64
+    d.row_rank = _ptr(keep(arrays["row_rank"], np.int32))
+    d.row_off = _ptr(keep(arrays["row_off"], np.int64))
+    U = _data(keep, arrays["U_data"], c128)
+    d.U_data, d.U_len = _ptr(U), len(U)
+    d.col_rank = _ptr(keep(arrays["col_rank"], np.int32))
+    d.col_off = _ptr(keep(arrays["col_off"], np.int64))
+    V = _data(keep, arrays["V_data"], c128)
+    d.V_data, d.V_len = _ptr(V), len(V)
+    ar = keep(arrays["adm_row"], np.int32)
+    d.n_adm = len(ar)
+    d.adm_row = _ptr(ar)
+    d.adm_col = _ptr(keep(arrays["adm_col"], np.int32))
+    d.S_off = _ptr(keep(arrays["S_off"], np.int64))
+    S = _data(keep, arrays["S_data"], c128)
+    d.S_data, d.S_len = _ptr(S), len(S)
+    _dense(keep, d, arrays, c128)
+    return d, keep
+
+
+def h_desc_from_arrays(arrays: dict):
+    keep = _Keep()
+    c128 = np.asarray(arrays["X_data"]).dtype != np.complex64
+    d = HDesc()
+    _tree(keep, d, arrays)
+    d.data_type = UH_DATA_C128 if c128 else UH_DATA_C64
+    ar = keep(arrays["adm_row"], np.int32)
+    d.n_adm = len(ar)
+    d.adm_row = _ptr(ar)
+    d.adm_col = _ptr(keep(arrays["adm_col"], np.int32))
+    d.adm_rank = _ptr(keep(arrays["adm_rank"], np.int32))
+    d.X_off = _ptr(keep(arrays["X_off"], np.int64))
+    X = _data(keep, arrays["X_data"], c128)
+    d.X_data, d.X_len = _ptr(X), len(X)
+    d.Y_off = _ptr(keep(arrays["Y_off"], np.int64))
+    Y = _data(keep, arrays["Y_data"], c128)
+    d.Y_data, d.Y_len = _ptr(Y), len(Y)
+    _dense(keep, d, arrays, c128)
+    return d, keep
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class _Op:
+    _create = _destroy = _matvec = _matmat = _stats = _reserve = None
+
+    def __init__(self, desc, precision: str = "c64"):
+        self.precision = precision
+        self.c128 = precision == "c128"
+        h = _p()
+        check(self._create(C.byref(desc), _PREC[precision], C.byref(h)), self._create.__name__)
+        self.handle = h
+        s = Stats()
+        check(self._stats(self.handle, C.byref(s)), "stats")
+        self.n = s.n
+
+    def stats(self) -> dict:
+        s = Stats()
+        check(self._stats(self.handle, C.byref(s)), "stats")
+        return s.as_dict()
+
+    def _check_vec(self, t, cols=None):
+        import torch
+        want = torch.complex128 if self.c128 else torch.complex64
+        if not t.is_cuda or t.dtype != want:
+            raise TypeError(f"expected a CUDA tensor of {want}, got {t.dtype} on {t.device}")
+        if t.shape[0] != self.n:
+            raise ValueError(f"length {t.shape[0]} != n = {self.n}")
+
+    def matvec(self, x, y=None, stream=None):
+        """y = A x for a CUDA tensor x (original ordering). Asynchronous on the stream."""
+        import torch
+        self._check_vec(x)
+        if not x.is_contiguous():
+            raise ValueError("x must be contiguous")
+        if y is None:
+            y = torch.empty_like(x)
+        self._check_vec(y)
+        check(self._matvec(self.handle, x.data_ptr(), y.data_ptr(), _stream_handle(stream)),
+              "matvec")
+        return y
+
+    def matmat(self, X, Y=None, stream=None):
+        """Y = A X for an n x nrhs column-major CUDA tensor X (X.T contiguous, e.g.
+        torch.empty(nrhs, n).T). Asynchronous on the stream."""
+        import torch
+        self._check_vec(X)
+        n, r = X.shape
+        if X.stride(0) != 1:
+            raise ValueError("X must be column-major (stride(0) == 1)")
+        if Y is None:
+            Y = torch.empty((r, n), dtype=X.dtype, device=X.device).T
+        self._check_vec(Y)
+        if Y.stride(0) != 1 or Y.shape != X.shape:
+            raise ValueError("Y must be column-major with X's shape")
+        check(self._matmat(self.handle, r, X.data_ptr(), X.stride(1), Y.data_ptr(), Y.stride(1),
+                           _stream_handle(stream)), "matmat")
+        return Y
+
+    def reserve(self, max_nrhs: int):
+        check(self._reserve(self.handle, max_nrhs), "reserve")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class UHOp(_Op):
+    """Device-resident uniform H-matrix (uh_create)."""
+    _create = lib.uh_create
+    _destroy = lib.uh_destroy
+    _matvec = lib.uh_matvec
+    _matmat = lib.uh_matmat
+    _stats = lib.uh_stats
+    _reserve = lib.uh_reserve
+
+    @classmethod
+    def from_arrays(cls, arrays: dict, precision: str = "c64"):
+        desc, keep = uh_desc_from_arrays(arrays)
+        return cls(desc, precision)
+
+
+class HOp(_Op):
+    """Device-resident H-matrix (h_create), the plain form."""
+    _create = lib.h_create
+    _destroy = lib.h_destroy
+    _matvec = lib.h_matvec
+    _matmat = lib.h_matmat
+    _stats = lib.h_stats
+    _reserve = lib.h_reserve
+
+    @classmethod
+    def from_arrays(cls, arrays: dict, precision: str = "c64"):
+        desc, keep = h_desc_from_arrays(arrays)
+        return cls(desc, precision)

@@ -1,0 +1,129 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function include/uh.h declares,
+and rejects invalid descriptors with UH_EINVAL before touching the GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from tests.uh_testutil import h_arrays, oracle_ops, uh_arrays
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\**(\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def uh():
+    from paper_2405_15573_gb300 import uh as U
+    return U
+
+
+def test_header_symbols_exported(uh):
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            names += _declared(h)
+    assert "uh_matvec" in names and "h_matvec" in names and "uh_create" in names
+    for name in names:
+        assert hasattr(uh.lib, name), f"{name} declared but not exported"
+
+
+def test_version_and_error_string(uh):
+    assert "sm_103a" in uh.version()
+    assert uh.lib.uh_last_error() is not None
+
+
+def _small():
+    _, _, hf, h, op = oracle_ops(512, 3.0, 16, 1.0, 1e-6, 1e-8)
+    return uh_arrays(op), h_arrays(h)
+
+
+def _expect_einval(uh, arrays, match, kind="uh"):
+    desc, keep = (uh.uh_desc_from_arrays if kind == "uh" else uh.h_desc_from_arrays)(arrays)
+    h = C.c_void_p()
+    fn = uh.lib.uh_create if kind == "uh" else uh.lib.h_create
+    rc = fn(C.byref(desc), uh.UH_PREC_C64, C.byref(h))
+    assert rc == uh.UH_EINVAL
+    assert h.value is None
+    msg = uh.lib.uh_last_error().decode()
+    assert re.search(match, msg), msg
+
+
+def test_rejects_bad_permutation(uh):
+    a, _ = _small()
+    a = dict(a)
+    p = a["perm"].copy()
+    p[3] = p[4]
+    a["perm"] = p
+    _expect_einval(uh, a, "permutation")
+
+
+def test_rejects_missing_and_double_coverage(uh):
+    a, _ = _small()
+    b = dict(a)
+    b["dense_row"], b["dense_col"], b["D_off"] = a["dense_row"][1:], a["dense_col"][1:], a["D_off"][1:]
+    _expect_einval(uh, b, "not covered")
+    c = dict(a)
+    c["dense_row"] = np.concatenate([a["dense_row"], a["dense_row"][:1]])
+    c["dense_col"] = np.concatenate([a["dense_col"], a["dense_col"][:1]])
+    c["D_off"] = np.concatenate([a["D_off"], a["D_off"][:1]])
+    _expect_einval(uh, c, "covered twice")
+
+
+def test_rejects_out_of_range_data_and_ranks(uh):
+    a, h = _small()
+    b = dict(a)
+    b["S_off"] = a["S_off"].copy()
+    b["S_off"][-1] = len(a["S_data"])
+    _expect_einval(uh, b, "coupling matrix")
+    c = dict(a)
+    c["row_rank"] = a["row_rank"].copy()
+    r = int(np.flatnonzero(a["row_rank"] > 0)[0])
+    c["row_rank"][r] = 10 ** 6
+    _expect_einval(uh, c, "row_rank")
+    d = dict(a)
+    d["cl_size"] = a["cl_size"].copy()
+    d["cl_size"][1] = 10 ** 6
+    _expect_einval(uh, d, "outside")
+    e = dict(h)
+    e["adm_rank"] = h["adm_rank"].copy()
+    e["adm_rank"][0] = -1
+    _expect_einval(uh, e, "adm_rank", kind="h")
+
+
+def test_null_arguments(uh):
+    h = C.c_void_p()
+    assert uh.lib.uh_create(None, 0, C.byref(h)) == uh.UH_EINVAL
+    assert uh.lib.uh_destroy(None) == uh.UH_OK
+    assert uh.lib.uh_matvec(None, None, None, None) == uh.UH_EINVAL
+
+
+def _create_rc(uh, fn, desc, prec):
+    h = C.c_void_p()
+    rc = fn(C.byref(desc), prec, C.byref(h))
+    return rc, uh.lib.uh_last_error().decode(), h
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", [(2048, 4.0, 32, 1e-6), (1000, 6.0, 24, 1e-5), (97, 3.0, 16, 1e-6),
+                                  (40, 3.0, 64, 1e-6)])
+def test_packing_self_check_passes(uh, prec, case):
+    """Without a GPU, uh_create/h_create get through validation, packing and the packer's
+    self-check of every kernel address, and stop at the first CUDA call."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: creation succeeds instead")
+    n, k, leaf, eps = case
+    axes, noise = ((1.0, 0.7, 0.4), 0.01) if n == 1000 else ((1.0, 1.0, 1.0), 0.0)
+    _, _, hf, h, op = oracle_ops(n, k, leaf, 1.0, eps, 1e-8, axes, noise)
+    for mk, fn, arr in ((uh.uh_desc_from_arrays, uh.lib.uh_create, uh_arrays(op)),
+                        (uh.h_desc_from_arrays, uh.lib.h_create, h_arrays(h))):
+        desc, keep = mk(arr)
+        rc, msg, hd = _create_rc(uh, fn, desc, prec)
+        assert rc == uh.UH_ECUDA and "cudaGetDevice" in msg, msg
