@@ -1,0 +1,404 @@
+"""Benchmark of the UH matrix-vector product on one GB300 (or N independent replicas).
+
+Workload: the unit-sphere Helmholtz collocation operator, N = 32768 Fibonacci points, k = 16,
+leaf 64, eta = 1, eps = 1e-6 (ACA 1e-8), stored complex64 with FP32 accumulation, one right-hand
+side (complex normal, seed 0). The operator is built on the host by the library's builder
+(uh_build.h), uploaded once, and then timed:
+
+  value     UH matvecs/s, x and y resident on the GPU, L2 flushed before every matvec,
+            each matvec timed with CUDA events on the launching stream;
+  e2e       the same through host buffers: pinned x copied in, matvec, y copied out;
+  roofline  algorithmic bytes of one UH matvec (stored operator + vectors, Section 4.4) per
+            event-timed matvec, against the measured HBM copy bandwidth;
+  extra     the plain H-matrix matvec (Algorithm 5) on the same GPU, the complex128 UH matvec,
+            storage of both forms;
+  cpu_baseline  the FP64 oracle's UH matvec on the same operator, timed on one host core in a
+            spawned child process, also giving the relative error of the GPU result.
+
+`--impl reference` times that oracle matvec alone (the reference arm). Under torchrun every
+rank runs its own replica (the product has no exchange step to shard), rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "UH matvec/s & HBM GB/s vs H-matvec, same GB300, relerr≤5e-6; solve p50/p99"
+UNIT = "matvec/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 100 ms while running (SM clock, max clock, throttle reasons)."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- oracle child
+
+
+def _oracle_child(npz_path: str, out_path: str, seconds: float, min_reps: int):
+    """Runs in a fresh process with one BLAS thread: the oracle's UH matvec on the operator in
+    npz_path, first on x (result saved for the error check), then repeated for ~seconds."""
+    import types
+    from oracle import uh_oracle as O
+    z = {f[:-4]: np.load(os.path.join(npz_path, f), mmap_mode="r")
+         for f in os.listdir(npz_path) if f.endswith(".npy")}
+    n = int(z["n"])
+    begin, size, perm = z["cl_begin"], z["cl_size"], z["perm"]
+    tree = types.SimpleNamespace(n=n, perm=perm, begin=begin.tolist(), size=size.tolist())
+
+    def blocks(rank, off, data, clusters):
+        return {int(c): data[off[c]:off[c] + size[c] * rank[c]].reshape(rank[c], size[c]).T
+                for c in clusters}
+    rows = sorted(set(z["adm_row"].tolist()))
+    cols = sorted(set(z["adm_col"].tolist()))
+    U = blocks(z["row_rank"], z["row_off"], z["U_data"], rows)
+    V = blocks(z["col_rank"], z["col_off"], z["V_data"], cols)
+    S = {}
+    for t, s, o in zip(z["adm_row"], z["adm_col"], z["S_off"]):
+        lt, ls = int(z["row_rank"][t]), int(z["col_rank"][s])
+        S[(int(t), int(s))] = z["S_data"][o:o + lt * ls].reshape(ls, lt).T
+    near = {}
+    for t, s, o in zip(z["dense_row"], z["dense_col"], z["D_off"]):
+        m, k = int(size[t]), int(size[s])
+        near[(int(t), int(s))] = z["D_data"][o:o + m * k].reshape(k, m).T
+    adm = sorted(S)
+    uh = O.UHMatrix(tree, adm, sorted(near), U, V, S, near, {}, {})
+    x = z["x"]
+    y = O.uh_matvec(uh, x)
+    reps, t0 = 1, time.perf_counter()
+    t_first = None
+    while True:
+        O.uh_matvec(uh, x)
+        reps_done = reps
+        reps += 1
+        el = time.perf_counter() - t0
+        if t_first is None:
+            t_first = el
+        if el >= seconds and reps_done >= min_reps:
+            break
+    np.save(out_path + ".y.npy", y)
+    with open(out_path, "w") as f:
+        json.dump({"reps": reps_done, "seconds": el}, f)
+
+
+def dump_operator(model, x: np.ndarray, directory: str) -> None:
+    """Write the UH descriptor arrays (and x) as .npy files, straight from the builder's memory."""
+    for k, v in model.uh_arrays(copy=False).items():
+        np.save(os.path.join(directory, k + ".npy"), np.asarray(v))
+    np.save(os.path.join(directory, "x.npy"), x)
+
+
+def run_oracle_sample(directory: str, seconds: float, min_reps: int = 2):
+    """Spawn the oracle child on the dumped operator (memory-mapped); returns
+    (matvec/s, reps, seconds, y)."""
+    out = os.path.join(directory, "res.json")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", directory, out,
+                    str(seconds), str(min_reps)], check=True, env=env, cwd=ROOT)
+    r = json.load(open(out))
+    y = np.load(out + ".y.npy")
+    return r["reps"] / r["seconds"], r["reps"], r["seconds"], y
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def timed_matvecs(op, x, y, steps, flush, torch):
+    """Per-matvec CUDA-event times (ms) with an L2 flush (outside the events) before each."""
+    s = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(s)
+        op.matvec(x, y)
+        b.record(s)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def gpu_arm(args):
+    import torch
+    from paper_2405_15573_gb300 import inputs as I
+    from paper_2405_15573_gb300 import uh as U
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = I.SPHERE_32768
+    t0 = time.time()
+    model = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca)
+    build_s = time.time() - t0
+    uh64 = model.uh_op("c64")
+    h64 = model.h_op("c64")
+    uh128 = model.uh_op("c128")
+    st = uh64.stats()
+    hst = h64.stats()
+    x_np = w.x()
+    tmpdir = None
+    if not args.no_cpu_baseline and rank == 0:
+        tmpdir = tempfile.mkdtemp(prefix="uh_bench_")
+        dump_operator(model, x_np, tmpdir)
+    model.close()  # the ops hold their own device copies; free the host arrays
+    x = torch.from_numpy(x_np).to("cuda", torch.complex64)
+    y = torch.empty_like(x)
+    x128 = torch.from_numpy(x_np).to("cuda")
+    y128 = torch.empty_like(x128)
+    yh = torch.empty_like(x)
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        uh64.matvec(x, y)
+        h64.matvec(x, yh)
+        uh128.matvec(x128, y128)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_uh = timed_matvecs(uh64, x, y, args.steps, flush, torch)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_h = timed_matvecs(h64, x, yh, args.steps, flush, torch)
+    t_128 = timed_matvecs(uh128, x128, y128, max(10, args.steps // 10), flush, torch)
+    # End to end through host buffers: pinned x in, matvec, y out, every step.
+    xh = torch.from_numpy(x_np.astype(np.complex64)).pin_memory()
+    yhost = torch.empty_like(xh).pin_memory()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(e2e_steps):
+        x.copy_(xh, non_blocking=True)
+        uh64.matvec(x, y)
+        yhost.copy_(y, non_blocking=True)
+    e1.record(s)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / e2e_steps
+    time.sleep(0.2)
+    clk = clocks.stop()
+
+    ms_uh = statistics.mean(t_uh)
+    ms_max = ms_uh
+    if dist:
+        tt = torch.tensor([ms_uh, t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_max, t_e2e = float(tt[0]), float(tt[1])
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = _peaks()
+    gbs = st["algo_bytes_matvec"] / (ms_uh * 1e-3) / 1e9
+    gbs_h = hst["algo_bytes_matvec"] / (statistics.mean(t_h) * 1e-3) / 1e9
+    gbs_128 = uh128.stats()["algo_bytes_matvec"] / (statistics.mean(t_128) * 1e-3) / 1e9
+    y_np = y.cpu().numpy().astype(np.complex128)
+    y128_np = y128.cpu().numpy()
+
+    cpu = None
+    rel_oracle = None
+    if tmpdir is not None:
+        try:
+            rate, reps, secs, y_ref = run_oracle_sample(tmpdir, args.cpu_seconds)
+        finally:
+            import shutil
+            shutil.rmtree(tmpdir, ignore_errors=True)
+        rel_oracle = float(np.linalg.norm(y_np - y_ref) / np.linalg.norm(y_ref))
+        rel_oracle_128 = float(np.linalg.norm(y128_np - y_ref) / np.linalg.norm(y_ref))
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{reps} full FP64 UH matvecs of the same N=32768 operator "
+                         f"(NumPy, one BLAS thread) in {secs:.1f} s",
+               "relerr_c64_vs_oracle": rel_oracle, "relerr_c128_vs_oracle": rel_oracle_128}
+
+    out = {
+        "metric": METRIC, "value": world * 1e3 / ms_max, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic",
+        "config": {"workload": f"UH matvec, unit-sphere Helmholtz collocation N={w.n} k={w.wavenumber:g} "
+                               f"leaf {w.leaf} eta {w.eta:g} eps {w.eps:g}, complex64 storage, FP32 "
+                               f"accumulation, 1 RHS",
+                   "l2": "flushed before every timed matvec (2x L2 write, outside the events)",
+                   "parallelism": f"replicas x{world}", "operator_build_s": round(build_s, 2)},
+        "e2e": {"value": world * 1e3 / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
+                "d2h_bytes_per_step": int(y.numel() * 8)},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "peak_kind": peak_kind, "traffic": None,
+                     "kernel": "seg_gemv_kernel<float> (3 launches per matvec)",
+                     "algo_bytes_per_matvec": st["algo_bytes_matvec"],
+                     "frac_of_nominal_8000": gbs / 8000.0},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": args.steps * st["n_launches"],
+        "uh": {"ms_mean": ms_uh, "ms_median": statistics.median(t_uh), "ms_min": min(t_uh),
+               "GBps": gbs, "relerr_vs_oracle": rel_oracle, "stats": st},
+        "h": {"matvec_per_s": 1e3 / statistics.mean(t_h), "ms_mean": statistics.mean(t_h),
+              "ms_median": statistics.median(t_h), "ms_min": min(t_h), "GBps": gbs_h,
+              "algo_bytes": hst["algo_bytes_matvec"], "speedup_uh_over_h": statistics.mean(t_h) / ms_uh},
+        "uh_c128": {"matvec_per_s": 1e3 / statistics.mean(t_128), "ms_mean": statistics.mean(t_128),
+                    "GBps": gbs_128},
+        "storage": {"E_UH": st["E_U"] + st["E_V"] + st["E_S"] + st["E_D"],
+                    "E_H": hst["E_U"] + hst["E_V"] + hst["E_D"],
+                    "ratio_H_over_UH": (hst["E_U"] + hst["E_V"] + hst["E_D"]) /
+                                       (st["E_U"] + st["E_V"] + st["E_S"] + st["E_D"]),
+                    "ratio_adm": (hst["E_U"] + hst["E_V"]) / (st["E_U"] + st["E_V"] + st["E_S"])},
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+
+def reference_arm(args):
+    """The oracle (FP64 NumPy) UH matvec on the same workload, built by the oracle itself;
+    each step is one full oracle matvec on one host core."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import uh_oracle as O
+    from paper_2405_15573_gb300 import inputs as I
+    w = I.SPHERE_32768
+    t0 = time.time()
+    tree, hf, h, uh = O.build_operators(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca)
+    build_s = time.time() - t0
+    x = w.x()
+    for _ in range(args.warmup):
+        O.uh_matvec(uh, x)
+    ts = []
+    for _ in range(args.steps):
+        a = time.perf_counter()
+        O.uh_matvec(uh, x)
+        ts.append(time.perf_counter() - a)
+    ms = 1e3 * statistics.mean(ts)
+    v = 1e3 / ms
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", "0")) or os.cpu_count()
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"UH matvec (FP64 oracle), unit-sphere Helmholtz collocation "
+                                  f"N={w.n} k={w.wavenumber:g} leaf {w.leaf} eta {w.eta:g} eps {w.eps:g}, 1 RHS",
+                      "operator_build_s": round(build_s, 1)},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} full oracle UH matvecs of the N={w.n} operator"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--oracle-child":
+        _oracle_child(sys.argv[2], sys.argv[3], float(sys.argv[4]), int(sys.argv[5]))
+        return
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="uh", choices=["uh", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        args.steps = 5 if args.steps is None else args.steps
+        args.warmup = 1 if args.warmup is None else args.warmup
+        reference_arm(args)
+        return
+    args.steps = 2000 if args.steps is None else args.steps
+    args.warmup = 20 if args.warmup is None else max(3, args.warmup)
+    gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

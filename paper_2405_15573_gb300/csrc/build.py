@@ -23,7 +23,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["uh_gemv.cu"]
-CPP_SOURCES = ["uh_capi.cpp"]
+CPP_SOURCES = ["uh_capi.cpp", "uh_build.cpp"]
 
 
 def _run(cmd):
@@ -43,7 +43,7 @@ def _newer(src_list, target):
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(HERE, f) for f in os.listdir(HERE) if f.endswith(".h")]
-    headers.append(os.path.join(INCLUDE, "uh.h"))
+    headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     jobs = []
     objs = []
     for s in CU_SOURCES:
@@ -58,7 +58,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         obj = os.path.join(BUILD, s + ".o")
         objs.append(obj)
         if force or _newer([src] + headers, obj):
-            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-Wall", "-Wno-unused-function",
+            jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-Wall", "-Wno-unused-function",
                          "-I", INCLUDE, "-I", HERE, "-I", os.path.join(CUDA_HOME, "include"),
                          "-c", src, "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:

@@ -29,7 +29,9 @@ namespace {
 
 thread_local std::string g_err;
 
-int fail(int code, const char* fmt, ...) {
+}  // namespace
+
+int uh::set_error(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -38,6 +40,10 @@ int fail(int code, const char* fmt, ...) {
   g_err = buf;
   return code;
 }
+
+namespace {
+
+#define fail uh::set_error
 
 #define CUDA_TRY(call)                                                                   \
   do {                                                                                   \

@@ -58,6 +58,9 @@ struct SegGemvParams {
   uint32_t* sched;        // [2] work counter and exit counter, zero between launches
 };
 
+// Records a message for uh_last_error() (calling thread) and returns `code`.
+int set_error(int code, const char* fmt, ...);
+
 // Launch the segmented GEMV for complex128 (fp64) or complex64 (fp32 accumulation) data.
 cudaError_t launch_seg_gemv(bool c128, const SegGemvParams& p, int grid, cudaStream_t stream);
 

@@ -296,3 +296,129 @@ class HOp(_Op):
     def from_arrays(cls, arrays: dict, precision: str = "c64"):
         desc, keep = h_desc_from_arrays(arrays)
         return cls(desc, precision)
+
+
+# ------------------------------------------------------------------ host-side builder (uh_build.h)
+
+class BuildParams(C.Structure):
+    _fields_ = [("wavenumber", C.c_double), ("leaf", _i32), ("eta", C.c_double),
+                ("eps", C.c_double), ("tol_aca", C.c_double), ("nthreads", _i32)]
+
+
+class BuildInfo(C.Structure):
+    _fields_ = [("n", _i64), ("n_clusters", _i64), ("n_adm", _i64), ("n_dense", _i64),
+                ("depth", _i32), ("csp", _i32), ("kmax_aca", _i32), ("kmax_h", _i32),
+                ("lmax", _i32), ("seconds_tree", C.c_double), ("seconds_aca", C.c_double),
+                ("seconds_bases", C.c_double), ("seconds_dense", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+lib.uhb_build_helmholtz.argtypes = [_i64, _p, C.POINTER(BuildParams), C.POINTER(_p)]
+lib.uhb_uh_desc.argtypes = [_p, C.POINTER(UHDesc)]
+lib.uhb_h_desc.argtypes = [_p, C.POINTER(HDesc)]
+lib.uhb_info.argtypes = [_p, C.POINTER(BuildInfo)]
+lib.uhb_free.argtypes = [_p]
+for _f in (lib.uhb_build_helmholtz, lib.uhb_uh_desc, lib.uhb_h_desc, lib.uhb_info, lib.uhb_free):
+    _f.restype = C.c_int
+
+
+def _view(ptr, count, dtype):
+    if count == 0 or not ptr:
+        return np.zeros(0, dtype)
+    nbytes = int(count) * np.dtype(dtype).itemsize
+    buf = (C.c_char * nbytes).from_address(ptr)
+    return np.frombuffer(buf, dtype=dtype, count=int(count))
+
+
+class HelmholtzModel:
+    """Synthetic Helmholtz collocation operator built on the host (uh_build.h) in both UH and
+    H form. The arrays live in the library; uh_op()/h_op() upload them to the GPU."""
+
+    def __init__(self, points, wavenumber, leaf, eta, eps, tol_aca, nthreads: int = 0):
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        prm = BuildParams(float(wavenumber), int(leaf), float(eta), float(eps), float(tol_aca),
+                          int(nthreads))
+        h = _p()
+        check(lib.uhb_build_helmholtz(len(pts), pts.ctypes.data, C.byref(prm), C.byref(h)),
+              "uhb_build_helmholtz")
+        self.handle = h
+        self.n = len(pts)
+
+    def info(self) -> dict:
+        i = BuildInfo()
+        check(lib.uhb_info(self.handle, C.byref(i)), "uhb_info")
+        return i.as_dict()
+
+    def uh_desc(self) -> UHDesc:
+        d = UHDesc()
+        check(lib.uhb_uh_desc(self.handle, C.byref(d)), "uhb_uh_desc")
+        return d
+
+    def h_desc(self) -> HDesc:
+        d = HDesc()
+        check(lib.uhb_h_desc(self.handle, C.byref(d)), "uhb_h_desc")
+        return d
+
+    def uh_op(self, precision: str = "c64") -> "UHOp":
+        return UHOp(self.uh_desc(), precision)
+
+    def h_op(self, precision: str = "c64") -> "HOp":
+        return HOp(self.h_desc(), precision)
+
+    def _tree_arrays(self, t):
+        ncl = t.n_clusters
+        return dict(n=t.n, perm=_view(t.perm, t.n, np.int64),
+                    cl_begin=_view(t.cl_begin, ncl, np.int64),
+                    cl_size=_view(t.cl_size, ncl, np.int64))
+
+    def _dense_arrays(self, d):
+        k = d.n_dense
+        return dict(dense_row=_view(d.row_cl, k, np.int32),
+                    dense_col=_view(d.col_cl, k, np.int32),
+                    D_off=_view(d.off, k, np.int64),
+                    D_data=_view(d.data, d.len, np.complex128))
+
+    def uh_arrays(self, copy: bool = True) -> dict:
+        """The UH descriptor arrays (same names as uh_desc_from_arrays takes): copies, or with
+        copy=False views into the model that are valid until close()."""
+        d = self.uh_desc()
+        ncl = d.tree.n_clusters
+        a = self._tree_arrays(d.tree)
+        a.update(row_rank=_view(d.row_rank, ncl, np.int32),
+                 row_off=_view(d.row_off, ncl, np.int64),
+                 U_data=_view(d.U_data, d.U_len, np.complex128),
+                 col_rank=_view(d.col_rank, ncl, np.int32),
+                 col_off=_view(d.col_off, ncl, np.int64),
+                 V_data=_view(d.V_data, d.V_len, np.complex128),
+                 adm_row=_view(d.adm_row, d.n_adm, np.int32),
+                 adm_col=_view(d.adm_col, d.n_adm, np.int32),
+                 S_off=_view(d.S_off, d.n_adm, np.int64),
+                 S_data=_view(d.S_data, d.S_len, np.complex128))
+        a.update(self._dense_arrays(d.dense))
+        return {k: (v.copy() if copy and isinstance(v, np.ndarray) else v) for k, v in a.items()}
+
+    def h_arrays(self) -> dict:
+        d = self.h_desc()
+        a = self._tree_arrays(d.tree)
+        a.update(adm_row=_view(d.adm_row, d.n_adm, np.int32),
+                 adm_col=_view(d.adm_col, d.n_adm, np.int32),
+                 adm_rank=_view(d.adm_rank, d.n_adm, np.int32),
+                 X_off=_view(d.X_off, d.n_adm, np.int64),
+                 X_data=_view(d.X_data, d.X_len, np.complex128),
+                 Y_off=_view(d.Y_off, d.n_adm, np.int64),
+                 Y_data=_view(d.Y_data, d.Y_len, np.complex128))
+        a.update(self._dense_arrays(d.dense))
+        return {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in a.items()}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.uhb_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
