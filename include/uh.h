@@ -215,6 +215,35 @@ int h_reserve(h_op* op, int32_t max_nrhs);
  * E_U = sum_b k_b |tau|, E_V = sum_b k_b |sigma|, E_S = 0. */
 int h_stats(const h_op* op, uh_stats_t* out);
 
+/* ---------------------------------------------------------------- allocation-free block product */
+/*
+ * y = U (S (V^* x)) for one admissible block tau x sigma of a UH-matrix (the block form of
+ * Def. 2.4), computed in the forward, coupling and backward steps of the UH product. The paper has
+ * no counterpart to this entry point: it is here for callers that cannot call cudaMalloc - code
+ * running while a stream is being captured into a CUDA graph, or code that must keep to device
+ * memory handed out by its own arena or a framework's allocator. It allocates nothing: the
+ * intermediate vectors live in a fixed device array inside the library (266,240 bytes, held on
+ * every GPU that loads the library until the process exits).
+ *  m, n      block size |tau| x |sigma|, >= 1
+ *  lt, ls    ranks l_tau, l_sigma, each in [0, 256] (the limit set by the fixed array; larger
+ *            ranks are rejected with UH_EINVAL) and lt <= m, ls <= n
+ *  U         device, m x lt column-major, leading dimension ldu >= m
+ *  S         device, lt x ls column-major, lds >= lt
+ *  V         device, n x ls column-major, ldv >= n
+ *  x         device, n values; y device, m values (overwritten); x, y must not overlap
+ *  precision UH_PREC_C128 (complex128, FP64) or UH_PREC_C64 (complex64, FP32 accumulation);
+ *            every array has that element type
+ *  stream    cudaStream_t as void*; the call is asynchronous on it.
+ * All calls share the fixed array, and each call overwrites it before reading it, so nothing
+ * carries over between calls; but calls that overlap on the GPU (on different streams, or on
+ * several host threads without ordering) race on it and give wrong results. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture begins.
+ */
+int uh_block_apply_noalloc(int64_t m, int64_t n, int32_t lt, int32_t ls, const void* U, int64_t ldu,
+                           const void* S, int64_t lds, const void* V, int64_t ldv, const void* x,
+                           void* y, int32_t precision, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,7 @@ for _name, _args in [
     ("h_matmat", [_p, _i32, _p, _i64, _p, _i64, _p]),
     ("h_reserve", [_p, _i32]),
     ("h_stats", [_p, C.POINTER(Stats)]),
+    ("uh_block_apply_noalloc", [_i64, _i64, _i32, _i32, _p, _i64, _p, _i64, _p, _i64, _p, _p, _i32, _p]),
 ]:
     getattr(lib, _name).argtypes = _args
     getattr(lib, _name).restype = C.c_int
@@ -266,6 +267,25 @@ class _Op:
             self.close()
         except Exception:
             pass
+
+
+def block_apply_noalloc(U, S, V, x, y, stream=None):
+    """y = U (S (V^* x)) for one UH block without any allocation by the library (uh.h,
+    uh_block_apply_noalloc). U (m x lt), S (lt x ls), V (n x ls) are column-major CUDA tensors
+    (tensor.T contiguous), x (n) and y (m) contiguous; all complex128 or all complex64."""
+    import torch
+    c128 = x.dtype == torch.complex128
+    m, lt = U.shape
+    n, ls = V.shape
+    for name, t in (("U", U), ("S", S), ("V", V)):
+        if t.dim() != 2 or t.stride(0) != 1 or t.dtype != x.dtype or not t.is_cuda:
+            raise ValueError(f"{name} must be a column-major CUDA matrix of {x.dtype}")
+    check(lib.uh_block_apply_noalloc(m, n, lt, ls, U.data_ptr(), max(U.stride(1), m), S.data_ptr(),
+                                     max(S.stride(1), lt), V.data_ptr(), max(V.stride(1), n),
+                                     x.data_ptr(), y.data_ptr(),
+                                     UH_PREC_C128 if c128 else UH_PREC_C64, _stream_handle(stream)),
+          "uh_block_apply_noalloc")
+    return y
 
 
 class UHOp(_Op):
