@@ -196,6 +196,33 @@ def timed_matvecs(op, x, y, steps, flush, torch):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def profile_arm(args):
+    """Only one op (uh64, h64 or uh128) of the benchmark workload: build, warm up, run `steps`
+    products and print their mean time. For profiler captures of a single kernel."""
+    import torch
+    from paper_2405_15573_gb300 import inputs as I
+    from paper_2405_15573_gb300 import uh as U
+    w = I.SPHERE_32768
+    model = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca)
+    prec = "c128" if args.profile_op.endswith("128") else "c64"
+    op = model.uh_op(prec) if args.profile_op.startswith("uh") else model.h_op(prec)
+    model.close()
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    x = torch.from_numpy(w.x()).to("cuda", dt)
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        op.matvec(x, y)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        op.matvec(x, y)
+    b.record()
+    op.check()
+    print(json.dumps({"profile_op": args.profile_op, "ms_mean": a.elapsed_time(b) / args.steps,
+                      "algo_bytes": op.stats()["algo_bytes_matvec"]}))
+
+
 def gpu_arm(args):
     import torch
     from paper_2405_15573_gb300 import inputs as I
@@ -389,7 +416,13 @@ def main():
     ap.add_argument("--impl", default="uh", choices=["uh", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-op", choices=["uh64", "h64", "uh128"], default=None)
     args = ap.parse_args()
+    if args.profile_op:
+        args.steps = 5 if args.steps is None else args.steps
+        args.warmup = 3 if args.warmup is None else args.warmup
+        profile_arm(args)
+        return
     if args.impl == "reference":
         args.steps = 5 if args.steps is None else args.steps
         args.warmup = 1 if args.warmup is None else args.warmup

@@ -148,6 +148,13 @@ int uh_destroy(uh_op* op);
 int uh_matvec(uh_op* op, const void* x, void* y, void* stream);
 
 /*
+ * Waits for `stream` and reports whether a bounded device-side wait of this op's products ran
+ * out since the last check (UH_ETIMEOUT, status then cleared) - which only happens if the GPU
+ * could not run all of the product's CTAs at once. UH_OK otherwise.
+ */
+int uh_check(uh_op* op, void* stream);
+
+/*
  * Y = A^UH X for nrhs right-hand sides: X is n x nrhs column-major with leading dimension ldx
  * (>= n), Y likewise with ldy; types as for uh_matvec. nrhs >= 1. The first call with a given
  * nrhs may allocate scratch (call uh_reserve beforehand to avoid that).
@@ -211,6 +218,8 @@ int h_matvec(h_op* op, const void* x, void* y, void* stream);
 int h_matmat(h_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy,
              void* stream);
 int h_reserve(h_op* op, int32_t max_nrhs);
+/* As uh_check. */
+int h_check(h_op* op, void* stream);
 /* Fills the fields that apply: E_D, n_adm, n_dense, algo_bytes_matvec (elem_bytes*(E_H+2n+2 sum k_b)),
  * E_U = sum_b k_b |tau|, E_V = sum_b k_b |sigma|, E_S = 0. */
 int h_stats(const h_op* op, uh_stats_t* out);

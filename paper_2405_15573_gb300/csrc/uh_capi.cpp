@@ -1,15 +1,19 @@
-// C ABI of the UH / H matrix-vector library: descriptor validation, packing of every product
-// phase into segmented-GEMV work items (see uh_internal.h), device upload, and the launches.
+// C ABI of the UH / H matrix-vector library: descriptor validation, packing of a product into the
+// streaming kernel's device program (uh_program.h), device upload, and the launch.
 //
-// UH matvec (Algorithm 6, Section 4.4) = three launches of the segmented GEMV:
-//   launch 0: forward transform xhat_sigma = V_sigma^* x|_sigma   (chunks of xhat)
-//             + near field y|_tile += A|_b x|_sigma               (chunks of y row tiles)
-//   launch 1: coupling yhat_tau = sum_{sigma in row(tau)} S_b xhat_sigma
-//   launch 2: backward transform y|_tile += U_tau|_tile yhat_tau  (same y chunks as the near field)
-// H matvec (Algorithm 5) = two launches: t_b = Y_b^* x|_sigma (+ near field), then
-// y|_tile += X_b|_tile t_b. Row tiles are the segments between consecutive row-cluster
-// boundaries of all blocks, cut to at most kHpMax rows, so each tile lies inside every row
-// cluster it meets and every y element is written by exactly one chunk.
+// UH matvec (Algorithm 6, Section 4.4) as chunks of outputs, in the schedule groups every CTA runs
+// in order (uh_program.h):
+//   permutation  xp = x in cluster order, one slice per CTA;
+//   forward      xhat_sigma = V_sigma^* xp|_sigma                 (chunks of xhat, z1);
+//   near field   z3|_tile = sum_b A|_b|_tile xp|_sigma            (row tiles with a backward part),
+//                or y|_tile directly (row tiles without one); split into two groups around the
+//                coupling so that each CTA has independent work while the coupling's inputs finish;
+//   coupling     yhat_tau = sum_{sigma in row(tau)} S_b xhat_sigma  (chunks of yhat, z2);
+//   backward     y|_tile = z3|_tile + sum_{tau > tile} U_tau|_tile yhat_tau.
+// H matvec (Algorithm 5): permutation; t_b = Y_b^* xp|_sigma (z1); near field; then
+// y|_tile = z3|_tile + sum_b X_b|_tile t_b. Row tiles are the segments between consecutive
+// row-cluster boundaries of all blocks, cut to at most 64 rows, so each tile lies inside every row
+// cluster it meets and each y entry is written by exactly one chunk.
 #include <algorithm>
 #include <complex>
 #include <cstdarg>
@@ -20,14 +24,24 @@
 #include <vector>
 
 #include "uh.h"
+#include "uh_debug.h"
 #include "uh_internal.h"
+#include "uh_program.h"
 
 using cd = std::complex<double>;
 using cf = std::complex<float>;
 
+namespace uh {
+cudaError_t stream_prepare(bool c128);
+cudaError_t stream_occupancy(bool c128, int* blocks_per_sm);
+cudaError_t stream_launch(bool c128, const StreamParams& p, int grid, cudaStream_t stream);
+}  // namespace uh
+
 namespace {
 
 thread_local std::string g_err;
+// > 0 while uh_pack_check / h_pack_check run: pack for this many CTAs, check, make no CUDA call.
+thread_local int g_pack_only_ncta = 0;
 
 }  // namespace
 
@@ -51,150 +65,13 @@ namespace {
     if (e_ != cudaSuccess) return fail(UH_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
-// Reads complex elements of either data type as complex<double>.
-struct Src {
-  const void* p = nullptr;
-  int type = UH_DATA_C128;
-  cd at(int64_t i) const {
-    if (type == UH_DATA_C128) return static_cast<const cd*>(p)[i];
-    const cf f = static_cast<const cf*>(p)[i];
-    return cd(f.real(), f.imag());
-  }
-};
+using uh::Src;
+using uh::ColSpec;
+using uh::ProgramBuilder;
 
 struct Tile {
   int64_t p0;
   int32_t h;
-};
-
-// A source column: rows i = 0..h-1 are src[off + i*step] (conjugated if conj).
-struct ColRef {
-  int64_t off;
-  int64_t step;
-  int32_t idx;
-};
-
-struct Launch {
-  int32_t first, count;
-  int in0;   // 0: none, 1: z1, 2: z2
-  int out;   // 0: none, 1: z1, 2: z2
-};
-
-// Host-side program under construction: chunks, items and packed tiles (in complex<double>,
-// converted to the op's element type at upload).
-struct Program {
-  std::vector<uh::Chunk> chunks;
-  std::vector<int> chunk_launch;  // launch whose items complete the chunk's inputs' consumers
-  std::vector<uh::Item> items;
-  std::vector<int> item_launch;
-  std::vector<cd> M;
-  std::vector<int32_t> colidx;
-  int epl = 1;                   // complex values per 16-byte load (2 for c64, 1 for c128)
-  int64_t target_bytes = 32768;  // bytes of one item's tile
-  int elem_bytes = 16;
-
-  int add_chunk(int kind, int64_t dst, int h, int launch) {
-    uh::Chunk c{};
-    c.dst = dst;
-    c.h = h;
-    c.kind = kind;
-    chunks.push_back(c);
-    chunk_launch.push_back(launch);
-    return static_cast<int>(chunks.size()) - 1;
-  }
-
-  // Emit the columns `cols` (each read from `src`) as items for chunk `chunk` in `launch`.
-  void add_columns(int chunk, int launch, const Src& src, bool conj, const std::vector<ColRef>& cols) {
-    const int h = chunks[chunk].h;
-    const int hp = (h + epl - 1) / epl * epl;
-    const int64_t ncols = static_cast<int64_t>(cols.size());
-    if (ncols == 0) return;
-    int64_t per = target_bytes / (static_cast<int64_t>(hp) * elem_bytes);
-    per = std::max<int64_t>(8, std::min<int64_t>(per, uh::kMaxCols));
-    const int64_t nitems = (ncols + per - 1) / per;
-    for (int64_t q = 0; q < nitems; ++q) {
-      const int64_t c0 = ncols * q / nitems, c1 = ncols * (q + 1) / nitems;
-      uh::Item it{};
-      it.data_off = static_cast<int64_t>(M.size());
-      it.hp = hp;
-      it.ncols = static_cast<int32_t>(c1 - c0);
-      it.idx_off = static_cast<int32_t>(colidx.size());
-      it.chunk = chunk;
-      it.part = -1;
-      M.resize(M.size() + static_cast<size_t>((c1 - c0) * hp), cd(0, 0));
-      cd* dst = M.data() + it.data_off;
-      for (int64_t c = c0; c < c1; ++c) {
-        const ColRef& r = cols[c];
-        for (int i = 0; i < h; ++i) {
-          const cd v = src.at(r.off + i * r.step);
-          dst[(c - c0) * hp + i] = conj ? std::conj(v) : v;
-        }
-        colidx.push_back(r.idx);
-      }
-      items.push_back(it);
-      item_launch.push_back(launch);
-    }
-  }
-
-  // Chunks that received no item (possible when all their blocks have rank 0) get one empty
-  // item, in the chunk's own launch, which writes zeros.
-  void add_empty_items() {
-    std::vector<int> cnt(chunks.size(), 0);
-    for (const auto& it : items) cnt[it.chunk]++;
-    for (size_t c = 0; c < chunks.size(); ++c) {
-      if (cnt[c]) continue;
-      uh::Item it{};
-      it.data_off = static_cast<int64_t>(M.size());
-      it.hp = (chunks[c].h + epl - 1) / epl * epl;
-      it.ncols = 0;
-      it.idx_off = static_cast<int32_t>(colidx.size());
-      it.chunk = static_cast<int32_t>(c);
-      it.part = -1;
-      items.push_back(it);
-      item_launch.push_back(chunk_launch[c]);
-    }
-  }
-
-  // Assign partial slots (creation order within each chunk) and order each launch's items
-  // largest first. Returns the launch table.
-  std::vector<Launch> finalize(int nlaunch, int32_t* nslots) {
-    std::vector<int> cnt(chunks.size(), 0);
-    for (const auto& it : items) cnt[it.chunk]++;
-    int32_t slot = 0;
-    for (size_t c = 0; c < chunks.size(); ++c) {
-      chunks[c].nparts = cnt[c];
-      chunks[c].part_base = cnt[c] > 1 ? slot : -1;
-      if (cnt[c] > 1) slot += cnt[c];
-    }
-    std::vector<int> seen(chunks.size(), 0);
-    for (auto& it : items) {
-      const auto& ch = chunks[it.chunk];
-      it.part = ch.nparts > 1 ? ch.part_base + seen[it.chunk] : -1;
-      seen[it.chunk]++;
-    }
-    *nslots = slot;
-    std::vector<size_t> order(items.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
-      if (item_launch[a] != item_launch[b]) return item_launch[a] < item_launch[b];
-      return static_cast<int64_t>(items[a].hp) * items[a].ncols >
-             static_cast<int64_t>(items[b].hp) * items[b].ncols;
-    });
-    std::vector<uh::Item> sorted;
-    sorted.reserve(items.size());
-    std::vector<Launch> launches(nlaunch, Launch{0, 0, 0, 0});
-    for (int l = 0; l < nlaunch; ++l) launches[l].first = -1;
-    for (size_t k = 0; k < order.size(); ++k) {
-      const int l = item_launch[order[k]];
-      if (launches[l].first < 0) launches[l].first = static_cast<int32_t>(k);
-      launches[l].count++;
-      sorted.push_back(items[order[k]]);
-    }
-    for (int l = 0; l < nlaunch; ++l)
-      if (launches[l].first < 0) launches[l].first = 0;
-    items.swap(sorted);
-    return launches;
-  }
 };
 
 // ------------------------------------------------------------------------- validation
@@ -248,7 +125,7 @@ int make_tiles_and_check(const Tree& T, const std::vector<int32_t>& brow, const 
   tiles->clear();
   for (size_t i = 0; i + 1 < bp.size(); ++i) {
     const int64_t len = bp[i + 1] - bp[i];
-    const int64_t k = (len + uh::kHpMax - 1) / uh::kHpMax;
+    const int64_t k = (len + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
     for (int64_t q = 0; q < k; ++q) {
       const int64_t a = bp[i] + len * q / k, e = bp[i] + len * (q + 1) / k;
       tiles->push_back(Tile{a, static_cast<int32_t>(e - a)});
@@ -305,29 +182,33 @@ int check_dense(const Tree& T, const uh_dense_desc& d) {
 
 // ------------------------------------------------------------------------- op
 
+// Device wait bound: about two seconds at the GB300's maximum SM clock.
+constexpr long long kTimeoutCycles = 4000000000LL;
+
 struct OpBase {
   int device = 0;
   bool c128 = true;
   int64_t n = 0;
+  int ncta = 1;
+  uint64_t epoch = 0;  // products launched since creation (or since the last reported timeout)
   void* d_M = nullptr;
-  int32_t* d_colidx = nullptr;
-  uh::Item* d_items = nullptr;
-  uh::Chunk* d_chunks = nullptr;
+  uh::WorkItem* d_items = nullptr;
+  int32_t* d_cta = nullptr;
+  unsigned long long* d_done = nullptr;  // group counters
+  int64_t counter_total[uh::kNumCounters] = {0, 0, 0};
+  uint32_t* d_status = nullptr;
   int32_t* d_perm = nullptr;
+  void* d_xp = nullptr;
   void* d_z1 = nullptr;
   void* d_z2 = nullptr;
-  void* d_partials = nullptr;
-  uint32_t* d_cnt = nullptr;
-  uint32_t* d_sched = nullptr;
-  std::vector<Launch> launches;
-  int grid = 1;
+  void* d_z3 = nullptr;
   uh_stats_t st{};
 };
 
 void free_op(OpBase* o) {
   if (!o) return;
-  void* ptrs[] = {o->d_M, o->d_colidx, o->d_items, o->d_chunks, o->d_perm, o->d_z1,
-                  o->d_z2, o->d_partials, o->d_cnt, o->d_sched};
+  void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_status,
+                  o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -339,113 +220,105 @@ int upload(const void* host, size_t bytes, T** dev) {
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dev), bytes);
   if (e != cudaSuccess) {
     *dev = nullptr;
-    return fail(e == cudaErrorMemoryAllocation ? UH_ENOMEM : UH_ECUDA, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    return fail(e == cudaErrorMemoryAllocation ? UH_ENOMEM : UH_ECUDA, "cudaMalloc(%zu): %s", bytes,
+                cudaGetErrorString(e));
   }
   if (host) CUDA_TRY(cudaMemcpy(*dev, host, bytes, cudaMemcpyHostToDevice));
   else CUDA_TRY(cudaMemset(*dev, 0, bytes));
   return UH_OK;
 }
 
-// Checks every address the GEMV kernel derives from the program against the buffer it reads
-// or writes, before anything is uploaded: tiles inside M, column lists inside colidx, input
-// indices inside the launch's input vectors, destinations inside their outputs, partial slots
-// inside the partial buffer, heights within the kernel's limits.
-int self_check(const Program& P, const std::vector<Launch>& L, int64_t n, int64_t z1len, int64_t z2len,
-               int32_t nslots) {
-  const int64_t zlen[3] = {0, z1len, z2len};
-  const int64_t msize = static_cast<int64_t>(P.M.size());
-  const int64_t csize = static_cast<int64_t>(P.colidx.size());
-  for (size_t l = 0; l < L.size(); ++l) {
-    for (int32_t k = L[l].first; k < L[l].first + L[l].count; ++k) {
-      const uh::Item& it = P.items[k];
-      if (it.hp < P.epl || it.hp > uh::kHpMax || it.hp % P.epl || it.ncols < 0 || it.ncols > uh::kMaxCols ||
-          it.data_off < 0 || it.data_off + static_cast<int64_t>(it.ncols) * it.hp > msize ||
-          (it.data_off * P.elem_bytes) % 16 != 0 || it.idx_off < 0 ||
-          static_cast<int64_t>(it.idx_off) + it.ncols > csize || it.chunk < 0 ||
-          it.chunk >= static_cast<int32_t>(P.chunks.size()) || it.part >= nslots || it.part < -1)
-        return fail(UH_EINVAL, "internal packing error: item %d of launch %zu", k, l);
-      for (int32_t c = 0; c < it.ncols; ++c) {
-        const int32_t ix = P.colidx[it.idx_off + c];
-        if (ix >= 0 ? (L[l].in0 == 0 || ix >= zlen[L[l].in0]) : (-static_cast<int64_t>(ix) - 1 >= n))
-          return fail(UH_EINVAL, "internal packing error: input index %d of item %d, launch %zu", ix, k, l);
-      }
-      const uh::Chunk& ch = P.chunks[it.chunk];
-      if (ch.h < 1 || ch.h > it.hp || ch.dst < 0 ||
-          (ch.kind == 0 ? (L[l].out == 0 || ch.dst + ch.h > zlen[L[l].out]) : (ch.kind != 1 || ch.dst + ch.h > n)))
-        return fail(UH_EINVAL, "internal packing error: chunk %d of item %d, launch %zu", it.chunk, k, l);
-      if ((ch.nparts > 1) != (it.part >= 0) || (ch.nparts > 1 && ch.part_base + ch.nparts > nslots))
-        return fail(UH_EINVAL, "internal packing error: partial slots of chunk %d", it.chunk);
-    }
-  }
+// Number of CTAs of the persistent launch (one per SM when the kernel fits once per SM).
+int query_ncta(bool c128, int* ncta, int* device) {
+  CUDA_TRY(cudaGetDevice(device));
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, *device));
+  CUDA_TRY(uh::stream_prepare(c128));
+  int per = 0;
+  CUDA_TRY(uh::stream_occupancy(c128, &per));
+  if (per < 1) return fail(UH_ECUDA, "streaming kernel does not fit on an SM");
+  *ncta = sms * per;
   return UH_OK;
 }
 
-// Uploads a finished program and allocates scratch. z1/z2 lengths in complex elements.
-int upload_program(OpBase* o, Program& P, const Tree& T, int nlaunch, int64_t z1len, int64_t z2len,
-                   const int* in0, const int* out) {
-  int32_t nslots = 0;
-  P.add_empty_items();
-  o->launches = P.finalize(nlaunch, &nslots);
-  for (int l = 0; l < nlaunch; ++l) {
-    o->launches[l].in0 = in0[l];
-    o->launches[l].out = out[l];
-  }
+// Finalize, self-check and upload the program; allocate the scratch vectors.
+int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T) {
+  if (const char* e = P.finalize()) return fail(UH_EINVAL, "packing: %s", e);
+  if (const char* e = P.self_check()) return fail(UH_EINVAL, "internal packing error: %s", e);
   int rc;
-  if ((rc = self_check(P, o->launches, T.n, z1len, z2len, nslots))) return rc;
-  CUDA_TRY(cudaGetDevice(&o->device));
-  int sms = 0;
-  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o->device));
-  o->grid = std::max(1, sms * 8);
   const size_t eb = o->c128 ? 16 : 8;
   if (o->c128) {
     if ((rc = upload(P.M.data(), P.M.size() * sizeof(cd), &o->d_M))) return rc;
   } else {
     std::vector<cf> m32(P.M.size());
-    for (size_t i = 0; i < P.M.size(); ++i) m32[i] = cf(static_cast<float>(P.M[i].real()), static_cast<float>(P.M[i].imag()));
+    for (size_t i = 0; i < P.M.size(); ++i)
+      m32[i] = cf(static_cast<float>(P.M[i].real()), static_cast<float>(P.M[i].imag()));
     if ((rc = upload(m32.data(), m32.size() * sizeof(cf), &o->d_M))) return rc;
   }
-  if ((rc = upload(P.colidx.data(), P.colidx.size() * sizeof(int32_t), &o->d_colidx))) return rc;
-  if ((rc = upload(P.items.data(), P.items.size() * sizeof(uh::Item), &o->d_items))) return rc;
-  if ((rc = upload(P.chunks.data(), P.chunks.size() * sizeof(uh::Chunk), &o->d_chunks))) return rc;
+  if ((rc = upload(P.items.data(), P.items.size() * sizeof(uh::WorkItem), &o->d_items))) return rc;
+  if ((rc = upload(P.cta_begin.data(), P.cta_begin.size() * sizeof(int32_t), &o->d_cta))) return rc;
+  if ((rc = upload(static_cast<const void*>(nullptr), uh::kNumCounters * sizeof(unsigned long long), &o->d_done)))
+    return rc;
+  for (int c = 0; c < uh::kNumCounters; ++c) o->counter_total[c] = P.counter_total(c);
+  if ((rc = upload(static_cast<const void*>(nullptr), sizeof(uint32_t), &o->d_status))) return rc;
   if ((rc = upload(T.perm.data(), T.perm.size() * sizeof(int32_t), &o->d_perm))) return rc;
-  if ((rc = upload(static_cast<const void*>(nullptr), std::max<int64_t>(z1len, 1) * eb, &o->d_z1))) return rc;
-  if ((rc = upload(static_cast<const void*>(nullptr), std::max<int64_t>(z2len, 1) * eb, &o->d_z2))) return rc;
-  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max(nslots, 1)) * uh::kHpMax * eb, &o->d_partials))) return rc;
-  if ((rc = upload(static_cast<const void*>(nullptr), std::max<size_t>(P.chunks.size(), 1) * sizeof(uint32_t), &o->d_cnt))) return rc;
-  if ((rc = upload(static_cast<const void*>(nullptr), 4 * sizeof(uint32_t), &o->d_sched))) return rc;
-  o->st.packed_bytes = static_cast<int64_t>(P.M.size() * eb + P.colidx.size() * sizeof(int32_t));
-  o->st.device_bytes = o->st.packed_bytes + static_cast<int64_t>(P.items.size() * sizeof(uh::Item) +
-                       P.chunks.size() * sizeof(uh::Chunk) + T.n * 4 + (z1len + z2len) * eb +
-                       static_cast<int64_t>(std::max(nslots, 1)) * uh::kHpMax * eb);
-  o->st.n_launches = nlaunch;
+  void** z[4] = {&o->d_xp, &o->d_z1, &o->d_z2, &o->d_z3};
+  for (int k = 0; k < 4; ++k)
+    if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(P.src_len_[k], 2)) * eb, z[k])))
+      return rc;
+  o->st.packed_bytes = P.tile_bytes_total + P.input_bytes_total;
+  o->st.device_bytes = static_cast<int64_t>(P.M.size() * eb + P.items.size() * sizeof(uh::WorkItem) +
+                                            P.chunks.size() * (sizeof(uh::OutChunk) + 4) + T.n * 4) +
+                       (P.src_len_[0] + P.src_len_[1] + P.src_len_[2] + P.src_len_[3]) * static_cast<int64_t>(eb);
+  o->st.n_launches = 1;
   o->st.n_items = static_cast<int64_t>(P.items.size());
   return UH_OK;
 }
 
-int run_matvec(OpBase* o, const void* x, void* y, void* stream) {
+int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeout = kTimeoutCycles,
+               bool stall = false) {
   if (!x || !y) return fail(UH_EINVAL, "x and y must be device pointers");
   const size_t eb = o->c128 ? 16 : 8;
   const char* xa = static_cast<const char*>(x);
   const char* ya = static_cast<const char*>(y);
   if (xa < ya + o->n * eb && ya < xa + o->n * eb) return fail(UH_EINVAL, "x and y overlap");
+  ++o->epoch;
+  uh::StreamParams p{};
+  p.items = o->d_items;
+  p.cta_begin = o->d_cta;
+  p.group_done = o->d_done;
+  // A group is complete in call number `epoch` when its counter reaches epoch * (its chunks);
+  // the stall test asks for one call more, which no chunk ever delivers.
+  for (int c = 0; c < uh::kNumCounters; ++c)
+    p.need[c] = static_cast<unsigned long long>(stall ? o->epoch + 1u : o->epoch) *
+                static_cast<unsigned long long>(o->counter_total[c]);
+  p.M = o->d_M;
+  p.x = x;
+  p.y = y;
+  p.perm = o->d_perm;
+  p.xp = o->d_xp;
+  p.z1 = o->d_z1;
+  p.z2 = o->d_z2;
+  p.z3 = o->d_z3;
+  p.status = o->d_status;
+  p.timeout_cycles = timeout;
+  cudaError_t e = uh::stream_launch(o->c128, p, o->ncta, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(UH_ECUDA, "streaming kernel launch: %s", cudaGetErrorString(e));
+  return UH_OK;
+}
+
+int check_status(OpBase* o, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (const Launch& L : o->launches) {
-    uh::SegGemvParams p{};
-    p.items = o->d_items + L.first;
-    p.item_count = L.count;
-    p.chunks = o->d_chunks;
-    p.M = o->d_M;
-    p.colidx = o->d_colidx;
-    p.in0 = L.in0 == 1 ? o->d_z1 : (L.in0 == 2 ? o->d_z2 : nullptr);
-    p.in1 = x;
-    p.out_lin = L.out == 1 ? o->d_z1 : (L.out == 2 ? o->d_z2 : nullptr);
-    p.out_perm = y;
-    p.perm = o->d_perm;
-    p.partials = o->d_partials;
-    p.chunk_cnt = o->d_cnt;
-    p.sched = o->d_sched;
-    cudaError_t e = uh::launch_seg_gemv(o->c128, p, o->grid, s);
-    if (e != cudaSuccess) return fail(UH_ECUDA, "segmented GEMV launch: %s", cudaGetErrorString(e));
+  uint32_t v = 0;
+  CUDA_TRY(cudaMemcpyAsync(&v, o->d_status, sizeof v, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (v) {
+    // A call that ran out left its group counters short: restart the counting.
+    CUDA_TRY(cudaMemsetAsync(o->d_status, 0, sizeof(uint32_t), s));
+    CUDA_TRY(cudaMemsetAsync(o->d_done, 0, uh::kNumCounters * sizeof(unsigned long long), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    o->epoch = 0;
+    return fail(UH_ETIMEOUT, "a bounded device-side wait ran out (code %u)", v);
   }
   return UH_OK;
 }
@@ -456,35 +329,64 @@ int check_precision(int32_t precision) {
   return UH_OK;
 }
 
-void init_program(Program& P, bool c128) {
-  P.elem_bytes = c128 ? 16 : 8;
-  P.epl = c128 ? 1 : 2;
+// Row tiles covered by [r0, r1).
+template <class F>
+void for_tiles(const std::vector<Tile>& tiles, int64_t r0, int64_t r1, F f) {
+  auto it = std::lower_bound(tiles.begin(), tiles.end(), r0, [](const Tile& t, int64_t v) { return t.p0 < v; });
+  for (; it != tiles.end() && it->p0 < r1; ++it) f(static_cast<size_t>(it - tiles.begin()));
 }
 
-// Near-field items (launch `launch`): for every dense block and every row tile inside its row
-// cluster, the columns D_b[tile rows, :] with inputs x at the column cluster's positions.
-void add_near_field(Program& P, const Tree& T, const uh_dense_desc& d, int data_type,
-                    const std::vector<Tile>& tiles, const std::vector<int>& tile_chunk, int launch) {
-  Src src{d.data, data_type};
-  // Group dense blocks by tile so that each tile's columns form one stream.
-  std::vector<std::vector<int64_t>> per_tile(tiles.size());
-  for (int64_t i = 0; i < d.n_dense; ++i) {
-    const int64_t r0 = T.begin[d.row_cl[i]], r1 = r0 + T.size[d.row_cl[i]];
-    auto it = std::lower_bound(tiles.begin(), tiles.end(), r0, [](const Tile& t, int64_t v) { return t.p0 < v; });
-    for (; it != tiles.end() && it->p0 < r1; ++it) per_tile[it - tiles.begin()].push_back(i);
+// Permutation slices (group 0): one per CTA.
+void add_permute(ProgramBuilder& P, int64_t n, int ncta) {
+  const int64_t A = P.align();
+  for (int b = 0; b < ncta; ++b) {
+    const int64_t a = (n * b / ncta) / A * A;
+    const int64_t e = b == ncta - 1 ? n : (n * (b + 1) / ncta) / A * A;
+    if (e <= a) continue;
+    const int c = P.add_chunk(uh::kPermute, a, static_cast<int>(e - a), uh::kGroupPermute, uh::kCounterPermute);
+    P.add_columns(c, {});
   }
-  std::vector<ColRef> cols;
+}
+
+// Near-field chunks of the row tiles, alternating between the two near-field groups. A tile with a
+// backward part writes its z3 slot (the backward chunk adds it), otherwise y directly. Returns,
+// per tile, the near-field chunk writing z3 (or -1).
+std::vector<int> add_near_field(ProgramBuilder& P, const Tree& T, const uh_dense_desc& d, const Src& D,
+                                const std::vector<Tile>& tiles, const std::vector<char>& has_back,
+                                std::vector<char>* has_near) {
+  const int64_t A = P.align();
+  std::vector<std::vector<int64_t>> per_tile(tiles.size());
+  for (int64_t i = 0; i < d.n_dense; ++i)
+    for_tiles(tiles, T.begin[d.row_cl[i]], T.begin[d.row_cl[i]] + T.size[d.row_cl[i]],
+              [&](size_t t) { per_tile[t].push_back(i); });
+  std::vector<int> zchunk(tiles.size(), -1);
+  has_near->assign(tiles.size(), 0);
+  int64_t pos = 0;
+  std::vector<int64_t> slot(tiles.size(), -1);
   for (size_t t = 0; t < tiles.size(); ++t) {
+    (*has_near)[t] = !per_tile[t].empty();
+    if (per_tile[t].empty() || !has_back[t]) continue;
+    slot[t] = pos;
+    pos += ProgramBuilder::round_up(tiles[t].h, A);
+  }
+  P.set_source_len(uh::kSrcZ3, pos);
+  int parity = 0;
+  std::vector<ColSpec> cols;
+  for (size_t t = 0; t < tiles.size(); ++t) {
+    if (per_tile[t].empty()) continue;
+    const int group = (parity++ & 1) ? uh::kGroupNearB : uh::kGroupNearA;
+    const int c = slot[t] >= 0 ? P.add_chunk(uh::kToZ3, slot[t], tiles[t].h, group)
+                               : P.add_chunk(uh::kToY, tiles[t].p0, tiles[t].h, group);
+    if (slot[t] >= 0) zchunk[t] = c;
     cols.clear();
     for (int64_t i : per_tile[t]) {
       const int32_t tau = d.row_cl[i], sg = d.col_cl[i];
-      const int64_t m = T.size[tau];
-      const int64_t roff = tiles[t].p0 - T.begin[tau];
-      for (int64_t c = 0; c < T.size[sg]; ++c)
-        cols.push_back(ColRef{d.off[i] + c * m + roff, 1, -(T.perm[T.begin[sg] + c]) - 1});
+      cols.push_back(ColSpec{uh::kSrcXp, T.begin[sg], T.size[sg], &D, false, d.off[i] + tiles[t].p0 - T.begin[tau],
+                             T.size[tau], 1});
     }
-    P.add_columns(tile_chunk[t], launch, src, false, cols);
+    P.add_columns(c, cols);
   }
+  return zchunk;
 }
 
 void fill_common_stats(OpBase* o, const Tree& T, const uh_dense_desc& d, int32_t precision) {
@@ -505,7 +407,7 @@ struct h_op : OpBase {};
 extern "C" {
 
 const char* uh_last_error(void) { return g_err.c_str(); }
-const char* uh_version(void) { return "uh-gb300 0.1 (sm_103a)"; }
+const char* uh_version(void) { return "uh-gb300 0.2 (sm_103a)"; }
 
 int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   g_err.clear();
@@ -550,88 +452,97 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   std::vector<Tile> tiles;
   if ((rc = make_tiles_and_check(T, brow, bcol, &tiles))) return rc;
 
-  auto* o = new (std::nothrow) uh_op();
-  if (!o) return fail(UH_ENOMEM, "host allocation");
-  o->c128 = precision == UH_PREC_C128;
-  o->n = T.n;
-  Program P;
-  init_program(P, o->c128);
+  const bool c128 = precision == UH_PREC_C128;
+  int ncta = g_pack_only_ncta, device = 0;
+  if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
+  ProgramBuilder P(c128, T.n, ncta);
+  const int64_t A = P.align();
+  P.set_source_len(uh::kSrcXp, ProgramBuilder::round_up(T.n, A));
+  add_permute(P, T.n, ncta);
 
-  // xhat / yhat offsets (clusters in increasing number).
+  // xhat / yhat segments, 16-byte aligned, clusters in increasing number.
   std::vector<int64_t> xoff(T.ncl, -1), yoff(T.ncl, -1);
   int64_t nx = 0, ny = 0;
   for (int32_t c = 0; c < T.ncl; ++c) {
-    if (is_col[c] && d->col_rank[c] > 0) { xoff[c] = nx; nx += d->col_rank[c]; }
-    if (is_row[c] && d->row_rank[c] > 0) { yoff[c] = ny; ny += d->row_rank[c]; }
+    if (is_col[c] && d->col_rank[c] > 0) { xoff[c] = nx; nx += ProgramBuilder::round_up(d->col_rank[c], A); }
+    if (is_row[c] && d->row_rank[c] > 0) { yoff[c] = ny; ny += ProgramBuilder::round_up(d->row_rank[c], A); }
   }
-  // y tile chunks.
-  std::vector<int> tile_chunk(tiles.size());
-  for (size_t t = 0; t < tiles.size(); ++t) tile_chunk[t] = P.add_chunk(1, tiles[t].p0, tiles[t].h, 0);
+  P.set_source_len(uh::kSrcZ1, nx);
+  P.set_source_len(uh::kSrcZ2, ny);
 
-  // Launch 0: forward transform, chunks of at most kHpMax rows of V_sigma^*.
-  Src vs{d->V_data, d->data_type};
-  std::vector<ColRef> cols;
+  // Forward transform: chunks of at most 64 rows of V_sigma^*; column r = conj(V_sigma[r, rows]).
+  const Src V{d->V_data, d->data_type}, S{d->S_data, d->data_type}, U{d->U_data, d->data_type};
+  const Src D{d->dense.data, d->data_type};
   for (int32_t s = 0; s < T.ncl; ++s) {
     if (xoff[s] < 0) continue;
     const int32_t l = d->col_rank[s];
     const int64_t m = T.size[s];
-    const int k = (l + uh::kHpMax - 1) / uh::kHpMax;
+    const int k = (l + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
     for (int q = 0; q < k; ++q) {
       const int j0 = l * q / k, j1 = l * (q + 1) / k;
-      const int ch = P.add_chunk(0, xoff[s] + j0, j1 - j0, 0);
-      cols.clear();
-      // column r of V_sigma^*[j0:j1, :] = conj(V_sigma[r, j0:j1]), input x at position begin+r
-      for (int64_t r = 0; r < m; ++r)
-        cols.push_back(ColRef{d->col_off[s] + r + j0 * m, m, -(T.perm[T.begin[s] + r]) - 1});
-      P.add_columns(ch, 0, vs, true, cols);
+      const int c = P.add_chunk(uh::kToZ1, xoff[s] + j0, j1 - j0, uh::kGroupForward, uh::kCounterForward);
+      P.add_columns(c, {ColSpec{uh::kSrcXp, T.begin[s], m, &V, true, d->col_off[s] + j0 * m, 1, m}});
     }
   }
-  // Launch 0 (continued): near field.
-  add_near_field(P, T, d->dense, d->data_type, tiles, tile_chunk, 0);
-  // Launch 1: coupling, per row cluster tau, columns of [S_b]_{sigma in row(tau)}.
+  // Which row tiles have a backward part.
+  std::vector<std::vector<int32_t>> tile_rows(tiles.size());
+  for (int32_t t = 0; t < T.ncl; ++t)
+    if (yoff[t] >= 0) for_tiles(tiles, T.begin[t], T.begin[t] + T.size[t], [&](size_t i) { tile_rows[i].push_back(t); });
+  std::vector<char> has_back(tiles.size(), 0);
+  for (size_t i = 0; i < tiles.size(); ++i) has_back[i] = !tile_rows[i].empty();
+  std::vector<char> has_near;
+  const std::vector<int> zchunk = add_near_field(P, T, d->dense, D, tiles, has_back, &has_near);
+  // Coupling: per row cluster tau (chunks of at most 64 rows), columns [S_b]_{sigma in row(tau)}.
   std::vector<std::vector<int64_t>> row_blocks(T.ncl);
   for (int64_t i = 0; i < d->n_adm; ++i) row_blocks[d->adm_row[i]].push_back(i);
-  Src ss{d->S_data, d->data_type};
+  std::vector<ColSpec> cols;
   for (int32_t t = 0; t < T.ncl; ++t) {
     if (yoff[t] < 0) continue;
     auto& bl = row_blocks[t];
     std::stable_sort(bl.begin(), bl.end(), [&](int64_t a, int64_t b) { return d->adm_col[a] < d->adm_col[b]; });
     const int32_t l = d->row_rank[t];
-    const int k = (l + uh::kHpMax - 1) / uh::kHpMax;
+    const int k = (l + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
     for (int q = 0; q < k; ++q) {
       const int i0 = l * q / k, i1 = l * (q + 1) / k;
-      const int ch = P.add_chunk(0, yoff[t] + i0, i1 - i0, 1);
+      const int c = P.add_chunk(uh::kToZ2, yoff[t] + i0, i1 - i0, uh::kGroupCoupling, uh::kCounterCoupling);
       cols.clear();
       for (int64_t b : bl) {
         const int32_t s = d->adm_col[b];
-        const int32_t ls = d->col_rank[s];
-        for (int j = 0; j < ls; ++j) cols.push_back(ColRef{d->S_off[b] + static_cast<int64_t>(j) * l + i0, 1, static_cast<int32_t>(xoff[s] + j)});
+        if (xoff[s] < 0) continue;
+        cols.push_back(ColSpec{uh::kSrcZ1, xoff[s], d->col_rank[s], &S, false, d->S_off[b] + i0, l, 1});
       }
-      P.add_columns(ch, 1, ss, false, cols);
+      P.add_columns(c, cols);
     }
   }
-  // Launch 2: backward transform, per y tile, columns U_tau[tile rows, :] of every row
-  // cluster tau that contains the tile, inputs yhat_tau.
-  std::vector<std::vector<int32_t>> tile_rows(tiles.size());
-  for (int32_t t = 0; t < T.ncl; ++t) {
-    if (yoff[t] < 0) continue;
-    const int64_t r0 = T.begin[t], r1 = r0 + T.size[t];
-    auto it = std::lower_bound(tiles.begin(), tiles.end(), r0, [](const Tile& a, int64_t v) { return a.p0 < v; });
-    for (; it != tiles.end() && it->p0 < r1; ++it) tile_rows[it - tiles.begin()].push_back(t);
-  }
-  Src us{d->U_data, d->data_type};
+  // Backward transform (+ near-field base): per row tile, columns U_tau[tile rows, :].
   for (size_t ti = 0; ti < tiles.size(); ++ti) {
+    if (!has_back[ti]) {
+      // the near-field chunk writes y; a tile whose blocks all have rank 0 and no near field
+      // gets an empty chunk, which writes zeros
+      if (!has_near[ti]) P.add_columns(P.add_chunk(uh::kToY, tiles[ti].p0, tiles[ti].h, uh::kGroupBackward), {});
+      continue;
+    }
+    const int c = P.add_chunk(uh::kToY, tiles[ti].p0, tiles[ti].h, uh::kGroupBackward);
     cols.clear();
     for (int32_t t : tile_rows[ti]) {
       const int64_t m = T.size[t];
-      const int64_t roff = tiles[ti].p0 - T.begin[t];
-      for (int j = 0; j < d->row_rank[t]; ++j)
-        cols.push_back(ColRef{d->row_off[t] + j * m + roff, 1, static_cast<int32_t>(yoff[t] + j)});
+      cols.push_back(ColSpec{uh::kSrcZ2, yoff[t], d->row_rank[t], &U, false, d->row_off[t] + tiles[ti].p0 - T.begin[t], m, 1});
     }
-    P.add_columns(tile_chunk[ti], 2, us, false, cols);
+    P.add_columns(c, cols, zchunk[ti]);
   }
-  const int in0[3] = {0, 1, 2}, outsel[3] = {1, 2, 0};
-  if ((rc = upload_program(o, P, T, 3, nx, ny, in0, outsel))) { free_op(o); delete o; return rc; }
+
+  if (g_pack_only_ncta) {
+    if (const char* e = P.finalize()) return fail(UH_EINVAL, "packing: %s", e);
+    if (const char* e = P.self_check()) return fail(UH_EINVAL, "internal packing error: %s", e);
+    return UH_OK;
+  }
+  auto* o = new (std::nothrow) uh_op();
+  if (!o) return fail(UH_ENOMEM, "host allocation");
+  o->c128 = c128;
+  o->n = T.n;
+  o->ncta = ncta;
+  o->device = device;
+  if ((rc = upload_program(o, P, T))) { free_op(o); delete o; return rc; }
 
   // Statistics.
   fill_common_stats(o, T, d->dense, precision);
@@ -686,6 +597,11 @@ int uh_matvec(uh_op* op, const void* x, void* y, void* stream) {
   return run_matvec(op, x, y, stream);
 }
 
+int uh_check(uh_op* op, void* stream) {
+  if (!op) return fail(UH_EINVAL, "null op");
+  return check_status(op, stream);
+}
+
 int uh_stats(const uh_op* op, uh_stats_t* out) {
   if (!op || !out) return fail(UH_EINVAL, "null argument");
   *out = op->st;
@@ -720,59 +636,70 @@ int h_create(const h_desc* d, int32_t precision, h_op** out) {
   std::vector<Tile> tiles;
   if ((rc = make_tiles_and_check(T, brow, bcol, &tiles))) return rc;
 
-  auto* o = new (std::nothrow) h_op();
-  if (!o) return fail(UH_ENOMEM, "host allocation");
-  o->c128 = precision == UH_PREC_C128;
-  o->n = T.n;
-  Program P;
-  init_program(P, o->c128);
-  std::vector<int> tile_chunk(tiles.size());
-  for (size_t t = 0; t < tiles.size(); ++t) tile_chunk[t] = P.add_chunk(1, tiles[t].p0, tiles[t].h, 0);
-  // Launch 0: t_b = Y_b^* x|_sigma per block (chunks of at most kHpMax), plus the near field.
+  const bool c128 = precision == UH_PREC_C128;
+  int ncta = g_pack_only_ncta, device = 0;
+  if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
+  ProgramBuilder P(c128, T.n, ncta);
+  const int64_t A = P.align();
+  P.set_source_len(uh::kSrcXp, ProgramBuilder::round_up(T.n, A));
+  P.set_source_len(uh::kSrcZ2, 0);
+  add_permute(P, T.n, ncta);
+  // t_b = Y_b^* x|_sigma per admissible block, chunks of at most 64.
   std::vector<int64_t> toff(d->n_adm, -1);
   int64_t nt = 0;
-  Src ys{d->Y_data, d->data_type};
-  std::vector<ColRef> cols;
-  for (int64_t b = 0; b < d->n_adm; ++b) {
-    const int32_t k = d->adm_rank[b];
-    if (k == 0) continue;
-    toff[b] = nt;
-    nt += k;
-    const int32_t s = d->adm_col[b];
-    const int64_t m = T.size[s];
-    const int nq = (k + uh::kHpMax - 1) / uh::kHpMax;
-    for (int q = 0; q < nq; ++q) {
-      const int j0 = k * q / nq, j1 = k * (q + 1) / nq;
-      const int ch = P.add_chunk(0, toff[b] + j0, j1 - j0, 0);
-      cols.clear();
-      for (int64_t r = 0; r < m; ++r)
-        cols.push_back(ColRef{d->Y_off[b] + r + j0 * m, m, -(T.perm[T.begin[s] + r]) - 1});
-      P.add_columns(ch, 0, ys, true, cols);
-    }
-  }
-  add_near_field(P, T, d->dense, d->data_type, tiles, tile_chunk, 0);
-  // Launch 1: y|_tile += X_b|_tile t_b for every block whose row cluster contains the tile.
-  std::vector<std::vector<int64_t>> tile_blocks(tiles.size());
+  for (int64_t b = 0; b < d->n_adm; ++b)
+    if (d->adm_rank[b] > 0) { toff[b] = nt; nt += ProgramBuilder::round_up(d->adm_rank[b], A); }
+  P.set_source_len(uh::kSrcZ1, nt);
+  const Src Y{d->Y_data, d->data_type}, X{d->X_data, d->data_type}, D{d->dense.data, d->data_type};
   for (int64_t b = 0; b < d->n_adm; ++b) {
     if (toff[b] < 0) continue;
-    const int64_t r0 = T.begin[d->adm_row[b]], r1 = r0 + T.size[d->adm_row[b]];
-    auto it = std::lower_bound(tiles.begin(), tiles.end(), r0, [](const Tile& a, int64_t v) { return a.p0 < v; });
-    for (; it != tiles.end() && it->p0 < r1; ++it) tile_blocks[it - tiles.begin()].push_back(b);
+    const int32_t k = d->adm_rank[b];
+    const int32_t s = d->adm_col[b];
+    const int64_t m = T.size[s];
+    const int nq = (k + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
+    for (int q = 0; q < nq; ++q) {
+      const int j0 = k * q / nq, j1 = k * (q + 1) / nq;
+      const int c = P.add_chunk(uh::kToZ1, toff[b] + j0, j1 - j0, uh::kGroupForward, uh::kCounterForward);
+      P.add_columns(c, {ColSpec{uh::kSrcXp, T.begin[s], m, &Y, true, d->Y_off[b] + j0 * m, 1, m}});
+    }
   }
-  Src xs{d->X_data, d->data_type};
+  std::vector<std::vector<int64_t>> tile_blocks(tiles.size());
+  for (int64_t b = 0; b < d->n_adm; ++b)
+    if (toff[b] >= 0)
+      for_tiles(tiles, T.begin[d->adm_row[b]], T.begin[d->adm_row[b]] + T.size[d->adm_row[b]],
+                [&](size_t i) { tile_blocks[i].push_back(b); });
+  std::vector<char> has_back(tiles.size(), 0);
+  for (size_t i = 0; i < tiles.size(); ++i) has_back[i] = !tile_blocks[i].empty();
+  std::vector<char> has_near;
+  const std::vector<int> zchunk = add_near_field(P, T, d->dense, D, tiles, has_back, &has_near);
+  std::vector<ColSpec> cols;
   for (size_t ti = 0; ti < tiles.size(); ++ti) {
+    if (!has_back[ti]) {
+      if (!has_near[ti]) P.add_columns(P.add_chunk(uh::kToY, tiles[ti].p0, tiles[ti].h, uh::kGroupBackward), {});
+      continue;
+    }
+    const int c = P.add_chunk(uh::kToY, tiles[ti].p0, tiles[ti].h, uh::kGroupBackward);
     cols.clear();
     for (int64_t b : tile_blocks[ti]) {
       const int32_t t = d->adm_row[b];
       const int64_t m = T.size[t];
-      const int64_t roff = tiles[ti].p0 - T.begin[t];
-      for (int j = 0; j < d->adm_rank[b]; ++j)
-        cols.push_back(ColRef{d->X_off[b] + j * m + roff, 1, static_cast<int32_t>(toff[b] + j)});
+      cols.push_back(ColSpec{uh::kSrcZ1, toff[b], d->adm_rank[b], &X, false, d->X_off[b] + tiles[ti].p0 - T.begin[t], m, 1});
     }
-    P.add_columns(tile_chunk[ti], 1, xs, false, cols);
+    P.add_columns(c, cols, zchunk[ti]);
   }
-  const int in0[2] = {0, 1}, outsel[2] = {1, 0};
-  if ((rc = upload_program(o, P, T, 2, nt, 1, in0, outsel))) { free_op(o); delete o; return rc; }
+
+  if (g_pack_only_ncta) {
+    if (const char* e = P.finalize()) return fail(UH_EINVAL, "packing: %s", e);
+    if (const char* e = P.self_check()) return fail(UH_EINVAL, "internal packing error: %s", e);
+    return UH_OK;
+  }
+  auto* o = new (std::nothrow) h_op();
+  if (!o) return fail(UH_ENOMEM, "host allocation");
+  o->c128 = c128;
+  o->n = T.n;
+  o->ncta = ncta;
+  o->device = device;
+  if ((rc = upload_program(o, P, T))) { free_op(o); delete o; return rc; }
   fill_common_stats(o, T, d->dense, precision);
   int64_t ex = 0, ey = 0, sk = 0;
   for (int64_t b = 0; b < d->n_adm; ++b) {
@@ -802,10 +729,40 @@ int h_matvec(h_op* op, const void* x, void* y, void* stream) {
   return run_matvec(op, x, y, stream);
 }
 
+int h_check(h_op* op, void* stream) {
+  if (!op) return fail(UH_EINVAL, "null op");
+  return check_status(op, stream);
+}
+
 int h_stats(const h_op* op, uh_stats_t* out) {
   if (!op || !out) return fail(UH_EINVAL, "null argument");
   *out = op->st;
   return UH_OK;
+}
+
+int uh_pack_check(const uh_desc* desc, int32_t precision, int32_t ncta) {
+  if (ncta < 1) return fail(UH_EINVAL, "ncta = %d", ncta);
+  g_pack_only_ncta = ncta;
+  uh_op* o = nullptr;
+  const int rc = uh_create(desc, precision, &o);
+  g_pack_only_ncta = 0;
+  return rc;
+}
+
+int h_pack_check(const h_desc* desc, int32_t precision, int32_t ncta) {
+  if (ncta < 1) return fail(UH_EINVAL, "ncta = %d", ncta);
+  g_pack_only_ncta = ncta;
+  h_op* o = nullptr;
+  const int rc = h_create(desc, precision, &o);
+  g_pack_only_ncta = 0;
+  return rc;
+}
+
+int uh_debug_stalled_matvec(uh_op* op, const void* x, void* y, long long timeout_cycles, void* stream) {
+  if (!op) return fail(UH_EINVAL, "null op");
+  if (timeout_cycles < 1000 || timeout_cycles > kTimeoutCycles)
+    return fail(UH_EINVAL, "timeout_cycles %lld outside [1000, %lld]", timeout_cycles, kTimeoutCycles);
+  return run_matvec(op, x, y, stream, timeout_cycles, true);
 }
 
 int uh_matmat(uh_op*, int32_t, const void*, int64_t, void*, int64_t, void*) {

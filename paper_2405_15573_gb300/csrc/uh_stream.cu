@@ -1,0 +1,384 @@
+// Streaming matvec kernel (sm_103a): one persistent launch per UH or H matrix-vector product.
+// Layout of the work and the dependency rules: uh_stream.h.
+//
+// Roles in a CTA of 288 threads:
+//  - producer (lane 0 of warp 8): streams the CTA's item descriptors into a shared-memory ring;
+//    per item waits for its stage to be free, copies the descriptor into the stage's slot, arms
+//    the stage's full barrier with the byte count, copies the tile with one TMA bulk copy and,
+//    once every group the item's runs read from is complete (checked once per group and call,
+//    then remembered), each input run with one more bulk copy into the stage's input area.
+//  - consumers (warps 0-7): per item, wait for the stage, multiply the tile by the staged inputs
+//    into per-thread accumulators (thread = 16-byte row slice x column group), release the
+//    stage; at the end of a chunk reduce the column groups in a fixed tree order, add the
+//    near-field base if the chunk has one, write the outputs and, for chunks other CTAs wait on,
+//    add to the group counter.
+// Every wait is bounded (timeout_cycles); when one runs out the CTA records it in `status`,
+// stops issuing, lets the copies in flight land, and returns.
+#include <cuda_runtime.h>
+
+#include "uh_internal.h"
+#include "uh_stream.h"
+
+namespace uh {
+namespace {
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// TMA bulk copy global -> shared, completion counted on `bar` (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kStreamConsumers) : "memory");
+}
+
+__device__ __forceinline__ void cfma(float2& a, float2 m, float2 v) {
+  a.x = fmaf(m.x, v.x, fmaf(-m.y, v.y, a.x));
+  a.y = fmaf(m.x, v.y, fmaf(m.y, v.x, a.y));
+}
+__device__ __forceinline__ void cfma(double2& a, double2 m, double2 v) {
+  a.x = fma(m.x, v.x, fma(-m.y, v.y, a.x));
+  a.y = fma(m.x, v.y, fma(m.y, v.x, a.y));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+__device__ __forceinline__ void lds16(const float2* p, float2 (&m)[2]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  m[0] = make_float2(q.x, q.y);
+  m[1] = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void lds16(const double2* p, double2 (&m)[1]) { m[0] = *p; }
+
+// Bounded wait on an mbarrier phase; false if it ran out or the CTA is aborting.
+__device__ bool wait_parity(uint64_t* bar, uint32_t parity, long long budget, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 31u) == 0) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > budget) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ const void* src_ptr(const StreamParams& p, int src) {
+  return src == kSrcXp ? p.xp : src == kSrcZ1 ? p.z1 : src == kSrcZ2 ? p.z2 : p.z3;
+}
+
+struct Bars {
+  uint64_t* full;   // tile and runs landed (1 arrival + their bytes)
+  uint64_t* empty;  // stage consumed (one arrival per consumer warp)
+  uint64_t* desc;   // descriptor batch landed
+};
+__device__ __forceinline__ Bars bars_of(unsigned char* smem) {
+  uint64_t* b = reinterpret_cast<uint64_t*>(smem + kSmemBars);
+  return Bars{b, b + kStages, b + 2 * kStages};
+}
+
+// Orders this thread's earlier generic-proxy accesses before its later async-proxy (TMA) ones.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+template <typename R>
+__device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* smem) {
+  using T = typename Cx<R>::T;
+  unsigned char* stages = smem;
+  WorkItem* slots = reinterpret_cast<WorkItem*>(smem + kSmemSlots);
+  WorkItem* ring = reinterpret_cast<WorkItem*>(smem + kSmemDesc);
+  const Bars bar = bars_of(smem);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
+  const T* M = static_cast<const T*>(p.M);
+  const int n = i1 - i0;
+  auto issue_batch = [&](int batch) {
+    const int first = batch * kDescBatch;
+    if (first >= n) return;
+    const int cnt = n - first < kDescBatch ? n - first : kDescBatch;
+    const int q = batch % kDescBatches;
+    mbar_arrive_expect_tx(&bar.desc[q], static_cast<uint32_t>(cnt * sizeof(WorkItem)));
+    bulk_g2s(ring + q * kDescBatch, p.items + i0 + first, static_cast<uint32_t>(cnt * sizeof(WorkItem)),
+             &bar.desc[q]);
+  };
+  for (int b = 0; b < kDescBatches; ++b) issue_batch(b);
+  int seq = 0;
+  bool ok = true;
+  uint32_t ready = 0;  // groups known complete in this call
+  for (; seq < n; ++seq) {
+    const int batch = seq / kDescBatch;
+    if (seq % kDescBatch == 0 &&
+        !wait_parity(&bar.desc[batch % kDescBatches], static_cast<uint32_t>(batch / kDescBatches) & 1u,
+                     p.timeout_cycles, abort_flag)) {
+      atomicOr(p.status, 8u);
+      ok = false;
+      break;
+    }
+    const int s = seq % kStages;
+    const uint32_t k = static_cast<uint32_t>(seq / kStages);
+    if (k > 0 && !wait_parity(&bar.empty[s], (k - 1) & 1u, p.timeout_cycles, abort_flag)) {
+      atomicOr(p.status, 2u);
+      ok = false;
+      break;
+    }
+    const WorkItem& d = ring[(batch % kDescBatches) * kDescBatch + seq % kDescBatch];
+    slots[s] = d;
+    const WorkItem& it = slots[s];
+    if (seq % kDescBatch == kDescBatch - 1) {
+      // this batch's descriptors are copied out; refill its ring slots
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_batch(batch + kDescBatches);
+    }
+    unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
+    const uint32_t tile_bytes = static_cast<uint32_t>(it.ncols) * static_cast<uint32_t>(it.hp) * sizeof(T);
+    uint32_t bytes = tile_bytes;
+    for (int r = 0; r < it.nruns; ++r) bytes += static_cast<uint32_t>(it.runs[r].len) * sizeof(T);
+    mbar_arrive_expect_tx(&bar.full[s], bytes);
+    if (tile_bytes) bulk_g2s(st, M + it.tile_off, tile_bytes, &bar.full[s]);
+    const uint32_t deps = (static_cast<uint32_t>(it.flags) >> kDepShift) & ((1u << kNumCounters) - 1u);
+    if (deps & ~ready) {
+      const long long t0 = clock64();
+      for (;;) {
+        for (int g = 0; g < kNumCounters; ++g)
+          if (((deps & ~ready) >> g) & 1u)
+            if (ld_acquire_u64(p.group_done + g) >= p.need[g]) ready |= 1u << g;
+        if (!(deps & ~ready)) break;
+        __nanosleep(100);
+        if (*abort_flag || clock64() - t0 > p.timeout_cycles) {
+          atomicOr(p.status, 4u);
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) break;
+      fence_proxy_async();  // the acquire above before the bulk copies that read those inputs
+    }
+    uint32_t col = 0;
+    for (int r = 0; r < it.nruns; ++r) {
+      const Run run = it.runs[r];
+      bulk_g2s(st + kTileBytes + col * sizeof(T), static_cast<const T*>(src_ptr(p, run.src)) + run.start,
+               static_cast<uint32_t>(run.len) * sizeof(T), &bar.full[s]);
+      col += static_cast<uint32_t>(run.len);
+    }
+  }
+  if (!ok) {
+    *abort_flag = 1;
+    // Let every bulk copy already issued land before the CTA can exit: bounded waits on the
+    // stages of the last kStages items and on the descriptor batches in flight.
+    const int first = seq >= kStages ? seq - kStages + 1 : 0;
+    for (int q = first; q <= seq && q < n; ++q) {
+      const long long t0 = clock64();
+      while (!mbar_try_wait(&bar.full[q % kStages], static_cast<uint32_t>(q / kStages) & 1u) &&
+             clock64() - t0 < p.timeout_cycles) {
+      }
+    }
+    for (int b = seq / kDescBatch; b < seq / kDescBatch + kDescBatches && b * kDescBatch < n; ++b) {
+      const long long t0 = clock64();
+      while (!mbar_try_wait(&bar.desc[b % kDescBatches], static_cast<uint32_t>(b / kDescBatches) & 1u) &&
+             clock64() - t0 < p.timeout_cycles) {
+      }
+    }
+  }
+}
+
+template <typename R>
+__device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* smem) {
+  using T = typename Cx<R>::T;
+  constexpr int EPL = 16 / sizeof(T);
+  const int tid = threadIdx.x;
+  unsigned char* stages = smem;
+  T* sred = reinterpret_cast<T*>(smem + kSmemRed);
+  const WorkItem* slots = reinterpret_cast<const WorkItem*>(smem + kSmemSlots);
+  const Bars bar = bars_of(smem);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
+  volatile int* go = abort_flag + 1;  // go[0], go[1]: leader's decision, by item parity
+  const int n = i1 - i0;
+
+  T acc[EPL];
+  int need = 1, lanes = 1, groups = kStreamConsumers, lane = 0, g = tid, hpl = EPL;
+  for (int seq = 0; seq < n; ++seq) {
+    const int s = seq % kStages;
+    const uint32_t parity = static_cast<uint32_t>(seq / kStages) & 1u;
+    if (tid == 0) {
+      const bool ok = wait_parity(&bar.full[s], parity, p.timeout_cycles, abort_flag);
+      if (!ok && !*abort_flag) {
+        atomicOr(p.status, 1u);
+        *abort_flag = 1;
+      }
+      go[seq & 1] = ok ? 1 : 0;
+    }
+    consumer_sync();
+    if (!go[seq & 1]) break;
+    mbar_try_wait(&bar.full[s], parity);  // completed phase: each thread's own acquire
+    const WorkItem& sl = slots[s];
+    const int flags = sl.flags;
+    const int hp = sl.hp, nc = sl.ncols;
+    const int kind = sl.kind, h = sl.h, counter = sl.counter, base_off = sl.base_off;
+    const int64_t dst = sl.dst;
+    const unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
+    if (flags & kItemFirst) {
+      need = hp / EPL;
+      lanes = 1;
+      while (lanes < need) lanes <<= 1;
+      groups = kStreamConsumers / lanes;
+      lane = tid & (lanes - 1);
+      g = tid / lanes;
+      hpl = lanes * EPL;
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) acc[e] = T{0, 0};
+    }
+    if (kind == kPermute) {
+      const T* x = static_cast<const T*>(p.x);
+      T* xp = static_cast<T*>(p.xp);
+      for (int r = tid; r < h; r += kStreamConsumers) xp[dst + r] = x[p.perm[dst + r]];
+    } else if (lane < need) {
+      const T* tile = reinterpret_cast<const T*>(st) + lane * EPL;
+      const T* vin = reinterpret_cast<const T*>(st + kTileBytes);
+      int c = g;
+      for (; c + 3 * groups < nc; c += 4 * groups) {
+        T m0[EPL], m1[EPL], m2[EPL], m3[EPL];
+        lds16(tile + c * hp, m0);
+        lds16(tile + (c + groups) * hp, m1);
+        lds16(tile + (c + 2 * groups) * hp, m2);
+        lds16(tile + (c + 3 * groups) * hp, m3);
+        const T v0 = vin[c], v1 = vin[c + groups], v2 = vin[c + 2 * groups], v3 = vin[c + 3 * groups];
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          cfma(acc[e], m0[e], v0);
+          cfma(acc[e], m1[e], v1);
+          cfma(acc[e], m2[e], v2);
+          cfma(acc[e], m3[e], v3);
+        }
+      }
+      for (; c < nc; c += groups) {
+        T m0[EPL];
+        lds16(tile + c * hp, m0);
+        const T v0 = vin[c];
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) cfma(acc[e], m0[e], v0);
+      }
+    }
+    // The stage (tile, inputs, slot) has been read: release it to the producer.
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(&bar.empty[s]);
+    if (flags & kItemLast) {
+      if (kind == kPermute) {
+        __threadfence();
+        consumer_sync();
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) sred[g * hpl + lane * EPL + e] = acc[e];
+        consumer_sync();
+        for (int h2 = groups >> 1; h2 >= 1; h2 >>= 1) {
+          if (g < h2) {
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+              const int q = g * hpl + lane * EPL + e;
+              sred[q] = cadd(sred[q], sred[q + h2 * hpl]);
+            }
+          }
+          consumer_sync();
+        }
+        if (tid < h) {
+          T v = sred[tid];
+          // near-field partial of this row tile, written earlier by this same thread
+          if (flags & kItemBase) v = cadd(v, static_cast<const T*>(p.z3)[base_off + tid]);
+          if (kind == kToY) {
+            static_cast<T*>(p.y)[p.perm[dst + tid]] = v;
+          } else {
+            T* z = static_cast<T*>(kind == kToZ1 ? p.z1 : kind == kToZ2 ? p.z2 : p.z3);
+            z[dst + tid] = v;
+            if (counter >= 0) __threadfence();  // other CTAs read it after the counter
+          }
+        }
+        consumer_sync();  // outputs written; sred free for the next chunk
+      }
+      if (tid == 0 && counter >= 0) red_release_add(p.group_done + counter, 1ull);
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Bars bar = bars_of(smem);
+  volatile int* misc = reinterpret_cast<volatile int*>(smem + kSmemMisc);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&bar.full[s], 1);
+      mbar_init(&bar.empty[s], kStreamConsumerWarps);
+    }
+    for (int q = 0; q < kDescBatches; ++q) mbar_init(&bar.desc[q], 1);
+    for (int q = 0; q < 6; ++q) misc[q] = 0;  // abort, go[2], pf[2]
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int i0 = p.cta_begin[blockIdx.x], i1 = p.cta_begin[blockIdx.x + 1];
+  if (threadIdx.x >= kStreamConsumers) {
+    if (threadIdx.x == kStreamConsumers) producer<R>(p, i0, i1, smem);
+  } else {
+    consumers<R>(p, i0, i1, smem);
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+cudaError_t stream_prepare(bool c128) {
+  return c128 ? cudaFuncSetAttribute(stream_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kStreamSmemBytes)
+              : cudaFuncSetAttribute(stream_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kStreamSmemBytes);
+}
+
+cudaError_t stream_occupancy(bool c128, int* blocks_per_sm) {
+  return c128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stream_kernel<double>, kStreamThreads,
+                                                              kStreamSmemBytes)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stream_kernel<float>, kStreamThreads,
+                                                              kStreamSmemBytes);
+}
+
+cudaError_t stream_launch(bool c128, const StreamParams& p, int grid, cudaStream_t stream) {
+  void* args[] = {const_cast<StreamParams*>(&p)};
+  const void* fn = c128 ? reinterpret_cast<const void*>(stream_kernel<double>)
+                        : reinterpret_cast<const void*>(stream_kernel<float>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kStreamThreads), args, kStreamSmemBytes, stream);
+}
+
+}  // namespace uh

@@ -1,0 +1,113 @@
+// Device program of the streaming matvec kernel (uh_stream.cu), shared with the host packer.
+//
+// One matvec (UH: Algorithm 6; H: Algorithm 5) is ONE persistent launch, one CTA per SM. Its work
+// is a list of output chunks (at most 64 consecutive outputs each). Every chunk is owned by one
+// CTA and streamed as a sequence of work items; an item is one column-major tile of `hp` rows x
+// `ncols` columns (at most kTileBytes) together with the input values its columns multiply,
+// given as up to kMaxRuns contiguous runs of an input vector. In each CTA a producer warp copies
+// item tiles and input runs into a ring of kStages shared-memory stages with TMA bulk copies
+// (cp.async.bulk, mbarrier transaction counts); eight consumer warps multiply and accumulate, and
+// at the end of a chunk reduce the column groups and write the chunk's outputs.
+//
+// Dependencies are per phase group: an item that reads x in cluster order, xhat or yhat waits
+// (in its producer, before copying those runs) until every chunk of the group that writes that
+// vector has finished in this call, counted by a monotonic 64-bit counter per group. A producer
+// checks a group once per call and then remembers it. Each CTA's list is ordered by group and a
+// group only waits on earlier groups, so the waits end. The near-field partial of a row tile is
+// written and read back by the same consumer thread (its near-field and backward chunks are in
+// the same CTA), so it needs no flag.
+#pragma once
+
+#include <stdint.h>
+
+namespace uh {
+
+constexpr int kStreamConsumerWarps = 8;
+constexpr int kStreamConsumers = kStreamConsumerWarps * 32;
+constexpr int kStreamThreads = kStreamConsumers + 32;  // + producer warp
+constexpr int kStages = 5;
+constexpr int kTileBytes = 32768;
+constexpr int kStreamMaxCols = 512;
+constexpr int kInBytes = kStreamMaxCols * 16;  // a stage's input area (512 complex128 values)
+constexpr int kStageBytes = kTileBytes + kInBytes;
+constexpr int kMaxRuns = 6;
+constexpr int kStreamHpMax = 64;
+
+// Work-item descriptors are streamed into a ring of kDescRing entries, kDescBatch per copy.
+constexpr int kDescBatch = 8;
+constexpr int kDescBatches = 4;
+constexpr int kDescRing = kDescBatch * kDescBatches;
+
+// Shared-memory layout of the kernel (bytes).
+constexpr int kSmemRed = kStages * kStageBytes;                  // group reduction, 256 x 16 B
+constexpr int kSmemSlots = kSmemRed + 256 * 16;                  // per-stage copy of the item, 96 B each
+constexpr int kSmemDesc = kSmemSlots + kStages * 96;             // descriptor ring, 96 B each
+constexpr int kSmemBars = kSmemDesc + kDescRing * 96;            // full, empty [kStages], desc [kDescBatches]
+constexpr int kSmemMisc = kSmemBars + (2 * kStages + kDescBatches) * 8;  // abort flag, decision words
+constexpr int kStreamSmemBytes = kSmemMisc + 32;
+
+// Input vectors a run can read.
+enum : int8_t { kSrcXp = 0, kSrcZ1 = 1, kSrcZ2 = 2, kSrcZ3 = 3 };
+
+struct Run {
+  int32_t start;   // first element (a multiple of the 16-byte element count)
+  int16_t len;     // elements (likewise a multiple)
+  int8_t src;      // kSrc*
+  int8_t pad;
+};
+static_assert(sizeof(Run) == 8, "Run layout");
+
+// Item flags: chunk boundaries, near-field base, and the groups whose completion the item's runs
+// need (bits kDepShift + counter index).
+enum : int16_t { kItemFirst = 1, kItemLast = 2, kItemBase = 4 };
+constexpr int kDepShift = 8;
+enum : int { kCounterPermute = 0, kCounterForward = 1, kCounterCoupling = 2, kNumCounters = 3 };
+
+// Chunk outputs: kToZ1..kToZ3 write z[dst + r]; kToY writes y[perm[dst + r]]; kPermute fills
+// xp[dst + r] = x[perm[dst + r]] (no tile, no inputs). counter >= 0: the chunk's completion is
+// added to that group counter.
+enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kPermute = 4 };
+
+struct alignas(16) WorkItem {
+  int64_t tile_off;  // element offset of the tile in the packed matrix buffer
+  int64_t dst;       // the chunk's output offset (see kind)
+  int32_t hp;        // rows of the tile = padded chunk height
+  int32_t ncols;     // tile columns = staged input values (sum of the run lengths)
+  int32_t h;         // the chunk's height
+  int16_t kind;      // the chunk's output kind (kTo*, kPermute)
+  int16_t counter;   // the chunk's group counter, or -1
+  int16_t nruns;
+  int16_t flags;     // kItem* | dependency bits
+  int32_t base_off;  // kItemBase: the chunk adds z3[base_off + r] to output r
+  int32_t chunk;     // chunk number (host bookkeeping)
+  int32_t pad;
+  Run runs[kMaxRuns];
+};
+static_assert(sizeof(WorkItem) == 96, "WorkItem layout");
+
+// Host-side record of a chunk.
+struct OutChunk {
+  int64_t dst;
+  int32_t h;
+  int16_t kind;
+  int16_t counter;
+};
+
+struct StreamParams {
+  const WorkItem* items;
+  const int32_t* cta_begin;  // items of CTA b: [cta_begin[b], cta_begin[b + 1])
+  unsigned long long* group_done;  // [kNumCounters], monotonic over calls
+  unsigned long long need[kNumCounters];  // a group is complete when group_done >= need
+  const void* M;             // packed tiles
+  const void* x;             // input, original ordering
+  void* y;                   // output, original ordering
+  const int32_t* perm;       // position -> original index
+  void* xp;                  // x in cluster order (kSrcXp)
+  void* z1;                  // xhat or t_b (kSrcZ1)
+  void* z2;                  // yhat (kSrcZ2)
+  void* z3;                  // near-field partials of row tiles (base of the backward chunks)
+  uint32_t* status;          // nonzero after a bounded wait ran out
+  long long timeout_cycles;  // bound of every wait, in SM clock cycles
+};
+
+}  // namespace uh

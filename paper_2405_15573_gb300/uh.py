@@ -80,6 +80,11 @@ for _name, _args in [
     ("h_matmat", [_p, _i32, _p, _i64, _p, _i64, _p]),
     ("h_reserve", [_p, _i32]),
     ("h_stats", [_p, C.POINTER(Stats)]),
+    ("uh_check", [_p, _p]),
+    ("uh_pack_check", [C.POINTER(UHDesc), _i32, _i32]),
+    ("uh_debug_stalled_matvec", [_p, _p, _p, C.c_longlong, _p]),
+    ("h_pack_check", [C.POINTER(HDesc), _i32, _i32]),
+    ("h_check", [_p, _p]),
     ("uh_block_apply_noalloc", [_i64, _i64, _i32, _i32, _p, _i64, _p, _i64, _p, _i64, _p, _p, _i32, _p]),
 ]:
     getattr(lib, _name).argtypes = _args
@@ -199,7 +204,7 @@ def _stream_handle(stream):
 
 
 class _Op:
-    _create = _destroy = _matvec = _matmat = _stats = _reserve = None
+    _create = _destroy = _matvec = _matmat = _stats = _reserve = _check = None
 
     def __init__(self, desc, precision: str = "c64"):
         self.precision = precision
@@ -254,6 +259,10 @@ class _Op:
                            _stream_handle(stream)), "matmat")
         return Y
 
+    def check(self, stream=None):
+        """Synchronise the stream; raise UHError (UH_ETIMEOUT) if a device-side wait ran out."""
+        check(self._check(self.handle, _stream_handle(stream)), "check")
+
     def reserve(self, max_nrhs: int):
         check(self._reserve(self.handle, max_nrhs), "reserve")
 
@@ -296,6 +305,7 @@ class UHOp(_Op):
     _matmat = lib.uh_matmat
     _stats = lib.uh_stats
     _reserve = lib.uh_reserve
+    _check = lib.uh_check
 
     @classmethod
     def from_arrays(cls, arrays: dict, precision: str = "c64"):
@@ -311,6 +321,7 @@ class HOp(_Op):
     _matmat = lib.h_matmat
     _stats = lib.h_stats
     _reserve = lib.h_reserve
+    _check = lib.h_check
 
     @classmethod
     def from_arrays(cls, arrays: dict, precision: str = "c64"):

@@ -104,26 +104,18 @@ def test_null_arguments(uh):
     assert uh.lib.uh_matvec(None, None, None, None) == uh.UH_EINVAL
 
 
-def _create_rc(uh, fn, desc, prec):
-    h = C.c_void_p()
-    rc = fn(C.byref(desc), prec, C.byref(h))
-    return rc, uh.lib.uh_last_error().decode(), h
-
-
 @pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("ncta", [152, 148, 7, 1])
 @pytest.mark.parametrize("case", [(2048, 4.0, 32, 1e-6), (1000, 6.0, 24, 1e-5), (97, 3.0, 16, 1e-6),
                                   (40, 3.0, 64, 1e-6)])
-def test_packing_self_check_passes(uh, prec, case):
-    """Without a GPU, uh_create/h_create get through validation, packing and the packer's
-    self-check of every kernel address, and stop at the first CUDA call."""
-    import torch
-    if torch.cuda.is_available():
-        pytest.skip("a GPU is present: creation succeeds instead")
+def test_packing_self_check_passes(uh, prec, ncta, case):
+    """Validation, packing and the packer's check of every kernel address, for several CTA
+    counts, without a GPU (uh_debug.h)."""
     n, k, leaf, eps = case
     axes, noise = ((1.0, 0.7, 0.4), 0.01) if n == 1000 else ((1.0, 1.0, 1.0), 0.0)
     _, _, hf, h, op = oracle_ops(n, k, leaf, 1.0, eps, 1e-8, axes, noise)
-    for mk, fn, arr in ((uh.uh_desc_from_arrays, uh.lib.uh_create, uh_arrays(op)),
-                        (uh.h_desc_from_arrays, uh.lib.h_create, h_arrays(h))):
+    for mk, fn, arr in ((uh.uh_desc_from_arrays, uh.lib.uh_pack_check, uh_arrays(op)),
+                        (uh.h_desc_from_arrays, uh.lib.h_pack_check, h_arrays(h))):
         desc, keep = mk(arr)
-        rc, msg, hd = _create_rc(uh, fn, desc, prec)
-        assert rc == uh.UH_ECUDA and "cudaGetDevice" in msg, msg
+        rc = fn(C.byref(desc), prec, ncta)
+        assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()

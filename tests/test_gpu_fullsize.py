@@ -39,7 +39,7 @@ def _gpu(op, x, dt):
     xt = torch.from_numpy(x).to("cuda", dt)
     y = torch.full_like(xt, complex(float("nan"), float("nan")))
     op.matvec(xt, y)
-    torch.cuda.synchronize()
+    op.check()
     return y.cpu().numpy().astype(np.complex128)
 
 

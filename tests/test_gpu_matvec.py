@@ -30,7 +30,7 @@ def _run(op, x, torch):
     xt = torch.from_numpy(x).to("cuda", torch.complex128 if op.c128 else torch.complex64)
     y = torch.full_like(xt, complex(float("nan"), float("nan")))  # poisoned output
     op.matvec(xt, y)
-    torch.cuda.synchronize()
+    op.check()  # raises if a bounded device-side wait ran out
     return y.cpu().numpy().astype(np.complex128)
 
 
@@ -148,3 +148,22 @@ def test_c64_storage_input(U):
     op = U.UHOp.from_arrays(a, "c64")
     x = I.complex_normal(tree.n, 0)
     _check(_run(op, x, torch), O.uh_matvec(uh, x), TOL["c64"])
+
+
+def test_bounded_wait_runs_out_and_recovers(U):
+    """A product whose dependency waits look for an epoch nobody publishes: every such wait runs
+    out after ~1 ms of SM cycles, the kernel returns, uh_check reports UH_ETIMEOUT, and the next
+    ordinary product is exact (the context stays usable)."""
+    import torch
+    pts, tree, hf, h, uh = oracle_ops(*WORKLOADS["sphere2048"])
+    op = U.UHOp.from_arrays(uh_arrays(uh), "c128")
+    x = I.complex_normal(tree.n, 0)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    s = torch.cuda.current_stream().cuda_stream
+    assert U.lib.uh_debug_stalled_matvec(op.handle, xt.data_ptr(), y.data_ptr(), 2_000_000, s) == U.UH_OK
+    with pytest.raises(U.UHError) as e:
+        op.check()
+    assert e.value.code == U.UH_ETIMEOUT
+    op.check()  # status cleared
+    _check(_run(op, x, torch), O.uh_matvec(uh, x), 1e-12)
