@@ -122,7 +122,6 @@ template <typename R>
 __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* smem) {
   using T = typename Cx<R>::T;
   unsigned char* stages = smem;
-  WorkItem* slots = reinterpret_cast<WorkItem*>(smem + kSmemSlots);
   WorkItem* ring = reinterpret_cast<WorkItem*>(smem + kSmemDesc);
   const Bars bar = bars_of(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
@@ -137,7 +136,7 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
     bulk_g2s(ring + q * kDescBatch, p.items + i0 + first, static_cast<uint32_t>(cnt * sizeof(WorkItem)),
              &bar.desc[q]);
   };
-  for (int b = 0; b < kDescBatches; ++b) issue_batch(b);
+  for (int b = 0; b < kDescBatches; ++b) issue_batch(b);  // batches 0 .. kDescBatches-1
   int seq = 0;
   bool ok = true;
   uint32_t ready = 0;  // groups known complete in this call
@@ -157,13 +156,12 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
       ok = false;
       break;
     }
-    const WorkItem& d = ring[(batch % kDescBatches) * kDescBatch + seq % kDescBatch];
-    slots[s] = d;
-    const WorkItem& it = slots[s];
-    if (seq % kDescBatch == kDescBatch - 1) {
-      // this batch's descriptors are copied out; refill its ring slots
+    const WorkItem& it = ring[seq % kDescRing];
+    if (seq % kDescBatch == kDescBatch - 1 && batch >= 1) {
+      // The consumers have finished item seq - kStages (we waited for its stage), so they are
+      // past batch - 1: refill its ring slots with the batch kDescBatches further on.
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_batch(batch + kDescBatches);
+      issue_batch(batch - 1 + kDescBatches);
     }
     unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
     const uint32_t tile_bytes = static_cast<uint32_t>(it.ncols) * static_cast<uint32_t>(it.hp) * sizeof(T);
@@ -224,7 +222,7 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
   const int tid = threadIdx.x;
   unsigned char* stages = smem;
   T* sred = reinterpret_cast<T*>(smem + kSmemRed);
-  const WorkItem* slots = reinterpret_cast<const WorkItem*>(smem + kSmemSlots);
+  const WorkItem* ring = reinterpret_cast<const WorkItem*>(smem + kSmemDesc);
   const Bars bar = bars_of(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
   volatile int* go = abort_flag + 1;  // go[0], go[1]: leader's decision, by item parity
@@ -246,7 +244,7 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
     consumer_sync();
     if (!go[seq & 1]) break;
     mbar_try_wait(&bar.full[s], parity);  // completed phase: each thread's own acquire
-    const WorkItem& sl = slots[s];
+    const WorkItem& sl = ring[seq % kDescRing];
     const int flags = sl.flags;
     const int hp = sl.hp, nc = sl.ncols;
     const int kind = sl.kind, h = sl.h, counter = sl.counter, base_off = sl.base_off;
@@ -299,7 +297,6 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
     if ((tid & 31) == 0) mbar_arrive(&bar.empty[s]);
     if (flags & kItemLast) {
       if (kind == kPermute) {
-        __threadfence();
         consumer_sync();
       } else {
 #pragma unroll
@@ -324,12 +321,16 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
           } else {
             T* z = static_cast<T*>(kind == kToZ1 ? p.z1 : kind == kToZ2 ? p.z2 : p.z3);
             z[dst + tid] = v;
-            if (counter >= 0) __threadfence();  // other CTAs read it after the counter
           }
         }
         consumer_sync();  // outputs written; sred free for the next chunk
       }
-      if (tid == 0 && counter >= 0) red_release_add(p.group_done + counter, 1ull);
+      // One fence after the barrier publishes every consumer's outputs of this chunk before the
+      // counter that other CTAs wait on.
+      if (tid == 0 && counter >= 0) {
+        __threadfence();
+        red_release_add(p.group_done + counter, 1ull);
+      }
     }
   }
 }

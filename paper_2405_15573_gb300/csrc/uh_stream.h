@@ -34,14 +34,16 @@ constexpr int kMaxRuns = 6;
 constexpr int kStreamHpMax = 64;
 
 // Work-item descriptors are streamed into a ring of kDescRing entries, kDescBatch per copy.
+// The consumers read the descriptors in the ring; a batch is refilled only after the producer
+// has issued the whole next batch, when the consumers (at most kStages items behind) are past it.
 constexpr int kDescBatch = 8;
-constexpr int kDescBatches = 4;
+constexpr int kDescBatches = 8;
 constexpr int kDescRing = kDescBatch * kDescBatches;
+static_assert(kStages < kDescBatch, "consumers must be past a batch when it is refilled");
 
 // Shared-memory layout of the kernel (bytes).
 constexpr int kSmemRed = kStages * kStageBytes;                  // group reduction, 256 x 16 B
-constexpr int kSmemSlots = kSmemRed + 256 * 16;                  // per-stage copy of the item, 96 B each
-constexpr int kSmemDesc = kSmemSlots + kStages * 96;             // descriptor ring, 96 B each
+constexpr int kSmemDesc = kSmemRed + 256 * 16;                   // descriptor ring, 96 B each
 constexpr int kSmemBars = kSmemDesc + kDescRing * 96;            // full, empty [kStages], desc [kDescBatches]
 constexpr int kSmemMisc = kSmemBars + (2 * kStages + kDescBatches) * 8;  // abort flag, decision words
 constexpr int kStreamSmemBytes = kSmemMisc + 32;
