@@ -105,8 +105,11 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
   out.back().flags |= kItemLast;
   bytes_[chunk] += kChunkCost;
   if (base_chunk >= 0) {
+    for (WorkItem& it : out) {
+      it.flags |= kItemBaseAll;
+      it.base_off = static_cast<int32_t>(chunks[base_chunk].dst);
+    }
     out.back().flags |= kItemBase;
-    out.back().base_off = static_cast<int32_t>(chunks[base_chunk].dst);
     base_of_[chunk] = base_chunk;
   }
 }
@@ -217,6 +220,7 @@ const char* ProgramBuilder::self_check() const {
       const int dep_group[kNumCounters] = {kGroupPermute, kGroupForward, kGroupCoupling};
       for (int g = 0; g < kNumCounters; ++g)
         if (((deps >> g) & 1u) && dep_group[g] >= group_[it.chunk]) return "item waits on a later group";
+      if (((it.flags & kItemBaseAll) != 0) != (base_of_[it.chunk] >= 0)) return "base flag on the wrong chunk";
       if (it.flags & kItemBase) {
         if (!(it.flags & kItemLast)) return "base on an item that does not end its chunk";
         const int bc = base_of_[it.chunk];

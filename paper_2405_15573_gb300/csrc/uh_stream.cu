@@ -81,6 +81,13 @@ __device__ __forceinline__ void cfma(double2& a, double2 m, double2 v) {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
+__device__ __forceinline__ float2 shfl_xor(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ __forceinline__ double2 shfl_xor(double2 v, int m) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
 __device__ __forceinline__ void lds16(const float2* p, float2 (&m)[2]) {
   const float4 q = *reinterpret_cast<const float4*>(p);
   m[0] = make_float2(q.x, q.y);
@@ -229,7 +236,9 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
   const int n = i1 - i0;
 
   T acc[EPL];
+  T base = T{0, 0};
   int need = 1, lanes = 1, groups = kStreamConsumers, lane = 0, g = tid, hpl = EPL;
+  const int warp = tid >> 5;
   for (int seq = 0; seq < n; ++seq) {
     const int s = seq % kStages;
     const uint32_t parity = static_cast<uint32_t>(seq / kStages) & 1u;
@@ -250,6 +259,11 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
     const int kind = sl.kind, h = sl.h, counter = sl.counter, base_off = sl.base_off;
     const int64_t dst = sl.dst;
     const unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
+    if ((flags & kItemFirst) && (flags & kItemBaseAll) && tid < h) {
+      // near-field partial of this row tile, written earlier by this same thread; loaded now,
+      // added at the end of the chunk
+      base = static_cast<const T*>(p.z3)[base_off + tid];
+    }
     if (flags & kItemFirst) {
       need = hp / EPL;
       lanes = 1;
@@ -299,23 +313,24 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
       if (kind == kPermute) {
         consumer_sync();
       } else {
+        // Column groups in one warp (lanes < 32: groups g and g ^ (m / lanes) share a warp):
+        // butterfly over the group bits of the lane index, fixed order.
+        for (int m = lanes; m < 32; m <<= 1) {
 #pragma unroll
-        for (int e = 0; e < EPL; ++e) sred[g * hpl + lane * EPL + e] = acc[e];
-        consumer_sync();
-        for (int h2 = groups >> 1; h2 >= 1; h2 >>= 1) {
-          if (g < h2) {
-#pragma unroll
-            for (int e = 0; e < EPL; ++e) {
-              const int q = g * hpl + lane * EPL + e;
-              sred[q] = cadd(sred[q], sred[q + h2 * hpl]);
-            }
-          }
-          consumer_sync();
+          for (int e = 0; e < EPL; ++e) acc[e] = cadd(acc[e], shfl_xor(acc[e], m));
         }
+        // One partial per warp (lanes <= 32) or per group (lanes >= 32): at most 8 of them.
+        const int parts = lanes < 32 ? kStreamConsumerWarps : groups;
+        const int part = lanes < 32 ? warp : g;
+        if (lanes >= 32 || (tid & 31) < lanes) {
+#pragma unroll
+          for (int e = 0; e < EPL; ++e) sred[part * hpl + lane * EPL + e] = acc[e];
+        }
+        consumer_sync();
         if (tid < h) {
           T v = sred[tid];
-          // near-field partial of this row tile, written earlier by this same thread
-          if (flags & kItemBase) v = cadd(v, static_cast<const T*>(p.z3)[base_off + tid]);
+          for (int q = 1; q < parts; ++q) v = cadd(v, sred[q * hpl + tid]);
+          if (flags & kItemBase) v = cadd(v, base);
           if (kind == kToY) {
             static_cast<T*>(p.y)[p.perm[dst + tid]] = v;
           } else {
@@ -325,12 +340,9 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
         }
         consumer_sync();  // outputs written; sred free for the next chunk
       }
-      // One fence after the barrier publishes every consumer's outputs of this chunk before the
-      // counter that other CTAs wait on.
-      if (tid == 0 && counter >= 0) {
-        __threadfence();
-        red_release_add(p.group_done + counter, 1ull);
-      }
+      // The barrier above orders every consumer's outputs of this chunk before thread 0's
+      // release add, which publishes them to the CTAs that acquire the counter.
+      if (tid == 0 && counter >= 0) red_release_add(p.group_done + counter, 1ull);
     }
   }
 }

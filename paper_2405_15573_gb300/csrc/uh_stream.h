@@ -61,7 +61,7 @@ static_assert(sizeof(Run) == 8, "Run layout");
 
 // Item flags: chunk boundaries, near-field base, and the groups whose completion the item's runs
 // need (bits kDepShift + counter index).
-enum : int16_t { kItemFirst = 1, kItemLast = 2, kItemBase = 4 };
+enum : int16_t { kItemFirst = 1, kItemLast = 2, kItemBase = 4, kItemBaseAll = 8 };
 constexpr int kDepShift = 8;
 enum : int { kCounterPermute = 0, kCounterForward = 1, kCounterCoupling = 2, kNumCounters = 3 };
 
@@ -80,7 +80,8 @@ struct alignas(16) WorkItem {
   int16_t counter;   // the chunk's group counter, or -1
   int16_t nruns;
   int16_t flags;     // kItem* | dependency bits
-  int32_t base_off;  // kItemBase: the chunk adds z3[base_off + r] to output r
+  int32_t base_off;  // kItemBaseAll (every item of such a chunk), kItemBase (its last item): the
+                     // chunk adds z3[base_off + r] to output r
   int32_t chunk;     // chunk number (host bookkeeping)
   int32_t pad;
   Run runs[kMaxRuns];
