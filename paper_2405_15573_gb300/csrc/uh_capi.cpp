@@ -195,6 +195,7 @@ struct OpBase {
   uh::WorkItem* d_items = nullptr;
   int32_t* d_cta = nullptr;
   unsigned long long* d_done = nullptr;  // group counters
+  uh::Scatter* d_scatter = nullptr;
   int64_t counter_total[uh::kNumCounters] = {0, 0, 0};
   uint32_t* d_status = nullptr;
   int32_t* d_perm = nullptr;
@@ -207,7 +208,7 @@ struct OpBase {
 
 void free_op(OpBase* o) {
   if (!o) return;
-  void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_status,
+  void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_scatter, o->d_status,
                   o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -257,6 +258,7 @@ int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T) {
   }
   if ((rc = upload(P.items.data(), P.items.size() * sizeof(uh::WorkItem), &o->d_items))) return rc;
   if ((rc = upload(P.cta_begin.data(), P.cta_begin.size() * sizeof(int32_t), &o->d_cta))) return rc;
+  if ((rc = upload(P.scatter.data(), P.scatter.size() * sizeof(uh::Scatter), &o->d_scatter))) return rc;
   if ((rc = upload(static_cast<const void*>(nullptr), uh::kNumCounters * sizeof(unsigned long long), &o->d_done)))
     return rc;
   for (int c = 0; c < uh::kNumCounters; ++c) o->counter_total[c] = P.counter_total(c);
@@ -296,6 +298,7 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   p.x = x;
   p.y = y;
   p.perm = o->d_perm;
+  p.scatter = o->d_scatter;
   p.xp = o->d_xp;
   p.z1 = o->d_z1;
   p.z2 = o->d_z2;
@@ -460,61 +463,100 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   P.set_source_len(uh::kSrcXp, ProgramBuilder::round_up(T.n, A));
   add_permute(P, T.n, ncta);
 
-  // xhat / yhat segments, 16-byte aligned, clusters in increasing number.
-  std::vector<int64_t> xoff(T.ncl, -1), yoff(T.ncl, -1);
-  int64_t nx = 0, ny = 0;
+  // Blocks by row cluster (sorted by column cluster) and by column cluster (sorted by row).
+  std::vector<std::vector<int64_t>> row_blocks(T.ncl), col_blocks(T.ncl);
+  for (int64_t i = 0; i < d->n_adm; ++i) {
+    row_blocks[d->adm_row[i]].push_back(i);
+    col_blocks[d->adm_col[i]].push_back(i);
+  }
   for (int32_t c = 0; c < T.ncl; ++c) {
-    if (is_col[c] && d->col_rank[c] > 0) { xoff[c] = nx; nx += ProgramBuilder::round_up(d->col_rank[c], A); }
-    if (is_row[c] && d->row_rank[c] > 0) { yoff[c] = ny; ny += ProgramBuilder::round_up(d->row_rank[c], A); }
+    std::stable_sort(row_blocks[c].begin(), row_blocks[c].end(),
+                     [&](int64_t a, int64_t b) { return d->adm_col[a] < d->adm_col[b]; });
+    std::stable_sort(col_blocks[c].begin(), col_blocks[c].end(),
+                     [&](int64_t a, int64_t b) { return d->adm_row[a] < d->adm_row[b]; });
+  }
+  auto live = [&](int64_t b) { return d->row_rank[d->adm_row[b]] > 0 && d->col_rank[d->adm_col[b]] > 0; };
+  // z1: per row cluster tau, the coupling inputs [xhat_sigma]_{sigma in row(tau)} back to back
+  // (the forward chunks scatter each xhat_sigma into every segment that uses it).
+  std::vector<int64_t> xin(T.ncl, -1), xpos(d->n_adm, -1);
+  int64_t nx = 0;
+  for (int32_t t = 0; t < T.ncl; ++t) {
+    if (!is_row[t] || d->row_rank[t] == 0) continue;
+    xin[t] = nx;
+    int64_t pos = 0;
+    for (int64_t b : row_blocks[t])
+      if (live(b)) { xpos[b] = pos; pos += d->col_rank[d->adm_col[b]]; }
+    nx += ProgramBuilder::round_up(std::max<int64_t>(pos, 1), A);
   }
   P.set_source_len(uh::kSrcZ1, nx);
+  // Row tiles and the row clusters with a basis that contain them.
+  std::vector<std::vector<int32_t>> tile_rows(tiles.size());
+  for (int32_t t = 0; t < T.ncl; ++t)
+    if (is_row[t] && d->row_rank[t] > 0)
+      for_tiles(tiles, T.begin[t], T.begin[t] + T.size[t], [&](size_t i) { tile_rows[i].push_back(t); });
+  std::vector<char> has_back(tiles.size(), 0);
+  // z2: per row tile, the backward inputs [yhat_tau]_{tau contains the tile} back to back (the
+  // coupling chunks scatter each yhat_tau into every tile inside tau).
+  std::vector<int64_t> yin(tiles.size(), -1);
+  std::vector<std::vector<int64_t>> ypos(tiles.size());
+  int64_t ny = 0;
+  for (size_t i = 0; i < tiles.size(); ++i) {
+    has_back[i] = !tile_rows[i].empty();
+    if (!has_back[i]) continue;
+    yin[i] = ny;
+    int64_t pos = 0;
+    for (int32_t t : tile_rows[i]) { ypos[i].push_back(pos); pos += d->row_rank[t]; }
+    ny += ProgramBuilder::round_up(pos, A);
+  }
   P.set_source_len(uh::kSrcZ2, ny);
 
-  // Forward transform: chunks of at most 64 rows of V_sigma^*; column r = conj(V_sigma[r, rows]).
   const Src V{d->V_data, d->data_type}, S{d->S_data, d->data_type}, U{d->U_data, d->data_type};
   const Src D{d->dense.data, d->data_type};
+  // Forward transform: chunks of at most 64 rows of V_sigma^*; column r = conj(V_sigma[r, rows]).
   for (int32_t s = 0; s < T.ncl; ++s) {
-    if (xoff[s] < 0) continue;
+    if (!is_col[s] || d->col_rank[s] == 0) continue;
+    std::vector<int64_t> users;
+    for (int64_t b : col_blocks[s])
+      if (live(b)) users.push_back(b);
+    if (users.empty()) continue;
     const int32_t l = d->col_rank[s];
     const int64_t m = T.size[s];
     const int k = (l + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
     for (int q = 0; q < k; ++q) {
       const int j0 = l * q / k, j1 = l * (q + 1) / k;
-      const int c = P.add_chunk(uh::kToZ1, xoff[s] + j0, j1 - j0, uh::kGroupForward, uh::kCounterForward);
+      const int c = P.add_chunk(uh::kScatterZ1, 0, j1 - j0, uh::kGroupForward, uh::kCounterForward);
+      for (int64_t b : users) P.add_scatter(c, xin[d->adm_row[b]] + xpos[b] + j0, 0, j1 - j0);
       P.add_columns(c, {ColSpec{uh::kSrcXp, T.begin[s], m, &V, true, d->col_off[s] + j0 * m, 1, m}});
     }
   }
-  // Which row tiles have a backward part.
-  std::vector<std::vector<int32_t>> tile_rows(tiles.size());
-  for (int32_t t = 0; t < T.ncl; ++t)
-    if (yoff[t] >= 0) for_tiles(tiles, T.begin[t], T.begin[t] + T.size[t], [&](size_t i) { tile_rows[i].push_back(t); });
-  std::vector<char> has_back(tiles.size(), 0);
-  for (size_t i = 0; i < tiles.size(); ++i) has_back[i] = !tile_rows[i].empty();
   std::vector<char> has_near;
   const std::vector<int> zchunk = add_near_field(P, T, d->dense, D, tiles, has_back, &has_near);
-  // Coupling: per row cluster tau (chunks of at most 64 rows), columns [S_b]_{sigma in row(tau)}.
-  std::vector<std::vector<int64_t>> row_blocks(T.ncl);
-  for (int64_t i = 0; i < d->n_adm; ++i) row_blocks[d->adm_row[i]].push_back(i);
+  // Coupling: per row cluster tau (chunks of at most 64 rows), columns [S_b]_{sigma in row(tau)},
+  // inputs one run of z1; outputs scattered to the tiles inside tau.
   std::vector<ColSpec> cols;
   for (int32_t t = 0; t < T.ncl; ++t) {
-    if (yoff[t] < 0) continue;
-    auto& bl = row_blocks[t];
-    std::stable_sort(bl.begin(), bl.end(), [&](int64_t a, int64_t b) { return d->adm_col[a] < d->adm_col[b]; });
+    if (!is_row[t] || d->row_rank[t] == 0) continue;
     const int32_t l = d->row_rank[t];
     const int k = (l + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
     for (int q = 0; q < k; ++q) {
       const int i0 = l * q / k, i1 = l * (q + 1) / k;
-      const int c = P.add_chunk(uh::kToZ2, yoff[t] + i0, i1 - i0, uh::kGroupCoupling, uh::kCounterCoupling);
+      const int c = P.add_chunk(uh::kScatterZ2, 0, i1 - i0, uh::kGroupCoupling, uh::kCounterCoupling);
+      for_tiles(tiles, T.begin[t], T.begin[t] + T.size[t], [&](size_t ti) {
+        const auto& tr = tile_rows[ti];
+        const size_t w = std::find(tr.begin(), tr.end(), t) - tr.begin();
+        P.add_scatter(c, yin[ti] + ypos[ti][w] + i0, 0, i1 - i0);
+      });
       cols.clear();
-      for (int64_t b : bl) {
+      for (int64_t b : row_blocks[t]) {
+        if (!live(b)) continue;
         const int32_t s = d->adm_col[b];
-        if (xoff[s] < 0) continue;
-        cols.push_back(ColSpec{uh::kSrcZ1, xoff[s], d->col_rank[s], &S, false, d->S_off[b] + i0, l, 1});
+        cols.push_back(ColSpec{uh::kSrcZ1, xin[t] + xpos[b], d->col_rank[s], &S, false, d->S_off[b] + i0, l, 1});
       }
       P.add_columns(c, cols);
     }
   }
-  // Backward transform (+ near-field base): per row tile, columns U_tau[tile rows, :].
+  // Backward transform (+ near-field base): per row tile, columns U_tau[tile rows, :] of every
+  // row cluster tau containing the tile, inputs one run of z2.
   for (size_t ti = 0; ti < tiles.size(); ++ti) {
     if (!has_back[ti]) {
       // the near-field chunk writes y; a tile whose blocks all have rank 0 and no near field
@@ -524,9 +566,11 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
     }
     const int c = P.add_chunk(uh::kToY, tiles[ti].p0, tiles[ti].h, uh::kGroupBackward);
     cols.clear();
-    for (int32_t t : tile_rows[ti]) {
+    for (size_t w = 0; w < tile_rows[ti].size(); ++w) {
+      const int32_t t = tile_rows[ti][w];
       const int64_t m = T.size[t];
-      cols.push_back(ColSpec{uh::kSrcZ2, yoff[t], d->row_rank[t], &U, false, d->row_off[t] + tiles[ti].p0 - T.begin[t], m, 1});
+      cols.push_back(ColSpec{uh::kSrcZ2, yin[ti] + ypos[ti][w], d->row_rank[t], &U, false,
+                             d->row_off[t] + tiles[ti].p0 - T.begin[t], m, 1});
     }
     P.add_columns(c, cols, zchunk[ti]);
   }
@@ -644,23 +688,41 @@ int h_create(const h_desc* d, int32_t precision, h_op** out) {
   P.set_source_len(uh::kSrcXp, ProgramBuilder::round_up(T.n, A));
   P.set_source_len(uh::kSrcZ2, 0);
   add_permute(P, T.n, ncta);
-  // t_b = Y_b^* x|_sigma per admissible block, chunks of at most 64.
+  // t_b = Y_b^* x|_sigma. The blocks of one column cluster sigma share their input x|_sigma, so
+  // their rows Y_b^* are stacked (blocks in increasing row cluster) and cut into chunks of at most
+  // 64 rows; t holds each sigma's t_b consecutively.
   std::vector<int64_t> toff(d->n_adm, -1);
-  int64_t nt = 0;
+  std::vector<std::vector<int64_t>> col_blocks(T.ncl);
   for (int64_t b = 0; b < d->n_adm; ++b)
-    if (d->adm_rank[b] > 0) { toff[b] = nt; nt += ProgramBuilder::round_up(d->adm_rank[b], A); }
+    if (d->adm_rank[b] > 0) col_blocks[d->adm_col[b]].push_back(b);
+  int64_t nt = 0;
+  std::vector<int64_t> sbase(T.ncl, -1);
+  for (int32_t s = 0; s < T.ncl; ++s) {
+    auto& bl = col_blocks[s];
+    if (bl.empty()) continue;
+    std::stable_sort(bl.begin(), bl.end(), [&](int64_t a, int64_t b) { return d->adm_row[a] < d->adm_row[b]; });
+    sbase[s] = nt;
+    for (int64_t b : bl) { toff[b] = nt; nt += d->adm_rank[b]; }
+    nt = ProgramBuilder::round_up(nt, A);
+  }
   P.set_source_len(uh::kSrcZ1, nt);
   const Src Y{d->Y_data, d->data_type}, X{d->X_data, d->data_type}, D{d->dense.data, d->data_type};
-  for (int64_t b = 0; b < d->n_adm; ++b) {
-    if (toff[b] < 0) continue;
-    const int32_t k = d->adm_rank[b];
-    const int32_t s = d->adm_col[b];
+  std::vector<int64_t> rowoff;
+  for (int32_t s = 0; s < T.ncl; ++s) {
+    const auto& bl = col_blocks[s];
+    if (bl.empty()) continue;
     const int64_t m = T.size[s];
-    const int nq = (k + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
-    for (int q = 0; q < nq; ++q) {
-      const int j0 = k * q / nq, j1 = k * (q + 1) / nq;
-      const int c = P.add_chunk(uh::kToZ1, toff[b] + j0, j1 - j0, uh::kGroupForward, uh::kCounterForward);
-      P.add_columns(c, {ColSpec{uh::kSrcXp, T.begin[s], m, &Y, true, d->Y_off[b] + j0 * m, 1, m}});
+    rowoff.clear();  // row (b, j) of the stack: conj(Y_b[:, j]) starts at Y_off[b] + j * |sigma|
+    for (int64_t b : bl)
+      for (int j = 0; j < d->adm_rank[b]; ++j) rowoff.push_back(d->Y_off[b] + j * m);
+    const int64_t rows = static_cast<int64_t>(rowoff.size());
+    const int64_t nq = (rows + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
+    for (int64_t q = 0; q < nq; ++q) {
+      const int64_t r0 = rows * q / nq, r1 = rows * (q + 1) / nq;
+      const int c = P.add_chunk(uh::kToZ1, sbase[s] + r0, static_cast<int>(r1 - r0), uh::kGroupForward, uh::kCounterForward);
+      ColSpec cs{uh::kSrcXp, T.begin[s], m, &Y, true, 0, 1, 0};
+      cs.rowoff = rowoff.data() + r0;
+      P.add_columns(c, {cs});
     }
   }
   std::vector<std::vector<int64_t>> tile_blocks(tiles.size());

@@ -27,10 +27,11 @@ int ProgramBuilder::add_chunk(int kind, int64_t dst, int h, int group, int count
 }
 
 namespace {
-// Scheduling costs of an item and of a chunk end, in bytes streamed in the same time (measured
-// on GB300: ~0.1 us per item and ~1 us per chunk end at ~45 GB/s per SM).
+// Scheduling costs of an item and of a chunk end, in bytes streamed in the same time (GB300
+// traces: a CTA streams ~45 GB/s; consumers spend ~0.1 us of fixed cost per item beyond the
+// streaming and ~1 us per chunk end).
 constexpr int64_t kItemCost = 4096;
-constexpr int64_t kChunkCost = 40960;
+constexpr int64_t kChunkCost = 49152;
 int counter_of_source(int src) {
   return src == kSrcXp ? kCounterPermute : src == kSrcZ1 ? kCounterForward : src == kSrcZ2 ? kCounterCoupling : -1;
 }
@@ -39,7 +40,8 @@ int counter_of_source(int src) {
 void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, int base_chunk) {
   const int h = chunks[chunk].h;
   const int64_t hp = chunks[chunk].kind == kPermute ? A_ : std::max<int64_t>(A_, round_up(h, A_));
-  int64_t maxcols = std::min<int64_t>(kStreamMaxCols, kTileBytes / (hp * eb_));
+  // an item's tile (hp x ncols) and its inputs (ncols) share one stage buffer
+  int64_t maxcols = std::min<int64_t>(kStreamMaxCols, std::min<int64_t>(kTileBytes / (hp * eb_), kStageBytes / ((hp + 1) * eb_)));
   maxcols = maxcols / A_ * A_;
   auto& out = chunk_items_[chunk];
   WorkItem cur{};
@@ -59,10 +61,23 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
     input_bytes_total += static_cast<int64_t>(cur.ncols) * eb_;
     open = false;
   };
-  for (const ColSpec& cs : cols) {
-    if (cs.len <= 0) continue;
-    const int64_t a = cs.start / A_ * A_;
-    const int64_t b = round_up(cs.start + cs.len, A_);
+  // Consecutive specs that continue each other in the same input vector form one run (one copy),
+  // padded to 16 bytes only at its two ends.
+  size_t k0 = 0;
+  while (k0 < cols.size()) {
+    if (cols[k0].len <= 0) {
+      ++k0;
+      continue;
+    }
+    size_t k1 = k0 + 1;
+    while (k1 < cols.size() && cols[k1].len > 0 && cols[k1].src == cols[k0].src &&
+           cols[k1].start == cols[k1 - 1].start + cols[k1 - 1].len)
+      ++k1;
+    const int src = cols[k0].src;
+    const int64_t lo = cols[k0].start, hi = cols[k1 - 1].start + cols[k1 - 1].len;
+    const int64_t a = lo / A_ * A_;
+    const int64_t b = round_up(hi, A_);
+    size_t spec = k0;  // spec holding the current position
     int64_t p = a;
     while (p < b) {
       if (!open) start_item();
@@ -75,26 +90,29 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
       Run run{};
       run.start = static_cast<int32_t>(p);
       run.len = static_cast<int16_t>(take);
-      run.src = static_cast<int8_t>(cs.src);
+      run.src = static_cast<int8_t>(src);
       cur.runs[cur.nruns++] = run;
-      const int ctr = counter_of_source(cs.src);
+      const int ctr = counter_of_source(src);
       if (ctr >= 0) cur.flags |= static_cast<int16_t>(1 << (kDepShift + ctr));
       // tile columns for input positions p .. p + take - 1
       const size_t base = M.size();
       M.resize(base + static_cast<size_t>(take * hp), cd(0, 0));
       for (int64_t q = 0; q < take; ++q) {
         const int64_t pos = p + q;
-        if (pos < cs.start || pos >= cs.start + cs.len) continue;  // alignment padding column
+        if (pos < lo || pos >= hi) continue;  // alignment padding column
+        while (pos >= cols[spec].start + cols[spec].len) ++spec;
+        const ColSpec& cs = cols[spec];
         cd* col = M.data() + base + static_cast<size_t>(q * hp);
-        const int64_t o = cs.off + (pos - cs.start) * cs.colstep;
+        const int64_t q0 = (pos - cs.start) * cs.colstep;
         for (int i = 0; i < h; ++i) {
-          const cd v = cs.mat->at(o + i * cs.rowstep);
+          const cd v = cs.mat->at(cs.rowoff ? cs.rowoff[i] + q0 : cs.off + q0 + i * cs.rowstep);
           col[i] = cs.conj ? std::conj(v) : v;
         }
       }
       cur.ncols += static_cast<int32_t>(take);
       p += take;
     }
+    k0 = k1;
   }
   close_item();
   if (out.empty()) {  // no columns: one empty item writes zeros (or, for a permutation slice, runs it)
@@ -107,11 +125,22 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
   if (base_chunk >= 0) {
     for (WorkItem& it : out) {
       it.flags |= kItemBaseAll;
-      it.base_off = static_cast<int32_t>(chunks[base_chunk].dst);
+      it.aux = static_cast<int32_t>(chunks[base_chunk].dst);
     }
     out.back().flags |= kItemBase;
     base_of_[chunk] = base_chunk;
   }
+}
+
+void ProgramBuilder::add_scatter(int chunk, int64_t dst, int lo, int hi) {
+  OutChunk& c = chunks[chunk];
+  if (c.nscat == 0) c.scat0 = static_cast<int32_t>(scatter.size());
+  Scatter e{};
+  e.dst = static_cast<int32_t>(dst);
+  e.lo = static_cast<int16_t>(lo);
+  e.hi = static_cast<int16_t>(hi);
+  scatter.push_back(e);
+  c.nscat++;
 }
 
 const char* ProgramBuilder::finalize() {
@@ -163,6 +192,10 @@ const char* ProgramBuilder::finalize() {
         it.h = chunks[c].h;
         it.kind = chunks[c].kind;
         it.counter = chunks[c].counter;
+        if (chunks[c].kind == kScatterZ1 || chunks[c].kind == kScatterZ2) {
+          it.aux = chunks[c].scat0;
+          it.naux = chunks[c].nscat;
+        }
         items.push_back(it);
       }
   }
@@ -188,6 +221,8 @@ const char* ProgramBuilder::self_check() const {
       const OutChunk& ch = chunks[it.chunk];
       if (it.dst != ch.dst || it.h != ch.h || it.kind != ch.kind || it.counter != ch.counter)
         return "item does not carry its chunk's output fields";
+      if ((ch.kind == kScatterZ1 || ch.kind == kScatterZ2) && (it.aux != ch.scat0 || it.naux != ch.nscat))
+        return "item does not carry its chunk's scatter list";
       // chunk items contiguous inside one CTA, first/last marks
       if (it.flags & kItemFirst) {
         if (open_chunk >= 0 || seen[it.chunk]) return "chunk items not contiguous";
@@ -199,7 +234,8 @@ const char* ProgramBuilder::self_check() const {
       if (it.hp < A_ || it.hp > kStreamHpMax || it.hp % A_ || (ch.kind != kPermute && it.hp < ch.h))
         return "item height";
       if (it.ncols < 0 || it.ncols > kStreamMaxCols ||
-          static_cast<int64_t>(it.ncols) * it.hp * eb_ > kTileBytes)
+          static_cast<int64_t>(it.ncols) * it.hp * eb_ > kTileBytes ||
+          static_cast<int64_t>(it.ncols) * (it.hp + 1) * eb_ > kStageBytes)
         return "item tile size";
       if (it.tile_off < 0 || (it.tile_off * eb_) % 16 || it.tile_off + static_cast<int64_t>(it.ncols) * it.hp > msize)
         return "item tile outside the packed buffer or misaligned";
@@ -225,9 +261,9 @@ const char* ProgramBuilder::self_check() const {
         if (!(it.flags & kItemLast)) return "base on an item that does not end its chunk";
         const int bc = base_of_[it.chunk];
         if (bc < 0 || cta_of_[bc] != b || cta_of_[it.chunk] != b || chunks[bc].kind != kToZ3 ||
-            chunks[bc].dst != it.base_off || chunks[bc].h != ch.h || !seen[bc] || group_[bc] >= group_[it.chunk])
+            chunks[bc].dst != it.aux || chunks[bc].h != ch.h || !seen[bc] || group_[bc] >= group_[it.chunk])
           return "near-field base not written earlier in the same CTA";
-        if (it.base_off < 0 || it.base_off + static_cast<int64_t>(ch.h) > src_len_[kSrcZ3]) return "base outside z3";
+        if (it.aux < 0 || it.aux + static_cast<int64_t>(ch.h) > src_len_[kSrcZ3]) return "base outside z3";
       }
     }
     if (open_chunk >= 0) return "chunk not closed in its CTA";
@@ -249,6 +285,18 @@ const char* ProgramBuilder::self_check() const {
       case kToY:
         if (ch.dst + ch.h > n_) return "chunk outside y";
         break;
+      case kScatterZ1:
+      case kScatterZ2: {
+        const int64_t len = src_len_[ch.kind == kScatterZ1 ? kSrcZ1 : kSrcZ2];
+        if (ch.nscat < 1 || ch.scat0 < 0 || ch.scat0 + static_cast<int64_t>(ch.nscat) > static_cast<int64_t>(scatter.size()))
+          return "scatter list";
+        for (int k = 0; k < ch.nscat; ++k) {
+          const Scatter& e = scatter[ch.scat0 + k];
+          if (e.lo < 0 || e.hi > ch.h || e.lo >= e.hi || e.dst < 0 || e.dst + static_cast<int64_t>(e.hi - e.lo) > len)
+            return "scatter entry outside its vector";
+        }
+        break;
+      }
       case kPermute:
         if (ch.dst + ch.h > n_ || ch.dst + ch.h > src_len_[kSrcXp]) return "permutation slice outside x";
         break;

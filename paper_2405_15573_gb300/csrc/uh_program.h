@@ -23,14 +23,15 @@ struct Src {
 };
 
 // Consecutive input positions [start, start + len) of vector `src`; tile column q (for input
-// position start + q) holds rows i = 0..h-1 of mat[off + q * colstep + i * rowstep] (conjugated
-// if conj).
+// position start + q) holds rows i = 0..h-1 of mat[off + q * colstep + i * rowstep], or, with a
+// row offset table, mat[rowoff[i] + q * colstep] (conjugated if conj).
 struct ColSpec {
   int src;
   int64_t start, len;
   const Src* mat;
   bool conj;
   int64_t off, colstep, rowstep;
+  const int64_t* rowoff = nullptr;
 };
 
 // Schedule groups, in the order every CTA runs them. Flags only point to earlier groups.
@@ -53,6 +54,9 @@ class ProgramBuilder {
   // (near-field, kToZ3) chunk, which is placed in the same CTA ahead of it.
   void add_columns(int chunk, const std::vector<ColSpec>& cols, int base_chunk = -1);
 
+  // Scatter kinds: outputs lo <= r < hi of `chunk` also go to z[dst + r - lo].
+  void add_scatter(int chunk, int64_t dst, int lo, int hi);
+
   // Assign chunks to CTAs (phase groups in order, longest processing time first within a group;
   // a chunk with a base goes to its base chunk's CTA) and lay the items out by CTA.
   const char* finalize();
@@ -66,6 +70,7 @@ class ProgramBuilder {
   std::vector<int32_t> cta_begin;     // ncta + 1
   std::vector<OutChunk> chunks;
   std::vector<cd> M;                  // packed tiles (converted to the element type at upload)
+  std::vector<Scatter> scatter;       // scatter entries
   int64_t src_len_[4] = {0, 0, 0, 0};
   int64_t tile_bytes_total = 0, input_bytes_total = 0;
 

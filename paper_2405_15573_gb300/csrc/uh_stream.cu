@@ -197,7 +197,7 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
     uint32_t col = 0;
     for (int r = 0; r < it.nruns; ++r) {
       const Run run = it.runs[r];
-      bulk_g2s(st + kTileBytes + col * sizeof(T), static_cast<const T*>(src_ptr(p, run.src)) + run.start,
+      bulk_g2s(st + tile_bytes + col * sizeof(T), static_cast<const T*>(src_ptr(p, run.src)) + run.start,
                static_cast<uint32_t>(run.len) * sizeof(T), &bar.full[s]);
       col += static_cast<uint32_t>(run.len);
     }
@@ -237,6 +237,9 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
 
   T acc[EPL];
   T base = T{0, 0};
+  int out_idx = 0;
+  Scatter* sscat = reinterpret_cast<Scatter*>(smem + kSmemScat);
+  T* svals = reinterpret_cast<T*>(smem + kSmemVals);
   int need = 1, lanes = 1, groups = kStreamConsumers, lane = 0, g = tid, hpl = EPL;
   const int warp = tid >> 5;
   for (int seq = 0; seq < n; ++seq) {
@@ -252,17 +255,23 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
     }
     consumer_sync();
     if (!go[seq & 1]) break;
-    mbar_try_wait(&bar.full[s], parity);  // completed phase: each thread's own acquire
+    // The leader's acquire of the full barrier, then the consumer barrier, order the stage's
+    // bulk-copied data before every consumer thread's reads.
     const WorkItem& sl = ring[seq % kDescRing];
     const int flags = sl.flags;
     const int hp = sl.hp, nc = sl.ncols;
-    const int kind = sl.kind, h = sl.h, counter = sl.counter, base_off = sl.base_off;
+    const int kind = sl.kind, h = sl.h, counter = sl.counter, aux = sl.aux, naux = sl.naux;
     const int64_t dst = sl.dst;
     const unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
-    if ((flags & kItemFirst) && (flags & kItemBaseAll) && tid < h) {
-      // near-field partial of this row tile, written earlier by this same thread; loaded now,
-      // added at the end of the chunk
-      base = static_cast<const T*>(p.z3)[base_off + tid];
+    if ((flags & kItemFirst) && (kind == kScatterZ1 || kind == kScatterZ2)) {
+      // the chunk's scatter entries, used at its end
+      for (int k = tid; k < naux && k < 256; k += kStreamConsumers) sscat[k] = p.scatter[aux + k];
+    }
+    if ((flags & kItemFirst) && tid < h) {
+      // near-field partial of this row tile, written earlier by this same thread, and the
+      // output's original index: loaded now, used at the end of the chunk
+      if (flags & kItemBaseAll) base = static_cast<const T*>(p.z3)[aux + tid];
+      if (kind == kToY) out_idx = p.perm[dst + tid];
     }
     if (flags & kItemFirst) {
       need = hp / EPL;
@@ -281,22 +290,19 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
       for (int r = tid; r < h; r += kStreamConsumers) xp[dst + r] = x[p.perm[dst + r]];
     } else if (lane < need) {
       const T* tile = reinterpret_cast<const T*>(st) + lane * EPL;
-      const T* vin = reinterpret_cast<const T*>(st + kTileBytes);
+      const T* vin = reinterpret_cast<const T*>(st) + static_cast<size_t>(nc) * hp;  // inputs after the tile
       int c = g;
-      for (; c + 3 * groups < nc; c += 4 * groups) {
-        T m0[EPL], m1[EPL], m2[EPL], m3[EPL];
-        lds16(tile + c * hp, m0);
-        lds16(tile + (c + groups) * hp, m1);
-        lds16(tile + (c + 2 * groups) * hp, m2);
-        lds16(tile + (c + 3 * groups) * hp, m3);
-        const T v0 = vin[c], v1 = vin[c + groups], v2 = vin[c + 2 * groups], v3 = vin[c + 3 * groups];
+      for (; c + 7 * groups < nc; c += 8 * groups) {
+        T m[8][EPL], v[8];
 #pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-          cfma(acc[e], m0[e], v0);
-          cfma(acc[e], m1[e], v1);
-          cfma(acc[e], m2[e], v2);
-          cfma(acc[e], m3[e], v3);
+        for (int u = 0; u < 8; ++u) {
+          lds16(tile + (c + u * groups) * hp, m[u]);
+          v[u] = vin[c + u * groups];
         }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int e = 0; e < EPL; ++e) cfma(acc[e], m[u][e], v[u]);
       }
       for (; c < nc; c += groups) {
         T m0[EPL];
@@ -332,13 +338,25 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
           for (int q = 1; q < parts; ++q) v = cadd(v, sred[q * hpl + tid]);
           if (flags & kItemBase) v = cadd(v, base);
           if (kind == kToY) {
-            static_cast<T*>(p.y)[p.perm[dst + tid]] = v;
+            static_cast<T*>(p.y)[out_idx] = v;
+          } else if (kind == kScatterZ1 || kind == kScatterZ2) {
+            svals[tid] = v;
           } else {
             T* z = static_cast<T*>(kind == kToZ1 ? p.z1 : kind == kToZ2 ? p.z2 : p.z3);
             z[dst + tid] = v;
           }
         }
         consumer_sync();  // outputs written; sred free for the next chunk
+        if (kind == kScatterZ1 || kind == kScatterZ2) {
+          // (entry, row) pairs over all consumer threads: each entry's rows are consecutive
+          T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : p.z2);
+          for (int w = tid; w < naux * h; w += kStreamConsumers) {
+            const int k = w / h, r = w - k * h;
+            const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];
+            if (r >= e.lo && r < e.hi) z[e.dst + r - e.lo] = svals[r];
+          }
+          consumer_sync();  // svals and sscat free for the next chunk
+        }
       }
       // The barrier above orders every consumer's outputs of this chunk before thread 0's
       // release add, which publishes them to the CTAs that acquire the counter.

@@ -25,11 +25,10 @@ namespace uh {
 constexpr int kStreamConsumerWarps = 8;
 constexpr int kStreamConsumers = kStreamConsumerWarps * 32;
 constexpr int kStreamThreads = kStreamConsumers + 32;  // + producer warp
-constexpr int kStages = 5;
-constexpr int kTileBytes = 32768;
-constexpr int kStreamMaxCols = 512;
-constexpr int kInBytes = kStreamMaxCols * 16;  // a stage's input area (512 complex128 values)
-constexpr int kStageBytes = kTileBytes + kInBytes;
+constexpr int kStages = 6;
+constexpr int kTileBytes = 32768;       // largest tile of an item
+constexpr int kStreamMaxCols = 512;     // largest column count of an item
+constexpr int kStageBytes = 34816;      // an item's tile and inputs (inputs at the tile's end)
 constexpr int kMaxRuns = 6;
 constexpr int kStreamHpMax = 64;
 
@@ -42,9 +41,11 @@ constexpr int kDescRing = kDescBatch * kDescBatches;
 static_assert(kStages < kDescBatch, "consumers must be past a batch when it is refilled");
 
 // Shared-memory layout of the kernel (bytes).
-constexpr int kSmemRed = kStages * kStageBytes;                  // group reduction, 256 x 16 B
-constexpr int kSmemDesc = kSmemRed + 256 * 16;                   // descriptor ring, 96 B each
-constexpr int kSmemBars = kSmemDesc + kDescRing * 96;            // full, empty [kStages], desc [kDescBatches]
+constexpr int kSmemRed = kStages * kStageBytes;                  // group reduction, one 16 B slot per consumer thread
+constexpr int kSmemDesc = kSmemRed + kStreamConsumers * 16;      // descriptor ring, 96 B each
+constexpr int kSmemScat = kSmemDesc + kDescRing * 96;            // scatter entries of the open chunk (256 x 8 B)
+constexpr int kSmemVals = kSmemScat + 256 * 8;                    // a chunk's outputs before they are scattered
+constexpr int kSmemBars = kSmemVals + 64 * 16;                    // full, empty [kStages], desc [kDescBatches]
 constexpr int kSmemMisc = kSmemBars + (2 * kStages + kDescBatches) * 8;  // abort flag, decision words
 constexpr int kStreamSmemBytes = kSmemMisc + 32;
 
@@ -66,9 +67,17 @@ constexpr int kDepShift = 8;
 enum : int { kCounterPermute = 0, kCounterForward = 1, kCounterCoupling = 2, kNumCounters = 3 };
 
 // Chunk outputs: kToZ1..kToZ3 write z[dst + r]; kToY writes y[perm[dst + r]]; kPermute fills
-// xp[dst + r] = x[perm[dst + r]] (no tile, no inputs). counter >= 0: the chunk's completion is
-// added to that group counter.
-enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kPermute = 4 };
+// xp[dst + r] = x[perm[dst + r]] (no tile, no inputs); kScatterZ1 / kScatterZ2 write output r to
+// z[e.dst + r - e.lo] for every scatter entry e with e.lo <= r < e.hi (the chunk's entries are
+// scatter[aux .. aux + naux)): each consumer chunk then finds its inputs in one contiguous run.
+// counter >= 0: the chunk's completion is added to that group counter.
+enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kPermute = 4, kScatterZ1 = 5, kScatterZ2 = 6 };
+
+struct Scatter {
+  int32_t dst;
+  int16_t lo, hi;
+};
+static_assert(sizeof(Scatter) == 8, "Scatter layout");
 
 struct alignas(16) WorkItem {
   int64_t tile_off;  // element offset of the tile in the packed matrix buffer
@@ -80,10 +89,10 @@ struct alignas(16) WorkItem {
   int16_t counter;   // the chunk's group counter, or -1
   int16_t nruns;
   int16_t flags;     // kItem* | dependency bits
-  int32_t base_off;  // kItemBaseAll (every item of such a chunk), kItemBase (its last item): the
-                     // chunk adds z3[base_off + r] to output r
+  int32_t aux;       // kItemBaseAll (every item of such a chunk), kItemBase (its last item): the
+                     // chunk adds z3[aux + r] to output r; scatter kinds: first scatter entry
   int32_t chunk;     // chunk number (host bookkeeping)
-  int32_t pad;
+  int32_t naux;      // scatter kinds: number of scatter entries
   Run runs[kMaxRuns];
 };
 static_assert(sizeof(WorkItem) == 96, "WorkItem layout");
@@ -94,6 +103,7 @@ struct OutChunk {
   int32_t h;
   int16_t kind;
   int16_t counter;
+  int32_t scat0 = 0, nscat = 0;  // scatter entries of scatter kinds
 };
 
 struct StreamParams {
@@ -105,6 +115,7 @@ struct StreamParams {
   const void* x;             // input, original ordering
   void* y;                   // output, original ordering
   const int32_t* perm;       // position -> original index
+  const Scatter* scatter;    // scatter entries of the scatter kinds
   void* xp;                  // x in cluster order (kSrcXp)
   void* z1;                  // xhat or t_b (kSrcZ1)
   void* z2;                  // yhat (kSrcZ2)
