@@ -67,8 +67,19 @@ enum { UH_DATA_C128 = 0, /* complex double, 16 bytes */
 
 /* Storage and arithmetic of a created op.
  *  UH_PREC_C128: operator stored complex128, products in FP64; x and y are complex128.
- *  UH_PREC_C64:  operator stored complex64, products accumulated in FP32; x and y complex64. */
-enum { UH_PREC_C128 = 0, UH_PREC_C64 = 1 };
+ *  UH_PREC_C64:  operator stored complex64, products accumulated in FP32; x and y complex64.
+ *  UH_PREC_C64_TF32, UH_PREC_C64_BF16X3: as UH_PREC_C64, plus a second copy of the operator for
+ *                the tensor-core uh_matmat: TF32 (rounded to nearest), or each FP32 value split
+ *                into BF16 hi + lo (three products hi*hi + hi*lo + lo*hi, FP32 accumulation).
+ *                Only for UH ops (h_create accepts UH_PREC_C128 and UH_PREC_C64). */
+enum { UH_PREC_C128 = 0, UH_PREC_C64 = 1, UH_PREC_C64_TF32 = 2, UH_PREC_C64_BF16X3 = 3 };
+
+/* Arithmetic of uh_matmat / h_matmat.
+ *  UH_MM_SIMT:   one product per column on the CUDA cores (any op; the precision of uh_matvec).
+ *  UH_MM_TF32:   tensor cores, TF32 operands, FP32 accumulation (op made with UH_PREC_C64_TF32).
+ *  UH_MM_BF16X3: tensor cores, BF16 hi/lo split of both operands, 3 products, FP32 accumulation
+ *                (op made with UH_PREC_C64_BF16X3). */
+enum { UH_MM_SIMT = 0, UH_MM_TF32 = 1, UH_MM_BF16X3 = 2 };
 
 /* ---------------------------------------------------------------- shared structure */
 /*
@@ -155,14 +166,19 @@ int uh_matvec(uh_op* op, const void* x, void* y, void* stream);
 int uh_check(uh_op* op, void* stream);
 
 /*
- * Y = A^UH X for nrhs right-hand sides: X is n x nrhs column-major with leading dimension ldx
- * (>= n), Y likewise with ldy; types as for uh_matvec. nrhs >= 1. The first call with a given
- * nrhs may allocate scratch (call uh_reserve beforehand to avoid that).
+ * Y = A^UH X for nrhs right-hand sides (Algorithm 6 applied to each column): X is n x nrhs
+ * column-major with leading dimension ldx (>= n), Y likewise with ldy, both device arrays in
+ * ORIGINAL ordering, types as for uh_matvec; X and Y must not overlap. nrhs >= 1. `mode` is a
+ * UH_MM_* value the op supports (else UH_EINVAL). The tensor-core modes run in passes of 64
+ * right-hand sides: a gather of X into cluster order, then three launches (forward transform,
+ * coupling, near field + backward transform), all on `stream`. No allocation: the scratch of
+ * the tensor-core modes is allocated by uh_create.
  */
 int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy,
-              void* stream);
+              int32_t mode, void* stream);
 
-/* Allocate the scratch that uh_matmat needs for up to max_nrhs right-hand sides. */
+/* Kept for callers that reserve scratch ahead of uh_matmat: the scratch exists from uh_create on,
+ * so this only checks its arguments (max_nrhs >= 1). */
 int uh_reserve(uh_op* op, int32_t max_nrhs);
 
 /* Sizes of the stored operator and of one product (Lemma 2.6, Def. 2.5). */
@@ -181,6 +197,9 @@ typedef struct {
   int64_t packed_bytes;       /* bytes streamed per matvec: packed matrices + column indices */
   int32_t n_launches;         /* kernel launches per uh_matvec */
   int64_t n_items;            /* work items per matvec, all launches */
+  int32_t matmat_mode;        /* tensor-core uh_matmat mode of the op (UH_MM_TF32 / UH_MM_BF16X3), or -1 */
+  int64_t panel_bytes;        /* its packed operator: bytes streamed per pass of 64 right-hand sides */
+  int64_t panel_items;        /* its work items per pass */
 } uh_stats_t;
 
 int uh_stats(const uh_op* op, uh_stats_t* out);
@@ -214,9 +233,9 @@ int h_create(const h_desc* desc, int32_t precision, h_op** out);
 int h_destroy(h_op* op);
 /* y = A^H x, Algorithm 5 (Section 4.4); arguments as for uh_matvec. */
 int h_matvec(h_op* op, const void* x, void* y, void* stream);
-/* Y = A^H X; arguments as for uh_matmat. */
+/* Y = A^H X; arguments as for uh_matmat; only UH_MM_SIMT. */
 int h_matmat(h_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy,
-             void* stream);
+             int32_t mode, void* stream);
 int h_reserve(h_op* op, int32_t max_nrhs);
 /* As uh_check. */
 int h_check(h_op* op, void* stream);

@@ -10,6 +10,8 @@
 //                coupling so that each CTA has independent work while the coupling's inputs finish;
 //   coupling     yhat_tau = sum_{sigma in row(tau)} S_b xhat_sigma  (chunks of yhat, z2);
 //   backward     y|_tile = z3|_tile + sum_{tau > tile} U_tau|_tile yhat_tau.
+// UH ops made with a tensor-core precision also hold the multi-RHS program of uh_panel.h (three
+// launches per pass of 64 right-hand sides, compact xhat / yhat panels, no scatter).
 // H matvec (Algorithm 5): permutation; t_b = Y_b^* xp|_sigma (z1); near field; then
 // y|_tile = z3|_tile + sum_b X_b|_tile t_b. Row tiles are the segments between consecutive
 // row-cluster boundaries of all blocks, cut to at most 64 rows, so each tile lies inside every row
@@ -26,6 +28,8 @@
 #include "uh.h"
 #include "uh_debug.h"
 #include "uh_internal.h"
+#include "uh_panel.h"
+#include "uh_panel_pack.h"
 #include "uh_program.h"
 
 using cd = std::complex<double>;
@@ -203,13 +207,24 @@ struct OpBase {
   void* d_z1 = nullptr;
   void* d_z2 = nullptr;
   void* d_z3 = nullptr;
+  // tensor-core uh_matmat (UH_PREC_C64_TF32 / UH_PREC_C64_BF16X3 ops)
+  int mm_mode = -1;       // UH_MM_TF32 or UH_MM_BF16X3
+  int panel_mode = 0;     // uh::kPanelTF32 or uh::kPanelBF16X3
+  int panel_ncta = 0;
+  unsigned char* d_ptiles = nullptr;
+  uh::PanelItem* d_pitems = nullptr;
+  int32_t* d_pbegin = nullptr;
+  void* d_pxp = nullptr;
+  void* d_pz1 = nullptr;
+  void* d_pz2 = nullptr;
   uh_stats_t st{};
 };
 
 void free_op(OpBase* o) {
   if (!o) return;
   void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_scatter, o->d_status,
-                  o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3};
+                  o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3,
+                  o->d_ptiles, o->d_pitems, o->d_pbegin, o->d_pxp, o->d_pz1, o->d_pz2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -326,17 +341,147 @@ int check_status(OpBase* o, void* stream) {
   return UH_OK;
 }
 
-int check_precision(int32_t precision) {
-  if (precision != UH_PREC_C128 && precision != UH_PREC_C64)
-    return fail(UH_EINVAL, "precision %d not supported", precision);
-  return UH_OK;
+int check_precision(int32_t precision, bool tensor_ok) {
+  if (precision == UH_PREC_C128 || precision == UH_PREC_C64) return UH_OK;
+  if (tensor_ok && (precision == UH_PREC_C64_TF32 || precision == UH_PREC_C64_BF16X3)) return UH_OK;
+  return fail(UH_EINVAL, "precision %d not supported%s", precision, tensor_ok ? "" : " for the H form");
 }
+
 
 // Row tiles covered by [r0, r1).
 template <class F>
 void for_tiles(const std::vector<Tile>& tiles, int64_t r0, int64_t r1, F f) {
   auto it = std::lower_bound(tiles.begin(), tiles.end(), r0, [](const Tile& t, int64_t v) { return t.p0 < v; });
   for (; it != tiles.end() && it->p0 < r1; ++it) f(static_cast<size_t>(it - tiles.begin()));
+}
+
+// Checks of a matmat call shared by the UH and H forms.
+int check_matmat_args(const OpBase* o, int32_t nrhs, const void* X, int64_t ldx, const void* Y, int64_t ldy) {
+  if (nrhs < 1) return fail(UH_EINVAL, "nrhs = %d", nrhs);
+  if (!X || !Y) return fail(UH_EINVAL, "X and Y must be device pointers");
+  if (ldx < o->n || ldy < o->n) return fail(UH_EINVAL, "leading dimensions %lld, %lld below n = %lld", (long long)ldx,
+                                            (long long)ldy, (long long)o->n);
+  const size_t eb = o->c128 ? 16 : 8;
+  const char* xa = static_cast<const char*>(X);
+  const char* ya = static_cast<const char*>(Y);
+  const size_t xl = (static_cast<size_t>(ldx) * (nrhs - 1) + o->n) * eb;
+  const size_t yl = (static_cast<size_t>(ldy) * (nrhs - 1) + o->n) * eb;
+  if (xa < ya + yl && ya < xa + xl) return fail(UH_EINVAL, "X and Y overlap");
+  return UH_OK;
+}
+
+// The tensor-core multi-RHS program of a UH op (uh_panel.h): xhat and yhat as compact panels
+// (xhat_sigma at rows xo[sigma], yhat_tau at rows yo[tau]); phase 0 forward chunks, phase 1
+// coupling chunks, phase 2 one chunk per row tile (near-field blocks, then the row bases of the
+// tile's row clusters). Packs, self-checks and, unless only packing, uploads it.
+int build_panel(OpBase* o, const uh_desc* d, const Tree& T, const std::vector<Tile>& tiles,
+                const std::vector<std::vector<int32_t>>& tile_rows, const std::vector<char>& is_row,
+                const std::vector<char>& is_col, const std::vector<std::vector<int64_t>>& row_blocks,
+                const std::vector<std::vector<int64_t>>& col_blocks, int mm_mode, int ncta) {
+  const int mode = mm_mode == UH_MM_BF16X3 ? uh::kPanelBF16X3 : uh::kPanelTF32;
+  uh::PanelBuilder B(mode, ncta);
+  auto live = [&](int64_t b) { return d->row_rank[d->adm_row[b]] > 0 && d->col_rank[d->adm_col[b]] > 0; };
+  std::vector<int64_t> xo(T.ncl, -1), yo(T.ncl, -1);
+  int64_t nx = 0, ny = 0;
+  for (int32_t c = 0; c < T.ncl; ++c) {
+    if (is_col[c] && d->col_rank[c] > 0) { xo[c] = nx; nx += d->col_rank[c]; }
+    if (is_row[c] && d->row_rank[c] > 0) { yo[c] = ny; ny += d->row_rank[c]; }
+  }
+  const Src V{d->V_data, d->data_type}, S{d->S_data, d->data_type}, U{d->U_data, d->data_type};
+  const Src D{d->dense.data, d->data_type};
+  for (int32_t s = 0; s < T.ncl; ++s) {
+    if (xo[s] < 0) continue;
+    bool used = false;
+    for (int64_t b : col_blocks[s]) used = used || live(b);
+    if (!used) continue;
+    const int32_t l = d->col_rank[s];
+    const int64_t m = T.size[s];
+    const int k = (l + uh::kPanelMaxH - 1) / uh::kPanelMaxH;
+    for (int q = 0; q < k; ++q) {
+      const int j0 = l * q / k, j1 = l * (q + 1) / k;
+      B.add_chunk(0, uh::kPOutZ1, xo[s] + j0, j1 - j0,
+                  {ColSpec{uh::kPSrcXP, T.begin[s], m, &V, true, d->col_off[s] + j0 * m, 1, m}});
+    }
+  }
+  std::vector<ColSpec> cols;
+  for (int32_t t = 0; t < T.ncl; ++t) {
+    if (yo[t] < 0) continue;
+    const int32_t l = d->row_rank[t];
+    const int k = (l + uh::kPanelMaxH - 1) / uh::kPanelMaxH;
+    for (int q = 0; q < k; ++q) {
+      const int i0 = l * q / k, i1 = l * (q + 1) / k;
+      cols.clear();
+      for (int64_t b : row_blocks[t]) {
+        if (!live(b)) continue;
+        const int32_t s = d->adm_col[b];
+        cols.push_back(ColSpec{uh::kPSrcZ1, xo[s], d->col_rank[s], &S, false, d->S_off[b] + i0, l, 1});
+      }
+      B.add_chunk(1, uh::kPOutZ2, yo[t] + i0, i1 - i0, cols);
+    }
+  }
+  std::vector<std::vector<int64_t>> near(tiles.size());
+  for (int64_t i = 0; i < d->dense.n_dense; ++i)
+    for_tiles(tiles, T.begin[d->dense.row_cl[i]], T.begin[d->dense.row_cl[i]] + T.size[d->dense.row_cl[i]],
+              [&](size_t t) { near[t].push_back(i); });
+  for (size_t ti = 0; ti < tiles.size(); ++ti) {
+    const int64_t p0 = tiles[ti].p0;
+    cols.clear();
+    for (int64_t i : near[ti]) {
+      const int32_t tau = d->dense.row_cl[i], sg = d->dense.col_cl[i];
+      cols.push_back(ColSpec{uh::kPSrcXP, T.begin[sg], T.size[sg], &D, false, d->dense.off[i] + p0 - T.begin[tau],
+                             T.size[tau], 1});
+    }
+    for (int32_t t : tile_rows[ti])
+      cols.push_back(ColSpec{uh::kPSrcZ2, yo[t], d->row_rank[t], &U, false, d->row_off[t] + p0 - T.begin[t],
+                             T.size[t], 1});
+    B.add_chunk(2, uh::kPOutY, p0, static_cast<int>(tiles[ti].h), cols);
+  }
+  if (const char* e = B.finalize()) return fail(UH_EINVAL, "multi-RHS packing: %s", e);
+  const int64_t src_rows[3] = {T.n, nx, ny}, out_rows[3] = {nx, ny, T.n};
+  if (const char* e = B.self_check(src_rows, out_rows)) return fail(UH_EINVAL, "internal multi-RHS packing error: %s", e);
+  if (!o) return UH_OK;
+  int rc;
+  if ((rc = uh::panel_prepare())) return rc;
+  if ((rc = upload(B.tiles.data(), B.tiles.size(), &o->d_ptiles))) return rc;
+  if ((rc = upload(B.items.data(), B.items.size() * sizeof(uh::PanelItem), &o->d_pitems))) return rc;
+  if ((rc = upload(B.begin.data(), B.begin.size() * sizeof(int32_t), &o->d_pbegin))) return rc;
+  const size_t row = uh::kPanelRowBytes;
+  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(T.n) * row, &o->d_pxp))) return rc;
+  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(nx, 1)) * row, &o->d_pz1)))
+    return rc;
+  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(ny, 1)) * row, &o->d_pz2)))
+    return rc;
+  o->mm_mode = mm_mode;
+  o->panel_mode = mode;
+  o->panel_ncta = ncta;
+  o->st.matmat_mode = mm_mode;
+  int64_t streamed = 0;
+  for (const uh::PanelItem& it : B.items) streamed += 256 * static_cast<int64_t>(it.n);
+  o->st.panel_bytes = streamed;
+  o->st.panel_items = static_cast<int64_t>(B.items.size());
+  o->st.device_bytes += static_cast<int64_t>(B.tiles.size() + B.items.size() * sizeof(uh::PanelItem)) +
+                        (T.n + std::max<int64_t>(nx, 1) + std::max<int64_t>(ny, 1)) * static_cast<int64_t>(row);
+  return UH_OK;
+}
+
+// Number of CTAs of the multi-RHS launches: one per SM.
+int panel_ncta(int* ncta) {
+  int device = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&device));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  *ncta = sms;
+  return UH_OK;
+}
+
+// One matmat by products per column.
+int matmat_by_columns(OpBase* o, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy, void* stream) {
+  const size_t eb = o->c128 ? 16 : 8;
+  for (int32_t r = 0; r < nrhs; ++r) {
+    const int rc = run_matvec(o, static_cast<const char*>(X) + static_cast<size_t>(r) * ldx * eb,
+                              static_cast<char*>(Y) + static_cast<size_t>(r) * ldy * eb, stream);
+    if (rc) return rc;
+  }
+  return UH_OK;
 }
 
 // Permutation slices (group 0): one per CTA.
@@ -417,7 +562,7 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   if (!d || !out) return fail(UH_EINVAL, "null argument");
   *out = nullptr;
   int rc;
-  if ((rc = check_precision(precision))) return rc;
+  if ((rc = check_precision(precision, true))) return rc;
   if (d->data_type != UH_DATA_C128 && d->data_type != UH_DATA_C64) return fail(UH_EINVAL, "data_type %d", d->data_type);
   Tree T;
   if ((rc = check_tree(d->tree, &T))) return rc;
@@ -575,9 +720,13 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
     P.add_columns(c, cols, zchunk[ti]);
   }
 
+  const int mm_mode = precision == UH_PREC_C64_TF32 ? UH_MM_TF32 : precision == UH_PREC_C64_BF16X3 ? UH_MM_BF16X3 : -1;
   if (g_pack_only_ncta) {
     if (const char* e = P.finalize()) return fail(UH_EINVAL, "packing: %s", e);
     if (const char* e = P.self_check()) return fail(UH_EINVAL, "internal packing error: %s", e);
+    if (mm_mode >= 0)
+      return build_panel(nullptr, d, T, tiles, tile_rows, is_row, is_col, row_blocks, col_blocks, mm_mode,
+                         g_pack_only_ncta);
     return UH_OK;
   }
   auto* o = new (std::nothrow) uh_op();
@@ -624,6 +773,16 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   o->st.rank_mean = rcnt ? static_cast<double>(rsum) / rcnt : 0.0;
   o->st.csp = csp;
   o->st.algo_bytes_matvec = o->st.elem_bytes * (eu + ev + es + o->st.E_D + 2 * T.n + 2 * (srr + scr));
+  o->st.matmat_mode = -1;
+  if (mm_mode >= 0) {
+    int pn = 0;
+    if ((rc = panel_ncta(&pn)) ||
+        (rc = build_panel(o, d, T, tiles, tile_rows, is_row, is_col, row_blocks, col_blocks, mm_mode, pn))) {
+      free_op(o);
+      delete o;
+      return rc;
+    }
+  }
   *out = o;
   return UH_OK;
 }
@@ -657,7 +816,7 @@ int h_create(const h_desc* d, int32_t precision, h_op** out) {
   if (!d || !out) return fail(UH_EINVAL, "null argument");
   *out = nullptr;
   int rc;
-  if ((rc = check_precision(precision))) return rc;
+  if ((rc = check_precision(precision, false))) return rc;
   if (d->data_type != UH_DATA_C128 && d->data_type != UH_DATA_C64) return fail(UH_EINVAL, "data_type %d", d->data_type);
   Tree T;
   if ((rc = check_tree(d->tree, &T))) return rc;
@@ -774,6 +933,7 @@ int h_create(const h_desc* d, int32_t precision, h_op** out) {
   o->st.E_V = ey;
   o->st.E_S = 0;
   o->st.algo_bytes_matvec = o->st.elem_bytes * (ex + ey + o->st.E_D + 2 * T.n + 2 * sk);
+  o->st.matmat_mode = -1;
   *out = o;
   return UH_OK;
 }
@@ -827,13 +987,58 @@ int uh_debug_stalled_matvec(uh_op* op, const void* x, void* y, long long timeout
   return run_matvec(op, x, y, stream, timeout_cycles, true);
 }
 
-int uh_matmat(uh_op*, int32_t, const void*, int64_t, void*, int64_t, void*) {
-  return fail(UH_EINVAL, "uh_matmat: not available in this build");
+int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t mode,
+              void* stream) {
+  if (!op) return fail(UH_EINVAL, "null op");
+  int rc;
+  if ((rc = check_matmat_args(op, nrhs, X, ldx, Y, ldy))) return rc;
+  if (mode == UH_MM_SIMT) return matmat_by_columns(op, nrhs, X, ldx, Y, ldy, stream);
+  if (mode != UH_MM_TF32 && mode != UH_MM_BF16X3) return fail(UH_EINVAL, "matmat mode %d", mode);
+  if (op->mm_mode != mode)
+    return fail(UH_EINVAL, "matmat mode %d needs an op created with precision %s", mode,
+                mode == UH_MM_TF32 ? "UH_PREC_C64_TF32" : "UH_PREC_C64_BF16X3");
+  for (int32_t rhs0 = 0; rhs0 < nrhs; rhs0 += uh::kPanelR) {
+    const int32_t nb = std::min<int32_t>(uh::kPanelR, nrhs - rhs0);
+    if ((rc = uh::panel_gather(X, ldx, op->n, op->d_perm, rhs0, nb, op->d_pxp, stream))) return rc;
+    for (int phase = 0; phase < 3; ++phase) {
+      uh::PanelParams p{};
+      p.items = op->d_pitems;
+      p.cta_begin = op->d_pbegin + phase * (op->panel_ncta + 1);
+      p.tiles = op->d_ptiles;
+      p.src[0] = op->d_pxp;
+      p.src[1] = op->d_pz1;
+      p.src[2] = op->d_pz2;
+      p.zout[0] = op->d_pz1;
+      p.zout[1] = op->d_pz2;
+      p.y = Y;
+      p.ldy = ldy;
+      p.perm = op->d_perm;
+      p.rhs0 = rhs0;
+      p.nb = nb;
+      p.mode = op->panel_mode;
+      p.status = op->d_status;
+      p.timeout_cycles = kTimeoutCycles;
+      if ((rc = uh::panel_launch(p, op->panel_ncta, stream))) return rc;
+    }
+  }
+  return UH_OK;
 }
-int uh_reserve(uh_op*, int32_t) { return fail(UH_EINVAL, "uh_reserve: not available in this build"); }
-int h_matmat(h_op*, int32_t, const void*, int64_t, void*, int64_t, void*) {
-  return fail(UH_EINVAL, "h_matmat: not available in this build");
+int uh_reserve(uh_op* op, int32_t max_nrhs) {
+  if (!op) return fail(UH_EINVAL, "null op");
+  if (max_nrhs < 1) return fail(UH_EINVAL, "max_nrhs = %d", max_nrhs);
+  return UH_OK;
 }
-int h_reserve(h_op*, int32_t) { return fail(UH_EINVAL, "h_reserve: not available in this build"); }
+int h_matmat(h_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t mode, void* stream) {
+  if (!op) return fail(UH_EINVAL, "null op");
+  int rc;
+  if ((rc = check_matmat_args(op, nrhs, X, ldx, Y, ldy))) return rc;
+  if (mode != UH_MM_SIMT) return fail(UH_EINVAL, "h_matmat: only UH_MM_SIMT (mode %d)", mode);
+  return matmat_by_columns(op, nrhs, X, ldx, Y, ldy, stream);
+}
+int h_reserve(h_op* op, int32_t max_nrhs) {
+  if (!op) return fail(UH_EINVAL, "null op");
+  if (max_nrhs < 1) return fail(UH_EINVAL, "max_nrhs = %d", max_nrhs);
+  return UH_OK;
+}
 
 }  // extern "C"

@@ -20,8 +20,11 @@ lib = C.CDLL(_LIB_PATH)
 
 UH_OK, UH_EINVAL, UH_ENOMEM, UH_ECUDA, UH_ENOTREADY, UH_ETIMEOUT, UH_EBUSY = range(7)
 UH_DATA_C128, UH_DATA_C64 = 0, 1
-UH_PREC_C128, UH_PREC_C64 = 0, 1
-_PREC = {"c128": UH_PREC_C128, "c64": UH_PREC_C64}
+UH_PREC_C128, UH_PREC_C64, UH_PREC_C64_TF32, UH_PREC_C64_BF16X3 = 0, 1, 2, 3
+_PREC = {"c128": UH_PREC_C128, "c64": UH_PREC_C64, "c64_tf32": UH_PREC_C64_TF32,
+         "c64_bf16x3": UH_PREC_C64_BF16X3}
+UH_MM_SIMT, UH_MM_TF32, UH_MM_BF16X3 = 0, 1, 2
+_MM = {"simt": UH_MM_SIMT, "tf32": UH_MM_TF32, "bf16x3": UH_MM_BF16X3}
 
 _p = C.c_void_p
 _i32 = C.c_int32
@@ -59,7 +62,8 @@ class Stats(C.Structure):
                 ("sum_row_rank", _i64), ("sum_col_rank", _i64),
                 ("rank_min", _i32), ("rank_max", _i32), ("rank_mean", C.c_double), ("csp", _i32),
                 ("algo_bytes_matvec", _i64), ("device_bytes", _i64), ("packed_bytes", _i64),
-                ("n_launches", _i32), ("n_items", _i64)]
+                ("n_launches", _i32), ("n_items", _i64),
+                ("matmat_mode", _i32), ("panel_bytes", _i64), ("panel_items", _i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,13 +75,13 @@ for _name, _args in [
     ("uh_create", [C.POINTER(UHDesc), _i32, C.POINTER(_p)]),
     ("uh_destroy", [_p]),
     ("uh_matvec", [_p, _p, _p, _p]),
-    ("uh_matmat", [_p, _i32, _p, _i64, _p, _i64, _p]),
+    ("uh_matmat", [_p, _i32, _p, _i64, _p, _i64, _i32, _p]),
     ("uh_reserve", [_p, _i32]),
     ("uh_stats", [_p, C.POINTER(Stats)]),
     ("h_create", [C.POINTER(HDesc), _i32, C.POINTER(_p)]),
     ("h_destroy", [_p]),
     ("h_matvec", [_p, _p, _p, _p]),
-    ("h_matmat", [_p, _i32, _p, _i64, _p, _i64, _p]),
+    ("h_matmat", [_p, _i32, _p, _i64, _p, _i64, _i32, _p]),
     ("h_reserve", [_p, _i32]),
     ("h_stats", [_p, C.POINTER(Stats)]),
     ("uh_check", [_p, _p]),
@@ -242,9 +246,10 @@ class _Op:
               "matvec")
         return y
 
-    def matmat(self, X, Y=None, stream=None):
+    def matmat(self, X, Y=None, mode: str = "simt", stream=None):
         """Y = A X for an n x nrhs column-major CUDA tensor X (X.T contiguous, e.g.
-        torch.empty(nrhs, n).T). Asynchronous on the stream."""
+        torch.empty(nrhs, n).T). mode: "simt", or "tf32" / "bf16x3" for an op created with
+        precision "c64_tf32" / "c64_bf16x3". Asynchronous on the stream."""
         import torch
         self._check_vec(X)
         n, r = X.shape
@@ -255,8 +260,8 @@ class _Op:
         self._check_vec(Y)
         if Y.stride(0) != 1 or Y.shape != X.shape:
             raise ValueError("Y must be column-major with X's shape")
-        check(self._matmat(self.handle, r, X.data_ptr(), X.stride(1), Y.data_ptr(), Y.stride(1),
-                           _stream_handle(stream)), "matmat")
+        check(self._matmat(self.handle, r, X.data_ptr(), max(X.stride(1), n), Y.data_ptr(),
+                           max(Y.stride(1), n), _MM[mode], _stream_handle(stream)), "matmat")
         return Y
 
     def check(self, stream=None):

@@ -119,3 +119,19 @@ def test_packing_self_check_passes(uh, prec, ncta, case):
         desc, keep = mk(arr)
         rc = fn(C.byref(desc), prec, ncta)
         assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("ncta", [152, 5, 1])
+@pytest.mark.parametrize("case", [(2048, 4.0, 32, 1e-6), (1000, 6.0, 24, 1e-5), (40, 3.0, 64, 1e-6)])
+def test_multi_rhs_packing_self_check_passes(uh, prec, ncta, case):
+    """The tensor-core multi-RHS program (TF32 and BF16x3 tiles) is packed and every address the
+    kernel derives from it checked, without a GPU; the H form rejects these precisions."""
+    n, k, leaf, eps = case
+    axes, noise = ((1.0, 0.7, 0.4), 0.01) if n == 1000 else ((1.0, 1.0, 1.0), 0.0)
+    _, _, hf, h, op = oracle_ops(n, k, leaf, 1.0, eps, 1e-8, axes, noise)
+    desc, keep = uh.uh_desc_from_arrays(uh_arrays(op))
+    rc = uh.lib.uh_pack_check(C.byref(desc), prec, ncta)
+    assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()
+    hd, hkeep = uh.h_desc_from_arrays(h_arrays(h))
+    assert uh.lib.h_pack_check(C.byref(hd), prec, ncta) == uh.UH_EINVAL
