@@ -1,7 +1,7 @@
 // Tensor-core multi-RHS product (sm_103a): one phase of a pass per launch, one CTA per SM.
 // Layout of the work and of the operands: uh_panel.h.
 //
-// Roles in a CTA of 192 threads:
+// Roles in a CTA of 320 threads:
 //  - producer (lane 0 of warp 0): streams the CTA's item descriptors into a shared-memory ring
 //    (TMA bulk copies of 8); per item waits for a free stage, copies the descriptor into the
 //    stage's slot, and copies the item's B operand (one bulk copy) and its panel rows (one bulk
@@ -9,13 +9,14 @@
 //  - MMA issuer (lane 0 of warp 1; warp 1 also allocates and frees the tensor memory): per item
 //    waits for the converted A operand, issues the item's tcgen05.mma instructions into the
 //    chunk's accumulator (two accumulators of 128 columns alternate between chunks) and commits
-//    them to the barriers that free the stage, the A buffer and, at a chunk's end, the
-//    accumulator for the epilogue.
-//  - converters (warps 2-5, one A-operand row per thread): per item build operand A from the
-//    staged panel rows (TF32 rounding, or a BF16 hi/lo split) in the swizzled K-major layout;
-//    after the first item of the next chunk has been handed to the MMA issuer, read the finished
-//    accumulator (tcgen05.ld, each warp its 32-lane quarter), combine the real products into
-//    complex outputs and write them.
+//    them to the barriers that free the stage and, at a chunk's end, the accumulator for the
+//    epilogue.
+//  - converters (warps 2-9; thread = one A-operand row x one half of K): per item read the
+//    staged panel rows into registers and overwrite them with operand A (TF32 rounding, or a
+//    BF16 hi/lo split) in the swizzled K-major layout, so a stage holds the item's two operands
+//    and nothing else; after the first item of the next chunk has been handed to the MMA
+//    issuer, read the finished accumulator (tcgen05.ld; each warp its 32-lane quarter and half
+//    of the column blocks), combine the real products into complex outputs and write them.
 // Every wait is bounded (timeout_cycles); when one runs out the CTA records it in `status`, stops,
 // lets its copies and MMAs in flight finish, frees the tensor memory and returns.
 #include <cuda_bf16.h>
@@ -28,8 +29,8 @@
 namespace uh {
 namespace {
 
-constexpr int kThreads = 192;
-constexpr int kConverters = 128;
+constexpr int kThreads = 320;
+constexpr int kConverters = 256;
 constexpr int kDescBatch = 8;
 constexpr int kDescRing = 2 * kDescBatch;
 constexpr int kAccCols = 128;          // one accumulator: N <= 128 FP32 columns
@@ -37,21 +38,19 @@ constexpr uint32_t kTmemCols = 2 * kAccCols;
 
 // Shared memory (bytes from a 1024-aligned base).
 constexpr int kStageTile = 0;                                   // B operand
-constexpr int kStagePanel = kPanelTileMax;                      // staged panel rows
+constexpr int kStagePanel = kPanelTileMax;                      // staged panel rows, then operand A
 constexpr int kStageBytes = kPanelTileMax + kPanelRawMax;       // 64 KB
-constexpr int kOffA = kPanelStages * kStageBytes;               // A operands [2]
-constexpr int kOffSlots = kOffA + 2 * kPanelABytes;             // item descriptor per stage
+static_assert(kPanelRawMax == kPanelABytes, "operand A replaces the staged panel rows");
+constexpr int kOffSlots = kPanelStages * kStageBytes;           // item descriptor per stage
 constexpr int kOffRing = kOffSlots + kPanelStages * 96;         // descriptor ring
 constexpr int kOffBars = kOffRing + kDescRing * 96;
-// barriers: full[S], empty[S], afull[2], aempty[2], accfull[2], accempty[2], desc[2], done
-constexpr int kNumBars = 2 * kPanelStages + 2 + 2 + 2 + 2 + 2 + 1;
+// barriers: full[S], empty[S], afull[S], accfull[2], accempty[2], desc[2], done
+constexpr int kNumBars = 3 * kPanelStages + 2 + 2 + 2 + 1;
 constexpr int kOffMisc = kOffBars + kNumBars * 8;              // tmem base, abort, go words
 constexpr int kSmemBytes = kOffMisc + 64 + 1024;               // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory of one CTA");
-static_assert(kPanelStages == 2, "A buffers and stages alternate together");
-
 struct Bars {
-  uint64_t *full, *empty, *afull, *aempty, *accfull, *accempty, *desc, *done;
+  uint64_t *full, *empty, *afull, *accfull, *accempty, *desc, *done;
 };
 __device__ __forceinline__ Bars bars_of(unsigned char* sm) {
   uint64_t* b = reinterpret_cast<uint64_t*>(sm + kOffBars);
@@ -59,8 +58,7 @@ __device__ __forceinline__ Bars bars_of(unsigned char* sm) {
   r.full = b;
   r.empty = b + kPanelStages;
   r.afull = b + 2 * kPanelStages;
-  r.aempty = r.afull + 2;
-  r.accfull = r.aempty + 2;
+  r.accfull = r.afull + kPanelStages;
   r.accempty = r.accfull + 2;
   r.desc = r.accempty + 2;
   r.done = r.desc + 2;
@@ -116,6 +114,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// TMA bulk copy global -> shared with an L2 cache policy.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
 __device__ __forceinline__ void converters_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kConverters) : "memory");
 }
@@ -166,6 +173,10 @@ __device__ void producer(const PanelParams& p, int i0, int n, unsigned char* sm,
   };
   issue_batch(0);
   issue_batch(1);
+  // The operator is streamed once: its lines go first, so the panels (read by many items) stay.
+  uint64_t stream_once, keep;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_once));
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
   int j = 0;
   bool ok = true;
   for (; j < n; ++j) {
@@ -190,13 +201,13 @@ __device__ void producer(const PanelParams& p, int i0, int n, unsigned char* sm,
     unsigned char* st = sm + s * kStageBytes;
     const uint32_t tile_bytes = 256u * static_cast<uint32_t>(it.n);
     mbar_arrive_expect_tx(&bar.full[s], tile_bytes + static_cast<uint32_t>(it.nrows) * kPanelRowBytes);
-    bulk_g2s(st + kStageTile, p.tiles + it.tile_off, tile_bytes, &bar.full[s]);
+    bulk_g2s_hint(st + kStageTile, p.tiles + it.tile_off, tile_bytes, &bar.full[s], stream_once);
     uint32_t row = 0;
     for (int r = 0; r < it.nruns; ++r) {
       const PanelRun run = it.runs[r];
       const unsigned char* src = static_cast<const unsigned char*>(p.src[run.src]);
-      bulk_g2s(st + kStagePanel + row * kPanelRowBytes, src + static_cast<int64_t>(run.start) * kPanelRowBytes,
-               static_cast<uint32_t>(run.len) * kPanelRowBytes, &bar.full[s]);
+      bulk_g2s_hint(st + kStagePanel + row * kPanelRowBytes, src + static_cast<int64_t>(run.start) * kPanelRowBytes,
+                    static_cast<uint32_t>(run.len) * kPanelRowBytes, &bar.full[s], keep);
       row += static_cast<uint32_t>(run.len);
     }
     if (j % kDescBatch == kDescBatch - 1) {
@@ -223,7 +234,6 @@ __device__ void producer(const PanelParams& p, int i0, int n, unsigned char* sm,
 __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const Bars& bar, uint32_t tmem,
                            volatile int* abort_flag) {
   const PanelItem* slots = reinterpret_cast<const PanelItem*>(sm + kOffSlots);
-  const uint32_t a_base = smem_u32(sm + kOffA);
   const uint32_t st_base = smem_u32(sm);
   const bool bf = p.mode == kPanelBF16X3;
   // D FP32; A, B TF32 (2) or BF16 (1); both K-major; M = 128.
@@ -238,8 +248,8 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
     }
   };
   for (int j = 0; j < n; ++j) {
-    const int s = j % kPanelStages, a = j & 1;
-    if (!wait_parity(&bar.afull[a], static_cast<uint32_t>(j >> 1) & 1u, p.timeout_cycles, abort_flag) ||
+    const int s = j % kPanelStages;
+    if (!wait_parity(&bar.afull[s], static_cast<uint32_t>(j / kPanelStages) & 1u, p.timeout_cycles, abort_flag) ||
         !wait_parity(&bar.full[s], static_cast<uint32_t>(j / kPanelStages) & 1u, p.timeout_cycles, abort_flag)) {
       give_up();
       break;
@@ -255,7 +265,7 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
     tc_fence_after();
     const uint32_t d = tmem + static_cast<uint32_t>(c * kAccCols);
     const uint32_t idesc = idesc_base | (static_cast<uint32_t>(nn >> 3) << 17);
-    const uint32_t A = a_base + static_cast<uint32_t>(a * kPanelABytes);
+    const uint32_t A = st_base + static_cast<uint32_t>(s * kStageBytes + kStagePanel);
     const uint32_t B = st_base + static_cast<uint32_t>(s * kStageBytes + kStageTile);
     uint32_t acc = (flags & kPItemFirst) ? 0u : 1u;
     if (!bf) {
@@ -281,7 +291,6 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
     }
     issued = true;
     tc_commit(&bar.empty[s]);
-    tc_commit(&bar.aempty[a]);
     if (flags & kPItemLast) {
       tc_commit(&bar.accfull[c]);
       ++chunks;
@@ -295,42 +304,45 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
 }
 
 template <bool BF>
-__device__ __forceinline__ void convert_item(const float* raw, int nrows, unsigned char* A, int m) {
-  // Thread m builds row m of A: A[m][k] = component (m & 1) of right-hand side m / 2 in panel row k,
-  // i.e. raw[k * 2 kPanelR + m]; rows k >= nrows are zero.
-  unsigned char* rowbase = A + (m / 8) * 1024 + (m % 8) * 128;
-  if (!BF) {
-#pragma unroll 4
-    for (int c = 0; c < kPanelK / 4; ++c) {
-      uint32_t v[4];
+__device__ __forceinline__ void convert_item(unsigned char* panel, int nrows, int t) {
+  // Thread t builds half `hf` of row m of A: A[m][k] = component (m & 1) of right-hand side m / 2
+  // in panel row k, i.e. raw[k * 2 kPanelR + m], for k in [32 hf, 32 hf + 32); rows k >= nrows
+  // are zero. A replaces the staged rows in place: every thread reads its values before any
+  // thread writes.
+  const int m = t & 127, hf = t >> 7;
+  const float* raw = reinterpret_cast<const float*>(panel);
+  constexpr int kH = kPanelK / 2;
+  float v[kH];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int k = 4 * c + e;
-        v[e] = k < nrows ? tf32_rna(raw[k * 2 * kPanelR + m]) : 0u;
-      }
-      unsigned char* dst = rowbase + (c / 8) * (128 * 128) + (((c % 8) ^ (m % 8)) * 16);
-      *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+  for (int k = 0; k < kH; ++k) {
+    const int kk = hf * kH + k;
+    v[k] = kk < nrows ? raw[kk * 2 * kPanelR + m] : 0.0f;
+  }
+  converters_sync();
+  unsigned char* rowbase = panel + (m / 8) * 1024 + (m % 8) * 128;
+  if (!BF) {
+    // 32 TF32 values = one 128-byte segment (segment hf).
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      unsigned char* dst = rowbase + hf * (128 * 128) + ((c ^ (m % 8)) * 16);
+      *reinterpret_cast<uint4*>(dst) =
+          make_uint4(tf32_rna(v[4 * c]), tf32_rna(v[4 * c + 1]), tf32_rna(v[4 * c + 2]), tf32_rna(v[4 * c + 3]));
     }
   } else {
-#pragma unroll 2
-    for (int c = 0; c < kPanelK / 8; ++c) {
+    // 32 BF16 values = 16-byte chunks 4 hf .. 4 hf + 3 of the hi and lo planes.
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
       uint32_t hi[4], lo[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        uint32_t hw[2], lw[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int k = 8 * c + 2 * e + u;
-          const float f = k < nrows ? raw[k * 2 * kPanelR + m] : 0.0f;
-          const __nv_bfloat16 h = __float2bfloat16_rn(f);
-          const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
-          hw[u] = static_cast<uint32_t>(__bfloat16_as_ushort(h));
-          lw[u] = static_cast<uint32_t>(__bfloat16_as_ushort(l));
-        }
-        hi[e] = hw[0] | (hw[1] << 16);
-        lo[e] = lw[0] | (lw[1] << 16);
+        const float2 f = make_float2(v[8 * c + 2 * e], v[8 * c + 2 * e + 1]);
+        const __nv_bfloat162 h = __float22bfloat162_rn(f);
+        const float2 hf2 = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __float22bfloat162_rn(make_float2(f.x - hf2.x, f.y - hf2.y));
+        hi[e] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[e] = *reinterpret_cast<const uint32_t*>(&l);
       }
-      unsigned char* dst = rowbase + ((c ^ (m % 8)) * 16);
+      unsigned char* dst = rowbase + (((4 * hf + c) ^ (m % 8)) * 16);
       *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(dst + 128 * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
@@ -358,6 +370,7 @@ __device__ bool epilogue(const PanelParams& p, const Pending& ch, const Bars& ba
   tc_fence_after();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3;            // tensor-memory lane quarter of this warp
+  const int hf = (warp - 2) >> 2;    // which column blocks: 16 (2 b + hf) .. + 15
   const int m = 32 * q + lane;       // accumulator row
   const int r = m >> 1, part = m & 1;
   int pm0 = 0, pm1 = 0;
@@ -366,7 +379,7 @@ __device__ bool epilogue(const PanelParams& p, const Pending& ch, const Bars& ba
     if (32 + lane < ch.h) pm1 = p.perm[ch.out + 32 + lane];
   }
   const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(ch.c * kAccCols);
-  for (int n0 = 0; n0 < ch.n; n0 += 16) {
+  for (int n0 = 16 * hf; n0 < ch.n; n0 += 32) {
     uint32_t v[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -401,17 +414,15 @@ __device__ bool epilogue(const PanelParams& p, const Pending& ch, const Bars& ba
 template <bool BF>
 __device__ void converters(const PanelParams& p, int n, unsigned char* sm, const Bars& bar, uint32_t tmem,
                            volatile int* abort_flag, volatile int* go) {
-  const int t = threadIdx.x - 64;  // 0 .. 127
+  const int t = threadIdx.x - 64;  // 0 .. 255
   const PanelItem* slots = reinterpret_cast<const PanelItem*>(sm + kOffSlots);
   Pending pend{};
   bool pending = false;
   int chunks = 0;
   for (int j = 0; j < n; ++j) {
-    const int s = j % kPanelStages, a = j & 1;
+    const int s = j % kPanelStages;
     if (t == 0) {
-      bool ok = wait_parity(&bar.full[s], static_cast<uint32_t>(j / kPanelStages) & 1u, p.timeout_cycles, abort_flag);
-      if (ok && j >= 2)
-        ok = wait_parity(&bar.aempty[a], static_cast<uint32_t>((j >> 1) - 1) & 1u, p.timeout_cycles, abort_flag);
+      const bool ok = wait_parity(&bar.full[s], static_cast<uint32_t>(j / kPanelStages) & 1u, p.timeout_cycles, abort_flag);
       if (!ok && !*abort_flag) {
         atomicOr(p.status, 4u);
         *abort_flag = 1;
@@ -424,14 +435,10 @@ __device__ void converters(const PanelParams& p, int n, unsigned char* sm, const
     const PanelItem& it = slots[s];
     const int nrows = it.nrows, flags = it.flags;
     const Pending mine{it.out, it.h, it.n, it.kind, chunks & 1, chunks >> 1};
-    convert_item<BF>(reinterpret_cast<const float*>(sm + s * kStageBytes + kStagePanel), nrows,
-                     sm + kOffA + a * kPanelABytes, t);
+    convert_item<BF>(sm + s * kStageBytes + kStagePanel, nrows, t);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A writes before the MMA reads them
     converters_sync();
-    if (t == 0) {
-      mbar_arrive(&bar.afull[a]);
-      mbar_arrive(&bar.empty[s]);  // staged panel rows read
-    }
+    if (t == 0) mbar_arrive(&bar.afull[s]);
     if ((flags & kPItemFirst) && pending) {
       if (!epilogue(p, pend, bar, tmem, abort_flag, go, t)) return;
       pending = false;
@@ -457,11 +464,10 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelParams p)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kPanelStages; ++s) {
       mbar_init(&bar.full[s], 1);
-      mbar_init(&bar.empty[s], 2);  // converters (panel read) + MMA commit (tile read)
+      mbar_init(&bar.empty[s], 1);  // MMA commit: both operands read
+      mbar_init(&bar.afull[s], 1);
     }
     for (int q = 0; q < 2; ++q) {
-      mbar_init(&bar.afull[q], 1);
-      mbar_init(&bar.aempty[q], 1);
       mbar_init(&bar.accfull[q], 1);
       mbar_init(&bar.accempty[q], 1);
       mbar_init(&bar.desc[q], 1);

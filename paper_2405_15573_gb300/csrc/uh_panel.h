@@ -26,7 +26,7 @@ constexpr int kPanelR = 64;          // right-hand sides per pass (M = 2 kPanelR
 constexpr int kPanelK = 64;          // columns (panel rows) per item
 constexpr int kPanelMaxH = 64;       // outputs per chunk (N <= 128)
 constexpr int kPanelMaxRuns = 8;     // contiguous runs of panel rows per item
-constexpr int kPanelStages = 2;
+constexpr int kPanelStages = 3;
 constexpr int kPanelRowBytes = kPanelR * 8;                  // one panel row, complex64
 constexpr int kPanelTileMax = 256 * 2 * kPanelMaxH;          // B bytes at N = 128 (32 KB)
 constexpr int kPanelRawMax = kPanelK * kPanelRowBytes;       // staged panel rows (32 KB)
