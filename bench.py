@@ -13,7 +13,8 @@ side (complex normal, seed 0). The operator is built on the host by the library'
   roofline  algorithmic bytes of one UH matvec (stored operator + vectors, Section 4.4) per
             event-timed matvec, against the measured HBM copy bandwidth;
   extra     the plain H-matrix matvec (Algorithm 5) on the same GPU, the complex128 UH matvec,
-            storage of both forms;
+            storage of both forms; the multi-RHS product uh_matmat on the tensor cores (TF32
+            and BF16x3, 32 and 64 right-hand sides) against its CUDA-core (SIMT) result;
   cpu_baseline  the FP64 oracle's UH matvec on the same operator, timed on one host core in a
             spawned child process, also giving the relative error of the GPU result.
 
@@ -42,6 +43,14 @@ if ROOT not in sys.path:
 
 METRIC = "UH matvec/s & HBM GB/s vs H-matvec, same GB300, relerr≤5e-6; solve p50/p99"
 UNIT = "matvec/s"
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
 
 
 def _peaks():
@@ -235,6 +244,63 @@ def timed_matvecs(op, x, y, steps, flush, torch):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def _colmajor_rhs(torch, n, nrhs, seed0=100):
+    """n x nrhs column-major complex64 CUDA tensor of seeded complex normal columns."""
+    from paper_2405_15573_gb300 import inputs as I
+    X = np.stack([I.complex_normal(n, seed0 + j) for j in range(nrhs)], axis=0)
+    return torch.from_numpy(X.astype(np.complex64)).to("cuda").T
+
+
+def matmat_figures(model, n, steps, torch, peak_bf16):
+    """uh_matmat on the tensor cores (TF32, BF16x3) for 32 and 64 right-hand sides: mean time per
+    call (CUDA events, back to back), right-hand-side products per second, bytes of the packed
+    operator streamed per second, MMA throughput, and the relative error of each column against
+    the CUDA-core product of the same operator (complex64 storage, FP32 accumulation)."""
+    out = {}
+    ref_op = model.uh_op("c64")
+    X64 = _colmajor_rhs(torch, n, 64)
+    Yref = torch.empty((64, n), dtype=torch.complex64, device="cuda").T
+    ref_op.matmat(X64, Yref, mode="simt")
+    ref_op.check()
+    yref = Yref.cpu().numpy().astype(np.complex128)
+    del ref_op
+    # TF32 has half the BF16 tensor rate (2.25 vs 1.1 PFLOP/s nominal dense).
+    peaks = {"tf32": peak_bf16 * 1.1 / 2.25, "bf16x3": peak_bf16}
+    for mode in ("tf32", "bf16x3"):
+        op = model.uh_op("c64_" + mode)
+        st = op.stats()
+        for nrhs in (32, 64):
+            X = X64[:, :nrhs]
+            Y = torch.empty((nrhs, n), dtype=torch.complex64, device="cuda").T
+            for _ in range(3):
+                op.matmat(X, Y, mode=mode)
+            ms = timed_back_to_back(_MatmatStep(op, X, Y, mode), None, None, steps, torch)
+            op.check()
+            y = Y.cpu().numpy().astype(np.complex128)
+            err = max(float(np.linalg.norm(y[:, j] - yref[:, j]) / np.linalg.norm(yref[:, j]))
+                      for j in range(nrhs))
+            products = 3 if mode == "bf16x3" else 1
+            flops = products * 2 * 128 * 64 * st["panel_bytes"] / 256  # M = 128, K = 64 per 256 n bytes
+            tf = flops / (ms * 1e-3) / 1e12
+            out[f"{mode}_R{nrhs}"] = {
+                "ms": ms, "rhs_matvec_per_s": nrhs * 1e3 / ms,
+                "operator_GBps": st["panel_bytes"] / (ms * 1e-3) / 1e9,
+                "tensor_tflops": tf, "tensor_peak_tflops": peaks[mode], "tensor_frac": tf / peaks[mode],
+                "max_col_relerr_vs_simt": err}
+        del op
+    return out
+
+
+class _MatmatStep:
+    """Adapter so timed_back_to_back can time one matmat call per step."""
+
+    def __init__(self, op, X, Y, mode):
+        self.op, self.X, self.Y, self.mode = op, X, Y, mode
+
+    def matvec(self, _x, _y):
+        self.op.matmat(self.X, self.Y, mode=self.mode)
+
+
 def profile_arm(args):
     """Only one op (uh64, h64 or uh128) of the benchmark workload: build, warm up, run `steps`
     products and print their mean time. For profiler captures of a single kernel."""
@@ -243,19 +309,28 @@ def profile_arm(args):
     from paper_2405_15573_gb300 import uh as U
     w = I.SPHERE_32768
     model = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca)
-    prec = "c128" if args.profile_op.endswith("128") else "c64"
-    op = model.uh_op(prec) if args.profile_op.startswith("uh") else model.h_op(prec)
-    model.close()
-    dt = torch.complex128 if prec == "c128" else torch.complex64
-    x = torch.from_numpy(w.x()).to("cuda", dt)
-    y = torch.empty_like(x)
+    if args.profile_op.startswith("mm_"):
+        mode = args.profile_op[3:]
+        op = model.uh_op("c64_" + mode)
+        model.close()
+        X = _colmajor_rhs(torch, w.n, 64)
+        Y = torch.empty((64, w.n), dtype=torch.complex64, device="cuda").T
+        run = lambda: op.matmat(X, Y, mode=mode)  # noqa: E731
+    else:
+        prec = "c128" if args.profile_op.endswith("128") else "c64"
+        op = model.uh_op(prec) if args.profile_op.startswith("uh") else model.h_op(prec)
+        model.close()
+        dt = torch.complex128 if prec == "c128" else torch.complex64
+        x = torch.from_numpy(w.x()).to("cuda", dt)
+        y = torch.empty_like(x)
+        run = lambda: op.matvec(x, y)  # noqa: E731
     for _ in range(args.warmup):
-        op.matvec(x, y)
+        run()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(args.steps):
-        op.matvec(x, y)
+        run()
     b.record()
     op.check()
     print(json.dumps({"profile_op": args.profile_op, "ms_mean": a.elapsed_time(b) / args.steps,
@@ -290,6 +365,8 @@ def gpu_arm(args):
     if not args.no_cpu_baseline and rank == 0:
         tmpdir = tempfile.mkdtemp(prefix="uh_bench_")
         dump_operator(model, x_np, tmpdir)
+    peak_bf16 = _bf16_peak()
+    mm = None if args.no_matmat else matmat_figures(model, w.n, max(10, args.steps // 20), torch, peak_bf16)
     model.close()  # the ops hold their own device copies; free the host arrays
     x = torch.from_numpy(x_np).to("cuda", torch.complex64)
     y = torch.empty_like(x)
@@ -400,6 +477,7 @@ def gpu_arm(args):
                            "note": "2x-L2 write before every step, outside the events"}},
         "h": {"matvec_per_s": 1e3 / ms_h, "ms_mean": ms_h, "GBps": gbs_h,
               "algo_bytes": hst["algo_bytes_matvec"], "speedup_uh_over_h": ms_h / ms_uh},
+        "uh_matmat": mm,
         "uh_c128": {"matvec_per_s": 1e3 / ms_128, "ms_mean": ms_128, "GBps": gbs_128,
                     "bound": "fp64 FMA (8 flops per complex multiply-add of a 16-byte element)"},
         "storage": {"E_UH": st["E_U"] + st["E_V"] + st["E_S"] + st["E_D"],
@@ -462,7 +540,8 @@ def main():
     ap.add_argument("--impl", default="uh", choices=["uh", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile-op", choices=["uh64", "h64", "uh128"], default=None)
+    ap.add_argument("--profile-op", choices=["uh64", "h64", "uh128", "mm_tf32", "mm_bf16x3"], default=None)
+    ap.add_argument("--no-matmat", action="store_true")
     args = ap.parse_args()
     if args.profile_op:
         args.steps = 5 if args.steps is None else args.steps
