@@ -467,7 +467,10 @@ def gpu_arm(args):
                      "frac": gbs / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "kernel": "stream_kernel<float> (one persistent launch per matvec)",
                      "algo_bytes_per_matvec": st["algo_bytes_matvec"],
-                     "frac_of_nominal_8000": gbs / 8000.0},
+                     "frac_of_nominal_8000": gbs / 8000.0,
+                     "l2_flushed": {"achieved": st["algo_bytes_matvec"] / (statistics.mean(t_uh_fl) * 1e-3) / 1e9,
+                                    "frac": st["algo_bytes_matvec"] / (statistics.mean(t_uh_fl) * 1e-3) / 1e9 / peak,
+                                    "note": "same kernel, 2x-L2 write before every matvec (outside the events)"}},
         "cpu_baseline": cpu,
         "clocks": clk,
         "gpu_launches": args.steps * st["n_launches"],
