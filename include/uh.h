@@ -204,6 +204,44 @@ typedef struct {
 
 int uh_stats(const uh_op* op, uh_stats_t* out);
 
+/* ---------------------------------------------------------------- batched operators */
+/*
+ * Many independent UH operators applied together (Algorithm 6 for each; the operators share no
+ * data). The batch packs all of them into ONE device program, so one launch of the streaming
+ * kernel computes every operator's product: its work list is flattened across the operators
+ * (each phase of Algorithm 6 over all operators, longest chunks first), instead of one launch
+ * per operator. The paper has no batched product; its per-cluster independence (Section 4.4)
+ * is what lets the chunks of different operators share one schedule.
+ */
+typedef struct uh_batch uh_batch;
+
+/*
+ * Validate descs[0..count-1] (each as uh_create does; the message names the failing operator)
+ * and create the batch with storage `precision` (UH_PREC_C128 or UH_PREC_C64). The descriptors'
+ * arrays are copied; the caller keeps them. count >= 1; the points of all operators together
+ * must number at most 2^31 - 1.
+ */
+int uh_batch_create(const uh_desc* const* descs, int32_t count, int32_t precision, uh_batch** out);
+int uh_batch_destroy(uh_batch* batch);
+
+/* offsets[0..count]: operator k's points are positions [offsets[k], offsets[k+1]) of the batch
+ * vectors; offsets[count] is the total. */
+int uh_batch_offsets(const uh_batch* batch, int64_t* offsets);
+
+/*
+ * y_k = A_k x_k for every operator k, in one launch: x and y are device arrays of offsets[count]
+ * complex values (the operators' vectors back to back, each in its ORIGINAL ordering), types as
+ * for uh_matvec; they must not overlap. Asynchronous on `stream`.
+ */
+int uh_batch_matvec(uh_batch* batch, const void* x, void* y, void* stream);
+
+/* As uh_check. */
+int uh_batch_check(uh_batch* batch, void* stream);
+
+/* Sums over the operators (counts, bytes; n = total points; rank_min / rank_max / csp over all
+ * operators, rank_mean over all bases); the packing figures are those of the batch program. */
+int uh_batch_stats(const uh_batch* batch, uh_stats_t* out);
+
 /* ---------------------------------------------------------------- H operator (plain form) */
 /*
  * H-matrix (Def. 2.3): admissible block i = (adm_row[i], adm_col[i]) with rank adm_rank[i] = k_b

@@ -344,7 +344,8 @@ int check_status(OpBase* o, void* stream) {
 int check_precision(int32_t precision, bool tensor_ok) {
   if (precision == UH_PREC_C128 || precision == UH_PREC_C64) return UH_OK;
   if (tensor_ok && (precision == UH_PREC_C64_TF32 || precision == UH_PREC_C64_BF16X3)) return UH_OK;
-  return fail(UH_EINVAL, "precision %d not supported%s", precision, tensor_ok ? "" : " for the H form");
+  return fail(UH_EINVAL, "precision %d not supported%s", precision,
+              tensor_ok ? "" : " here (UH_PREC_C128 or UH_PREC_C64 only)");
 }
 
 
@@ -499,9 +500,11 @@ void add_permute(ProgramBuilder& P, int64_t n, int ncta) {
 // Near-field chunks of the row tiles, alternating between the two near-field groups. A tile with a
 // backward part writes its z3 slot (the backward chunk adds it), otherwise y directly. Returns,
 // per tile, the near-field chunk writing z3 (or -1).
+// offN: position of the operator's first point in the program's vectors; z3pos: next free z3 slot
+// (advanced; when null the slots start at 0 and the z3 length is set here).
 std::vector<int> add_near_field(ProgramBuilder& P, const Tree& T, const uh_dense_desc& d, const Src& D,
                                 const std::vector<Tile>& tiles, const std::vector<char>& has_back,
-                                std::vector<char>* has_near) {
+                                std::vector<char>* has_near, int64_t offN = 0, int64_t* z3pos = nullptr) {
   const int64_t A = P.align();
   std::vector<std::vector<int64_t>> per_tile(tiles.size());
   for (int64_t i = 0; i < d.n_dense; ++i)
@@ -509,7 +512,7 @@ std::vector<int> add_near_field(ProgramBuilder& P, const Tree& T, const uh_dense
               [&](size_t t) { per_tile[t].push_back(i); });
   std::vector<int> zchunk(tiles.size(), -1);
   has_near->assign(tiles.size(), 0);
-  int64_t pos = 0;
+  int64_t pos = z3pos ? *z3pos : 0;
   std::vector<int64_t> slot(tiles.size(), -1);
   for (size_t t = 0; t < tiles.size(); ++t) {
     (*has_near)[t] = !per_tile[t].empty();
@@ -517,20 +520,21 @@ std::vector<int> add_near_field(ProgramBuilder& P, const Tree& T, const uh_dense
     slot[t] = pos;
     pos += ProgramBuilder::round_up(tiles[t].h, A);
   }
-  P.set_source_len(uh::kSrcZ3, pos);
+  if (z3pos) *z3pos = pos;
+  else P.set_source_len(uh::kSrcZ3, pos);
   int parity = 0;
   std::vector<ColSpec> cols;
   for (size_t t = 0; t < tiles.size(); ++t) {
     if (per_tile[t].empty()) continue;
     const int group = (parity++ & 1) ? uh::kGroupNearB : uh::kGroupNearA;
     const int c = slot[t] >= 0 ? P.add_chunk(uh::kToZ3, slot[t], tiles[t].h, group)
-                               : P.add_chunk(uh::kToY, tiles[t].p0, tiles[t].h, group);
+                               : P.add_chunk(uh::kToY, offN + tiles[t].p0, tiles[t].h, group);
     if (slot[t] >= 0) zchunk[t] = c;
     cols.clear();
     for (int64_t i : per_tile[t]) {
       const int32_t tau = d.row_cl[i], sg = d.col_cl[i];
-      cols.push_back(ColSpec{uh::kSrcXp, T.begin[sg], T.size[sg], &D, false, d.off[i] + tiles[t].p0 - T.begin[tau],
-                             T.size[tau], 1});
+      cols.push_back(ColSpec{uh::kSrcXp, offN + T.begin[sg], T.size[sg], &D, false,
+                             d.off[i] + tiles[t].p0 - T.begin[tau], T.size[tau], 1});
     }
     P.add_columns(c, cols);
   }
@@ -547,44 +551,43 @@ void fill_common_stats(OpBase* o, const Tree& T, const uh_dense_desc& d, int32_t
   o->st.E_D = ed;
 }
 
-}  // namespace
 
-struct uh_op : OpBase {};
-struct h_op : OpBase {};
-
-extern "C" {
-
-const char* uh_last_error(void) { return g_err.c_str(); }
-const char* uh_version(void) { return "uh-gb300 0.2 (sm_103a)"; }
-
-int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
-  g_err.clear();
-  if (!d || !out) return fail(UH_EINVAL, "null argument");
-  *out = nullptr;
-  int rc;
-  if ((rc = check_precision(precision, true))) return rc;
-  if (d->data_type != UH_DATA_C128 && d->data_type != UH_DATA_C64) return fail(UH_EINVAL, "data_type %d", d->data_type);
+// A validated UH descriptor and the structure derived from it.
+struct UHPrep {
+  const uh_desc* d = nullptr;
   Tree T;
+  std::vector<char> is_row, is_col;
+  std::vector<Tile> tiles;
+  std::vector<std::vector<int64_t>> row_blocks, col_blocks;  // sorted by column / row cluster
+  std::vector<std::vector<int32_t>> tile_rows;               // row clusters with a basis containing each tile
+};
+
+int prepare_uh(const uh_desc* d, UHPrep* u) {
+  int rc;
+  if (d->data_type != UH_DATA_C128 && d->data_type != UH_DATA_C64) return fail(UH_EINVAL, "data_type %d", d->data_type);
+  u->d = d;
+  Tree& T = u->T;
   if ((rc = check_tree(d->tree, &T))) return rc;
   if (d->n_adm < 0) return fail(UH_EINVAL, "n_adm < 0");
   if (d->n_adm > 0 && (!d->adm_row || !d->adm_col || !d->S_off || !d->S_data || !d->row_rank || !d->row_off ||
                        !d->col_rank || !d->col_off || !d->U_data || !d->V_data))
     return fail(UH_EINVAL, "admissible part incomplete");
   if ((rc = check_dense(T, d->dense))) return rc;
-  std::vector<char> is_row(T.ncl, 0), is_col(T.ncl, 0);
+  u->is_row.assign(T.ncl, 0);
+  u->is_col.assign(T.ncl, 0);
   for (int64_t i = 0; i < d->n_adm; ++i) {
     if ((rc = check_cluster_index(T, d->adm_row[i], "adm_row", i))) return rc;
     if ((rc = check_cluster_index(T, d->adm_col[i], "adm_col", i))) return rc;
-    is_row[d->adm_row[i]] = 1;
-    is_col[d->adm_col[i]] = 1;
+    u->is_row[d->adm_row[i]] = 1;
+    u->is_col[d->adm_col[i]] = 1;
   }
   for (int32_t c = 0; c < T.ncl; ++c) {
-    if (is_row[c]) {
+    if (u->is_row[c]) {
       const int32_t l = d->row_rank[c];
       if (l < 0 || l > T.size[c]) return fail(UH_EINVAL, "row_rank[%d] = %d outside [0, %lld]", c, l, (long long)T.size[c]);
       if ((rc = check_range(d->row_off[c], T.size[c] * l, d->U_len, "row basis", c))) return rc;
     }
-    if (is_col[c]) {
+    if (u->is_col[c]) {
       const int32_t l = d->col_rank[c];
       if (l < 0 || l > T.size[c]) return fail(UH_EINVAL, "col_rank[%d] = %d outside [0, %lld]", c, l, (long long)T.size[c]);
       if ((rc = check_range(d->col_off[c], T.size[c] * l, d->V_len, "column basis", c))) return rc;
@@ -597,54 +600,64 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   std::vector<int32_t> brow, bcol;
   for (int64_t i = 0; i < d->n_adm; ++i) { brow.push_back(d->adm_row[i]); bcol.push_back(d->adm_col[i]); }
   for (int64_t i = 0; i < d->dense.n_dense; ++i) { brow.push_back(d->dense.row_cl[i]); bcol.push_back(d->dense.col_cl[i]); }
-  std::vector<Tile> tiles;
-  if ((rc = make_tiles_and_check(T, brow, bcol, &tiles))) return rc;
-
-  const bool c128 = precision == UH_PREC_C128;
-  int ncta = g_pack_only_ncta, device = 0;
-  if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
-  ProgramBuilder P(c128, T.n, ncta);
-  const int64_t A = P.align();
-  P.set_source_len(uh::kSrcXp, ProgramBuilder::round_up(T.n, A));
-  add_permute(P, T.n, ncta);
-
-  // Blocks by row cluster (sorted by column cluster) and by column cluster (sorted by row).
-  std::vector<std::vector<int64_t>> row_blocks(T.ncl), col_blocks(T.ncl);
+  if ((rc = make_tiles_and_check(T, brow, bcol, &u->tiles))) return rc;
+  u->row_blocks.assign(T.ncl, {});
+  u->col_blocks.assign(T.ncl, {});
   for (int64_t i = 0; i < d->n_adm; ++i) {
-    row_blocks[d->adm_row[i]].push_back(i);
-    col_blocks[d->adm_col[i]].push_back(i);
+    u->row_blocks[d->adm_row[i]].push_back(i);
+    u->col_blocks[d->adm_col[i]].push_back(i);
   }
   for (int32_t c = 0; c < T.ncl; ++c) {
-    std::stable_sort(row_blocks[c].begin(), row_blocks[c].end(),
+    std::stable_sort(u->row_blocks[c].begin(), u->row_blocks[c].end(),
                      [&](int64_t a, int64_t b) { return d->adm_col[a] < d->adm_col[b]; });
-    std::stable_sort(col_blocks[c].begin(), col_blocks[c].end(),
+    std::stable_sort(u->col_blocks[c].begin(), u->col_blocks[c].end(),
                      [&](int64_t a, int64_t b) { return d->adm_row[a] < d->adm_row[b]; });
   }
+  u->tile_rows.assign(u->tiles.size(), {});
+  for (int32_t t = 0; t < T.ncl; ++t)
+    if (u->is_row[t] && d->row_rank[t] > 0)
+      for_tiles(u->tiles, T.begin[t], T.begin[t] + T.size[t], [&](size_t i) { u->tile_rows[i].push_back(t); });
+  return UH_OK;
+}
+
+// Vector offsets of one operator inside a program that may hold several (a batch): its points
+// start at position n in xp and y; its z1, z2 and z3 parts start at x, y, z3 (all advanced past
+// what the operator uses).
+struct Offsets {
+  int64_t n = 0, x = 0, y = 0, z3 = 0;
+};
+
+// The forward, near-field, coupling and backward chunks of one UH operator (Algorithm 6), with
+// the scatter layout of z1 / z2 (see the file comment). The permutation chunks and the source
+// lengths are the caller's.
+void add_uh_program(ProgramBuilder& P, const UHPrep& u, Offsets* off) {
+  const uh_desc* d = u.d;
+  const Tree& T = u.T;
+  const int64_t A = P.align();
+  const auto& tiles = u.tiles;
+  const auto& row_blocks = u.row_blocks;
+  const auto& col_blocks = u.col_blocks;
+  const auto& tile_rows = u.tile_rows;
+  const int64_t on = off->n;
   auto live = [&](int64_t b) { return d->row_rank[d->adm_row[b]] > 0 && d->col_rank[d->adm_col[b]] > 0; };
   // z1: per row cluster tau, the coupling inputs [xhat_sigma]_{sigma in row(tau)} back to back
   // (the forward chunks scatter each xhat_sigma into every segment that uses it).
   std::vector<int64_t> xin(T.ncl, -1), xpos(d->n_adm, -1);
-  int64_t nx = 0;
+  int64_t nx = off->x;
   for (int32_t t = 0; t < T.ncl; ++t) {
-    if (!is_row[t] || d->row_rank[t] == 0) continue;
+    if (!u.is_row[t] || d->row_rank[t] == 0) continue;
     xin[t] = nx;
     int64_t pos = 0;
     for (int64_t b : row_blocks[t])
       if (live(b)) { xpos[b] = pos; pos += d->col_rank[d->adm_col[b]]; }
     nx += ProgramBuilder::round_up(std::max<int64_t>(pos, 1), A);
   }
-  P.set_source_len(uh::kSrcZ1, nx);
-  // Row tiles and the row clusters with a basis that contain them.
-  std::vector<std::vector<int32_t>> tile_rows(tiles.size());
-  for (int32_t t = 0; t < T.ncl; ++t)
-    if (is_row[t] && d->row_rank[t] > 0)
-      for_tiles(tiles, T.begin[t], T.begin[t] + T.size[t], [&](size_t i) { tile_rows[i].push_back(t); });
   std::vector<char> has_back(tiles.size(), 0);
   // z2: per row tile, the backward inputs [yhat_tau]_{tau contains the tile} back to back (the
   // coupling chunks scatter each yhat_tau into every tile inside tau).
   std::vector<int64_t> yin(tiles.size(), -1);
   std::vector<std::vector<int64_t>> ypos(tiles.size());
-  int64_t ny = 0;
+  int64_t ny = off->y;
   for (size_t i = 0; i < tiles.size(); ++i) {
     has_back[i] = !tile_rows[i].empty();
     if (!has_back[i]) continue;
@@ -653,13 +666,11 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
     for (int32_t t : tile_rows[i]) { ypos[i].push_back(pos); pos += d->row_rank[t]; }
     ny += ProgramBuilder::round_up(pos, A);
   }
-  P.set_source_len(uh::kSrcZ2, ny);
-
   const Src V{d->V_data, d->data_type}, S{d->S_data, d->data_type}, U{d->U_data, d->data_type};
   const Src D{d->dense.data, d->data_type};
   // Forward transform: chunks of at most 64 rows of V_sigma^*; column r = conj(V_sigma[r, rows]).
   for (int32_t s = 0; s < T.ncl; ++s) {
-    if (!is_col[s] || d->col_rank[s] == 0) continue;
+    if (!u.is_col[s] || d->col_rank[s] == 0) continue;
     std::vector<int64_t> users;
     for (int64_t b : col_blocks[s])
       if (live(b)) users.push_back(b);
@@ -671,16 +682,16 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
       const int j0 = l * q / k, j1 = l * (q + 1) / k;
       const int c = P.add_chunk(uh::kScatterZ1, 0, j1 - j0, uh::kGroupForward, uh::kCounterForward);
       for (int64_t b : users) P.add_scatter(c, xin[d->adm_row[b]] + xpos[b] + j0, 0, j1 - j0);
-      P.add_columns(c, {ColSpec{uh::kSrcXp, T.begin[s], m, &V, true, d->col_off[s] + j0 * m, 1, m}});
+      P.add_columns(c, {ColSpec{uh::kSrcXp, on + T.begin[s], m, &V, true, d->col_off[s] + j0 * m, 1, m}});
     }
   }
   std::vector<char> has_near;
-  const std::vector<int> zchunk = add_near_field(P, T, d->dense, D, tiles, has_back, &has_near);
+  const std::vector<int> zchunk = add_near_field(P, T, d->dense, D, tiles, has_back, &has_near, on, &off->z3);
   // Coupling: per row cluster tau (chunks of at most 64 rows), columns [S_b]_{sigma in row(tau)},
   // inputs one run of z1; outputs scattered to the tiles inside tau.
   std::vector<ColSpec> cols;
   for (int32_t t = 0; t < T.ncl; ++t) {
-    if (!is_row[t] || d->row_rank[t] == 0) continue;
+    if (!u.is_row[t] || d->row_rank[t] == 0) continue;
     const int32_t l = d->row_rank[t];
     const int k = (l + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
     for (int q = 0; q < k; ++q) {
@@ -706,10 +717,10 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
     if (!has_back[ti]) {
       // the near-field chunk writes y; a tile whose blocks all have rank 0 and no near field
       // gets an empty chunk, which writes zeros
-      if (!has_near[ti]) P.add_columns(P.add_chunk(uh::kToY, tiles[ti].p0, tiles[ti].h, uh::kGroupBackward), {});
+      if (!has_near[ti]) P.add_columns(P.add_chunk(uh::kToY, on + tiles[ti].p0, tiles[ti].h, uh::kGroupBackward), {});
       continue;
     }
-    const int c = P.add_chunk(uh::kToY, tiles[ti].p0, tiles[ti].h, uh::kGroupBackward);
+    const int c = P.add_chunk(uh::kToY, on + tiles[ti].p0, tiles[ti].h, uh::kGroupBackward);
     cols.clear();
     for (size_t w = 0; w < tile_rows[ti].size(); ++w) {
       const int32_t t = tile_rows[ti][w];
@@ -719,26 +730,22 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
     }
     P.add_columns(c, cols, zchunk[ti]);
   }
+  off->n += T.n;
+  off->x = nx;
+  off->y = ny;
+}
 
-  const int mm_mode = precision == UH_PREC_C64_TF32 ? UH_MM_TF32 : precision == UH_PREC_C64_BF16X3 ? UH_MM_BF16X3 : -1;
-  if (g_pack_only_ncta) {
-    if (const char* e = P.finalize()) return fail(UH_EINVAL, "packing: %s", e);
-    if (const char* e = P.self_check()) return fail(UH_EINVAL, "internal packing error: %s", e);
-    if (mm_mode >= 0)
-      return build_panel(nullptr, d, T, tiles, tile_rows, is_row, is_col, row_blocks, col_blocks, mm_mode,
-                         g_pack_only_ncta);
-    return UH_OK;
-  }
-  auto* o = new (std::nothrow) uh_op();
-  if (!o) return fail(UH_ENOMEM, "host allocation");
-  o->c128 = c128;
-  o->n = T.n;
-  o->ncta = ncta;
-  o->device = device;
-  if ((rc = upload_program(o, P, T))) { free_op(o); delete o; return rc; }
-
-  // Statistics.
-  fill_common_stats(o, T, d->dense, precision);
+// Sizes of one UH operator and of its product (uh_stats_t); elem_bytes s.
+void uh_fill_stats(const UHPrep& u, int32_t precision, int s, uh_stats_t* st) {
+  const uh_desc* d = u.d;
+  const Tree& T = u.T;
+  st->n = T.n;
+  st->precision = precision;
+  st->elem_bytes = s;
+  st->n_dense = d->dense.n_dense;
+  int64_t ed = 0;
+  for (int64_t i = 0; i < d->dense.n_dense; ++i) ed += T.size[d->dense.row_cl[i]] * T.size[d->dense.col_cl[i]];
+  st->E_D = ed;
   int64_t eu = 0, ev = 0, es = 0, nrb = 0, ncb = 0, srr = 0, scr = 0;
   int32_t rmin = INT32_MAX, rmax = 0;
   int64_t rsum = 0, rcnt = 0;
@@ -751,33 +758,93 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   int32_t csp = 0;
   for (int32_t c = 0; c < T.ncl; ++c) {
     csp = std::max(csp, std::max(rowc[c], colc[c]));
-    if (is_row[c]) {
+    if (u.is_row[c]) {
       nrb++; eu += T.size[c] * d->row_rank[c]; srr += d->row_rank[c];
       if (d->row_rank[c] > 0) { rmin = std::min(rmin, d->row_rank[c]); rmax = std::max(rmax, d->row_rank[c]); rsum += d->row_rank[c]; rcnt++; }
     }
-    if (is_col[c]) {
+    if (u.is_col[c]) {
       ncb++; ev += T.size[c] * d->col_rank[c]; scr += d->col_rank[c];
       if (d->col_rank[c] > 0) { rmin = std::min(rmin, d->col_rank[c]); rmax = std::max(rmax, d->col_rank[c]); rsum += d->col_rank[c]; rcnt++; }
     }
   }
-  o->st.n_row_bases = nrb;
-  o->st.n_col_bases = ncb;
-  o->st.n_adm = d->n_adm;
-  o->st.E_U = eu;
-  o->st.E_V = ev;
-  o->st.E_S = es;
-  o->st.sum_row_rank = srr;
-  o->st.sum_col_rank = scr;
-  o->st.rank_min = rcnt ? rmin : 0;
-  o->st.rank_max = rmax;
-  o->st.rank_mean = rcnt ? static_cast<double>(rsum) / rcnt : 0.0;
-  o->st.csp = csp;
-  o->st.algo_bytes_matvec = o->st.elem_bytes * (eu + ev + es + o->st.E_D + 2 * T.n + 2 * (srr + scr));
-  o->st.matmat_mode = -1;
+  st->n_row_bases = nrb;
+  st->n_col_bases = ncb;
+  st->n_adm = d->n_adm;
+  st->E_U = eu;
+  st->E_V = ev;
+  st->E_S = es;
+  st->sum_row_rank = srr;
+  st->sum_col_rank = scr;
+  st->rank_min = rcnt ? rmin : 0;
+  st->rank_max = rmax;
+  st->rank_mean = rcnt ? static_cast<double>(rsum) / rcnt : 0.0;
+  st->csp = csp;
+  st->algo_bytes_matvec = s * (eu + ev + es + ed + 2 * T.n + 2 * (srr + scr));
+  st->matmat_mode = -1;
+}
+
+}  // namespace
+
+struct uh_op : OpBase {};
+struct h_op : OpBase {};
+struct uh_batch : OpBase {
+  std::vector<int64_t> offsets;  // count + 1
+};
+
+extern "C" {
+
+const char* uh_last_error(void) { return g_err.c_str(); }
+const char* uh_version(void) { return "uh-gb300 0.2 (sm_103a)"; }
+
+int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
+  g_err.clear();
+  if (!d || !out) return fail(UH_EINVAL, "null argument");
+  *out = nullptr;
+  int rc;
+  if ((rc = check_precision(precision, true))) return rc;
+  UHPrep u;
+  if ((rc = prepare_uh(d, &u))) return rc;
+  const Tree& T = u.T;
+
+  const bool c128 = precision == UH_PREC_C128;
+  int ncta = g_pack_only_ncta, device = 0;
+  if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
+  ProgramBuilder P(c128, T.n, ncta);
+  const int64_t A = P.align();
+  add_permute(P, T.n, ncta);
+  Offsets off;
+  add_uh_program(P, u, &off);
+  P.set_source_len(uh::kSrcXp, ProgramBuilder::round_up(T.n, A));
+  P.set_source_len(uh::kSrcZ1, off.x);
+  P.set_source_len(uh::kSrcZ2, off.y);
+  P.set_source_len(uh::kSrcZ3, off.z3);
+
+  const int mm_mode = precision == UH_PREC_C64_TF32 ? UH_MM_TF32 : precision == UH_PREC_C64_BF16X3 ? UH_MM_BF16X3 : -1;
+  if (g_pack_only_ncta) {
+    if (const char* e = P.finalize()) return fail(UH_EINVAL, "packing: %s", e);
+    if (const char* e = P.self_check()) return fail(UH_EINVAL, "internal packing error: %s", e);
+    if (mm_mode >= 0)
+      return build_panel(nullptr, d, T, u.tiles, u.tile_rows, u.is_row, u.is_col, u.row_blocks, u.col_blocks, mm_mode,
+                         g_pack_only_ncta);
+    return UH_OK;
+  }
+  auto* o = new (std::nothrow) uh_op();
+  if (!o) return fail(UH_ENOMEM, "host allocation");
+  o->c128 = c128;
+  o->n = T.n;
+  o->ncta = ncta;
+  o->device = device;
+  if ((rc = upload_program(o, P, T))) { free_op(o); delete o; return rc; }
+  const uh_stats_t packed = o->st;  // packing figures filled by the upload
+  uh_fill_stats(u, precision, c128 ? 16 : 8, &o->st);
+  o->st.packed_bytes = packed.packed_bytes;
+  o->st.device_bytes = packed.device_bytes;
+  o->st.n_launches = packed.n_launches;
+  o->st.n_items = packed.n_items;
   if (mm_mode >= 0) {
     int pn = 0;
     if ((rc = panel_ncta(&pn)) ||
-        (rc = build_panel(o, d, T, tiles, tile_rows, is_row, is_col, row_blocks, col_blocks, mm_mode, pn))) {
+        (rc = build_panel(o, d, T, u.tiles, u.tile_rows, u.is_row, u.is_col, u.row_blocks, u.col_blocks, mm_mode, pn))) {
       free_op(o);
       delete o;
       return rc;
@@ -960,6 +1027,141 @@ int h_stats(const h_op* op, uh_stats_t* out) {
   if (!op || !out) return fail(UH_EINVAL, "null argument");
   *out = op->st;
   return UH_OK;
+}
+
+int uh_batch_create(const uh_desc* const* descs, int32_t count, int32_t precision, uh_batch** out) {
+  g_err.clear();
+  if (!descs || !out) return fail(UH_EINVAL, "null argument");
+  *out = nullptr;
+  if (count < 1) return fail(UH_EINVAL, "count = %d", count);
+  int rc;
+  if ((rc = check_precision(precision, false))) return rc;
+  std::vector<UHPrep> preps(count);
+  int64_t total = 0;
+  for (int32_t k = 0; k < count; ++k) {
+    if (!descs[k]) return fail(UH_EINVAL, "operator %d: null descriptor", k);
+    if ((rc = prepare_uh(descs[k], &preps[k]))) {
+      const std::string msg = g_err;
+      return fail(rc, "operator %d: %s", k, msg.c_str());
+    }
+    total += preps[k].T.n;
+    if (total > INT32_MAX) return fail(UH_EINVAL, "the batch holds more than 2^31 - 1 points");
+  }
+  const bool c128 = precision == UH_PREC_C128;
+  int ncta = g_pack_only_ncta, device = 0;
+  if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
+  ProgramBuilder P(c128, total, ncta);
+  const int64_t A = P.align();
+  add_permute(P, total, ncta);
+  // The batch as one operator on the concatenated vectors: position offsets[k] + i of the
+  // cluster order is point perm_k[i] of operator k, i.e. entry offsets[k] + perm_k[i].
+  Tree all;
+  all.n = total;
+  all.perm.resize(static_cast<size_t>(total));
+  std::vector<int64_t> offsets(count + 1, 0);
+  Offsets off;
+  for (int32_t k = 0; k < count; ++k) {
+    offsets[k] = off.n;
+    for (int64_t i = 0; i < preps[k].T.n; ++i)
+      all.perm[off.n + i] = static_cast<int32_t>(off.n + preps[k].T.perm[i]);
+    add_uh_program(P, preps[k], &off);
+  }
+  offsets[count] = off.n;
+  P.set_source_len(uh::kSrcXp, ProgramBuilder::round_up(total, A));
+  P.set_source_len(uh::kSrcZ1, off.x);
+  P.set_source_len(uh::kSrcZ2, off.y);
+  P.set_source_len(uh::kSrcZ3, off.z3);
+  if (g_pack_only_ncta) {
+    if (const char* e = P.finalize()) return fail(UH_EINVAL, "packing: %s", e);
+    if (const char* e = P.self_check()) return fail(UH_EINVAL, "internal packing error: %s", e);
+    return UH_OK;
+  }
+  auto* o = new (std::nothrow) uh_batch();
+  if (!o) return fail(UH_ENOMEM, "host allocation");
+  o->c128 = c128;
+  o->n = total;
+  o->ncta = ncta;
+  o->device = device;
+  o->offsets = offsets;
+  if ((rc = upload_program(o, P, all))) { free_op(o); delete o; return rc; }
+  const uh_stats_t packed = o->st;
+  uh_stats_t sum{};
+  double rank_total = 0.0;
+  int64_t rank_count = 0;
+  sum.rank_min = INT32_MAX;
+  for (int32_t k = 0; k < count; ++k) {
+    uh_stats_t st{};
+    uh_fill_stats(preps[k], precision, c128 ? 16 : 8, &st);
+    sum.n_row_bases += st.n_row_bases;
+    sum.n_col_bases += st.n_col_bases;
+    sum.n_adm += st.n_adm;
+    sum.n_dense += st.n_dense;
+    sum.E_U += st.E_U;
+    sum.E_V += st.E_V;
+    sum.E_S += st.E_S;
+    sum.E_D += st.E_D;
+    sum.sum_row_rank += st.sum_row_rank;
+    sum.sum_col_rank += st.sum_col_rank;
+    if (st.rank_max > 0) sum.rank_min = std::min(sum.rank_min, st.rank_min);
+    sum.rank_max = std::max(sum.rank_max, st.rank_max);
+    const int64_t nb = st.n_row_bases + st.n_col_bases;
+    rank_total += st.rank_mean * static_cast<double>(nb);
+    rank_count += nb;
+    sum.csp = std::max(sum.csp, st.csp);
+    sum.algo_bytes_matvec += st.algo_bytes_matvec;
+  }
+  if (sum.rank_max == 0) sum.rank_min = 0;
+  sum.rank_mean = rank_count ? rank_total / static_cast<double>(rank_count) : 0.0;
+  sum.n = total;
+  sum.precision = precision;
+  sum.elem_bytes = c128 ? 16 : 8;
+  sum.packed_bytes = packed.packed_bytes;
+  sum.device_bytes = packed.device_bytes;
+  sum.n_launches = packed.n_launches;
+  sum.n_items = packed.n_items;
+  sum.matmat_mode = -1;
+  o->st = sum;
+  *out = o;
+  return UH_OK;
+}
+
+int uh_batch_destroy(uh_batch* batch) {
+  if (!batch) return UH_OK;
+  cudaDeviceSynchronize();
+  free_op(batch);
+  delete batch;
+  return UH_OK;
+}
+
+int uh_batch_offsets(const uh_batch* batch, int64_t* offsets) {
+  if (!batch || !offsets) return fail(UH_EINVAL, "null argument");
+  std::copy(batch->offsets.begin(), batch->offsets.end(), offsets);
+  return UH_OK;
+}
+
+int uh_batch_matvec(uh_batch* batch, const void* x, void* y, void* stream) {
+  if (!batch) return fail(UH_EINVAL, "null batch");
+  return run_matvec(batch, x, y, stream);
+}
+
+int uh_batch_check(uh_batch* batch, void* stream) {
+  if (!batch) return fail(UH_EINVAL, "null batch");
+  return check_status(batch, stream);
+}
+
+int uh_batch_stats(const uh_batch* batch, uh_stats_t* out) {
+  if (!batch || !out) return fail(UH_EINVAL, "null argument");
+  *out = batch->st;
+  return UH_OK;
+}
+
+int uh_batch_pack_check(const uh_desc* const* descs, int32_t count, int32_t precision, int32_t ncta) {
+  if (ncta < 1) return fail(UH_EINVAL, "ncta = %d", ncta);
+  g_pack_only_ncta = ncta;
+  uh_batch* o = nullptr;
+  const int rc = uh_batch_create(descs, count, precision, &o);
+  g_pack_only_ncta = 0;
+  return rc;
 }
 
 int uh_pack_check(const uh_desc* desc, int32_t precision, int32_t ncta) {

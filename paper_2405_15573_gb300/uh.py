@@ -90,6 +90,13 @@ for _name, _args in [
     ("h_pack_check", [C.POINTER(HDesc), _i32, _i32]),
     ("h_check", [_p, _p]),
     ("uh_block_apply_noalloc", [_i64, _i64, _i32, _i32, _p, _i64, _p, _i64, _p, _i64, _p, _p, _i32, _p]),
+    ("uh_batch_create", [C.POINTER(C.POINTER(UHDesc)), _i32, _i32, C.POINTER(_p)]),
+    ("uh_batch_destroy", [_p]),
+    ("uh_batch_offsets", [_p, C.POINTER(_i64)]),
+    ("uh_batch_matvec", [_p, _p, _p, _p]),
+    ("uh_batch_check", [_p, _p]),
+    ("uh_batch_stats", [_p, C.POINTER(Stats)]),
+    ("uh_batch_pack_check", [C.POINTER(C.POINTER(UHDesc)), _i32, _i32, _i32]),
 ]:
     getattr(lib, _name).argtypes = _args
     getattr(lib, _name).restype = C.c_int
@@ -316,6 +323,65 @@ class UHOp(_Op):
     def from_arrays(cls, arrays: dict, precision: str = "c64"):
         desc, keep = uh_desc_from_arrays(arrays)
         return cls(desc, precision)
+
+
+def _desc_array(descs):
+    return (C.POINTER(UHDesc) * len(descs))(*[C.pointer(d) for d in descs])
+
+
+class UHBatch:
+    """Many independent UH operators applied in one launch (uh.h, uh_batch_*). x and y of
+    matvec() hold the operators' vectors back to back: operator k at offsets[k]:offsets[k+1]."""
+
+    def __init__(self, descs, precision: str = "c64"):
+        self.precision = precision
+        self.c128 = precision == "c128"
+        self.count = len(descs)
+        h = _p()
+        check(lib.uh_batch_create(_desc_array(descs), self.count, _PREC[precision], C.byref(h)),
+              "uh_batch_create")
+        self.handle = h
+        off = (_i64 * (self.count + 1))()
+        check(lib.uh_batch_offsets(self.handle, off), "uh_batch_offsets")
+        self.offsets = np.array(off[:], dtype=np.int64)
+        self.n = int(self.offsets[-1])
+
+    @classmethod
+    def from_arrays(cls, arrays_list, precision: str = "c64"):
+        built = [uh_desc_from_arrays(a) for a in arrays_list]
+        return cls([d for d, _ in built], precision)
+
+    def stats(self) -> dict:
+        s = Stats()
+        check(lib.uh_batch_stats(self.handle, C.byref(s)), "uh_batch_stats")
+        return s.as_dict()
+
+    def matvec(self, x, y=None, stream=None):
+        import torch
+        want = torch.complex128 if self.c128 else torch.complex64
+        if not x.is_cuda or x.dtype != want or x.shape[0] != self.n or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous CUDA tensor of {self.n} {want}")
+        if y is None:
+            y = torch.empty_like(x)
+        if not y.is_cuda or y.dtype != want or y.shape[0] != self.n or not y.is_contiguous():
+            raise ValueError(f"y must be a contiguous CUDA tensor of {self.n} {want}")
+        check(lib.uh_batch_matvec(self.handle, x.data_ptr(), y.data_ptr(), _stream_handle(stream)),
+              "uh_batch_matvec")
+        return y
+
+    def check(self, stream=None):
+        check(lib.uh_batch_check(self.handle, _stream_handle(stream)), "uh_batch_check")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.uh_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class HOp(_Op):

@@ -135,3 +135,44 @@ def test_multi_rhs_packing_self_check_passes(uh, prec, ncta, case):
     assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()
     hd, hkeep = uh.h_desc_from_arrays(h_arrays(h))
     assert uh.lib.h_pack_check(C.byref(hd), prec, ncta) == uh.UH_EINVAL
+
+
+BATCH_CASES = [(512, 3.0, 16, 1e-6), (1000, 6.0, 24, 1e-5), (97, 3.0, 16, 1e-6), (40, 3.0, 64, 1e-6),
+               (2048, 4.0, 32, 1e-6)]
+
+
+def _batch_arrays():
+    out = []
+    for n, k, leaf, eps in BATCH_CASES:
+        axes, noise = ((1.0, 0.7, 0.4), 0.01) if n == 1000 else ((1.0, 1.0, 1.0), 0.0)
+        _, _, hf, h, op = oracle_ops(n, k, leaf, 1.0, eps, 1e-8, axes, noise)
+        out.append(uh_arrays(op))
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("ncta", [152, 7, 1])
+def test_batch_packing_self_check_passes(uh, prec, ncta):
+    """Five operators of uneven size (one all dense, odd sizes) packed as one device program,
+    every kernel address checked, without a GPU."""
+    built = [uh.uh_desc_from_arrays(a) for a in _batch_arrays()]
+    arr = uh._desc_array([d for d, _ in built])
+    rc = uh.lib.uh_batch_pack_check(arr, len(built), prec, ncta)
+    assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()
+
+
+def test_batch_rejects_bad_operator_and_precision(uh):
+    arrays = _batch_arrays()
+    bad = dict(arrays[2])
+    p = bad["perm"].copy()
+    p[0] = p[1]
+    bad["perm"] = p
+    arrays[2] = bad
+    built = [uh.uh_desc_from_arrays(a) for a in arrays]
+    arr = uh._desc_array([d for d, _ in built])
+    assert uh.lib.uh_batch_pack_check(arr, len(built), 1, 7) == uh.UH_EINVAL
+    assert "operator 2" in uh.lib.uh_last_error().decode()
+    good = [uh.uh_desc_from_arrays(a) for a in _batch_arrays()[:2]]
+    arr = uh._desc_array([d for d, _ in good])
+    assert uh.lib.uh_batch_pack_check(arr, 2, uh.UH_PREC_C64_TF32, 7) == uh.UH_EINVAL
+    assert uh.lib.uh_batch_pack_check(arr, 0, 1, 7) == uh.UH_EINVAL
