@@ -1,7 +1,7 @@
 // Streaming matvec kernel (sm_103a): one persistent launch per UH or H matrix-vector product.
 // Layout of the work and the dependency rules: uh_stream.h.
 //
-// Roles in a CTA of 288 threads:
+// Roles in a CTA of 320 threads:
 //  - producer (lane 0 of warp 8): streams the CTA's item descriptors into a shared-memory ring;
 //    per item waits for its stage to be free, copies the descriptor into the stage's slot, arms
 //    the stage's full barrier with the byte count, copies the tile with one TMA bulk copy and,
@@ -11,7 +11,8 @@
 //    into per-thread accumulators (thread = 16-byte row slice x column group), release the
 //    stage; at the end of a chunk reduce the column groups in a fixed tree order, add the
 //    near-field base if the chunk has one, write the outputs and, for chunks other CTAs wait on,
-//    add to the group counter.
+//    hand the group counter to the publisher (each warp arrives after its own stores).
+//  - publisher (lane 0 of warp 9): per handed-over chunk, red.release on its group counter.
 // Every wait is bounded (timeout_cycles); when one runs out the CTA records it in `status`,
 // stops issuing, lets the copies in flight land, and returns.
 #include <cuda_runtime.h>
@@ -113,14 +114,63 @@ __device__ __forceinline__ const void* src_ptr(const StreamParams& p, int src) {
 }
 
 struct Bars {
-  uint64_t* full;   // tile and runs landed (1 arrival + their bytes)
-  uint64_t* empty;  // stage consumed (one arrival per consumer warp)
-  uint64_t* desc;   // descriptor batch landed
+  uint64_t* full;       // tile and runs landed (1 arrival + their bytes)
+  uint64_t* empty;      // stage consumed (one arrival per consumer warp)
+  uint64_t* desc;       // descriptor batch landed
+  uint64_t* pub_full;   // a finished chunk's outputs stored (one arrival per consumer warp)
+  uint64_t* pub_empty;  // the publisher has taken the slot (1 arrival)
 };
 __device__ __forceinline__ Bars bars_of(unsigned char* smem) {
   uint64_t* b = reinterpret_cast<uint64_t*>(smem + kSmemBars);
-  return Bars{b, b + kStages, b + 2 * kStages};
+  uint64_t* q = b + 2 * kStages + kDescBatches;
+  return Bars{b, b + kStages, b + 2 * kStages, q, q + kPubRing};
 }
+
+// Consumers: hand group counter `counter` (or -1: no more) to the publisher as release number
+// `np`. Each warp arrives after its own stores (the warp barrier orders its lanes' stores before
+// lane 0's arrive); thread 0 writes the counter first. Called by whole warps; false when aborting.
+__device__ __forceinline__ bool publish(const Bars& bar, int* pub_ctr, int np, int counter, const StreamParams& p,
+                                        volatile int* abort_flag) {
+  const int k = np % kPubRing;
+  __syncwarp();
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    if (np >= kPubRing)
+      ok = wait_parity(&bar.pub_empty[k], static_cast<uint32_t>(np / kPubRing - 1) & 1u, p.timeout_cycles, abort_flag);
+    if (ok) {
+      if (threadIdx.x == 0) *reinterpret_cast<volatile int*>(pub_ctr + k) = counter;
+      mbar_arrive(&bar.pub_full[k]);
+    } else if (!*abort_flag) {
+      atomicOr(p.status, 16u);
+      *abort_flag = 1;
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Publisher: releases until the consumers hand over -1 (or the CTA aborts).
+__device__ void publisher(const StreamParams& p, unsigned char* smem) {
+  const Bars bar = bars_of(smem);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
+  const volatile int* pub_ctr = reinterpret_cast<const volatile int*>(smem + kSmemPub);
+  for (int j = 0;; ++j) {
+    const int k = j % kPubRing;
+    if (!wait_parity(&bar.pub_full[k], static_cast<uint32_t>(j / kPubRing) & 1u, p.timeout_cycles, abort_flag)) {
+      if (!*abort_flag) {
+        atomicOr(p.status, 32u);
+        *abort_flag = 1;
+      }
+      return;
+    }
+    const int c = pub_ctr[k];
+    mbar_arrive(&bar.pub_empty[k]);
+    if (c < 0) return;
+    // The consumers' stores happen before their arrives, which this thread has acquired; the
+    // release makes them visible to every CTA that acquires the counter.
+    red_release_add(p.group_done + c, 1ull);
+  }
+}
+
 
 // Orders this thread's earlier generic-proxy accesses before its later async-proxy (TMA) ones.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
@@ -228,8 +278,8 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
   constexpr int EPL = 16 / sizeof(T);
   const int tid = threadIdx.x;
   unsigned char* stages = smem;
-  T* sred = reinterpret_cast<T*>(smem + kSmemRed);
   const WorkItem* ring = reinterpret_cast<const WorkItem*>(smem + kSmemDesc);
+  int* pub_ctr = reinterpret_cast<int*>(smem + kSmemPub);
   const Bars bar = bars_of(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
   volatile int* go = abort_flag + 1;  // go[0], go[1]: leader's decision, by item parity
@@ -238,10 +288,10 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
   T acc[EPL];
   T base = T{0, 0};
   int out_idx = 0;
-  Scatter* sscat = reinterpret_cast<Scatter*>(smem + kSmemScat);
-  T* svals = reinterpret_cast<T*>(smem + kSmemVals);
   int need = 1, lanes = 1, groups = kStreamConsumers, lane = 0, g = tid, hpl = EPL;
   const int warp = tid >> 5;
+  int nchunk = 0;  // reduced chunks so far: their parity selects the chunk-end buffers
+  int np = 0;      // releases handed to the publisher
   for (int seq = 0; seq < n; ++seq) {
     const int s = seq % kStages;
     const uint32_t parity = static_cast<uint32_t>(seq / kStages) & 1u;
@@ -263,6 +313,10 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
     const int kind = sl.kind, h = sl.h, counter = sl.counter, aux = sl.aux, naux = sl.naux;
     const int64_t dst = sl.dst;
     const unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
+    const int rb = nchunk & 1;
+    T* sred = reinterpret_cast<T*>(smem + kSmemRed) + rb * (kStreamConsumers * EPL);
+    Scatter* sscat = reinterpret_cast<Scatter*>(smem + kSmemScat) + rb * 256;
+    T* svals = reinterpret_cast<T*>(smem + kSmemVals) + rb * (64 * EPL);
     if ((flags & kItemFirst) && (kind == kScatterZ1 || kind == kScatterZ2)) {
       // the chunk's scatter entries, used at its end
       for (int k = tid; k < naux && k < 256; k += kStreamConsumers) sscat[k] = p.scatter[aux + k];
@@ -316,9 +370,7 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(&bar.empty[s]);
     if (flags & kItemLast) {
-      if (kind == kPermute) {
-        consumer_sync();
-      } else {
+      if (kind != kPermute) {
         // Column groups in one warp (lanes < 32: groups g and g ^ (m / lanes) share a warp):
         // butterfly over the group bits of the lane index, fixed order.
         for (int m = lanes; m < 32; m <<= 1) {
@@ -346,8 +398,8 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
             z[dst + tid] = v;
           }
         }
-        consumer_sync();  // outputs written; sred free for the next chunk
         if (kind == kScatterZ1 || kind == kScatterZ2) {
+          consumer_sync();  // svals written
           // (entry, row) pairs over all consumer threads: each entry's rows are consecutive
           T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : p.z2);
           for (int w = tid; w < naux * h; w += kStreamConsumers) {
@@ -355,14 +407,17 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
             const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];
             if (r >= e.lo && r < e.hi) z[e.dst + r - e.lo] = svals[r];
           }
-          consumer_sync();  // svals and sscat free for the next chunk
         }
+        // sred, svals and sscat of this parity are next written two chunks on, after the next
+        // chunk end's barrier.
+        ++nchunk;
       }
-      // The barrier above orders every consumer's outputs of this chunk before thread 0's
-      // release add, which publishes them to the CTAs that acquire the counter.
-      if (tid == 0 && counter >= 0) red_release_add(p.group_done + counter, 1ull);
+      // On failure the abort flag is set; the leader's next wait then ends the loop for all.
+      if (counter >= 0) publish(bar, pub_ctr, np++, counter, p, abort_flag);
     }
   }
+  // No more releases: let the publisher finish (skipped when aborting; decided per warp).
+  if (__shfl_sync(0xffffffffu, *abort_flag ? 0 : 1, 0)) publish(bar, pub_ctr, np, -1, p, abort_flag);
 }
 
 template <typename R>
@@ -376,12 +431,18 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamP
       mbar_init(&bar.empty[s], kStreamConsumerWarps);
     }
     for (int q = 0; q < kDescBatches; ++q) mbar_init(&bar.desc[q], 1);
+    for (int q = 0; q < kPubRing; ++q) {
+      mbar_init(&bar.pub_full[q], kStreamConsumerWarps);
+      mbar_init(&bar.pub_empty[q], 1);
+    }
     for (int q = 0; q < 6; ++q) misc[q] = 0;  // abort, go[2], pf[2]
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   const int i0 = p.cta_begin[blockIdx.x], i1 = p.cta_begin[blockIdx.x + 1];
-  if (threadIdx.x >= kStreamConsumers) {
+  if (threadIdx.x >= kStreamConsumers + 32) {
+    if (threadIdx.x == kStreamConsumers + 32) publisher(p, smem);
+  } else if (threadIdx.x >= kStreamConsumers) {
     if (threadIdx.x == kStreamConsumers) producer<R>(p, i0, i1, smem);
   } else {
     consumers<R>(p, i0, i1, smem);

@@ -13,7 +13,9 @@
 // (in its producer, before copying those runs) until every chunk of the group that writes that
 // vector has finished in this call, counted by a monotonic 64-bit counter per group. A producer
 // checks a group once per call and then remembers it. Each CTA's list is ordered by group and a
-// group only waits on earlier groups, so the waits end. The near-field partial of a row tile is
+// group only waits on earlier groups, so the waits end. The release that publishes a finished
+// chunk to the other CTAs (red.release on the group counter) is issued by a publisher warp, fed
+// through a ring of mbarriers, so that its wait for the chunk's stores is off the consumers' path. The near-field partial of a row tile is
 // written and read back by the same consumer thread (its near-field and backward chunks are in
 // the same CTA), so it needs no flag.
 #pragma once
@@ -24,7 +26,8 @@ namespace uh {
 
 constexpr int kStreamConsumerWarps = 8;
 constexpr int kStreamConsumers = kStreamConsumerWarps * 32;
-constexpr int kStreamThreads = kStreamConsumers + 32;  // + producer warp
+constexpr int kStreamThreads = kStreamConsumers + 64;  // + producer warp + publisher warp
+constexpr int kPubRing = 16;  // group-counter releases in flight from consumers to the publisher
 constexpr int kStages = 6;
 constexpr int kTileBytes = 32768;       // largest tile of an item
 constexpr int kStreamMaxCols = 512;     // largest column count of an item
@@ -40,14 +43,18 @@ constexpr int kDescBatches = 8;
 constexpr int kDescRing = kDescBatch * kDescBatches;
 static_assert(kStages < kDescBatch, "consumers must be past a batch when it is refilled");
 
-// Shared-memory layout of the kernel (bytes).
-constexpr int kSmemRed = kStages * kStageBytes;                  // group reduction, one 16 B slot per consumer thread
-constexpr int kSmemDesc = kSmemRed + kStreamConsumers * 16;      // descriptor ring, 96 B each
-constexpr int kSmemScat = kSmemDesc + kDescRing * 96;            // scatter entries of the open chunk (256 x 8 B)
-constexpr int kSmemVals = kSmemScat + 256 * 8;                    // a chunk's outputs before they are scattered
-constexpr int kSmemBars = kSmemVals + 64 * 16;                    // full, empty [kStages], desc [kDescBatches]
-constexpr int kSmemMisc = kSmemBars + (2 * kStages + kDescBatches) * 8;  // abort flag, decision words
-constexpr int kStreamSmemBytes = kSmemMisc + 32;
+// Shared-memory layout of the kernel (bytes). The chunk-end buffers are double-buffered by chunk
+// parity, so a chunk end needs no barrier after its last use of them.
+constexpr int kSmemRed = kStages * kStageBytes;                  // group reduction [2], one 16 B slot per consumer thread
+constexpr int kSmemDesc = kSmemRed + 2 * kStreamConsumers * 16;  // descriptor ring, 96 B each
+constexpr int kSmemScat = kSmemDesc + kDescRing * 96;            // scatter entries of a chunk [2] (256 x 8 B)
+constexpr int kSmemVals = kSmemScat + 2 * 256 * 8;                // a chunk's outputs before they are scattered [2]
+constexpr int kSmemBars = kSmemVals + 2 * 64 * 16;                // full, empty [kStages], desc [kDescBatches],
+                                                                  // pub_full, pub_empty [kPubRing]
+constexpr int kSmemMisc = kSmemBars + (2 * kStages + kDescBatches + 2 * kPubRing) * 8;  // abort flag, decision words
+constexpr int kSmemPub = kSmemMisc + 32;                          // group counter of each release [kPubRing]
+constexpr int kStreamSmemBytes = kSmemPub + kPubRing * 4;
+static_assert(kStreamSmemBytes <= 227 * 1024, "shared memory of one CTA");
 
 // Input vectors a run can read.
 enum : int8_t { kSrcXp = 0, kSrcZ1 = 1, kSrcZ2 = 2, kSrcZ3 = 3 };
