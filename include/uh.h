@@ -242,6 +242,54 @@ int uh_batch_check(uh_batch* batch, void* stream);
  * operators, rank_mean over all bases); the packing figures are those of the batch program. */
 int uh_batch_stats(const uh_batch* batch, uh_stats_t* out);
 
+/* ---------------------------------------------------------------- serving: GMRES solves */
+/*
+ * A server runs GMRES(restart) solves A x = b with resident UH ops (the paper's application of
+ * the product: solving the boundary integral equation, Sections 1 and 7). Solves are admitted in
+ * submission order while their device workspace ((restart + 4) n complex128 values and a little
+ * more) fits in the budget and fewer than max_active run, and are advanced together in rounds
+ * (one step of every running solve per round: continuous batching). In a solve the operator's
+ * products run in its precision (complex64 storage with FP32 accumulation for UH_PREC_C64 ops);
+ * the residual r = b - A x recomputed at every restart, the Arnoldi orthogonalisation (classical
+ * Gram-Schmidt, two passes), the norms and the update x += V y run in FP64 on the GPU. A solve
+ * ends as converged only when the recomputed residual of the returned x satisfies
+ * ||b - A x|| <= tol ||b||. Its arithmetic does not depend on the other solves running with it.
+ * The server uses the device current at uh_server_create and its own stream; the ops it is
+ * given must live on that device, outlive their solves, and not be used elsewhere meanwhile.
+ */
+typedef struct uh_server uh_server;
+
+typedef struct {
+  int32_t status;       /* UH_OK, or the error that ended the solve */
+  int32_t converged;    /* 1 if ||b - A x|| <= tol ||b|| for the returned x */
+  int32_t iterations;   /* Arnoldi steps (one operator product each), all cycles */
+  int32_t restarts;     /* cycles ended by an update x += V y */
+  double rel_residual;  /* ||b - A x|| / ||b|| of the returned x (FP64 residual, product in the op's precision) */
+  double queue_s;       /* submission -> admission, seconds */
+  double latency_s;     /* submission -> completion, seconds */
+} uh_solve_info;
+
+/* max_active >= 1 solves at a time, hbm_budget_bytes for their workspaces, at most
+ * queue_capacity solves waiting for admission. */
+int uh_server_create(int32_t max_active, int64_t hbm_budget_bytes, int32_t queue_capacity, uh_server** out);
+/* Stops the server: waiting solves are dropped, running ones end with UH_ECUDA; frees everything. */
+int uh_server_destroy(uh_server* server);
+
+/*
+ * Submit the solve of op x = b; b: host array of n complex128 values (copied). tol > 0, restart in
+ * [1, 60], maxit >= 1 (Arnoldi steps). Returns a ticket, or UH_EBUSY when the solve cannot be
+ * admitted now and queue_capacity solves are already waiting, UH_EINVAL when its workspace alone
+ * exceeds the budget.
+ */
+int uh_solve_submit(uh_server* server, uh_op* op, const void* b, double tol, int32_t restart, int32_t maxit,
+                    uint64_t* ticket);
+
+/*
+ * UH_ENOTREADY while the solve waits or runs. When it has ended: fills info, copies x (host array
+ * of n complex128, may be NULL) and forgets the ticket; returns UH_OK, or the solve's error.
+ */
+int uh_solve_poll(uh_server* server, uint64_t ticket, void* x, uh_solve_info* info);
+
 /* ---------------------------------------------------------------- H operator (plain form) */
 /*
  * H-matrix (Def. 2.3): admissible block i = (adm_row[i], adm_col[i]) with rank adm_rank[i] = k_b

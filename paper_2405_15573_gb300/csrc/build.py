@@ -22,8 +22,8 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["uh_stream.cu", "uh_noalloc.cu", "uh_panel.cu"]
-CPP_SOURCES = ["uh_capi.cpp", "uh_program.cpp", "uh_build.cpp", "uh_panel_pack.cpp"]
+CU_SOURCES = ["uh_stream.cu", "uh_noalloc.cu", "uh_panel.cu", "uh_solve.cu"]
+CPP_SOURCES = ["uh_capi.cpp", "uh_program.cpp", "uh_build.cpp", "uh_panel_pack.cpp", "uh_serve.cpp"]
 
 
 def _run(cmd):
@@ -58,7 +58,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         obj = os.path.join(BUILD, s + ".o")
         objs.append(obj)
         if force or _newer([src] + headers, obj):
-            jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-Wall", "-Wno-unused-function",
+            jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-pthread", "-Wall", "-Wno-unused-function",
                          "-I", INCLUDE, "-I", HERE, "-I", os.path.join(CUDA_HOME, "include"),
                          "-c", src, "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
@@ -67,7 +67,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
                 print(out)
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        _run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp"])
+        _run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-Xcompiler", "-pthread", "-lgomp"])
         shutil.move(tmp, LIB)
     return LIB
 

@@ -1,0 +1,465 @@
+// Serving runtime: GMRES(m) solves A x = b with resident UH operators, admitted by device-memory
+// footprint and advanced together in rounds (continuous batching).
+//
+// One worker thread owns a CUDA stream. Each round it admits queued solves while the admitted
+// footprint stays within the budget and fewer than max_active are running, then issues ONE step
+// of every active solve (all asynchronous on the stream), synchronises once, and updates the
+// solves' small host-side state (Givens rotations of the Hessenberg matrix, convergence). A solve
+// is restarted GMRES with its matrix-vector products in the operator's precision (complex64
+// storage, FP32 accumulation for UH_PREC_C64 ops) and everything else in FP64 on the GPU: the
+// true residual r = b - A x at every restart, classical Gram-Schmidt applied twice for the
+// Arnoldi basis, the norms and the solution update x += V y. The restarts with the recomputed
+// FP64 residual are the refinement: a solve only stops as converged when the true residual of
+// the returned x is below the tolerance. The kernel sequence of a solve depends only on its own
+// data, so its result is the same whether it runs alone or among other solves.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "uh.h"
+#include "uh_internal.h"
+#include "uh_solve.h"
+
+using cd = std::complex<double>;
+
+namespace {
+
+#define fail uh::set_error
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+enum Phase { kStart, kArnoldi, kUpdate, kFinish, kDone };
+
+struct Solve {
+  uint64_t ticket = 0;
+  uh_op* op = nullptr;
+  int64_t n = 0;
+  bool c64 = true;
+  double tol = 1e-6;
+  int m = 30, maxit = 300;
+  std::vector<cd> b;
+  double bnorm = 0.0;
+  int64_t footprint = 0;
+  // device
+  void *V = nullptr, *x = nullptr, *db = nullptr, *w = nullptr, *v32 = nullptr, *y32 = nullptr;
+  void *h1 = nullptr, *h2 = nullptr, *y = nullptr, *part = nullptr;
+  double* scal = nullptr;
+  // pinned host
+  cd *hh1 = nullptr, *hh2 = nullptr, *hy = nullptr, *hx = nullptr;
+  double* hscal = nullptr;
+  // GMRES state
+  Phase phase = kStart;
+  bool x_zero = true;
+  int j = 0, iters = 0, restarts = 0;
+  std::vector<cd> H, g, sn;
+  std::vector<double> cs;
+  double resid = 0.0;
+  int status = UH_OK;
+  bool converged = false;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  std::vector<cd> result;
+};
+
+int64_t footprint_of(int64_t n, int m) {
+  const int64_t nb = uh::solve_partials(n);
+  return (m + 1 + 3) * n * 16 + 2 * n * 8 + 3 * (m + 2) * 16 + (m + 1) * nb * 16 + 64;
+}
+
+}  // namespace
+
+struct uh_server {
+  int device = 0;
+  int max_active = 8;
+  int64_t budget = 0, used = 0;
+  int queue_cap = 64;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Solve*> pending;
+  std::vector<Solve*> active;
+  std::map<uint64_t, std::unique_ptr<Solve>> all;  // every solve not yet collected by poll
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+};
+
+namespace {
+
+void free_solve(Solve* s) {
+  void* dev[] = {s->V, s->x, s->db, s->w, s->v32, s->y32, s->h1, s->h2, s->y, s->part, s->scal};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  void* host[] = {s->hh1, s->hh2, s->hy, s->hx, s->hscal};
+  for (void* p : host)
+    if (p) cudaFreeHost(p);
+  s->V = s->x = s->db = s->w = s->v32 = s->y32 = s->h1 = s->h2 = s->y = s->part = nullptr;
+  s->scal = nullptr;
+  s->hh1 = s->hh2 = s->hy = s->hx = nullptr;
+  s->hscal = nullptr;
+}
+
+int alloc_solve(Solve* s, cudaStream_t st) {
+  const int64_t n = s->n;
+  const int m = s->m;
+  const int64_t nb = uh::solve_partials(n);
+  auto dev = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+  auto host = [&](void** p, size_t bytes) { return cudaMallocHost(p, bytes) == cudaSuccess; };
+  bool ok = dev(&s->V, static_cast<size_t>((m + 1) * n) * 16) && dev(&s->x, n * 16) && dev(&s->db, n * 16) &&
+            dev(&s->w, n * 16) && dev(&s->v32, n * 8) && dev(&s->y32, n * 8) && dev(&s->h1, (m + 2) * 16) &&
+            dev(&s->h2, (m + 2) * 16) && dev(&s->y, (m + 2) * 16) &&
+            dev(&s->part, static_cast<size_t>((m + 1) * nb) * 16) && dev(reinterpret_cast<void**>(&s->scal), 16) &&
+            host(reinterpret_cast<void**>(&s->hh1), (m + 2) * 16) &&
+            host(reinterpret_cast<void**>(&s->hh2), (m + 2) * 16) &&
+            host(reinterpret_cast<void**>(&s->hy), (m + 2) * 16) && host(reinterpret_cast<void**>(&s->hx), n * 16) &&
+            host(reinterpret_cast<void**>(&s->hscal), 16);
+  if (!ok) {
+    cudaGetLastError();
+    free_solve(s);
+    return UH_ENOMEM;
+  }
+  if (cudaMemcpyAsync(s->db, s->b.data(), n * 16, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(s->x, 0, n * 16, st) != cudaSuccess)
+    return UH_ECUDA;
+  s->H.assign(static_cast<size_t>((m + 1) * m), cd(0, 0));
+  s->g.assign(m + 1, cd(0, 0));
+  s->cs.assign(m, 0.0);
+  s->sn.assign(m, cd(0, 0));
+  return UH_OK;
+}
+
+// The operator's product of basis or solution vector `v` (complex128) into `out` (complex128).
+int apply_op(Solve* s, const void* v, void* out, cudaStream_t st) {
+  int rc;
+  if (s->c64) {
+    if ((rc = uh::vec_d2f(v, s->v32, s->n, st))) return rc;
+    if ((rc = uh_matvec(s->op, s->v32, s->y32, st))) return rc;
+    return uh::vec_f2d(s->y32, out, s->n, st);
+  }
+  return uh_matvec(s->op, v, out, st);
+}
+
+// Kernels of the start of a cycle: V_0 = (b - A x) / ||b - A x||, the norm copied to the host.
+int issue_start(Solve* s, cudaStream_t st) {
+  int rc;
+  if (s->x_zero) {
+    if (cudaMemcpyAsync(s->V, s->db, s->n * 16, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return UH_ECUDA;
+  } else {
+    if ((rc = apply_op(s, s->x, s->w, st))) return rc;
+    if ((rc = uh::vec_residual(s->db, s->w, false, s->V, s->n, st))) return rc;
+  }
+  if ((rc = uh::vec_norm(s->V, s->n, s->part, s->scal, nullptr, st))) return rc;
+  if ((rc = uh::vec_scale(s->V, s->scal, s->V, s->n, st))) return rc;
+  return cudaMemcpyAsync(s->hscal, s->scal, 16, cudaMemcpyDeviceToHost, st) == cudaSuccess ? UH_OK : UH_ECUDA;
+}
+
+// One Arnoldi step j: w = A V_j, two passes of classical Gram-Schmidt against V_0..V_j,
+// V_{j+1} = w / ||w||; both coefficient passes and the norm copied to the host.
+int issue_arnoldi(Solve* s, cudaStream_t st) {
+  int rc;
+  const int64_t n = s->n;
+  const int cnt = s->j + 1;
+  const char* Vj = static_cast<const char*>(s->V) + static_cast<size_t>(s->j) * n * 16;
+  if ((rc = apply_op(s, Vj, s->w, st))) return rc;
+  if ((rc = uh::vec_dots(s->V, n, cnt, s->w, s->part, s->h1, false, st))) return rc;
+  if ((rc = uh::vec_combine(s->V, n, cnt, s->h1, -1.0, s->w, st))) return rc;
+  if ((rc = uh::vec_dots(s->V, n, cnt, s->w, s->part, s->h2, false, st))) return rc;
+  if ((rc = uh::vec_combine(s->V, n, cnt, s->h2, -1.0, s->w, st))) return rc;
+  if ((rc = uh::vec_norm(s->w, n, s->part, s->scal, nullptr, st))) return rc;
+  char* Vn = static_cast<char*>(s->V) + static_cast<size_t>(cnt) * n * 16;
+  if ((rc = uh::vec_scale(s->w, s->scal, Vn, n, st))) return rc;
+  if (cudaMemcpyAsync(s->hh1, s->h1, cnt * 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(s->hh2, s->h2, cnt * 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(s->hscal, s->scal, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return UH_ECUDA;
+  return UH_OK;
+}
+
+// x += V_0..V_{cnt-1} y (y from the host), then the next cycle's start.
+int issue_update(Solve* s, int cnt, cudaStream_t st) {
+  int rc;
+  if (cudaMemcpyAsync(s->y, s->hy, cnt * 16, cudaMemcpyHostToDevice, st) != cudaSuccess) return UH_ECUDA;
+  if ((rc = uh::vec_combine(s->V, s->n, cnt, s->y, 1.0, s->x, st))) return rc;
+  s->x_zero = false;
+  return issue_start(s, st);
+}
+
+int issue_finish(Solve* s, cudaStream_t st) {
+  return cudaMemcpyAsync(s->hx, s->x, s->n * 16, cudaMemcpyDeviceToHost, st) == cudaSuccess ? UH_OK : UH_ECUDA;
+}
+
+int issue(Solve* s, cudaStream_t st) {
+  switch (s->phase) {
+    case kStart: return issue_start(s, st);
+    case kArnoldi: return issue_arnoldi(s, st);
+    case kUpdate: return issue_update(s, s->j + 1, st);
+    case kFinish: return issue_finish(s, st);
+    default: return UH_OK;
+  }
+}
+
+// After the start of a cycle (or an update followed by a start): the true residual decides.
+void after_start(Solve* s) {
+  s->resid = s->hscal[0];
+  const double rel = s->bnorm > 0 ? s->resid / s->bnorm : 0.0;
+  if (rel <= s->tol || s->iters >= s->maxit || s->resid == 0.0) {
+    s->converged = rel <= s->tol;
+    s->phase = kFinish;
+    return;
+  }
+  std::fill(s->g.begin(), s->g.end(), cd(0, 0));
+  s->g[0] = cd(s->resid, 0);
+  s->j = 0;
+  s->phase = kArnoldi;
+}
+
+// After Arnoldi step j: rotate the new Hessenberg column, update the residual estimate.
+void after_arnoldi(Solve* s) {
+  const int j = s->j, m = s->m;
+  cd* col = &s->H[static_cast<size_t>(j) * (m + 1)];
+  for (int i = 0; i <= j; ++i) col[i] = s->hh1[i] + s->hh2[i];
+  const double hnext = s->hscal[0];
+  col[j + 1] = cd(hnext, 0);
+  for (int i = 0; i < j; ++i) {
+    const cd a = col[i], b = col[i + 1];
+    col[i] = s->cs[i] * a + s->sn[i] * b;
+    col[i + 1] = -std::conj(s->sn[i]) * a + s->cs[i] * b;
+  }
+  const cd a = col[j], b = col[j + 1];
+  const double rho = std::sqrt(std::norm(a) + std::norm(b));
+  if (std::abs(a) == 0.0) {
+    s->cs[j] = 0.0;
+    s->sn[j] = cd(1, 0);
+    col[j] = b;
+  } else {
+    const cd ph = a / std::abs(a);
+    s->cs[j] = std::abs(a) / rho;
+    s->sn[j] = ph * std::conj(b) / rho;
+    col[j] = ph * rho;
+  }
+  col[j + 1] = cd(0, 0);
+  s->g[j + 1] = -std::conj(s->sn[j]) * s->g[j];
+  s->g[j] = s->cs[j] * s->g[j];
+  s->iters++;
+  const double est = std::abs(s->g[j + 1]) / (s->bnorm > 0 ? s->bnorm : 1.0);
+  if (est <= s->tol || j + 1 == m || s->iters >= s->maxit || hnext == 0.0) {
+    // y = R^{-1} g, R the rotated (j+1) x (j+1) upper triangle.
+    for (int i = j; i >= 0; --i) {
+      cd v = s->g[i];
+      for (int k = i + 1; k <= j; ++k) v -= s->H[static_cast<size_t>(k) * (m + 1) + i] * s->hy[k];
+      const cd d = s->H[static_cast<size_t>(i) * (m + 1) + i];
+      s->hy[i] = d != cd(0, 0) ? v / d : cd(0, 0);
+    }
+    s->restarts++;
+    s->phase = kUpdate;
+  } else {
+    s->j = j + 1;
+  }
+}
+
+void after(Solve* s) {
+  switch (s->phase) {
+    case kStart:
+    case kUpdate: after_start(s); break;
+    case kArnoldi: after_arnoldi(s); break;
+    case kFinish:
+      s->result.assign(s->hx, s->hx + s->n);
+      s->phase = kDone;
+      break;
+    default: break;
+  }
+}
+
+void worker_main(uh_server* sv) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    std::vector<Solve*> round;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      while (!sv->pending.empty() && static_cast<int>(sv->active.size()) < sv->max_active &&
+             sv->used + sv->pending.front()->footprint <= sv->budget) {
+        Solve* s = sv->pending.front();
+        sv->pending.pop_front();
+        sv->used += s->footprint;
+        s->t_admit = now_s();
+        sv->active.push_back(s);
+      }
+      if (sv->active.empty()) {
+        if (sv->stop) return;
+        sv->cv.wait_for(lk, std::chrono::milliseconds(20));
+        continue;
+      }
+      if (sv->stop) {
+        for (Solve* s : sv->active) {
+          free_solve(s);
+          s->status = UH_ECUDA;
+          s->phase = kDone;
+        }
+        sv->active.clear();
+        return;
+      }
+      round = sv->active;
+    }
+    // Allocate new solves' workspaces, then issue one step of every active solve.
+    for (Solve* s : round) {
+      if (s->phase == kDone) continue;
+      if (!s->V) {
+        const int rc = alloc_solve(s, sv->stream);
+        if (rc) {
+          s->status = rc;
+          s->phase = kDone;
+          continue;
+        }
+      }
+      const int rc = issue(s, sv->stream);
+      if (rc) {
+        s->status = rc;
+        s->phase = kDone;
+      }
+    }
+    const cudaError_t e = cudaStreamSynchronize(sv->stream);
+    // Bounded waits of the products that ran out (a GPU that could not run a product's CTAs
+    // together) end the solves that used that op.
+    std::vector<uh_op*> checked;
+    for (Solve* s : round) {
+      if (s->phase == kDone || std::find(checked.begin(), checked.end(), s->op) != checked.end()) continue;
+      checked.push_back(s->op);
+      if (uh_check(s->op, sv->stream) != UH_OK)
+        for (Solve* t : round)
+          if (t->op == s->op) { t->status = UH_ETIMEOUT; t->phase = kDone; }
+    }
+    for (Solve* s : round) {
+      if (e != cudaSuccess && s->phase != kDone) {
+        s->status = UH_ECUDA;
+        s->phase = kDone;
+      }
+      if (s->phase != kDone) after(s);
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    std::vector<Solve*> still;
+    for (Solve* s : sv->active) {
+      if (s->phase == kDone) {
+        s->t_done = now_s();
+        free_solve(s);
+        sv->used -= s->footprint;
+      } else {
+        still.push_back(s);
+      }
+    }
+    sv->active.swap(still);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int uh_server_create(int32_t max_active, int64_t hbm_budget_bytes, int32_t queue_capacity, uh_server** out) {
+  if (!out) return fail(UH_EINVAL, "null argument");
+  *out = nullptr;
+  if (max_active < 1 || hbm_budget_bytes < 1 || queue_capacity < 1)
+    return fail(UH_EINVAL, "max_active %d, budget %lld, queue capacity %d must be >= 1", max_active,
+                (long long)hbm_budget_bytes, queue_capacity);
+  auto* sv = new (std::nothrow) uh_server();
+  if (!sv) return fail(UH_ENOMEM, "host allocation");
+  sv->max_active = max_active;
+  sv->budget = hbm_budget_bytes;
+  sv->queue_cap = queue_capacity;
+  if (cudaGetDevice(&sv->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete sv;
+    return fail(UH_ECUDA, "stream creation failed");
+  }
+  sv->worker = std::thread(worker_main, sv);
+  *out = sv;
+  return UH_OK;
+}
+
+int uh_server_destroy(uh_server* sv) {
+  if (!sv) return UH_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    sv->pending.clear();
+  }
+  sv->cv.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  cudaStreamDestroy(sv->stream);
+  delete sv;
+  return UH_OK;
+}
+
+int uh_solve_submit(uh_server* sv, uh_op* op, const void* b, double tol, int32_t restart, int32_t maxit,
+                    uint64_t* ticket) {
+  if (!sv || !op || !b || !ticket) return fail(UH_EINVAL, "null argument");
+  if (!(tol > 0.0) || restart < 1 || restart > 60 || maxit < 1)
+    return fail(UH_EINVAL, "tol %g, restart %d (1..60), maxit %d", tol, restart, maxit);
+  uh_stats_t st{};
+  int rc;
+  if ((rc = uh_stats(op, &st))) return rc;
+  auto s = std::make_unique<Solve>();
+  s->op = op;
+  s->n = st.n;
+  s->c64 = st.precision != UH_PREC_C128;
+  s->tol = tol;
+  s->m = restart;
+  s->maxit = maxit;
+  s->b.assign(static_cast<const cd*>(b), static_cast<const cd*>(b) + st.n);
+  double nb = 0.0;
+  for (const cd& v : s->b) nb += std::norm(v);
+  s->bnorm = std::sqrt(nb);
+  s->footprint = footprint_of(st.n, restart);
+  s->t_submit = now_s();
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (s->footprint > sv->budget)
+    return fail(UH_EINVAL, "a solve of n = %lld needs %lld bytes, above the budget %lld", (long long)st.n,
+                (long long)s->footprint, (long long)sv->budget);
+  const bool fits_now = static_cast<int>(sv->active.size()) < sv->max_active && sv->pending.empty() &&
+                        sv->used + s->footprint <= sv->budget;
+  if (!fits_now && static_cast<int>(sv->pending.size()) >= sv->queue_cap)
+    return fail(UH_EBUSY, "admission limit reached and %d solves queued", sv->queue_cap);
+  s->ticket = sv->next_ticket++;
+  *ticket = s->ticket;
+  sv->pending.push_back(s.get());
+  sv->all[s->ticket] = std::move(s);
+  sv->cv.notify_all();
+  return UH_OK;
+}
+
+int uh_solve_poll(uh_server* sv, uint64_t ticket, void* x, uh_solve_info* info) {
+  if (!sv) return fail(UH_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) return fail(UH_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+  Solve* s = it->second.get();
+  const bool queued = std::find(sv->pending.begin(), sv->pending.end(), s) != sv->pending.end();
+  const bool running = std::find(sv->active.begin(), sv->active.end(), s) != sv->active.end();
+  if (queued || running || s->phase != kDone) return UH_ENOTREADY;
+  if (info) {
+    info->status = s->status;
+    info->converged = s->converged ? 1 : 0;
+    info->iterations = s->iters;
+    info->restarts = s->restarts;
+    info->rel_residual = s->bnorm > 0 ? s->resid / s->bnorm : 0.0;
+    info->queue_s = s->t_admit - s->t_submit;
+    info->latency_s = s->t_done - s->t_submit;
+  }
+  if (x && s->status == UH_OK) std::memcpy(x, s->result.data(), s->result.size() * sizeof(cd));
+  const int status = s->status;
+  sv->all.erase(it);
+  return status == UH_OK ? UH_OK : fail(status, "solve %llu failed", (unsigned long long)ticket);
+}
+
+}  // extern "C"

@@ -97,6 +97,10 @@ for _name, _args in [
     ("uh_batch_check", [_p, _p]),
     ("uh_batch_stats", [_p, C.POINTER(Stats)]),
     ("uh_batch_pack_check", [C.POINTER(C.POINTER(UHDesc)), _i32, _i32, _i32]),
+    ("uh_server_create", [_i32, _i64, _i32, C.POINTER(_p)]),
+    ("uh_server_destroy", [_p]),
+    ("uh_solve_submit", [_p, _p, _p, C.c_double, _i32, _i32, C.POINTER(C.c_uint64)]),
+    ("uh_solve_poll", [_p, C.c_uint64, _p, _p]),
 ]:
     getattr(lib, _name).argtypes = _args
     getattr(lib, _name).restype = C.c_int
@@ -375,6 +379,72 @@ class UHBatch:
     def close(self):
         if getattr(self, "handle", None):
             lib.uh_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("status", _i32), ("converged", _i32), ("iterations", _i32), ("restarts", _i32),
+                ("rel_residual", C.c_double), ("queue_s", C.c_double), ("latency_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Server:
+    """GMRES serving runtime (uh.h, uh_server_* / uh_solve_*): submit(op, b) returns a ticket,
+    poll(ticket) returns None until the solve has ended, then (x, info)."""
+
+    def __init__(self, max_active: int = 8, hbm_budget: int = 8 << 30, queue_capacity: int = 64):
+        h = _p()
+        check(lib.uh_server_create(max_active, hbm_budget, queue_capacity, C.byref(h)), "uh_server_create")
+        self.handle = h
+        self._n = {}
+
+    def submit(self, op, b, tol: float = 1e-6, restart: int = 30, maxit: int = 300):
+        """Ticket of the solve op x = b (b: n complex values, copied), or None if the server is
+        busy (UH_EBUSY)."""
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        if b.shape != (op.n,):
+            raise ValueError(f"b must have {op.n} entries")
+        t = C.c_uint64()
+        rc = lib.uh_solve_submit(self.handle, op.handle, b.ctypes.data, float(tol), restart, maxit, C.byref(t))
+        if rc == UH_EBUSY:
+            return None
+        check(rc, "uh_solve_submit")
+        self._n[t.value] = op.n
+        return t.value
+
+    def poll(self, ticket: int):
+        n = self._n.get(ticket)
+        x = np.empty(n, np.complex128) if n is not None else None
+        info = SolveInfo()
+        rc = lib.uh_solve_poll(self.handle, ticket, None if x is None else x.ctypes.data, C.byref(info))
+        if rc == UH_ENOTREADY:
+            return None
+        self._n.pop(ticket, None)
+        check(rc, "uh_solve_poll")
+        return x, info.as_dict()
+
+    def wait(self, ticket: int, timeout: float = 60.0, interval: float = 1e-4):
+        import time
+        t0 = time.time()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.time() - t0 > timeout:
+                raise TimeoutError(f"solve {ticket} not done after {timeout} s")
+            time.sleep(interval)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.uh_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

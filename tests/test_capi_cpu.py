@@ -176,3 +176,15 @@ def test_batch_rejects_bad_operator_and_precision(uh):
     arr = uh._desc_array([d for d, _ in good])
     assert uh.lib.uh_batch_pack_check(arr, 2, uh.UH_PREC_C64_TF32, 7) == uh.UH_EINVAL
     assert uh.lib.uh_batch_pack_check(arr, 0, 1, 7) == uh.UH_EINVAL
+
+
+def test_server_argument_checks(uh):
+    h = C.c_void_p()
+    assert uh.lib.uh_server_create(0, 1 << 30, 4, C.byref(h)) == uh.UH_EINVAL
+    assert uh.lib.uh_server_create(4, 0, 4, C.byref(h)) == uh.UH_EINVAL
+    assert uh.lib.uh_server_create(4, 1 << 30, 0, C.byref(h)) == uh.UH_EINVAL
+    assert h.value is None
+    assert uh.lib.uh_server_destroy(None) == uh.UH_OK
+    t = C.c_uint64()
+    assert uh.lib.uh_solve_submit(None, None, None, 1e-6, 30, 100, C.byref(t)) == uh.UH_EINVAL
+    assert uh.lib.uh_solve_poll(None, 1, None, None) == uh.UH_EINVAL

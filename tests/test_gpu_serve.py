@@ -1,0 +1,98 @@
+"""GPU tests of the serving runtime (uh_server_* / uh_solve_*): GMRES(30) solves of the collocation
+operator with its products in complex64 (FP32 accumulation) and the residual, orthogonalisation
+and update in FP64. Checked against the FP64 oracle: the true residual ||b - A x|| / ||b|| with
+the oracle's own UH operator, and the solution of the dense system of that operator. A solve's
+result must be bitwise the same alone and among other solves."""
+import numpy as np
+import pytest
+
+from oracle import uh_oracle as O
+from paper_2405_15573_gb300 import inputs as I
+from tests.uh_testutil import oracle_ops, relerr, uh_arrays
+
+pytestmark = pytest.mark.gpu
+
+SPHERE = (2048, 4.0, 32, 1.0, 1e-6, 1e-8, (1.0, 1.0, 1.0), 0.0)
+ELLIPSOID = (1000, 6.0, 24, 1.0, 1e-5, 1e-8, (1.0, 0.7, 0.4), 0.01)
+
+
+@pytest.fixture(scope="module")
+def U():
+    import torch  # noqa: F401
+    from paper_2405_15573_gb300 import uh
+    return uh
+
+
+@pytest.fixture(scope="module")
+def ops(U):
+    a = oracle_ops(*SPHERE)[4]
+    b = oracle_ops(*ELLIPSOID)[4]
+    return {"sphere": (a, U.UHOp.from_arrays(uh_arrays(a), "c64"), U.UHOp.from_arrays(uh_arrays(a), "c128")),
+            "ellipsoid": (b, U.UHOp.from_arrays(uh_arrays(b), "c64"), None)}
+
+
+def test_solve_converges_against_fp64_operator(U, ops):
+    uh, op64, _ = ops["sphere"]
+    srv = U.Server(max_active=4)
+    b = I.complex_normal(uh.tree.n, 3)
+    t = srv.submit(op64, b, tol=1e-6, restart=30, maxit=300)
+    x, info = srv.wait(t)
+    assert info["status"] == U.UH_OK and info["converged"] == 1
+    assert info["rel_residual"] <= 1e-6
+    true_res = np.linalg.norm(b - O.uh_matvec(uh, x)) / np.linalg.norm(b)
+    assert true_res <= 2e-6, true_res  # c64 storage of the operator adds ~1e-7
+    xref = np.linalg.solve(O.uh_to_dense(uh), b)
+    assert relerr(x, xref) <= 1e-5
+    assert info["latency_s"] >= info["queue_s"] >= 0
+    srv.close()
+
+
+def test_solve_complex128_op_reaches_tight_tolerance(U, ops):
+    uh, _, op128 = ops["sphere"]
+    srv = U.Server()
+    b = I.complex_normal(uh.tree.n, 4)
+    x, info = srv.wait(srv.submit(op128, b, tol=1e-11, restart=20, maxit=400))
+    assert info["converged"] == 1 and info["restarts"] >= 1
+    assert np.linalg.norm(b - O.uh_matvec(uh, x)) / np.linalg.norm(b) <= 1e-10
+    srv.close()
+
+
+def test_same_result_alone_and_in_a_mix(U, ops):
+    uh, op64, _ = ops["sphere"]
+    uh2, op2, _ = ops["ellipsoid"]
+    b = I.complex_normal(uh.tree.n, 5)
+    srv = U.Server(max_active=8)
+    x_alone, info_alone = srv.wait(srv.submit(op64, b))
+    others = [srv.submit(op2, I.complex_normal(uh2.tree.n, 20 + k), tol=1e-7) for k in range(4)]
+    others += [srv.submit(op64, I.complex_normal(uh.tree.n, 30 + k), restart=10) for k in range(2)]
+    mine = srv.submit(op64, b)
+    x_mix, info_mix = srv.wait(mine)
+    for t in others:
+        xo, io = srv.wait(t)
+        assert io["converged"] == 1
+    assert np.array_equal(x_alone, x_mix)
+    assert info_alone["iterations"] == info_mix["iterations"]
+    srv.close()
+
+
+def test_admission_busy_and_errors(U, ops):
+    uh, op64, _ = ops["sphere"]
+    b = I.complex_normal(uh.tree.n, 6)
+    srv = U.Server(max_active=1, queue_capacity=1)
+    tickets = [srv.submit(op64, b) for _ in range(3)]
+    assert None in tickets[1:]  # one running or waiting, one waiting, the rest refused (UH_EBUSY)
+    first = tickets[0]
+    assert srv.poll(first) is None or True  # may already be done on a fast GPU
+    for t in tickets:
+        if t is not None:
+            x, info = srv.wait(t)
+            assert info["converged"] == 1
+    with pytest.raises(U.UHError) as e:
+        srv.poll(10 ** 9)
+    assert e.value.code == U.UH_EINVAL
+    small = U.Server(hbm_budget=1 << 20)
+    with pytest.raises(U.UHError) as e:
+        small.submit(op64, b)  # workspace above the budget
+    assert e.value.code == U.UH_EINVAL
+    small.close()
+    srv.close()
