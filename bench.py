@@ -18,6 +18,11 @@ side (complex normal, seed 0). The operator is built on the host by the library'
   cpu_baseline  the FP64 oracle's UH matvec on the same operator, timed on one host core in a
             spawned child process, also giving the relative error of the GPU result.
 
+  serving   GMRES(30) solves from a pool of 8 resident operators (N up to 16384) with Poisson
+            arrivals at 200 and 1000 per second: solve latency p50 / p99 and solves per second.
+
+`--serve` runs the serving sweep alone (pool of 64 operators, N up to 65536, six arrival rates by
+default); `--batched` times 256 independent operators in one launch against one launch each.
 `--impl reference` times that oracle matvec alone (the reference arm), on the operator made by
 the host builder. Under torchrun every
 rank runs its own replica (the product has no exchange step to shard), rank 0 prints.
@@ -301,6 +306,104 @@ class _MatmatStep:
         self.op.matmat(self.X, self.Y, mode=self.mode)
 
 
+def build_models(workloads, threads=8):
+    """Host-side builds of several operators at once (the builder releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2405_15573_gb300 import uh as U
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda w: U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca,
+                                                      nthreads=2), workloads))
+
+
+def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30):
+    """GMRES(restart) solves served from a pool of resident complex64 UH operators (uh_server):
+    per arrival rate, `requests` solves with Poisson arrivals, each on a random operator of the
+    pool with a seeded right-hand side. Latency = submission to completion (library clock);
+    throughput = completed solves / wall time from the first submission to the last completion."""
+    from paper_2405_15573_gb300 import inputs as I
+    from paper_2405_15573_gb300 import uh as U
+    pool = I.serving_pool(pool_count, n_hi=n_hi)
+    t0 = time.time()
+    models = build_models(pool)
+    ops = [m.uh_op("c64") for m in models]
+    for m in models:
+        m.close()
+    build_s = time.time() - t0
+    srv = U.Server(max_active=32, hbm_budget=32 << 30, queue_capacity=1 << 20)
+    for o, w in zip(ops, pool):  # one solve per operator before timing
+        srv.wait(srv.submit(o, I.complex_normal(w.n, 7), tol=tol, restart=restart))
+    out = {"pool": pool_count, "n_range": [min(w.n for w in pool), max(w.n for w in pool)],
+           "operator_bytes_c64": int(sum(o.stats()["algo_bytes_matvec"] for o in ops)),
+           "build_s": round(build_s, 1), "tol": tol, "restart": restart, "rates": {}}
+    for lam in rates:
+        arr = I.poisson_arrivals(lam, requests, seed=int(lam))
+        which = np.random.default_rng(int(lam) + 1).integers(0, pool_count, size=requests)
+        bs = [I.complex_normal(pool[k].n, 100 + i) for i, k in enumerate(which)]
+        tickets = []
+        start = time.perf_counter()
+        for i in range(requests):
+            dt = arr[i] - (time.perf_counter() - start)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(ops[which[i]], bs[i], tol=tol, restart=restart, maxit=20 * restart))
+        res = [srv.wait(t, timeout=600) for t in tickets if t is not None]
+        wall = time.perf_counter() - start
+        lat = np.array([r[1]["latency_s"] for r in res])
+        out["rates"][str(int(lam))] = {
+            "requests": requests, "refused": sum(t is None for t in tickets),
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "solves_per_s": len(res) / wall,
+            "iterations_mean": float(np.mean([r[1]["iterations"] for r in res])),
+            "converged_frac": float(np.mean([r[1]["converged"] for r in res])),
+            "max_rel_residual": float(max(r[1]["rel_residual"] for r in res))}
+    srv.close()
+    del ops
+    return out
+
+
+def batched_figures(count, steps):
+    """One launch for `count` independent complex64 UH operators (uh_batch) against one launch
+    per operator (uh_matvec each), back to back, CUDA events; operator products per second."""
+    import torch
+    from paper_2405_15573_gb300 import inputs as I
+    from paper_2405_15573_gb300 import uh as U
+    pool = I.batched_pool(count)
+    t0 = time.time()
+    models = build_models(pool)
+    build_s = time.time() - t0
+    t0 = time.time()
+    batch = U.UHBatch([m.uh_desc() for m in models], "c64")
+    pack_s = time.time() - t0
+    ops = [m.uh_op("c64") for m in models]
+    for m in models:
+        m.close()
+    off = batch.offsets
+    x = torch.from_numpy(np.concatenate([w.x() for w in pool])).to("cuda", torch.complex64)
+    y, y2 = torch.empty_like(x), torch.empty_like(x)
+
+    class Seq:
+        def matvec(self, _x, _y):
+            for k, op in enumerate(ops):
+                op.matvec(x[off[k]:off[k + 1]], y2[off[k]:off[k + 1]])
+    for _ in range(3):
+        batch.matvec(x, y)
+        Seq().matvec(None, None)
+    ms_b = timed_back_to_back(batch, x, y, steps, torch)
+    ms_s = timed_back_to_back(Seq(), None, None, max(3, steps // 5), torch)
+    batch.check()
+    st = batch.stats()
+    yb, ys = y.cpu().numpy().astype(np.complex128), y2.cpu().numpy().astype(np.complex128)
+    diff = max(float(np.linalg.norm(yb[off[k]:off[k + 1]] - ys[off[k]:off[k + 1]]) /
+                     np.linalg.norm(ys[off[k]:off[k + 1]])) for k in range(count))
+    peak, _ = _peaks()
+    return {"operators": count, "points": int(off[-1]), "build_s": round(build_s, 1), "pack_s": round(pack_s, 1),
+            "ms_batched": ms_b, "ms_separate": ms_s, "speedup": ms_s / ms_b,
+            "operator_matvecs_per_s": count * 1e3 / ms_b, "operator_matvecs_per_s_separate": count * 1e3 / ms_s,
+            "GBps": st["algo_bytes_matvec"] / (ms_b * 1e-3) / 1e9,
+            "frac": st["algo_bytes_matvec"] / (ms_b * 1e-3) / 1e9 / peak,
+            "algo_bytes": st["algo_bytes_matvec"], "max_rel_diff_vs_separate": diff}
+
+
 def profile_arm(args):
     """Only one op (uh64, h64 or uh128) of the benchmark workload: build, warm up, run `steps`
     products and print their mean time. For profiler captures of a single kernel."""
@@ -416,6 +519,7 @@ def gpu_arm(args):
     t_e2e = e0.elapsed_time(e1) / e2e_steps
     time.sleep(0.2)
     clk = clocks.stop()
+    serving = None if args.no_serving else serving_figures(8, 16384, (200, 1000), 200)
 
     ms_max = ms_uh
     if dist:
@@ -481,6 +585,7 @@ def gpu_arm(args):
         "h": {"matvec_per_s": 1e3 / ms_h, "ms_mean": ms_h, "GBps": gbs_h,
               "algo_bytes": hst["algo_bytes_matvec"], "speedup_uh_over_h": ms_h / ms_uh},
         "uh_matmat": mm,
+        "serving": serving,
         "uh_c128": {"matvec_per_s": 1e3 / ms_128, "ms_mean": ms_128, "GBps": gbs_128,
                     "bound": "fp64 FMA (8 flops per complex multiply-add of a 16-byte element)"},
         "storage": {"E_UH": st["E_U"] + st["E_V"] + st["E_S"] + st["E_D"],
@@ -545,7 +650,26 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-op", choices=["uh64", "h64", "uh128", "mm_tf32", "mm_bf16x3"], default=None)
     ap.add_argument("--no-matmat", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving sweep only (pool and rates below)")
+    ap.add_argument("--pool", type=int, default=64)
+    ap.add_argument("--n-hi", type=int, default=65536)
+    ap.add_argument("--rates", default="50,100,200,500,1000,2000")
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--batched", action="store_true", help="batched-operator timing only")
+    ap.add_argument("--operators", type=int, default=256)
     args = ap.parse_args()
+    if args.batched:
+        import torch
+        torch.cuda.init()
+        print(json.dumps({"batched": batched_figures(args.operators, args.steps or 20)}), flush=True)
+        return
+    if args.serve:
+        import torch
+        torch.cuda.init()
+        res = serving_figures(args.pool, args.n_hi, [float(v) for v in args.rates.split(",")], args.requests)
+        print(json.dumps({"serving": res}), flush=True)
+        return
     if args.profile_op:
         args.steps = 5 if args.steps is None else args.steps
         args.warmup = 3 if args.warmup is None else args.warmup

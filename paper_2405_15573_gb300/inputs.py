@@ -110,3 +110,26 @@ def batched_pool(count: int = 256, seed0: int = 0) -> list[Workload]:
         out.append(Workload(f"pool{j}-N{n}", n, k, 32, 1.0, 1e-6, 1e-8, axes=axes,
                             geom_seed=seed0 + j, x_seed=seed0 + j))
     return out
+
+
+def serving_pool(count: int = 64, seed0: int = 1000, n_lo: int = 4096, n_hi: int = 65536) -> list[Workload]:
+    """Resident operators of the serving workload: N uniform in [n_lo, n_hi], k uniform in
+    [2, 24], sphere or ellipsoid (axes uniform in [0.5, 1]), leaf 32, eta 1, eps 1e-6 (ACA 1e-8);
+    seeds seed0.."""
+    out = []
+    for j in range(count):
+        r = np.random.default_rng(seed0 + j)
+        n = int(r.integers(n_lo, n_hi + 1))
+        k = float(r.uniform(2.0, 24.0))
+        if r.uniform() < 0.5:
+            axes = (1.0, 1.0, 1.0)
+        else:
+            axes = tuple(float(a) for a in r.uniform(0.5, 1.0, size=3))
+        out.append(Workload(f"serve{j}-N{n}", n, k, 32, 1.0, 1e-6, 1e-8, axes=axes,
+                            geom_seed=seed0 + j, x_seed=seed0 + j))
+    return out
+
+
+def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
+    """Arrival times (seconds from 0) of `count` requests of a Poisson process of the given rate."""
+    return np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=count))
