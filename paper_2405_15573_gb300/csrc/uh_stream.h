@@ -28,10 +28,10 @@ constexpr int kStreamConsumerWarps = 8;
 constexpr int kStreamConsumers = kStreamConsumerWarps * 32;
 constexpr int kStreamThreads = kStreamConsumers + 64;  // + producer warp + publisher warp
 constexpr int kPubRing = 16;  // group-counter releases in flight from consumers to the publisher
-constexpr int kStages = 6;
-constexpr int kTileBytes = 32768;       // largest tile of an item
+constexpr int kStages = 3;
+constexpr int kTileBytes = 65536;       // largest tile of an item
 constexpr int kStreamMaxCols = 512;     // largest column count of an item
-constexpr int kStageBytes = 34816;      // an item's tile and inputs (inputs at the tile's end)
+constexpr int kStageBytes = 69632;      // an item's tile and inputs (inputs at the tile's end)
 constexpr int kMaxRuns = 6;
 constexpr int kStreamHpMax = 64;
 
