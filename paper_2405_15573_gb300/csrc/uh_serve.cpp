@@ -43,6 +43,16 @@ double now_s() {
 
 enum Phase { kStart, kArnoldi, kUpdate, kFinish, kDone };
 
+// Device and pinned host buffers of one solve; kept after the solve for reuse by the next solve of
+// the same shape.
+struct Workspace {
+  int64_t n = 0;
+  int m = 0;
+  void *V = nullptr, *x = nullptr, *db = nullptr, *w = nullptr, *v32 = nullptr, *y32 = nullptr;
+  void *y = nullptr, *part = nullptr, *small = nullptr;  // small: h1 [m+2], h2 [m+2], scal [2 doubles]
+  cd *hy = nullptr, *hx = nullptr, *hsmall = nullptr;
+};
+
 struct Solve {
   uint64_t ticket = 0;
   uh_op* op = nullptr;
@@ -53,13 +63,15 @@ struct Solve {
   std::vector<cd> b;
   double bnorm = 0.0;
   int64_t footprint = 0;
-  // device
+  // workspace (device, pinned host) and views into it
+  Workspace ws;
+  bool has_ws = false;
   void *V = nullptr, *x = nullptr, *db = nullptr, *w = nullptr, *v32 = nullptr, *y32 = nullptr;
   void *h1 = nullptr, *h2 = nullptr, *y = nullptr, *part = nullptr;
   double* scal = nullptr;
-  // pinned host
   cd *hh1 = nullptr, *hh2 = nullptr, *hy = nullptr, *hx = nullptr;
   double* hscal = nullptr;
+  bool v32_ready = false;  // v32 holds complex64(V_j) for the next Arnoldi step
   // GMRES state
   Phase phase = kStart;
   bool x_zero = true;
@@ -91,6 +103,7 @@ struct uh_server {
   std::deque<Solve*> pending;
   std::vector<Solve*> active;
   std::map<uint64_t, std::unique_ptr<Solve>> all;  // every solve not yet collected by poll
+  std::vector<Workspace> spare;                    // workspaces of finished solves
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread worker;
@@ -98,40 +111,88 @@ struct uh_server {
 
 namespace {
 
-void free_solve(Solve* s) {
-  void* dev[] = {s->V, s->x, s->db, s->w, s->v32, s->y32, s->h1, s->h2, s->y, s->part, s->scal};
+void free_workspace(Workspace& w) {
+  void* dev[] = {w.V, w.x, w.db, w.w, w.v32, w.y32, w.y, w.part, w.small};
   for (void* p : dev)
     if (p) cudaFree(p);
-  void* host[] = {s->hh1, s->hh2, s->hy, s->hx, s->hscal};
+  void* host[] = {w.hy, w.hx, w.hsmall};
   for (void* p : host)
     if (p) cudaFreeHost(p);
-  s->V = s->x = s->db = s->w = s->v32 = s->y32 = s->h1 = s->h2 = s->y = s->part = nullptr;
-  s->scal = nullptr;
-  s->hh1 = s->hh2 = s->hy = s->hx = nullptr;
-  s->hscal = nullptr;
+  w = Workspace{};
 }
 
-int alloc_solve(Solve* s, cudaStream_t st) {
-  const int64_t n = s->n;
-  const int m = s->m;
+int alloc_workspace(Workspace& w, int64_t n, int m) {
   const int64_t nb = uh::solve_partials(n);
+  const size_t small = static_cast<size_t>(2 * (m + 2) + 1) * 16;
+  w.n = n;
+  w.m = m;
   auto dev = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
   auto host = [&](void** p, size_t bytes) { return cudaMallocHost(p, bytes) == cudaSuccess; };
-  bool ok = dev(&s->V, static_cast<size_t>((m + 1) * n) * 16) && dev(&s->x, n * 16) && dev(&s->db, n * 16) &&
-            dev(&s->w, n * 16) && dev(&s->v32, n * 8) && dev(&s->y32, n * 8) && dev(&s->h1, (m + 2) * 16) &&
-            dev(&s->h2, (m + 2) * 16) && dev(&s->y, (m + 2) * 16) &&
-            dev(&s->part, static_cast<size_t>((m + 1) * nb) * 16) && dev(reinterpret_cast<void**>(&s->scal), 16) &&
-            host(reinterpret_cast<void**>(&s->hh1), (m + 2) * 16) &&
-            host(reinterpret_cast<void**>(&s->hh2), (m + 2) * 16) &&
-            host(reinterpret_cast<void**>(&s->hy), (m + 2) * 16) && host(reinterpret_cast<void**>(&s->hx), n * 16) &&
-            host(reinterpret_cast<void**>(&s->hscal), 16);
+  const bool ok = dev(&w.V, static_cast<size_t>((m + 1) * n) * 16) && dev(&w.x, n * 16) && dev(&w.db, n * 16) &&
+                  dev(&w.w, n * 16) && dev(&w.v32, n * 8) && dev(&w.y32, n * 8) && dev(&w.y, (m + 2) * 16) &&
+                  dev(&w.part, static_cast<size_t>((m + 1) * nb) * 16) && dev(&w.small, small) &&
+                  host(reinterpret_cast<void**>(&w.hy), (m + 2) * 16) &&
+                  host(reinterpret_cast<void**>(&w.hx), n * 16) &&
+                  host(reinterpret_cast<void**>(&w.hsmall), small);
   if (!ok) {
     cudaGetLastError();
-    free_solve(s);
+    free_workspace(w);
     return UH_ENOMEM;
   }
-  if (cudaMemcpyAsync(s->db, s->b.data(), n * 16, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(s->x, 0, n * 16, st) != cudaSuccess)
+  return UH_OK;
+}
+
+void bind_workspace(Solve* s) {
+  Workspace& w = s->ws;
+  const int m = s->m;
+  s->V = w.V; s->x = w.x; s->db = w.db; s->w = w.w; s->v32 = w.v32; s->y32 = w.y32; s->y = w.y; s->part = w.part;
+  s->h1 = w.small;
+  s->h2 = static_cast<char*>(w.small) + (m + 2) * 16;
+  s->scal = reinterpret_cast<double*>(static_cast<char*>(w.small) + 2 * (m + 2) * 16);
+  s->hy = w.hy; s->hx = w.hx;
+  s->hh1 = w.hsmall;
+  s->hh2 = w.hsmall + (m + 2);
+  s->hscal = reinterpret_cast<double*>(w.hsmall + 2 * (m + 2));
+}
+
+// A workspace for solve s: a spare one of its shape, else a new one (spares are freed first if
+// the allocation fails).
+int take_workspace(uh_server* sv, Solve* s) {
+  for (size_t i = 0; i < sv->spare.size(); ++i)
+    if (sv->spare[i].n == s->n && sv->spare[i].m == s->m) {
+      s->ws = sv->spare[i];
+      sv->spare.erase(sv->spare.begin() + static_cast<std::ptrdiff_t>(i));
+      s->has_ws = true;
+      bind_workspace(s);
+      return UH_OK;
+    }
+  int rc = alloc_workspace(s->ws, s->n, s->m);
+  if (rc) {
+    for (Workspace& w : sv->spare) free_workspace(w);
+    sv->spare.clear();
+    rc = alloc_workspace(s->ws, s->n, s->m);
+    if (rc) return rc;
+  }
+  s->has_ws = true;
+  bind_workspace(s);
+  return UH_OK;
+}
+
+// Workspace back to the spares (at most max_active of them are kept).
+void release_workspace(uh_server* sv, Solve* s) {
+  if (!s->has_ws) return;
+  if (static_cast<int>(sv->spare.size()) < sv->max_active) sv->spare.push_back(s->ws);
+  else free_workspace(s->ws);
+  s->ws = Workspace{};
+  s->has_ws = false;
+}
+
+int start_solve(uh_server* sv, Solve* s, cudaStream_t st) {
+  const int rc = take_workspace(sv, s);
+  if (rc) return rc;
+  const int m = s->m;
+  if (cudaMemcpyAsync(s->db, s->b.data(), s->n * 16, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(s->x, 0, s->n * 16, st) != cudaSuccess)
     return UH_ECUDA;
   s->H.assign(static_cast<size_t>((m + 1) * m), cd(0, 0));
   s->g.assign(m + 1, cd(0, 0));
@@ -140,51 +201,58 @@ int alloc_solve(Solve* s, cudaStream_t st) {
   return UH_OK;
 }
 
-// The operator's product of basis or solution vector `v` (complex128) into `out` (complex128).
-int apply_op(Solve* s, const void* v, void* out, cudaStream_t st) {
+// out = A v (complex128 out; for complex64 ops through v32 / y32). With out null, a complex64 op
+// leaves its product in y32 for the caller to widen; v32_ready: v32 already holds complex64(v).
+int apply_op(Solve* s, const void* v, void* out, cudaStream_t st, bool v32_ready = false) {
   int rc;
   if (s->c64) {
-    if ((rc = uh::vec_d2f(v, s->v32, s->n, st))) return rc;
+    if (!v32_ready && (rc = uh::vec_d2f(v, s->v32, s->n, st))) return rc;
     if ((rc = uh_matvec(s->op, s->v32, s->y32, st))) return rc;
-    return uh::vec_f2d(s->y32, out, s->n, st);
+    return out ? uh::vec_f2d(s->y32, out, s->n, st) : UH_OK;
   }
   return uh_matvec(s->op, v, out, st);
 }
 
-// Kernels of the start of a cycle: V_0 = (b - A x) / ||b - A x||, the norm copied to the host.
+// Kernels of the start of a cycle: V_0 = (b - A x) / ||b - A x|| (and its complex64 copy for the
+// next product), the norm copied to the host.
 int issue_start(Solve* s, cudaStream_t st) {
   int rc;
   if (s->x_zero) {
     if (cudaMemcpyAsync(s->V, s->db, s->n * 16, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return UH_ECUDA;
   } else {
-    if ((rc = apply_op(s, s->x, s->w, st))) return rc;
-    if ((rc = uh::vec_residual(s->db, s->w, false, s->V, s->n, st))) return rc;
+    if ((rc = apply_op(s, s->x, s->c64 ? nullptr : s->w, st))) return rc;
+    if ((rc = uh::vec_residual(s->db, s->c64 ? s->y32 : s->w, s->c64, s->V, s->n, st))) return rc;
   }
   if ((rc = uh::vec_norm(s->V, s->n, s->part, s->scal, nullptr, st))) return rc;
-  if ((rc = uh::vec_scale(s->V, s->scal, s->V, s->n, st))) return rc;
+  if ((rc = uh::vec_scale_f(s->V, s->scal, s->V, s->c64 ? s->v32 : nullptr, s->n, st))) return rc;
+  s->v32_ready = s->c64;
   return cudaMemcpyAsync(s->hscal, s->scal, 16, cudaMemcpyDeviceToHost, st) == cudaSuccess ? UH_OK : UH_ECUDA;
 }
 
 // One Arnoldi step j: w = A V_j, two passes of classical Gram-Schmidt against V_0..V_j,
-// V_{j+1} = w / ||w||; both coefficient passes and the norm copied to the host.
+// V_{j+1} = w / ||w|| (and its complex64 copy); both coefficient passes and the norm copied to
+// the host in one copy.
 int issue_arnoldi(Solve* s, cudaStream_t st) {
   int rc;
   const int64_t n = s->n;
   const int cnt = s->j + 1;
   const char* Vj = static_cast<const char*>(s->V) + static_cast<size_t>(s->j) * n * 16;
-  if ((rc = apply_op(s, Vj, s->w, st))) return rc;
-  if ((rc = uh::vec_dots(s->V, n, cnt, s->w, s->part, s->h1, false, st))) return rc;
+  if (s->c64) {
+    if ((rc = apply_op(s, Vj, nullptr, st, s->v32_ready))) return rc;
+    if ((rc = uh::vec_dots_f(s->V, n, cnt, s->y32, s->w, s->part, s->h1, st))) return rc;
+  } else {
+    if ((rc = apply_op(s, Vj, s->w, st))) return rc;
+    if ((rc = uh::vec_dots(s->V, n, cnt, s->w, s->part, s->h1, false, st))) return rc;
+  }
   if ((rc = uh::vec_combine(s->V, n, cnt, s->h1, -1.0, s->w, st))) return rc;
   if ((rc = uh::vec_dots(s->V, n, cnt, s->w, s->part, s->h2, false, st))) return rc;
   if ((rc = uh::vec_combine(s->V, n, cnt, s->h2, -1.0, s->w, st))) return rc;
   if ((rc = uh::vec_norm(s->w, n, s->part, s->scal, nullptr, st))) return rc;
   char* Vn = static_cast<char*>(s->V) + static_cast<size_t>(cnt) * n * 16;
-  if ((rc = uh::vec_scale(s->w, s->scal, Vn, n, st))) return rc;
-  if (cudaMemcpyAsync(s->hh1, s->h1, cnt * 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(s->hh2, s->h2, cnt * 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(s->hscal, s->scal, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return UH_ECUDA;
-  return UH_OK;
+  if ((rc = uh::vec_scale_f(s->w, s->scal, Vn, s->c64 ? s->v32 : nullptr, n, st))) return rc;
+  s->v32_ready = s->c64;
+  const size_t small = static_cast<size_t>(2 * (s->m + 2) + 1) * 16;
+  return cudaMemcpyAsync(s->hh1, s->h1, small, cudaMemcpyDeviceToHost, st) == cudaSuccess ? UH_OK : UH_ECUDA;
 }
 
 // x += V_0..V_{cnt-1} y (y from the host), then the next cycle's start.
@@ -297,17 +365,23 @@ void worker_main(uh_server* sv) {
         sv->active.push_back(s);
       }
       if (sv->active.empty()) {
-        if (sv->stop) return;
+        if (sv->stop) {
+          for (Workspace& w : sv->spare) free_workspace(w);
+          sv->spare.clear();
+          return;
+        }
         sv->cv.wait_for(lk, std::chrono::milliseconds(20));
         continue;
       }
       if (sv->stop) {
         for (Solve* s : sv->active) {
-          free_solve(s);
+          release_workspace(sv, s);
           s->status = UH_ECUDA;
           s->phase = kDone;
         }
         sv->active.clear();
+        for (Workspace& w : sv->spare) free_workspace(w);
+        sv->spare.clear();
         return;
       }
       round = sv->active;
@@ -315,8 +389,8 @@ void worker_main(uh_server* sv) {
     // Allocate new solves' workspaces, then issue one step of every active solve.
     for (Solve* s : round) {
       if (s->phase == kDone) continue;
-      if (!s->V) {
-        const int rc = alloc_solve(s, sv->stream);
+      if (!s->has_ws) {
+        const int rc = start_solve(sv, s, sv->stream);
         if (rc) {
           s->status = rc;
           s->phase = kDone;
@@ -330,29 +404,23 @@ void worker_main(uh_server* sv) {
       }
     }
     const cudaError_t e = cudaStreamSynchronize(sv->stream);
-    // Bounded waits of the products that ran out (a GPU that could not run a product's CTAs
-    // together) end the solves that used that op.
-    std::vector<uh_op*> checked;
-    for (Solve* s : round) {
-      if (s->phase == kDone || std::find(checked.begin(), checked.end(), s->op) != checked.end()) continue;
-      checked.push_back(s->op);
-      if (uh_check(s->op, sv->stream) != UH_OK)
-        for (Solve* t : round)
-          if (t->op == s->op) { t->status = UH_ETIMEOUT; t->phase = kDone; }
-    }
     for (Solve* s : round) {
       if (e != cudaSuccess && s->phase != kDone) {
         s->status = UH_ECUDA;
         s->phase = kDone;
       }
-      if (s->phase != kDone) after(s);
+      if (s->phase == kDone) continue;
+      after(s);
+      // A finished solve: did a bounded wait of one of the op's products run out meanwhile (a
+      // GPU that could not run a product's CTAs together)?
+      if (s->phase == kDone && s->status == UH_OK && uh_check(s->op, sv->stream) != UH_OK) s->status = UH_ETIMEOUT;
     }
     std::lock_guard<std::mutex> lk(sv->mu);
     std::vector<Solve*> still;
     for (Solve* s : sv->active) {
       if (s->phase == kDone) {
         s->t_done = now_s();
-        free_solve(s);
+        release_workspace(sv, s);
         sv->used -= s->footprint;
       } else {
         still.push_back(s);

@@ -127,6 +127,37 @@ __global__ void norm_finish_kernel(const double* __restrict__ part, int nb, doub
   if (hcol) *hcol = make_double2(nrm, 0.0);
 }
 
+// v = w * scale[1] and, if v32 is not null, v32 = complex64(v) (the next product's input).
+__global__ void scale_f_kernel(const double2* __restrict__ w, const double* __restrict__ scale, double2* __restrict__ v,
+                               float2* __restrict__ v32, int64_t n) {
+  const double f = scale[1];
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double2 r = make_double2(w[k].x * f, w[k].y * f);
+    v[k] = r;
+    if (v32) v32[k] = make_float2(static_cast<float>(r.x), static_cast<float>(r.y));
+  }
+}
+
+// Like dots_kernel, with w given as complex64 y; blocks of row 0 also write w = complex128(y).
+__global__ void dots_f_kernel(const double2* __restrict__ V, int64_t n, const float2* __restrict__ y,
+                              double2* __restrict__ w, double2* __restrict__ part) {
+  __shared__ double2 sh[kThreads];
+  const int i = blockIdx.y;
+  const int nb = gridDim.x;
+  const int64_t per = (n + nb - 1) / nb;
+  const int64_t k0 = blockIdx.x * per, k1 = k0 + per < n ? k0 + per : n;
+  const double2* v = V + static_cast<int64_t>(i) * n;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += kThreads) {
+    const double2 wk = make_double2(y[k].x, y[k].y);
+    if (i == 0) w[k] = wk;
+    acc = acc + cmul_conj(v[k], wk);
+  }
+  const double2 s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[static_cast<int64_t>(i) * nb + blockIdx.x] = s;
+}
+
 // v = w * scale[1] (the inverse norm on the device).
 __global__ void scale_kernel(const double2* __restrict__ w, const double* __restrict__ scale, double2* __restrict__ v,
                              int64_t n) {
@@ -193,6 +224,22 @@ int vec_norm(const void* w, int64_t n, void* part, double* out, void* hcol, cuda
   if (rc) return rc;
   norm_finish_kernel<<<1, 32, 0, s>>>(static_cast<const double*>(part), nb, out, static_cast<double2*>(hcol));
   return launched("norm");
+}
+
+int vec_scale_f(const void* w, const double* scale, void* v, void* v32, int64_t n, cudaStream_t s) {
+  scale_f_kernel<<<grid_for(n), kThreads, 0, s>>>(static_cast<const double2*>(w), scale, static_cast<double2*>(v),
+                                                  static_cast<float2*>(v32), n);
+  return launched("scaling");
+}
+
+int vec_dots_f(const void* V, int64_t n, int cnt, const void* y, void* w, void* part, void* h, cudaStream_t s) {
+  const int nb = solve_partials(n);
+  dots_f_kernel<<<dim3(nb, cnt), kThreads, 0, s>>>(static_cast<const double2*>(V), n, static_cast<const float2*>(y),
+                                                    static_cast<double2*>(w), static_cast<double2*>(part));
+  int rc = launched("block dot products");
+  if (rc) return rc;
+  dots_finish_kernel<<<1, 64, 0, s>>>(static_cast<const double2*>(part), nb, cnt, static_cast<double2*>(h), 0);
+  return launched("block dot products");
 }
 
 int vec_scale(const void* w, const double* scale, void* v, int64_t n, cudaStream_t s) {

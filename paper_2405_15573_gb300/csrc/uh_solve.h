@@ -25,5 +25,9 @@ int vec_combine(const void* V, int64_t n, int cnt, const void* c, double sign, v
 int vec_norm(const void* w, int64_t n, void* part, double* out, void* hcol, cudaStream_t s);
 // v = w * scale[1].
 int vec_scale(const void* w, const double* scale, void* v, int64_t n, cudaStream_t s);
+// v = w * scale[1] and v32 = complex64(v) (v32 may be null).
+int vec_scale_f(const void* w, const double* scale, void* v, void* v32, int64_t n, cudaStream_t s);
+// As vec_dots (no accumulation) with w given as complex64 y; also writes w = complex128(y).
+int vec_dots_f(const void* V, int64_t n, int cnt, const void* y, void* w, void* part, void* h, cudaStream_t s);
 
 }  // namespace uh
