@@ -41,6 +41,8 @@ typedef struct {
   double eps;         /* relative truncation of bases and H blocks, in [0, 1) */
   double tol_aca;     /* relative ACA / recompression tolerance, in (0, 1) */
   int32_t nthreads;   /* OpenMP threads; <= 0: the OpenMP default */
+  int32_t strong;     /* 0: weak admissibility min(diam) <= eta dist (eq. (3.3));
+                         1: strong admissibility max(diam) <= eta dist (eq. (3.2)) */
 } uhb_params;
 
 typedef struct {

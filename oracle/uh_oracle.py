@@ -156,23 +156,27 @@ def box_dist(lo1, hi1, lo2, hi2) -> float:
     return float(np.linalg.norm(gap))
 
 
-def admissible(tree: ClusterTree, t: int, s: int, eta: float) -> bool:
-    """Weak admissibility (eq. (3.3)) on bounding boxes, reading R1/R2."""
+def admissible(tree: ClusterTree, t: int, s: int, eta: float, strong: bool = False) -> bool:
+    """Admissibility on bounding boxes (readings R1/R2): the weak condition of eq. (3.3),
+    min(diam tau, diam sigma) <= eta dist, or with strong=True the strong condition of eq. (3.2),
+    max(diam tau, diam sigma) <= eta dist; both need dist > 0."""
     dist = box_dist(tree.lo[t], tree.hi[t], tree.lo[s], tree.hi[s])
     if dist <= 0.0:
         return False
-    return min(box_diam(tree.lo[t], tree.hi[t]), box_diam(tree.lo[s], tree.hi[s])) <= eta * dist
+    dt, ds = box_diam(tree.lo[t], tree.hi[t]), box_diam(tree.lo[s], tree.hi[s])
+    return (max(dt, ds) if strong else min(dt, ds)) <= eta * dist
 
 
-def block_tree(tree: ClusterTree, eta: float):
-    """Leaves of the level-conserving block cluster tree, s(b) = s(tau) x s(sigma).
+def block_tree(tree: ClusterTree, eta: float, strong: bool = False):
+    """Leaves of the level-conserving block cluster tree, s(b) = s(tau) x s(sigma), under the weak
+    (default) or strong admissibility condition.
 
     Returns (P_plus, P_minus): lists of (tau, sigma) cluster pairs (admissible, dense)."""
     adm, dense = [], []
     stack = [(0, 0)]
     while stack:
         t, s = stack.pop()
-        if admissible(tree, t, s, eta):
+        if admissible(tree, t, s, eta, strong):
             adm.append((t, s))
         elif tree.is_leaf(t) or tree.is_leaf(s):
             dense.append((t, s))
@@ -558,13 +562,13 @@ def power_iteration_norm(apply, apply_adj, n: int, iters: int = 30, seed: int = 
 # ----------------------------------------------------------------------------------------------
 
 
-def build_operators(points, wavenumber, leaf, eta, eps, tol_aca):
+def build_operators(points, wavenumber, leaf, eta, eps, tol_aca, strong: bool = False):
     """points -> cluster tree -> block tree -> ACA H-matrix at tol_aca -> (H at eps, UH at eps).
 
     The H form used for comparison keeps each block's singular values above eps * sigma_1; the UH
-    form is Algorithm 2 applied to the tol_aca blocks."""
+    form is Algorithm 2 applied to the tol_aca blocks. strong: strong admissibility (eq. (3.2))."""
     tree = ClusterTree(points, leaf)
-    adm, dense = block_tree(tree, eta)
+    adm, dense = block_tree(tree, eta, strong)
     h_fine, sv = build_h(points, tree, adm, dense, wavenumber, tol_aca)
     uh = uniform_compression(h_fine, eps)
     h = truncate_h(h_fine, sv, eps)

@@ -474,7 +474,9 @@ int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* prm, 
     auto [a, b] = stack.back();
     stack.pop_back();
     const double d = B.dist(a, b);
-    if (d > 0 && std::min(B.diam(a), B.diam(b)) <= prm->eta * d) {
+    // weak (eq. (3.3)): min of the two diameters; strong (eq. (3.2)): max
+    const double dm = prm->strong ? std::max(B.diam(a), B.diam(b)) : std::min(B.diam(a), B.diam(b));
+    if (d > 0 && dm <= prm->eta * d) {
       adm.push_back({a, b});
     } else if (B.cl[a].child0 < 0 || B.cl[b].child0 < 0) {
       dense.push_back({a, b});

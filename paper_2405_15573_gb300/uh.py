@@ -474,7 +474,7 @@ class HOp(_Op):
 
 class BuildParams(C.Structure):
     _fields_ = [("wavenumber", C.c_double), ("leaf", _i32), ("eta", C.c_double),
-                ("eps", C.c_double), ("tol_aca", C.c_double), ("nthreads", _i32)]
+                ("eps", C.c_double), ("tol_aca", C.c_double), ("nthreads", _i32), ("strong", _i32)]
 
 
 class BuildInfo(C.Structure):
@@ -508,10 +508,10 @@ class HelmholtzModel:
     """Synthetic Helmholtz collocation operator built on the host (uh_build.h) in both UH and
     H form. The arrays live in the library; uh_op()/h_op() upload them to the GPU."""
 
-    def __init__(self, points, wavenumber, leaf, eta, eps, tol_aca, nthreads: int = 0):
+    def __init__(self, points, wavenumber, leaf, eta, eps, tol_aca, nthreads: int = 0, strong: bool = False):
         pts = np.ascontiguousarray(points, dtype=np.float64)
         prm = BuildParams(float(wavenumber), int(leaf), float(eta), float(eps), float(tol_aca),
-                          int(nthreads))
+                          int(nthreads), 1 if strong else 0)
         h = _p()
         check(lib.uhb_build_helmholtz(len(pts), pts.ctypes.data, C.byref(prm), C.byref(h)),
               "uhb_build_helmholtz")

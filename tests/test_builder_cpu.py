@@ -35,12 +35,14 @@ def _oracle_view(a):
     return U, V, S, near
 
 
-@pytest.mark.parametrize("case", [(2048, 4.0, 32, 1e-6, (1.0, 1.0, 1.0), 0.0),
-                                  (1000, 6.0, 24, 1e-5, (1.0, 0.7, 0.4), 0.01)])
+@pytest.mark.parametrize("case", [(2048, 4.0, 32, 1e-6, (1.0, 1.0, 1.0), 0.0, False),
+                                  (1000, 6.0, 24, 1e-5, (1.0, 0.7, 0.4), 0.01, False),
+                                  (1000, 6.0, 24, 1e-5, (1.0, 0.7, 0.4), 0.01, True)],
+                         ids=["sphere2048", "ellipsoid1000", "ellipsoid1000_strong"])
 def test_builder_matches_oracle(U, case):
-    n, k, leaf, eps, axes, noise = case
-    pts, tree, hf, h, uh = oracle_ops(n, k, leaf, 1.0, eps, 1e-8, axes, noise)
-    m = U.HelmholtzModel(pts, k, leaf, 1.0, eps, 1e-8, nthreads=2)
+    n, k, leaf, eps, axes, noise, strong = case
+    pts, tree, hf, h, uh = oracle_ops(n, k, leaf, 1.0, eps, 1e-8, axes, noise, strong=strong)
+    m = U.HelmholtzModel(pts, k, leaf, 1.0, eps, 1e-8, nthreads=2, strong=strong)
     a = m.uh_arrays()
     # identical trees and block partitions
     assert np.array_equal(a["perm"], tree.perm)

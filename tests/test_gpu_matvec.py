@@ -45,6 +45,8 @@ WORKLOADS = {
     "sphere2048": (2048, 4.0, 32, 1.0, 1e-6, 1e-8, (1.0, 1.0, 1.0), 0.0),
     # ragged: N not a power of two, noisy ellipsoid, leaf 24 (odd leaf sizes, uneven levels)
     "ellipsoid1000": (1000, 6.0, 24, 1.0, 1e-5, 1e-8, (1.0, 0.7, 0.4), 0.01),
+    # the same ellipsoid under strong admissibility (eq. (3.2)): a finer partition
+    "ellipsoid1000_strong": (1000, 6.0, 24, 1.0, 1e-5, 1e-8, (1.0, 0.7, 0.4), 0.01, 0, True),
 }
 
 

@@ -123,6 +123,42 @@ def test_block_tree_partition_brute_force(tree1000):
         assert not O.admissible(t, a, b, 1.0)
 
 
+def test_strong_admissibility_partition(tree1000):
+    """Strong admissibility (eq. (3.2), max of the diameters): still an exact partition of I x J,
+    every admissible leaf satisfies the strong condition (hence the weak one), and the dense part
+    contains the weak partition's dense part."""
+    pts, t = tree1000
+    adm, dense = O.block_tree(t, 1.0, strong=True)
+    cover = np.zeros((1000, 1000), dtype=np.int32)
+    for (a, b) in adm + dense:
+        cover[np.ix_(t.indices(a), t.indices(b))] += 1
+    assert (cover == 1).all()
+    for (a, b) in adm:
+        d = O.box_dist(t.lo[a], t.hi[a], t.lo[b], t.hi[b])
+        assert max(O.box_diam(t.lo[a], t.hi[a]), O.box_diam(t.lo[b], t.hi[b])) <= d
+        assert O.admissible(t, a, b, 1.0) and O.admissible(t, a, b, 1.0, strong=True)
+        assert not O.admissible(t, t.parent[a], t.parent[b], 1.0, strong=True)
+    for (a, b) in dense:
+        assert not O.admissible(t, a, b, 1.0, strong=True)
+    # A strongly admissible pair is weakly admissible, so the weak recursion stops at or above
+    # every strong leaf: each weakly dense block is strongly dense as well.
+    wadm, wdense = O.block_tree(t, 1.0)
+    assert set(wdense) <= set(dense)
+    e_strong = sum(t.size[a] * t.size[b] for a, b in dense)
+    e_weak = sum(t.size[a] * t.size[b] for a, b in wdense)
+    assert e_strong > e_weak
+    # a pair that is weakly but not strongly admissible: one small cluster near a large one
+    found = False
+    for a in range(t.n_clusters):
+        for b in range(t.n_clusters):
+            if O.admissible(t, a, b, 1.0) and not O.admissible(t, a, b, 1.0, strong=True):
+                found = True
+                break
+        if found:
+            break
+    assert found
+
+
 def test_box_measures_bound_point_measures(tree1000):
     pts, t = tree1000
     rng = np.random.default_rng(0)

@@ -91,14 +91,14 @@ def h_arrays(h: O.HMatrix, dtype=np.complex128) -> dict:
 
 @functools.lru_cache(maxsize=8)
 def oracle_ops(n: int, wavenumber: float, leaf: int, eta: float, eps: float, tol_aca: float,
-               axes=(1.0, 1.0, 1.0), noise: float = 0.0, seed: int = 0):
+               axes=(1.0, 1.0, 1.0), noise: float = 0.0, seed: int = 0, strong: bool = False):
     """(points, tree, h_fine, h, uh) for a Fibonacci sphere/ellipsoid workload, built once."""
     from paper_2405_15573_gb300 import inputs as I
     if axes == (1.0, 1.0, 1.0) and not noise:
         pts = I.fibonacci_sphere(n)
     else:
         pts = I.ellipsoid_points(n, axes, noise, seed)
-    tree, hf, h, uh = O.build_operators(pts, wavenumber, leaf, eta, eps, tol_aca)
+    tree, hf, h, uh = O.build_operators(pts, wavenumber, leaf, eta, eps, tol_aca, strong)
     return pts, tree, hf, h, uh
 
 
