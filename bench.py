@@ -202,6 +202,22 @@ def run_oracle_sample(directory: str, seconds: float, min_reps: int = 2, warmup:
 # ----------------------------------------------------------------------------- GPU arm
 
 
+def replica_times(ms, e2e_ms, dist, device):
+    """Per-step times of this rank -> the slowest rank's (all-reduce MAX over the process group),
+    which set the whole job's time; unchanged without a process group."""
+    if dist is None:
+        return ms, e2e_ms
+    import torch
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0]), float(t[1])
+
+
+def job_value(world, ms_max):
+    """Whole-job products per second: every rank runs its own replica, one product per step."""
+    return world * 1e3 / ms_max
+
+
 def timed_back_to_back(op, x, y, steps, torch):
     """Mean CUDA-event time (ms) of `steps` matvecs launched back to back on the current stream."""
     s = torch.cuda.current_stream()
@@ -521,11 +537,7 @@ def gpu_arm(args):
     clk = clocks.stop()
     serving = None if args.no_serving else serving_figures(8, 16384, (200, 1000), 200)
 
-    ms_max = ms_uh
-    if dist:
-        tt = torch.tensor([ms_uh, t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_max, t_e2e = float(tt[0]), float(tt[1])
+    ms_max, t_e2e = replica_times(ms_uh, t_e2e, dist, "cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -555,7 +567,7 @@ def gpu_arm(args):
                "relerr_c64_vs_oracle": rel_oracle, "relerr_c128_vs_oracle": rel_oracle_128}
 
     out = {
-        "metric": METRIC, "value": world * 1e3 / ms_max, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": job_value(world, ms_max), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
         "data": "synthetic",
@@ -565,7 +577,7 @@ def gpu_arm(args):
                    "l2": "inputs larger than L2: the packed operator is "
                          f"{st['packed_bytes'] / 2**20:.0f} MiB, every step streams all of it; no flush",
                    "parallelism": f"replicas x{world}", "operator_build_s": round(build_s, 2)},
-        "e2e": {"value": world * 1e3 / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
+        "e2e": {"value": job_value(world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
                 "d2h_bytes_per_step": int(y.numel() * 8)},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "peak_kind": peak_kind, "traffic": traffic,
