@@ -19,7 +19,7 @@ side (complex normal, seed 0). The operator is built on the host by the library'
             spawned child process, also giving the relative error of the GPU result.
 
   serving   GMRES(30) solves from a pool of 8 resident operators (N up to 16384) with Poisson
-            arrivals at 200 and 1000 per second: solve latency p50 / p99 and solves per second.
+            arrivals at 200, 1000 and 2000 per second: solve latency p50 / p99 and solves per second.
 
 `--serve` runs the serving sweep alone (pool of 64 operators, N up to 65536, six arrival rates by
 default); `--batched` times 256 independent operators in one launch against one launch each.
@@ -535,7 +535,7 @@ def gpu_arm(args):
     t_e2e = e0.elapsed_time(e1) / e2e_steps
     time.sleep(0.2)
     clk = clocks.stop()
-    serving = None if args.no_serving else serving_figures(8, 16384, (200, 1000), 200)
+    serving = None if args.no_serving else serving_figures(8, 16384, (200, 1000, 2000), 200)
 
     ms_max, t_e2e = replica_times(ms_uh, t_e2e, dist, "cuda")
     if rank != 0:

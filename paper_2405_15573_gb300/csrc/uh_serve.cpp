@@ -1,10 +1,13 @@
 // Serving runtime: GMRES(m) solves A x = b with resident UH operators, admitted by device-memory
 // footprint and advanced together in rounds (continuous batching).
 //
-// One worker thread owns a CUDA stream. Each round it admits queued solves while the admitted
-// footprint stays within the budget and fewer than max_active are running, then issues ONE step
-// of every active solve (all asynchronous on the stream), synchronises once, and updates the
-// solves' small host-side state (Givens rotations of the Hessenberg matrix, convergence). A solve
+// One worker thread owns one CUDA stream per running solve. Each round it admits queued solves
+// while the admitted footprint stays within the budget and fewer than max_active are running,
+// then issues ONE step of every active solve (asynchronous, each on its solve's stream, so the
+// small vector kernels of different solves overlap), synchronises, and updates the solves' small
+// host-side state (Givens rotations of the Hessenberg matrix, convergence). The products of one
+// operator are chained across streams by an event in launch order: they share the operator's
+// scratch and its per-call group counters. A solve
 // is restarted GMRES with its matrix-vector products in the operator's precision (complex64
 // storage, FP32 accumulation for UH_PREC_C64 ops) and everything else in FP64 on the GPU: the
 // true residual r = b - A x at every restart, classical Gram-Schmidt applied twice for the
@@ -72,6 +75,8 @@ struct Solve {
   cd *hh1 = nullptr, *hh2 = nullptr, *hy = nullptr, *hx = nullptr;
   double* hscal = nullptr;
   bool v32_ready = false;  // v32 holds complex64(V_j) for the next Arnoldi step
+  int slot = -1;           // index of the solve's stream
+  cudaStream_t st = nullptr;
   // GMRES state
   Phase phase = kStart;
   bool x_zero = true;
@@ -97,7 +102,9 @@ struct uh_server {
   int max_active = 8;
   int64_t budget = 0, used = 0;
   int queue_cap = 64;
-  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> streams;          // one per running solve (slots)
+  std::vector<char> slot_used;
+  std::map<uh_op*, cudaEvent_t> op_done;      // the last product launched per op
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Solve*> pending;
@@ -203,14 +210,29 @@ int start_solve(uh_server* sv, Solve* s, cudaStream_t st) {
 
 // out = A v (complex128 out; for complex64 ops through v32 / y32). With out null, a complex64 op
 // leaves its product in y32 for the caller to widen; v32_ready: v32 already holds complex64(v).
+// The per-op event that orders that op's products across the solves' streams.
+thread_local std::map<uh_op*, cudaEvent_t>* g_op_done = nullptr;
+
+int ordered_matvec(uh_op* op, const void* x, void* y, cudaStream_t st) {
+  cudaEvent_t& ev = (*g_op_done)[op];
+  if (!ev) {
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return UH_ECUDA;
+  } else if (cudaStreamWaitEvent(st, ev, 0) != cudaSuccess) {
+    return UH_ECUDA;
+  }
+  const int rc = uh_matvec(op, x, y, st);
+  if (rc) return rc;
+  return cudaEventRecord(ev, st) == cudaSuccess ? UH_OK : UH_ECUDA;
+}
+
 int apply_op(Solve* s, const void* v, void* out, cudaStream_t st, bool v32_ready = false) {
   int rc;
   if (s->c64) {
     if (!v32_ready && (rc = uh::vec_d2f(v, s->v32, s->n, st))) return rc;
-    if ((rc = uh_matvec(s->op, s->v32, s->y32, st))) return rc;
+    if ((rc = ordered_matvec(s->op, s->v32, s->y32, st))) return rc;
     return out ? uh::vec_f2d(s->y32, out, s->n, st) : UH_OK;
   }
-  return uh_matvec(s->op, v, out, st);
+  return ordered_matvec(s->op, v, out, st);
 }
 
 // Kernels of the start of a cycle: V_0 = (b - A x) / ||b - A x|| (and its complex64 copy for the
@@ -352,6 +374,7 @@ void after(Solve* s) {
 
 void worker_main(uh_server* sv) {
   cudaSetDevice(sv->device);
+  g_op_done = &sv->op_done;
   for (;;) {
     std::vector<Solve*> round;
     {
@@ -362,6 +385,13 @@ void worker_main(uh_server* sv) {
         sv->pending.pop_front();
         sv->used += s->footprint;
         s->t_admit = now_s();
+        for (int k = 0; k < static_cast<int>(sv->slot_used.size()); ++k)
+          if (!sv->slot_used[k]) {
+            sv->slot_used[k] = 1;
+            s->slot = k;
+            s->st = sv->streams[k];
+            break;
+          }
         sv->active.push_back(s);
       }
       if (sv->active.empty()) {
@@ -390,20 +420,24 @@ void worker_main(uh_server* sv) {
     for (Solve* s : round) {
       if (s->phase == kDone) continue;
       if (!s->has_ws) {
-        const int rc = start_solve(sv, s, sv->stream);
+        const int rc = start_solve(sv, s, s->st);
         if (rc) {
           s->status = rc;
           s->phase = kDone;
           continue;
         }
       }
-      const int rc = issue(s, sv->stream);
+      const int rc = issue(s, s->st);
       if (rc) {
         s->status = rc;
         s->phase = kDone;
       }
     }
-    const cudaError_t e = cudaStreamSynchronize(sv->stream);
+    cudaError_t e = cudaSuccess;
+    for (Solve* s : round) {
+      const cudaError_t es = cudaStreamSynchronize(s->st);
+      if (es != cudaSuccess) e = es;
+    }
     for (Solve* s : round) {
       if (e != cudaSuccess && s->phase != kDone) {
         s->status = UH_ECUDA;
@@ -413,7 +447,7 @@ void worker_main(uh_server* sv) {
       after(s);
       // A finished solve: did a bounded wait of one of the op's products run out meanwhile (a
       // GPU that could not run a product's CTAs together)?
-      if (s->phase == kDone && s->status == UH_OK && uh_check(s->op, sv->stream) != UH_OK) s->status = UH_ETIMEOUT;
+      if (s->phase == kDone && s->status == UH_OK && uh_check(s->op, s->st) != UH_OK) s->status = UH_ETIMEOUT;
     }
     std::lock_guard<std::mutex> lk(sv->mu);
     std::vector<Solve*> still;
@@ -422,6 +456,7 @@ void worker_main(uh_server* sv) {
         s->t_done = now_s();
         release_workspace(sv, s);
         sv->used -= s->footprint;
+        if (s->slot >= 0) sv->slot_used[s->slot] = 0;
       } else {
         still.push_back(s);
       }
@@ -445,8 +480,14 @@ int uh_server_create(int32_t max_active, int64_t hbm_budget_bytes, int32_t queue
   sv->max_active = max_active;
   sv->budget = hbm_budget_bytes;
   sv->queue_cap = queue_capacity;
-  if (cudaGetDevice(&sv->device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  bool ok = cudaGetDevice(&sv->device) == cudaSuccess;
+  sv->streams.assign(max_active, nullptr);
+  sv->slot_used.assign(max_active, 0);
+  for (int k = 0; ok && k < max_active; ++k)
+    ok = cudaStreamCreateWithFlags(&sv->streams[k], cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    for (cudaStream_t st : sv->streams)
+      if (st) cudaStreamDestroy(st);
     delete sv;
     return fail(UH_ECUDA, "stream creation failed");
   }
@@ -464,7 +505,9 @@ int uh_server_destroy(uh_server* sv) {
   }
   sv->cv.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
-  cudaStreamDestroy(sv->stream);
+  for (cudaStream_t st : sv->streams) cudaStreamDestroy(st);
+  for (auto& kv : sv->op_done)
+    if (kv.second) cudaEventDestroy(kv.second);
   delete sv;
   return UH_OK;
 }
