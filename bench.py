@@ -331,6 +331,21 @@ def build_models(workloads, threads=8):
                                                       nthreads=2), workloads))
 
 
+def build_ops(workloads, precision="c64", threads=4):
+    """Device ops of several operators; each host model is freed as soon as its op is uploaded, so
+    at most `threads` models are held on the host at a time."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2405_15573_gb300 import uh as U
+
+    def one(w):
+        m = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca, nthreads=4)
+        op = m.uh_op(precision)
+        m.close()
+        return op
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(one, workloads))
+
+
 def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30):
     """GMRES(restart) solves served from a pool of resident complex64 UH operators (uh_server):
     per arrival rate, `requests` solves with Poisson arrivals, each on a random operator of the
@@ -340,10 +355,7 @@ def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30):
     from paper_2405_15573_gb300 import uh as U
     pool = I.serving_pool(pool_count, n_hi=n_hi)
     t0 = time.time()
-    models = build_models(pool)
-    ops = [m.uh_op("c64") for m in models]
-    for m in models:
-        m.close()
+    ops = build_ops(pool)
     build_s = time.time() - t0
     srv = U.Server(max_active=32, hbm_budget=32 << 30, queue_capacity=1 << 20)
     for o, w in zip(ops, pool):  # one solve per operator before timing
