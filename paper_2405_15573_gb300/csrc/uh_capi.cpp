@@ -198,9 +198,12 @@ struct OpBase {
   void* d_M = nullptr;
   uh::WorkItem* d_items = nullptr;
   int32_t* d_cta = nullptr;
-  unsigned long long* d_done = nullptr;  // group counters
+  unsigned long long* d_done = nullptr;  // group counters, the pool ticket, the flags
+  int64_t done_len = 0;
   uh::Scatter* d_scatter = nullptr;
-  int64_t counter_total[uh::kNumCounters] = {0, 0, 0};
+  uh::PoolRange* d_pool = nullptr;
+  int64_t pool_chunks = 0;
+  int64_t counter_total[uh::kNumCounters] = {};
   uint32_t* d_status = nullptr;
   int32_t* d_perm = nullptr;
   void* d_xp = nullptr;
@@ -222,7 +225,7 @@ struct OpBase {
 
 void free_op(OpBase* o) {
   if (!o) return;
-  void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_scatter, o->d_status,
+  void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_scatter, o->d_pool, o->d_status,
                   o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3,
                   o->d_ptiles, o->d_pitems, o->d_pbegin, o->d_pxp, o->d_pz1, o->d_pz2};
   for (void* p : ptrs)
@@ -274,7 +277,10 @@ int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T) {
   if ((rc = upload(P.items.data(), P.items.size() * sizeof(uh::WorkItem), &o->d_items))) return rc;
   if ((rc = upload(P.cta_begin.data(), P.cta_begin.size() * sizeof(int32_t), &o->d_cta))) return rc;
   if ((rc = upload(P.scatter.data(), P.scatter.size() * sizeof(uh::Scatter), &o->d_scatter))) return rc;
-  if ((rc = upload(static_cast<const void*>(nullptr), uh::kNumCounters * sizeof(unsigned long long), &o->d_done)))
+  if ((rc = upload(P.pool.data(), P.pool.size() * sizeof(uh::PoolRange), &o->d_pool))) return rc;
+  o->pool_chunks = static_cast<int64_t>(P.pool.size());
+  o->done_len = uh::kFlagBase + P.flag_count();
+  if ((rc = upload(static_cast<const void*>(nullptr), o->done_len * sizeof(unsigned long long), &o->d_done)))
     return rc;
   for (int c = 0; c < uh::kNumCounters; ++c) o->counter_total[c] = P.counter_total(c);
   if ((rc = upload(static_cast<const void*>(nullptr), sizeof(uint32_t), &o->d_status))) return rc;
@@ -303,7 +309,12 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   uh::StreamParams p{};
   p.items = o->d_items;
   p.cta_begin = o->d_cta;
+  p.pool = o->d_pool;
+  p.pool_chunks = o->pool_chunks;
   p.group_done = o->d_done;
+  // every call takes pool_chunks + ncta tickets (each CTA stops after one past the end)
+  p.ticket_base = (o->epoch - 1u) * static_cast<unsigned long long>(o->pool_chunks + o->ncta);
+  p.flag_need = stall ? o->epoch + 1u : o->epoch;
   // A group is complete in call number `epoch` when its counter reaches epoch * (its chunks);
   // the stall test asks for one call more, which no chunk ever delivers.
   for (int c = 0; c < uh::kNumCounters; ++c)
@@ -333,7 +344,7 @@ int check_status(OpBase* o, void* stream) {
   if (v) {
     // A call that ran out left its group counters short: restart the counting.
     CUDA_TRY(cudaMemsetAsync(o->d_status, 0, sizeof(uint32_t), s));
-    CUDA_TRY(cudaMemsetAsync(o->d_done, 0, uh::kNumCounters * sizeof(unsigned long long), s));
+    CUDA_TRY(cudaMemsetAsync(o->d_done, 0, o->done_len * sizeof(unsigned long long), s));
     CUDA_TRY(cudaStreamSynchronize(s));
     o->epoch = 0;
     return fail(UH_ETIMEOUT, "a bounded device-side wait ran out (code %u)", v);
@@ -497,9 +508,10 @@ void add_permute(ProgramBuilder& P, int64_t n, int ncta) {
   }
 }
 
-// Near-field chunks of the row tiles, alternating between the two near-field groups. A tile with a
-// backward part writes its z3 slot (the backward chunk adds it), otherwise y directly. Returns,
-// per tile, the near-field chunk writing z3 (or -1).
+// Near-field chunks of the row tiles, alternating between the two near-field groups (static,
+// before the coupling; and the first part of the pool). A tile with a backward part writes its z3
+// slot (the backward chunk adds it), otherwise y directly. Returns, per tile, the near-field chunk
+// writing z3 (or -1).
 // offN: position of the operator's first point in the program's vectors; z3pos: next free z3 slot
 // (advanced; when null the slots start at 0 and the z3 length is set here).
 std::vector<int> add_near_field(ProgramBuilder& P, const Tree& T, const uh_dense_desc& d, const Src& D,

@@ -16,13 +16,17 @@ int ProgramBuilder::add_chunk(int kind, int64_t dst, int h, int group, int count
   c.dst = dst;
   c.h = h;
   c.kind = static_cast<int16_t>(kind);
+  if (kind == kToZ3) {  // a near-field partial: releases a flag of its own
+    counter = kCounterFlag;
+    c.flag = static_cast<int32_t>(nflags_++);
+  }
   c.counter = static_cast<int16_t>(counter);
   chunks.push_back(c);
   group_.push_back(group);
   base_of_.push_back(-1);
   bytes_.push_back(0);
   chunk_items_.emplace_back();
-  if (counter >= 0) counter_total_[counter]++;
+  if (counter >= 0 && counter < kNumCounters) counter_total_[counter]++;
   return static_cast<int>(chunks.size()) - 1;
 }
 
@@ -119,17 +123,40 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
     start_item();
     close_item();
   }
+  if (base_chunk >= 0) {
+    // The near-field partial, staged after the last item's inputs (an extra item without columns
+    // when the last one has no room for it).
+    const int64_t hb = round_up(h, A_);
+    const WorkItem& last = out.back();
+    if (last.nruns == kMaxRuns || (static_cast<int64_t>(last.ncols) * (hp + 1) + hb) * eb_ > kStageBytes) {
+      start_item();
+      close_item();
+    }
+    WorkItem& it = out.back();
+    Run run{};
+    run.start = static_cast<int32_t>(chunks[base_chunk].dst);
+    run.len = static_cast<int16_t>(hb);
+    run.src = kSrcZ3;
+    it.runs[it.nruns++] = run;
+    it.flags |= kItemBase;
+    it.aux = static_cast<int32_t>(chunks[base_chunk].dst);
+    it.naux = chunks[base_chunk].flag;
+    bytes_[chunk] += hb * eb_;
+    input_bytes_total += hb * eb_;
+    base_of_[chunk] = base_chunk;
+  }
   out.front().flags |= kItemFirst;
   out.back().flags |= kItemLast;
   bytes_[chunk] += kChunkCost;
-  if (base_chunk >= 0) {
-    for (WorkItem& it : out) {
-      it.flags |= kItemBaseAll;
-      it.aux = static_cast<int32_t>(chunks[base_chunk].dst);
-    }
-    out.back().flags |= kItemBase;
-    base_of_[chunk] = base_chunk;
+}
+
+bool ProgramBuilder::covered_by_cta(int reader, const std::vector<int>& list, int base_pos) const {
+  const uint32_t deps = static_cast<uint32_t>((chunk_items_[reader].back().flags >> kDepShift)) & ((1u << kNumCounters) - 1u);
+  for (size_t k = static_cast<size_t>(base_pos) + 1; k < list.size(); ++k) {
+    const int ctr = chunks[list[k]].counter;
+    if (ctr >= 0 && ctr < kNumCounters && ((deps >> ctr) & 1u)) return true;
   }
+  return false;
 }
 
 void ProgramBuilder::add_scatter(int chunk, int64_t dst, int lo, int hi) {
@@ -148,6 +175,8 @@ const char* ProgramBuilder::finalize() {
   std::vector<std::vector<int>> per_cta(ncta_);
   std::vector<int64_t> load(ncta_, 0);
   cta_of_.assign(nchunk, -1);
+  pool_pos_.assign(nchunk, -1);
+  std::vector<int> pool_order;
   using Entry = std::pair<int64_t, int>;  // (load, cta), smallest first
   for (int g = 0; g < kNumGroups; ++g) {
     std::vector<int> ids;
@@ -163,17 +192,24 @@ const char* ProgramBuilder::finalize() {
       continue;
     }
     std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return bytes_[a] > bytes_[b]; });
-    for (int c : ids) {  // chunks with a base go to their base chunk's CTA
-      if (base_of_[c] < 0) continue;
-      const int b = cta_of_[base_of_[c]];
-      per_cta[b].push_back(c);
-      cta_of_[c] = b;
-      load[b] += bytes_[c];
+    if (g >= kFirstPoolGroup) {
+      // Largest first; a chunk whose near-field partial comes from the pool goes after every chunk
+      // whose partial was written in the static part, in the order its partial was handed out
+      // (so that it is likely complete when the chunk is taken).
+      auto key = [&](int c) -> int64_t {
+        const int b = base_of_[c];
+        return b >= 0 && pool_pos_[b] >= 0 ? 1 + pool_pos_[b] : 0;
+      };
+      std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return key(a) < key(b); });
+      for (int c : ids) {
+        pool_pos_[c] = static_cast<int>(pool_order.size());
+        pool_order.push_back(c);
+      }
+      continue;
     }
     std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> pq;
     for (int b = 0; b < ncta_; ++b) pq.push({load[b], b});
     for (int c : ids) {
-      if (base_of_[c] >= 0) continue;
       auto [l, b] = pq.top();
       pq.pop();
       per_cta[b].push_back(c);
@@ -182,48 +218,148 @@ const char* ProgramBuilder::finalize() {
       pq.push({load[b], b});
     }
   }
+  // A reader of a static near-field partial needs no flag when the partial's CTA publishes, later
+  // in its list, a chunk of a group the reader waits for: that release also publishes the partial
+  // (the same consumer threads stored it earlier).
+  std::vector<char> covered(nchunk, 0);
+  {
+    std::vector<int> pos_in_cta(nchunk, -1);
+    for (int b = 0; b < ncta_; ++b)
+      for (size_t k = 0; k < per_cta[b].size(); ++k) pos_in_cta[per_cta[b][k]] = static_cast<int>(k);
+    for (int c = 0; c < nchunk; ++c) {
+      const int bc = base_of_[c];
+      if (bc < 0 || cta_of_[bc] < 0) continue;
+      covered[c] = covered_by_cta(c, per_cta[cta_of_[bc]], pos_in_cta[bc]);
+    }
+  }
   items.clear();
+  auto emit = [&](int c) {
+    for (WorkItem it : chunk_items_[c]) {
+      it.dst = chunks[c].dst;
+      it.h = chunks[c].h;
+      it.kind = chunks[c].kind;
+      it.counter = chunks[c].counter;
+      if (chunks[c].kind == kScatterZ1 || chunks[c].kind == kScatterZ2) {
+        it.aux = chunks[c].scat0;
+        it.naux = chunks[c].nscat;
+      }
+      if (chunks[c].counter == kCounterFlag) it.naux = chunks[c].flag;
+      if ((it.flags & kItemBase) && covered[c]) it.naux = -1;
+      items.push_back(it);
+    }
+  };
   cta_begin.assign(ncta_ + 1, 0);
   for (int b = 0; b < ncta_; ++b) {
     cta_begin[b] = static_cast<int32_t>(items.size());
-    for (int c : per_cta[b])
-      for (WorkItem it : chunk_items_[c]) {
-        it.dst = chunks[c].dst;
-        it.h = chunks[c].h;
-        it.kind = chunks[c].kind;
-        it.counter = chunks[c].counter;
-        if (chunks[c].kind == kScatterZ1 || chunks[c].kind == kScatterZ2) {
-          it.aux = chunks[c].scat0;
-          it.naux = chunks[c].nscat;
-        }
-        items.push_back(it);
-      }
+    for (int c : per_cta[b]) emit(c);
   }
   cta_begin[ncta_] = static_cast<int32_t>(items.size());
+  pool.clear();
+  for (int c : pool_order) {
+    PoolRange r{};
+    r.begin = static_cast<int32_t>(items.size());
+    emit(c);
+    r.end = static_cast<int32_t>(items.size());
+    pool.push_back(r);
+  }
   if (items.size() > static_cast<size_t>(INT32_MAX)) return "too many work items";
   return nullptr;
 }
 
 const char* ProgramBuilder::self_check() const {
   const int nchunk = static_cast<int>(chunks.size());
-  if (static_cast<int>(cta_begin.size()) != ncta_ + 1 || cta_begin[0] != 0 ||
-      cta_begin[ncta_] != static_cast<int32_t>(items.size()))
-    return "CTA item ranges";
+  if (static_cast<int>(cta_begin.size()) != ncta_ + 1 || cta_begin[0] != 0) return "CTA item ranges";
   for (int b = 0; b < ncta_; ++b)
     if (cta_begin[b] > cta_begin[b + 1]) return "CTA item ranges not monotone";
+  if (static_cast<int>(pool_pos_.size()) != nchunk || static_cast<int>(cta_of_.size()) != nchunk) return "placement";
+  // Where each counter's chunks are: the latest static group, the latest pool position.
+  int last_static[kNumCounters], last_pool[kNumCounters];
+  for (int g = 0; g < kNumCounters; ++g) last_static[g] = last_pool[g] = -1;
+  for (int c = 0; c < nchunk; ++c) {
+    const int ctr = chunks[c].counter;
+    if ((ctr < -1 || ctr >= kNumCounters) && ctr != kCounterFlag) return "chunk counter";
+    if ((ctr == kCounterFlag) != (chunks[c].kind == kToZ3)) return "flag of a chunk that is no near-field partial";
+    if (ctr == kCounterFlag && (chunks[c].flag < 0 || chunks[c].flag >= nflags_)) return "chunk flag";
+    if (ctr < 0 || ctr == kCounterFlag) continue;
+    if (pool_pos_[c] >= 0) last_pool[ctr] = std::max(last_pool[ctr], pool_pos_[c]);
+    else last_static[ctr] = std::max(last_static[ctr], group_[c]);
+  }
   const int64_t msize = static_cast<int64_t>(M.size());
   std::vector<int> seen(nchunk, 0);
+  // Checks of one item of chunk list position `pos` (a static CTA: -1, the pool: its ticket).
+  auto check_item = [&](const WorkItem& it, int pos) -> const char* {
+    if (it.chunk < 0 || it.chunk >= nchunk) return "item chunk out of range";
+    const OutChunk& ch = chunks[it.chunk];
+    if (it.dst != ch.dst || it.h != ch.h || it.kind != ch.kind || it.counter != ch.counter)
+      return "item does not carry its chunk's output fields";
+    if ((ch.kind == kScatterZ1 || ch.kind == kScatterZ2) && (it.aux != ch.scat0 || it.naux != ch.nscat))
+      return "item does not carry its chunk's scatter list";
+    if (it.hp < A_ || it.hp > kStreamHpMax || it.hp % A_ || (ch.kind != kPermute && it.hp < ch.h))
+      return "item height";
+    if (it.nruns < 0 || it.nruns > kMaxRuns) return "item run count";
+    const bool has_base = (it.flags & kItemBase) != 0;
+    if (has_base && (!(it.flags & kItemLast) || it.nruns < 1)) return "base on an item that does not end its chunk";
+    if (ch.counter == kCounterFlag && it.naux != ch.flag) return "item does not carry its chunk's flag";
+    int64_t cols = 0, staged = 0;
+    uint32_t deps = 0;
+    for (int r = 0; r < it.nruns; ++r) {
+      const Run& run = it.runs[r];
+      if (has_base && r == it.nruns - 1) {
+        const int bc = base_of_[it.chunk];
+        if (bc < 0 || chunks[bc].kind != kToZ3 || chunks[bc].h != ch.h ||
+            run.src != kSrcZ3 || run.start != chunks[bc].dst || it.aux != run.start || run.len != round_up(ch.h, A_))
+          return "near-field base run";
+        if (it.naux != chunks[bc].flag) {
+          // no flag: the base's CTA must publish a group this item waits for after the base
+          if (it.naux != -1 || cta_of_[bc] < 0) return "near-field base flag";
+          const int b = cta_of_[bc];
+          bool after = false, cov = false;
+          for (int32_t k = cta_begin[b]; k < cta_begin[b + 1]; ++k) {
+            const WorkItem& o = items[k];
+            if (o.chunk == bc && (o.flags & kItemLast)) after = true;
+            else if (after && (o.flags & kItemLast) && o.counter >= 0 && o.counter < kNumCounters &&
+                     ((it.flags >> (kDepShift + o.counter)) & 1))
+              cov = true;
+          }
+          if (!cov) return "near-field base neither flagged nor published by a later group";
+        }
+        // the flag's chunk is static, or handed out before this one; static chunks wait on no flag
+        if (pos < 0 || pool_pos_[bc] >= pos) return "near-field base handed out after its reader";
+        if (run.start < 0 || run.start + static_cast<int64_t>(run.len) > src_len_[kSrcZ3]) return "base outside z3";
+      } else {
+        if (run.src < 0 || run.src > 2 || run.len <= 0 || run.len % A_ || run.start < 0 || run.start % A_ ||
+            run.start + static_cast<int64_t>(run.len) > src_len_[run.src])
+          return "run outside its input vector or misaligned";
+        cols += run.len;
+      }
+      if (counter_of_source(run.src) >= 0) deps |= 1u << counter_of_source(run.src);
+      staged += run.len;
+    }
+    if (cols != it.ncols) return "item runs do not match its columns";
+    if (it.ncols < 0 || it.ncols > kStreamMaxCols || static_cast<int64_t>(it.ncols) * it.hp * eb_ > kTileBytes ||
+        (static_cast<int64_t>(it.ncols) * it.hp + staged) * eb_ > kStageBytes)
+      return "item tile size";
+    if (it.tile_off < 0 || (it.tile_off * eb_) % 16 || it.tile_off + static_cast<int64_t>(it.ncols) * it.hp > msize)
+      return "item tile outside the packed buffer or misaligned";
+    if (((static_cast<uint32_t>(it.flags) >> kDepShift) & ((1u << kNumCounters) - 1u)) != deps ||
+        (static_cast<uint32_t>(it.flags) >> (kDepShift + kNumCounters)) != 0)
+      return "item dependency bits";
+    // every wait ends: static items wait on static groups run earlier in every CTA; pool items on
+    // those and on chunks handed out before them
+    for (int g = 0; g < kNumCounters; ++g) {
+      if (!((deps >> g) & 1u)) continue;
+      if (pos < 0 ? (last_pool[g] >= 0 || last_static[g] >= group_[it.chunk]) : last_pool[g] >= pos)
+        return "item waits on a later group";
+    }
+    return nullptr;
+  };
+  // static lists
   for (int b = 0; b < ncta_; ++b) {
     int open_chunk = -1;
     for (int32_t k = cta_begin[b]; k < cta_begin[b + 1]; ++k) {
       const WorkItem& it = items[k];
-      if (it.chunk < 0 || it.chunk >= nchunk) return "item chunk out of range";
-      const OutChunk& ch = chunks[it.chunk];
-      if (it.dst != ch.dst || it.h != ch.h || it.kind != ch.kind || it.counter != ch.counter)
-        return "item does not carry its chunk's output fields";
-      if ((ch.kind == kScatterZ1 || ch.kind == kScatterZ2) && (it.aux != ch.scat0 || it.naux != ch.nscat))
-        return "item does not carry its chunk's scatter list";
-      // chunk items contiguous inside one CTA, first/last marks
+      if (const char* e = check_item(it, -1)) return e;
+      if (pool_pos_[it.chunk] >= 0 || cta_of_[it.chunk] != b) return "static item of a chunk placed elsewhere";
       if (it.flags & kItemFirst) {
         if (open_chunk >= 0 || seen[it.chunk]) return "chunk items not contiguous";
         open_chunk = it.chunk;
@@ -231,47 +367,31 @@ const char* ProgramBuilder::self_check() const {
       }
       if (open_chunk != it.chunk) return "item outside its chunk's range";
       if (it.flags & kItemLast) open_chunk = -1;
-      if (it.hp < A_ || it.hp > kStreamHpMax || it.hp % A_ || (ch.kind != kPermute && it.hp < ch.h))
-        return "item height";
-      if (it.ncols < 0 || it.ncols > kStreamMaxCols ||
-          static_cast<int64_t>(it.ncols) * it.hp * eb_ > kTileBytes ||
-          static_cast<int64_t>(it.ncols) * (it.hp + 1) * eb_ > kStageBytes)
-        return "item tile size";
-      if (it.tile_off < 0 || (it.tile_off * eb_) % 16 || it.tile_off + static_cast<int64_t>(it.ncols) * it.hp > msize)
-        return "item tile outside the packed buffer or misaligned";
-      if (it.nruns < 0 || it.nruns > kMaxRuns) return "item run count";
-      int64_t cols = 0;
-      uint32_t deps = 0;
-      for (int r = 0; r < it.nruns; ++r) {
-        const Run& run = it.runs[r];
-        if (run.src < 0 || run.src > 2 || run.len <= 0 || run.len % A_ || run.start < 0 || run.start % A_ ||
-            run.start + static_cast<int64_t>(run.len) > src_len_[run.src])
-          return "run outside its input vector or misaligned";
-        deps |= 1u << counter_of_source(run.src);
-        cols += run.len;
-      }
-      if (cols != it.ncols) return "item runs do not match its columns";
-      if (((static_cast<uint32_t>(it.flags) >> kDepShift) & 7u) != deps) return "item dependency bits";
-      // a group waits only on groups that every CTA runs before it
-      const int dep_group[kNumCounters] = {kGroupPermute, kGroupForward, kGroupCoupling};
-      for (int g = 0; g < kNumCounters; ++g)
-        if (((deps >> g) & 1u) && dep_group[g] >= group_[it.chunk]) return "item waits on a later group";
-      if (((it.flags & kItemBaseAll) != 0) != (base_of_[it.chunk] >= 0)) return "base flag on the wrong chunk";
-      if (it.flags & kItemBase) {
-        if (!(it.flags & kItemLast)) return "base on an item that does not end its chunk";
-        const int bc = base_of_[it.chunk];
-        if (bc < 0 || cta_of_[bc] != b || cta_of_[it.chunk] != b || chunks[bc].kind != kToZ3 ||
-            chunks[bc].dst != it.aux || chunks[bc].h != ch.h || !seen[bc] || group_[bc] >= group_[it.chunk])
-          return "near-field base not written earlier in the same CTA";
-        if (it.aux < 0 || it.aux + static_cast<int64_t>(ch.h) > src_len_[kSrcZ3]) return "base outside z3";
-      }
     }
     if (open_chunk >= 0) return "chunk not closed in its CTA";
   }
+  // pool: consecutive ranges after the static items, one chunk each
+  int32_t at = cta_begin[ncta_];
+  for (size_t t = 0; t < pool.size(); ++t) {
+    const PoolRange& r = pool[t];
+    if (r.begin != at || r.end <= r.begin) return "pool ranges";
+    at = r.end;
+    const int c = items[r.begin].chunk;
+    if (c < 0 || c >= nchunk || pool_pos_[c] != static_cast<int>(t) || seen[c]) return "pool chunk";
+    seen[c] = 1;
+    for (int32_t k = r.begin; k < r.end; ++k) {
+      const WorkItem& it = items[k];
+      if (const char* e = check_item(it, static_cast<int>(t))) return e;
+      if (it.chunk != c || ((it.flags & kItemFirst) != 0) != (k == r.begin) || ((it.flags & kItemLast) != 0) != (k == r.end - 1))
+        return "pool chunk items";
+    }
+  }
+  if (at != static_cast<int32_t>(items.size())) return "items after the pool";
   for (int c = 0; c < nchunk; ++c) {
     if (!seen[c]) return "chunk without items";
     const OutChunk& ch = chunks[c];
     if (ch.h < 1 || ch.dst < 0) return "chunk size";
+    if ((base_of_[c] >= 0) != ((chunk_items_[c].back().flags & kItemBase) != 0)) return "base flag on the wrong chunk";
     switch (ch.kind) {
       case kToZ1:
         if (ch.dst + ch.h > src_len_[kSrcZ1]) return "chunk outside z1";

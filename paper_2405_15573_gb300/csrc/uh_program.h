@@ -34,9 +34,12 @@ struct ColSpec {
   const int64_t* rowoff = nullptr;
 };
 
-// Schedule groups, in the order every CTA runs them. Flags only point to earlier groups.
+// Schedule groups. The first four are static (a list per CTA, in this group order); the last two
+// form the pool, in this order, handed out by ticket. An item only waits on counters whose
+// chunks are static and in earlier groups, or earlier in the pool.
 enum Group { kGroupPermute = 0, kGroupForward = 1, kGroupNearA = 2, kGroupCoupling = 3, kGroupNearB = 4,
              kGroupBackward = 5, kNumGroups = 6 };
+constexpr int kFirstPoolGroup = kGroupNearB;
 
 class ProgramBuilder {
  public:
@@ -48,26 +51,31 @@ class ProgramBuilder {
   // Input vector lengths (elements, multiples of align()).
   void set_source_len(int src, int64_t len) { src_len_[src] = len; }
 
-  // counter: the group counter the chunk's completion is added to (kCounter*), or -1.
+  // counter: the group counter the chunk's completion is added to (kCounter*), or -1. A kToZ3
+  // chunk (a near-field partial) releases a flag of its own instead.
   int add_chunk(int kind, int64_t dst, int h, int group, int counter = -1);
   // The columns of one chunk, in order. base_chunk >= 0: the chunk adds the outputs of that
-  // (near-field, kToZ3) chunk, which is placed in the same CTA ahead of it.
+  // (near-field, kToZ3) chunk, staged as an extra run of its last item.
   void add_columns(int chunk, const std::vector<ColSpec>& cols, int base_chunk = -1);
 
   // Scatter kinds: outputs lo <= r < hi of `chunk` also go to z[dst + r - lo].
   void add_scatter(int chunk, int64_t dst, int lo, int hi);
 
-  // Assign chunks to CTAs (phase groups in order, longest processing time first within a group;
-  // a chunk with a base goes to its base chunk's CTA) and lay the items out by CTA.
+  // Assign the static chunks to CTAs (groups in order, longest processing time first within a
+  // group), order the pool (each pool group largest first) and lay the items out: static by CTA,
+  // then the pool.
   const char* finalize();
   // Checks every address the kernel derives from the program. Returns nullptr if all hold.
   const char* self_check() const;
   // Chunks feeding each group counter (the kernel waits for epoch * count).
   int64_t counter_total(int c) const { return counter_total_[c]; }
+  // Flags released by near-field partials (each once per call).
+  int64_t flag_count() const { return nflags_; }
 
   // Results.
   std::vector<WorkItem> items;        // by CTA
-  std::vector<int32_t> cta_begin;     // ncta + 1
+  std::vector<int32_t> cta_begin;     // ncta + 1 (static items)
+  std::vector<PoolRange> pool;        // pool chunks in ticket order (items after the static ones)
   std::vector<OutChunk> chunks;
   std::vector<cd> M;                  // packed tiles (converted to the element type at upload)
   std::vector<Scatter> scatter;       // scatter entries
@@ -80,10 +88,14 @@ class ProgramBuilder {
   int ncta_;
   int64_t A_;   // elements per 16 bytes
   int eb_;      // bytes per element
-  std::vector<int> group_, base_of_, cta_of_;
+  std::vector<int> group_, base_of_, cta_of_, pool_pos_;
   std::vector<int64_t> bytes_;
   std::vector<std::vector<WorkItem>> chunk_items_;
   int64_t counter_total_[kNumCounters] = {0, 0, 0};
+  // Whether `reader` (which adds the partial of the static chunk at base_pos in a CTA's list) is
+  // covered by a later chunk of that list publishing a group the reader's last item waits for.
+  bool covered_by_cta(int reader, const std::vector<int>& list, int base_pos) const;
+  int64_t nflags_ = 0;
 };
 
 }  // namespace uh

@@ -2,15 +2,16 @@
 // Layout of the work and the dependency rules: uh_stream.h.
 //
 // Roles in a CTA of 320 threads:
-//  - producer (lane 0 of warp 8): streams the CTA's item descriptors into a shared-memory ring;
-//    per item waits for its stage to be free, copies the descriptor into the stage's slot, arms
-//    the stage's full barrier with the byte count, copies the tile with one TMA bulk copy and,
-//    once every group the item's runs read from is complete (checked once per group and call,
-//    then remembered), each input run with one more bulk copy into the stage's input area.
+//  - producer (lane 0 of warp 8): streams the CTA's item descriptors into a shared-memory ring
+//    (its static list in batches, then pool chunks taken by ticket, in segments); per item waits
+//    for its stage to be free, arms the stage's full barrier with the byte count, copies the tile
+//    with one TMA bulk copy and, once every group the item's runs read from is complete (checked
+//    once per group and call, then remembered), each input run with one more bulk copy into the
+//    stage's input area. After its last item it marks the next ring slot as the end.
 //  - consumers (warps 0-7): per item, wait for the stage, multiply the tile by the staged inputs
 //    into per-thread accumulators (thread = 16-byte row slice x column group), release the
-//    stage; at the end of a chunk reduce the column groups in a fixed tree order, add the
-//    near-field base if the chunk has one, write the outputs and, for chunks other CTAs wait on,
+//    stage; at the end of a chunk reduce the column groups in a fixed tree order, add the staged
+//    near-field partial if the chunk has one, write the outputs and, for chunks other CTAs wait on,
 //    hand the group counter to the publisher (each warp arrives after its own stores).
 //  - publisher (lane 0 of warp 9): per handed-over chunk, red.release on its group counter.
 // Every wait is bounded (timeout_cycles); when one runs out the CTA records it in `status`,
@@ -119,15 +120,16 @@ struct Bars {
   uint64_t* desc;       // descriptor batch landed
   uint64_t* pub_full;   // a finished chunk's outputs stored (one arrival per consumer warp)
   uint64_t* pub_empty;  // the publisher has taken the slot (1 arrival)
+  uint64_t* pool;       // pool descriptor segment landed [2] (1 arrival + bytes)
 };
 __device__ __forceinline__ Bars bars_of(unsigned char* smem) {
   uint64_t* b = reinterpret_cast<uint64_t*>(smem + kSmemBars);
   uint64_t* q = b + 2 * kStages + kDescBatches;
-  return Bars{b, b + kStages, b + 2 * kStages, q, q + kPubRing};
+  return Bars{b, b + kStages, b + 2 * kStages, q, q + kPubRing, q + 2 * kPubRing};
 }
 
-// Consumers: hand group counter `counter` (or -1: no more) to the publisher as release number
-// `np`. Each warp arrives after its own stores (the warp barrier orders its lanes' stores before
+// Consumers: hand counter `counter` (index in group_done, or -1: no more) to the publisher as
+// release number `np`. Each warp arrives after its own stores (the warp barrier orders its lanes' stores before
 // lane 0's arrive); thread 0 writes the counter first. Called by whole warps; false when aborting.
 __device__ __forceinline__ bool publish(const Bars& bar, int* pub_ctr, int np, int counter, const StreamParams& p,
                                         volatile int* abort_flag) {
@@ -175,6 +177,14 @@ __device__ void publisher(const StreamParams& p, unsigned char* smem) {
 // Orders this thread's earlier generic-proxy accesses before its later async-proxy (TMA) ones.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
+// Bounded wait for the completion of an mbarrier phase on the way out of an aborted CTA (the
+// copies in flight must land before the CTA exits).
+__device__ __forceinline__ void drain(uint64_t* bar, uint32_t parity, long long budget) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity) && clock64() - t0 < budget) {
+  }
+}
+
 template <typename R>
 __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* smem) {
   using T = typename Cx<R>::T;
@@ -184,6 +194,7 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
   const T* M = static_cast<const T*>(p.M);
   const int n = i1 - i0;
+  int batches = 0;  // static descriptor batches issued
   auto issue_batch = [&](int batch) {
     const int first = batch * kDescBatch;
     if (first >= n) return;
@@ -192,88 +203,193 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
     mbar_arrive_expect_tx(&bar.desc[q], static_cast<uint32_t>(cnt * sizeof(WorkItem)));
     bulk_g2s(ring + q * kDescBatch, p.items + i0 + first, static_cast<uint32_t>(cnt * sizeof(WorkItem)),
              &bar.desc[q]);
+    batches = batch + 1;
   };
   for (int b = 0; b < kDescBatches; ++b) issue_batch(b);  // batches 0 .. kDescBatches-1
-  int seq = 0;
+  int seq = 0;      // items whose stage has been armed
   bool ok = true;
   uint32_t ready = 0;  // groups known complete in this call
-  for (; seq < n; ++seq) {
-    const int batch = seq / kDescBatch;
-    if (seq % kDescBatch == 0 &&
-        !wait_parity(&bar.desc[batch % kDescBatches], static_cast<uint32_t>(batch / kDescBatches) & 1u,
-                     p.timeout_cycles, abort_flag)) {
-      atomicOr(p.status, 8u);
-      ok = false;
-      break;
-    }
-    const int s = seq % kStages;
-    const uint32_t k = static_cast<uint32_t>(seq / kStages);
-    if (k > 0 && !wait_parity(&bar.empty[s], (k - 1) & 1u, p.timeout_cycles, abort_flag)) {
+
+  // Waits for the stage of item `sq` to be free.
+  auto stage_free = [&](int sq) -> bool {
+    const uint32_t k = static_cast<uint32_t>(sq / kStages);
+    if (k > 0 && !wait_parity(&bar.empty[sq % kStages], (k - 1) & 1u, p.timeout_cycles, abort_flag)) {
       atomicOr(p.status, 2u);
+      return false;
+    }
+    return true;
+  };
+  // Arms the stage of item `sq` (descriptor in its ring slot) and issues its copies. When a group
+  // wait runs out the input copies are still issued (valid addresses, stale values), so that the
+  // stage's barrier completes and the way out can wait for it.
+  auto copy_item = [&](int sq) -> bool {
+    // the descriptor in registers: six 16-byte shared loads issued together
+    WorkItem it;
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(ring + sq % kDescRing);
+      uint4* w = reinterpret_cast<uint4*>(&it);
+#pragma unroll
+      for (int k = 0; k < static_cast<int>(sizeof(WorkItem) / 16); ++k) w[k] = src[k];
+    }
+    const int s = sq % kStages;
+    unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
+    const uint32_t tile_bytes = static_cast<uint32_t>(it.ncols) * static_cast<uint32_t>(it.hp) * sizeof(T);
+    uint32_t bytes = tile_bytes;
+#pragma unroll
+    for (int r = 0; r < kMaxRuns; ++r)
+      if (r < it.nruns) bytes += static_cast<uint32_t>(it.runs[r].len) * sizeof(T);
+    mbar_arrive_expect_tx(&bar.full[s], bytes);
+    if (tile_bytes) bulk_g2s(st, M + it.tile_off, tile_bytes, &bar.full[s]);
+    const uint32_t deps = (static_cast<uint32_t>(it.flags) >> kDepShift) & ((1u << kNumCounters) - 1u);
+    const bool flag = (it.flags & kItemBase) && it.naux >= 0;
+    bool done = true;
+    if ((deps & ~ready) || flag) {
+      const long long t0 = clock64();
+      bool flag_set = !flag;
+      for (;;) {
+        for (int g = 0; g < kNumCounters; ++g)
+          if (((deps & ~ready) >> g) & 1u)
+            if (ld_acquire_u64(p.group_done + g) >= p.need[g]) ready |= 1u << g;
+        if (!flag_set) flag_set = ld_acquire_u64(p.group_done + kFlagBase + it.naux) >= p.flag_need;
+        if (!(deps & ~ready) && flag_set) break;
+        __nanosleep(100);
+        if (*abort_flag || clock64() - t0 > p.timeout_cycles) {
+          atomicOr(p.status, 4u);
+          done = false;
+          break;
+        }
+      }
+      fence_proxy_async();  // the acquires above before the bulk copies that read those inputs
+    }
+    uint32_t col = 0;
+#pragma unroll
+    for (int r = 0; r < kMaxRuns; ++r) {
+      if (r >= it.nruns) break;
+      const Run run = it.runs[r];
+      bulk_g2s(st + tile_bytes + col * sizeof(T), static_cast<const T*>(src_ptr(p, run.src)) + run.start,
+               static_cast<uint32_t>(run.len) * sizeof(T), &bar.full[s]);
+      col += static_cast<uint32_t>(run.len);
+    }
+    return done;
+  };
+
+  // ---- static list
+  int waited = 0;  // static descriptor batches waited for
+  while (seq < n) {
+    const int batch = seq / kDescBatch;
+    if (seq % kDescBatch == 0) {
+      if (!wait_parity(&bar.desc[batch % kDescBatches], static_cast<uint32_t>(batch / kDescBatches) & 1u,
+                       p.timeout_cycles, abort_flag)) {
+        atomicOr(p.status, 8u);
+        ok = false;
+        break;
+      }
+      waited = batch + 1;
+    }
+    if (!stage_free(seq)) {
       ok = false;
       break;
     }
-    const WorkItem& it = ring[seq % kDescRing];
     if (seq % kDescBatch == kDescBatch - 1 && batch >= 1) {
       // The consumers have finished item seq - kStages (we waited for its stage), so they are
       // past batch - 1: refill its ring slots with the batch kDescBatches further on.
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue_batch(batch - 1 + kDescBatches);
     }
-    unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
-    const uint32_t tile_bytes = static_cast<uint32_t>(it.ncols) * static_cast<uint32_t>(it.hp) * sizeof(T);
-    uint32_t bytes = tile_bytes;
-    for (int r = 0; r < it.nruns; ++r) bytes += static_cast<uint32_t>(it.runs[r].len) * sizeof(T);
-    mbar_arrive_expect_tx(&bar.full[s], bytes);
-    if (tile_bytes) bulk_g2s(st, M + it.tile_off, tile_bytes, &bar.full[s]);
-    const uint32_t deps = (static_cast<uint32_t>(it.flags) >> kDepShift) & ((1u << kNumCounters) - 1u);
-    if (deps & ~ready) {
-      const long long t0 = clock64();
-      for (;;) {
-        for (int g = 0; g < kNumCounters; ++g)
-          if (((deps & ~ready) >> g) & 1u)
-            if (ld_acquire_u64(p.group_done + g) >= p.need[g]) ready |= 1u << g;
-        if (!(deps & ~ready)) break;
-        __nanosleep(100);
-        if (*abort_flag || clock64() - t0 > p.timeout_cycles) {
-          atomicOr(p.status, 4u);
+    if (!copy_item(seq++)) {
+      ok = false;
+      break;
+    }
+  }
+
+  // ---- pool: a CTA takes chunks by ticket until its first ticket past the end. The next ticket is
+  // taken three items before the end of the current chunk and resolved after its last item is
+  // issued (the atomic's latency is hidden behind those items); descriptors are fetched into the
+  // ring one segment ahead.
+  unsigned long long* ticket = p.group_done + kTicketIndex;
+  const unsigned long long P = static_cast<unsigned long long>(p.pool_chunks);
+  int fetched = 0, landed = 0;  // pool segments fetched / waited for
+  int fseq = seq;               // ring position of the next fetched segment
+  auto fetch = [&](int g, int end) {
+    const int cnt = end - g < kPoolSeg ? end - g : kPoolSeg;
+    uint64_t* fb = &bar.pool[fetched & 1];
+    const int s0 = fseq % kDescRing;
+    const int c0 = cnt < kDescRing - s0 ? cnt : kDescRing - s0;
+    // the consumers' reads of these ring slots (observed through the stage barriers) before the copy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(fb, static_cast<uint32_t>(cnt * sizeof(WorkItem)));
+    bulk_g2s(ring + s0, p.items + g, static_cast<uint32_t>(c0 * sizeof(WorkItem)), fb);
+    if (c0 < cnt) bulk_g2s(ring, p.items + g + c0, static_cast<uint32_t>((cnt - c0) * sizeof(WorkItem)), fb);
+    fseq += cnt;
+    ++fetched;
+  };
+  if (ok) {
+    // ticket index in this call; a counter left short by an aborted call reads as past the end
+    const unsigned long long t0 = atomicAdd(ticket, 1ull) - p.ticket_base;
+    bool more = t0 < P;
+    PoolRange r{0, 0};
+    if (more) {
+      r = p.pool[t0];
+      fetch(r.begin, r.end);
+    }
+    while (more && ok) {
+      const int take_at = r.end - 3 > r.begin ? r.end - 3 : r.begin;
+      unsigned long long raw = 0ull;
+      bool more1 = false;
+      PoolRange r1{0, 0};
+      for (int g = r.begin; g < r.end && ok; g += kPoolSeg) {
+        const int cnt = r.end - g < kPoolSeg ? r.end - g : kPoolSeg;
+        if (!wait_parity(&bar.pool[landed & 1], static_cast<uint32_t>(landed >> 1) & 1u, p.timeout_cycles,
+                         abort_flag)) {
+          atomicOr(p.status, 8u);
           ok = false;
           break;
         }
+        ++landed;
+        if (g + cnt < r.end) fetch(g + cnt, r.end);  // the chunk's next segment
+        for (int j = 0; j < cnt; ++j) {
+          if (!stage_free(seq)) {
+            ok = false;
+            break;
+          }
+          if (g + j == take_at) raw = atomicAdd(ticket, 1ull);
+          if (!copy_item(seq++)) {
+            ok = false;
+            break;
+          }
+        }
       }
       if (!ok) break;
-      fence_proxy_async();  // the acquire above before the bulk copies that read those inputs
-    }
-    uint32_t col = 0;
-    for (int r = 0; r < it.nruns; ++r) {
-      const Run run = it.runs[r];
-      bulk_g2s(st + tile_bytes + col * sizeof(T), static_cast<const T*>(src_ptr(p, run.src)) + run.start,
-               static_cast<uint32_t>(run.len) * sizeof(T), &bar.full[s]);
-      col += static_cast<uint32_t>(run.len);
+      // the next chunk: its range, and the first segment of its descriptors
+      const unsigned long long t1 = raw - p.ticket_base;
+      more1 = t1 < P;
+      if (more1) {
+        r1 = p.pool[t1];
+        fetch(r1.begin, r1.end);
+      }
+      more = more1;
+      r = r1;
     }
   }
-  if (!ok) {
-    *abort_flag = 1;
-    // Let every bulk copy already issued land before the CTA can exit: bounded waits on the
-    // stages of the last kStages items and on the descriptor batches in flight.
-    const int first = seq >= kStages ? seq - kStages + 1 : 0;
-    for (int q = first; q <= seq && q < n; ++q) {
-      const long long t0 = clock64();
-      while (!mbar_try_wait(&bar.full[q % kStages], static_cast<uint32_t>(q / kStages) & 1u) &&
-             clock64() - t0 < p.timeout_cycles) {
-      }
-    }
-    for (int b = seq / kDescBatch; b < seq / kDescBatch + kDescBatches && b * kDescBatch < n; ++b) {
-      const long long t0 = clock64();
-      while (!mbar_try_wait(&bar.desc[b % kDescBatches], static_cast<uint32_t>(b / kDescBatches) & 1u) &&
-             clock64() - t0 < p.timeout_cycles) {
-      }
-    }
+  // ---- end mark: the next ring slot says kEnd; its stage's full barrier completes without bytes
+  if (ok && stage_free(seq)) {
+    reinterpret_cast<volatile int16_t*>(&ring[seq % kDescRing].kind)[0] = kEnd;
+    mbar_arrive(&bar.full[seq % kStages]);
+    return;
   }
+  *abort_flag = 1;
+  // Let every bulk copy already issued land before the CTA can exit: bounded waits on the stages
+  // of the last kStages armed items and on the descriptor copies in flight.
+  for (int q = seq >= kStages ? seq - kStages : 0; q < seq; ++q)
+    drain(&bar.full[q % kStages], static_cast<uint32_t>(q / kStages) & 1u, p.timeout_cycles);
+  for (int b = waited; b < batches; ++b)
+    drain(&bar.desc[b % kDescBatches], static_cast<uint32_t>(b / kDescBatches) & 1u, p.timeout_cycles);
+  for (int f = landed; f < fetched; ++f)
+    drain(&bar.pool[f & 1], static_cast<uint32_t>(f >> 1) & 1u, p.timeout_cycles);
 }
 
 template <typename R>
-__device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* smem) {
+__device__ void consumers(const StreamParams& p, unsigned char* smem) {
   using T = typename Cx<R>::T;
   constexpr int EPL = 16 / sizeof(T);
   const int tid = threadIdx.x;
@@ -283,7 +399,6 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
   const Bars bar = bars_of(smem);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
   volatile int* go = abort_flag + 1;  // go[0], go[1]: leader's decision, by item parity
-  const int n = i1 - i0;
 
   T acc[EPL];
   T base = T{0, 0};
@@ -292,7 +407,7 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
   const int warp = tid >> 5;
   int nchunk = 0;  // reduced chunks so far: their parity selects the chunk-end buffers
   int np = 0;      // releases handed to the publisher
-  for (int seq = 0; seq < n; ++seq) {
+  for (int seq = 0;; ++seq) {
     const int s = seq % kStages;
     const uint32_t parity = static_cast<uint32_t>(seq / kStages) & 1u;
     if (tid == 0) {
@@ -308,6 +423,7 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
     // The leader's acquire of the full barrier, then the consumer barrier, order the stage's
     // bulk-copied data before every consumer thread's reads.
     const WorkItem& sl = ring[seq % kDescRing];
+    if (sl.kind == kEnd) break;
     const int flags = sl.flags;
     const int hp = sl.hp, nc = sl.ncols;
     const int kind = sl.kind, h = sl.h, counter = sl.counter, aux = sl.aux, naux = sl.naux;
@@ -321,12 +437,8 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
       // the chunk's scatter entries, used at its end
       for (int k = tid; k < naux && k < 256; k += kStreamConsumers) sscat[k] = p.scatter[aux + k];
     }
-    if ((flags & kItemFirst) && tid < h) {
-      // near-field partial of this row tile, written earlier by this same thread, and the
-      // output's original index: loaded now, used at the end of the chunk
-      if (flags & kItemBaseAll) base = static_cast<const T*>(p.z3)[aux + tid];
-      if (kind == kToY) out_idx = p.perm[dst + tid];
-    }
+    // the output's original index: loaded now, used at the end of the chunk
+    if ((flags & kItemFirst) && tid < h && kind == kToY) out_idx = p.perm[dst + tid];
     if (flags & kItemFirst) {
       need = hp / EPL;
       lanes = 1;
@@ -366,6 +478,8 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
         for (int e = 0; e < EPL; ++e) cfma(acc[e], m0[e], v0);
       }
     }
+    // the near-field partial of this row tile, staged after the inputs
+    if ((flags & kItemBase) && tid < h) base = reinterpret_cast<const T*>(st)[static_cast<size_t>(nc) * hp + nc + tid];
     // The stage (tile, inputs, slot) has been read: release it to the producer.
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(&bar.empty[s]);
@@ -413,7 +527,8 @@ __device__ void consumers(const StreamParams& p, int i0, int i1, unsigned char* 
         ++nchunk;
       }
       // On failure the abort flag is set; the leader's next wait then ends the loop for all.
-      if (counter >= 0) publish(bar, pub_ctr, np++, counter, p, abort_flag);
+      if (counter >= 0)
+        publish(bar, pub_ctr, np++, counter == kCounterFlag ? kFlagBase + naux : counter, p, abort_flag);
     }
   }
   // No more releases: let the publisher finish (skipped when aborting; decided per warp).
@@ -431,6 +546,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamP
       mbar_init(&bar.empty[s], kStreamConsumerWarps);
     }
     for (int q = 0; q < kDescBatches; ++q) mbar_init(&bar.desc[q], 1);
+    for (int q = 0; q < 2; ++q) mbar_init(&bar.pool[q], 1);
     for (int q = 0; q < kPubRing; ++q) {
       mbar_init(&bar.pub_full[q], kStreamConsumerWarps);
       mbar_init(&bar.pub_empty[q], 1);
@@ -439,13 +555,12 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamP
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int i0 = p.cta_begin[blockIdx.x], i1 = p.cta_begin[blockIdx.x + 1];
   if (threadIdx.x >= kStreamConsumers + 32) {
     if (threadIdx.x == kStreamConsumers + 32) publisher(p, smem);
   } else if (threadIdx.x >= kStreamConsumers) {
-    if (threadIdx.x == kStreamConsumers) producer<R>(p, i0, i1, smem);
+    if (threadIdx.x == kStreamConsumers) producer<R>(p, p.cta_begin[blockIdx.x], p.cta_begin[blockIdx.x + 1], smem);
   } else {
-    consumers<R>(p, i0, i1, smem);
+    consumers<R>(p, smem);
   }
   __syncthreads();
 }

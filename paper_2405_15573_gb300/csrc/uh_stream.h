@@ -9,15 +9,24 @@
 // (cp.async.bulk, mbarrier transaction counts); eight consumer warps multiply and accumulate, and
 // at the end of a chunk reduce the column groups and write the chunk's outputs.
 //
-// Dependencies are per phase group: an item that reads x in cluster order, xhat or yhat waits
-// (in its producer, before copying those runs) until every chunk of the group that writes that
-// vector has finished in this call, counted by a monotonic 64-bit counter per group. A producer
-// checks a group once per call and then remembers it. Each CTA's list is ordered by group and a
-// group only waits on earlier groups, so the waits end. The release that publishes a finished
-// chunk to the other CTAs (red.release on the group counter) is issued by a publisher warp, fed
-// through a ring of mbarriers, so that its wait for the chunk's stores is off the consumers' path. The near-field partial of a row tile is
-// written and read back by the same consumer thread (its near-field and backward chunks are in
-// the same CTA), so it needs no flag.
+// Dependencies are per phase group: an item that reads x in cluster order, xhat, yhat or a
+// near-field partial waits (in its producer, before copying those runs) until every chunk of the
+// group that writes that vector has finished in this call, counted by a monotonic 64-bit counter
+// per group. A producer checks a group once per call and then remembers it. The release that
+// publishes a finished chunk to the other CTAs (red.release on the group counter) is issued by a
+// publisher warp, fed through a ring of mbarriers, so that its wait for the chunk's stores is off
+// the consumers' path.
+//
+// Work is placed in two parts. The static part (permutation, forward transform, the first half of
+// the near field, coupling) is a list per CTA, ordered by group; a group there only waits on
+// earlier groups. The pool (the second half of the near field, then the backward chunks) is one
+// list of chunks in a fixed order that the CTAs take from, one chunk per ticket of a global
+// counter, once their static list is issued. A CTA whose static part ran slowly takes fewer pool
+// chunks: the end times of the CTAs differ by about one pool chunk. A backward chunk adds its row
+// tile's near-field partial, written by any CTA: every near-field chunk that writes a partial
+// releases a flag of its own, and the backward chunk stages the partial like an input run once
+// that flag is set in this call. A pool chunk only waits on static groups and on flags of chunks
+// handed out before it, so every wait ends.
 #pragma once
 
 #include <stdint.h>
@@ -34,6 +43,9 @@ constexpr int kStreamMaxCols = 512;     // largest column count of an item
 constexpr int kStageBytes = 69632;      // an item's tile and inputs (inputs at the tile's end)
 constexpr int kMaxRuns = 6;
 constexpr int kStreamHpMax = 64;
+// Pool descriptors are fetched into the ring in segments of at most kPoolSeg items, one segment
+// ahead of the items being issued.
+constexpr int kPoolSeg = 16;
 
 // Work-item descriptors are streamed into a ring of kDescRing entries, kDescBatch per copy.
 // The consumers read the descriptors in the ring; a batch is refilled only after the producer
@@ -42,6 +54,7 @@ constexpr int kDescBatch = 8;
 constexpr int kDescBatches = 8;
 constexpr int kDescRing = kDescBatch * kDescBatches;
 static_assert(kStages < kDescBatch, "consumers must be past a batch when it is refilled");
+static_assert(2 * kPoolSeg + kStages <= kDescRing, "a fetched pool segment must not overwrite live descriptors");
 
 // Shared-memory layout of the kernel (bytes). The chunk-end buffers are double-buffered by chunk
 // parity, so a chunk end needs no barrier after its last use of them.
@@ -50,8 +63,8 @@ constexpr int kSmemDesc = kSmemRed + 2 * kStreamConsumers * 16;  // descriptor r
 constexpr int kSmemScat = kSmemDesc + kDescRing * 96;            // scatter entries of a chunk [2] (256 x 8 B)
 constexpr int kSmemVals = kSmemScat + 2 * 256 * 8;                // a chunk's outputs before they are scattered [2]
 constexpr int kSmemBars = kSmemVals + 2 * 64 * 16;                // full, empty [kStages], desc [kDescBatches],
-                                                                  // pub_full, pub_empty [kPubRing]
-constexpr int kSmemMisc = kSmemBars + (2 * kStages + kDescBatches + 2 * kPubRing) * 8;  // abort flag, decision words
+                                                                  // pub_full, pub_empty [kPubRing], pool [2]
+constexpr int kSmemMisc = kSmemBars + (2 * kStages + kDescBatches + 2 * kPubRing + 2) * 8;  // abort flag, decision words
 constexpr int kSmemPub = kSmemMisc + 32;                          // group counter of each release [kPubRing]
 constexpr int kStreamSmemBytes = kSmemPub + kPubRing * 4;
 static_assert(kStreamSmemBytes <= 227 * 1024, "shared memory of one CTA");
@@ -68,17 +81,26 @@ struct Run {
 static_assert(sizeof(Run) == 8, "Run layout");
 
 // Item flags: chunk boundaries, near-field base, and the groups whose completion the item's runs
-// need (bits kDepShift + counter index).
-enum : int16_t { kItemFirst = 1, kItemLast = 2, kItemBase = 4, kItemBaseAll = 8 };
+// need (bits kDepShift + counter index). kItemBase (on the last item of a chunk): the item's last
+// run is not a column input but the chunk's near-field partial z3[aux .. aux + h), staged after
+// the inputs, once flag naux is set (naux -1: the partial's CTA published it, before this item's
+// group counters, through a later chunk of those groups), and added to the outputs.
+enum : int16_t { kItemFirst = 1, kItemLast = 2, kItemBase = 4 };
 constexpr int kDepShift = 8;
 enum : int { kCounterPermute = 0, kCounterForward = 1, kCounterCoupling = 2, kNumCounters = 3 };
+// WorkItem::counter of a chunk that releases its own flag (number naux) instead of a group counter.
+constexpr int kCounterFlag = 15;
+// Layout of the counter array: group counters, the pool ticket, then the flags.
+constexpr int kTicketIndex = kNumCounters;
+constexpr int kFlagBase = kNumCounters + 1;
 
 // Chunk outputs: kToZ1..kToZ3 write z[dst + r]; kToY writes y[perm[dst + r]]; kPermute fills
 // xp[dst + r] = x[perm[dst + r]] (no tile, no inputs); kScatterZ1 / kScatterZ2 write output r to
 // z[e.dst + r - e.lo] for every scatter entry e with e.lo <= r < e.hi (the chunk's entries are
 // scatter[aux .. aux + naux)): each consumer chunk then finds its inputs in one contiguous run.
 // counter >= 0: the chunk's completion is added to that group counter.
-enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kPermute = 4, kScatterZ1 = 5, kScatterZ2 = 6 };
+// kEnd: written by a CTA's producer after its last item (never packed).
+enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kPermute = 4, kScatterZ1 = 5, kScatterZ2 = 6, kEnd = 7 };
 
 struct Scatter {
   int32_t dst;
@@ -96,10 +118,11 @@ struct alignas(16) WorkItem {
   int16_t counter;   // the chunk's group counter, or -1
   int16_t nruns;
   int16_t flags;     // kItem* | dependency bits
-  int32_t aux;       // kItemBaseAll (every item of such a chunk), kItemBase (its last item): the
-                     // chunk adds z3[aux + r] to output r; scatter kinds: first scatter entry
+  int32_t aux;       // kItemBase: the chunk adds z3[aux + r] to output r; scatter kinds: first
+                     // scatter entry
   int32_t chunk;     // chunk number (host bookkeeping)
-  int32_t naux;      // scatter kinds: number of scatter entries
+  int32_t naux;      // scatter kinds: number of scatter entries; kCounterFlag chunks: their flag;
+                     // kItemBase: the flag of the near-field partial
   Run runs[kMaxRuns];
 };
 static_assert(sizeof(WorkItem) == 96, "WorkItem layout");
@@ -111,13 +134,25 @@ struct OutChunk {
   int16_t kind;
   int16_t counter;
   int32_t scat0 = 0, nscat = 0;  // scatter entries of scatter kinds
+  int32_t flag = -1;             // near-field partials (kToZ3): the flag the chunk releases
+};
+
+struct PoolRange {
+  int32_t begin, end;  // items of a pool chunk: [begin, end)
 };
 
 struct StreamParams {
   const WorkItem* items;
-  const int32_t* cta_begin;  // items of CTA b: [cta_begin[b], cta_begin[b + 1])
-  unsigned long long* group_done;  // [kNumCounters], monotonic over calls
-  unsigned long long need[kNumCounters];  // a group is complete when group_done >= need
+  const int32_t* cta_begin;  // static items of CTA b: [cta_begin[b], cta_begin[b + 1])
+  const PoolRange* pool;     // [pool_chunks], in the order the tickets hand them out
+  int64_t pool_chunks;
+  unsigned long long* group_done;  // counters, monotonic over calls: [kNumCounters] group counters,
+                                   // [kTicketIndex] the pool ticket (every call adds pool_chunks +
+                                   // grid: one failed take per CTA), [kFlagBase + f] flag f (every
+                                   // call adds 1)
+  unsigned long long need[kNumCounters];  // a group is complete when its counter >= need
+  unsigned long long ticket_base;  // ticket value at the start of this call
+  unsigned long long flag_need;    // a flag is set in this call when it is >= flag_need
   const void* M;             // packed tiles
   const void* x;             // input, original ordering
   void* y;                   // output, original ordering
