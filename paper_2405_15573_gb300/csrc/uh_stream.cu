@@ -60,6 +60,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// The same with an L2 eviction policy (createpolicy) for the source lines.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -209,6 +218,11 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
   int seq = 0;      // items whose stage has been armed
   bool ok = true;
   uint32_t ready = 0;  // groups known complete in this call
+  // Tiles are read once per call: first out of L2, so that the vectors (a few MB, read by every
+  // call's input copies and permutation) stay in it across calls.
+  uint64_t stream_once, keep;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_once));
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
 
   // Waits for the stage of item `sq` to be free.
   auto stage_free = [&](int sq) -> bool {
@@ -239,7 +253,7 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
     for (int r = 0; r < kMaxRuns; ++r)
       if (r < it.nruns) bytes += static_cast<uint32_t>(it.runs[r].len) * sizeof(T);
     mbar_arrive_expect_tx(&bar.full[s], bytes);
-    if (tile_bytes) bulk_g2s(st, M + it.tile_off, tile_bytes, &bar.full[s]);
+    if (tile_bytes) bulk_g2s_hint(st, M + it.tile_off, tile_bytes, &bar.full[s], stream_once);
     const uint32_t deps = (static_cast<uint32_t>(it.flags) >> kDepShift) & ((1u << kNumCounters) - 1u);
     const bool flag = (it.flags & kItemBase) && it.naux >= 0;
     bool done = true;
@@ -266,8 +280,8 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
     for (int r = 0; r < kMaxRuns; ++r) {
       if (r >= it.nruns) break;
       const Run run = it.runs[r];
-      bulk_g2s(st + tile_bytes + col * sizeof(T), static_cast<const T*>(src_ptr(p, run.src)) + run.start,
-               static_cast<uint32_t>(run.len) * sizeof(T), &bar.full[s]);
+      bulk_g2s_hint(st + tile_bytes + col * sizeof(T), static_cast<const T*>(src_ptr(p, run.src)) + run.start,
+                    static_cast<uint32_t>(run.len) * sizeof(T), &bar.full[s], keep);
       col += static_cast<uint32_t>(run.len);
     }
     return done;
