@@ -203,6 +203,7 @@ struct OpBase {
   uh::Scatter* d_scatter = nullptr;
   uh::PoolRange* d_pool = nullptr;
   int64_t pool_chunks = 0;
+  int64_t perm_n = 0;  // positions of x permuted at the start of a product
   int64_t counter_total[uh::kNumCounters] = {};
   uint32_t* d_status = nullptr;
   int32_t* d_perm = nullptr;
@@ -279,6 +280,7 @@ int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T) {
   if ((rc = upload(P.scatter.data(), P.scatter.size() * sizeof(uh::Scatter), &o->d_scatter))) return rc;
   if ((rc = upload(P.pool.data(), P.pool.size() * sizeof(uh::PoolRange), &o->d_pool))) return rc;
   o->pool_chunks = static_cast<int64_t>(P.pool.size());
+  o->perm_n = P.permutation_length();
   o->done_len = uh::kFlagBase + P.flag_count();
   if ((rc = upload(static_cast<const void*>(nullptr), o->done_len * sizeof(unsigned long long), &o->d_done)))
     return rc;
@@ -322,6 +324,7 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
                 static_cast<unsigned long long>(o->counter_total[c]);
   p.M = o->d_M;
   p.x = x;
+  p.n = o->perm_n;
   p.y = y;
   p.perm = o->d_perm;
   p.scatter = o->d_scatter;
@@ -496,17 +499,6 @@ int matmat_by_columns(OpBase* o, int32_t nrhs, const void* X, int64_t ldx, void*
   return UH_OK;
 }
 
-// Permutation slices (group 0): one per CTA.
-void add_permute(ProgramBuilder& P, int64_t n, int ncta) {
-  const int64_t A = P.align();
-  for (int b = 0; b < ncta; ++b) {
-    const int64_t a = (n * b / ncta) / A * A;
-    const int64_t e = b == ncta - 1 ? n : (n * (b + 1) / ncta) / A * A;
-    if (e <= a) continue;
-    const int c = P.add_chunk(uh::kPermute, a, static_cast<int>(e - a), uh::kGroupPermute, uh::kCounterPermute);
-    P.add_columns(c, {});
-  }
-}
 
 // Near-field chunks of the row tiles, alternating between the two near-field groups (static,
 // before the coupling; and the first part of the pool). A tile with a backward part writes its z3
@@ -823,7 +815,7 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
   ProgramBuilder P(c128, T.n, ncta);
   const int64_t A = P.align();
-  add_permute(P, T.n, ncta);
+  P.set_permutation(T.n);
   Offsets off;
   add_uh_program(P, u, &off);
   P.set_source_len(uh::kSrcXp, ProgramBuilder::round_up(T.n, A));
@@ -925,7 +917,7 @@ int h_create(const h_desc* d, int32_t precision, h_op** out) {
   const int64_t A = P.align();
   P.set_source_len(uh::kSrcXp, ProgramBuilder::round_up(T.n, A));
   P.set_source_len(uh::kSrcZ2, 0);
-  add_permute(P, T.n, ncta);
+  P.set_permutation(T.n);
   // t_b = Y_b^* x|_sigma. The blocks of one column cluster sigma share their input x|_sigma, so
   // their rows Y_b^* are stacked (blocks in increasing row cluster) and cut into chunks of at most
   // 64 rows; t holds each sigma's t_b consecutively.
@@ -1064,7 +1056,7 @@ int uh_batch_create(const uh_desc* const* descs, int32_t count, int32_t precisio
   if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
   ProgramBuilder P(c128, total, ncta);
   const int64_t A = P.align();
-  add_permute(P, total, ncta);
+  P.set_permutation(total);
   // The batch as one operator on the concatenated vectors: position offsets[k] + i of the
   // cluster order is point perm_k[i] of operator k, i.e. entry offsets[k] + perm_k[i].
   Tree all;

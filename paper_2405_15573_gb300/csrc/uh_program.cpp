@@ -43,7 +43,7 @@ int counter_of_source(int src) {
 
 void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, int base_chunk) {
   const int h = chunks[chunk].h;
-  const int64_t hp = chunks[chunk].kind == kPermute ? A_ : std::max<int64_t>(A_, round_up(h, A_));
+  const int64_t hp = std::max<int64_t>(A_, round_up(h, A_));
   // an item's tile (hp x ncols) and its inputs (ncols) share one stage buffer
   int64_t maxcols = std::min<int64_t>(kStreamMaxCols, std::min<int64_t>(kTileBytes / (hp * eb_), kStageBytes / ((hp + 1) * eb_)));
   maxcols = maxcols / A_ * A_;
@@ -119,7 +119,7 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
     k0 = k1;
   }
   close_item();
-  if (out.empty()) {  // no columns: one empty item writes zeros (or, for a permutation slice, runs it)
+  if (out.empty()) {  // no columns: one empty item writes zeros
     start_item();
     close_item();
   }
@@ -182,15 +182,6 @@ const char* ProgramBuilder::finalize() {
     std::vector<int> ids;
     for (int c = 0; c < nchunk; ++c)
       if (group_[c] == g) ids.push_back(c);
-    if (g == kGroupPermute) {
-      for (size_t j = 0; j < ids.size(); ++j) {
-        const int b = static_cast<int>(j % ncta_);
-        per_cta[b].push_back(ids[j]);
-        cta_of_[ids[j]] = b;
-        load[b] += bytes_[ids[j]];
-      }
-      continue;
-    }
     std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return bytes_[a] > bytes_[b]; });
     if (g >= kFirstPoolGroup) {
       // Largest first; a chunk whose near-field partial comes from the pool goes after every chunk
@@ -268,6 +259,10 @@ const char* ProgramBuilder::finalize() {
 
 const char* ProgramBuilder::self_check() const {
   const int nchunk = static_cast<int>(chunks.size());
+  // the kernel permutes positions [0, perm_n) of x into xp, one slice per CTA, each CTA releasing
+  // the permutation counter once
+  if (perm_n_ < 0 || perm_n_ > src_len_[kSrcXp] || counter_total_[kCounterPermute] != ncta_)
+    return "permutation";
   if (static_cast<int>(cta_begin.size()) != ncta_ + 1 || cta_begin[0] != 0) return "CTA item ranges";
   for (int b = 0; b < ncta_; ++b)
     if (cta_begin[b] > cta_begin[b + 1]) return "CTA item ranges not monotone";
@@ -278,6 +273,7 @@ const char* ProgramBuilder::self_check() const {
   for (int c = 0; c < nchunk; ++c) {
     const int ctr = chunks[c].counter;
     if ((ctr < -1 || ctr >= kNumCounters) && ctr != kCounterFlag) return "chunk counter";
+    if (ctr == kCounterPermute) return "a chunk releasing the permutation counter";
     if ((ctr == kCounterFlag) != (chunks[c].kind == kToZ3)) return "flag of a chunk that is no near-field partial";
     if (ctr == kCounterFlag && (chunks[c].flag < 0 || chunks[c].flag >= nflags_)) return "chunk flag";
     if (ctr < 0 || ctr == kCounterFlag) continue;
@@ -294,7 +290,7 @@ const char* ProgramBuilder::self_check() const {
       return "item does not carry its chunk's output fields";
     if ((ch.kind == kScatterZ1 || ch.kind == kScatterZ2) && (it.aux != ch.scat0 || it.naux != ch.nscat))
       return "item does not carry its chunk's scatter list";
-    if (it.hp < A_ || it.hp > kStreamHpMax || it.hp % A_ || (ch.kind != kPermute && it.hp < ch.h))
+    if (it.hp < A_ || it.hp > kStreamHpMax || it.hp % A_ || it.hp < ch.h)
       return "item height";
     if (it.nruns < 0 || it.nruns > kMaxRuns) return "item run count";
     const bool has_base = (it.flags & kItemBase) != 0;
@@ -417,9 +413,6 @@ const char* ProgramBuilder::self_check() const {
         }
         break;
       }
-      case kPermute:
-        if (ch.dst + ch.h > n_ || ch.dst + ch.h > src_len_[kSrcXp]) return "permutation slice outside x";
-        break;
       default:
         return "chunk kind";
     }

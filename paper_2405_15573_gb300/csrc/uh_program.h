@@ -34,8 +34,9 @@ struct ColSpec {
   const int64_t* rowoff = nullptr;
 };
 
-// Schedule groups. The first four are static (a list per CTA, in this group order); the last two
-// form the pool, in this order, handed out by ticket. An item only waits on counters whose
+// Schedule groups. The first four are static (a list per CTA, in this group order; the permutation
+// group has no chunks: every CTA permutes a slice of x at entry); the last two form the pool, in
+// this order, handed out by ticket. An item only waits on counters whose
 // chunks are static and in earlier groups, or earlier in the pool.
 enum Group { kGroupPermute = 0, kGroupForward = 1, kGroupNearA = 2, kGroupCoupling = 3, kGroupNearB = 4,
              kGroupBackward = 5, kNumGroups = 6 };
@@ -50,6 +51,14 @@ class ProgramBuilder {
 
   // Input vector lengths (elements, multiples of align()).
   void set_source_len(int src, int64_t len) { src_len_[src] = len; }
+
+  // x in cluster order: the kernel permutes positions [0, n) into xp at entry, one slice per CTA,
+  // and every CTA releases the permutation counter once.
+  void set_permutation(int64_t n) {
+    perm_n_ = n;
+    counter_total_[kCounterPermute] = ncta_;
+  }
+  int64_t permutation_length() const { return perm_n_; }
 
   // counter: the group counter the chunk's completion is added to (kCounter*), or -1. A kToZ3
   // chunk (a near-field partial) releases a flag of its own instead.
@@ -96,6 +105,7 @@ class ProgramBuilder {
   // covered by a later chunk of that list publishing a group the reader's last item waits for.
   bool covered_by_cta(int reader, const std::vector<int>& list, int base_pos) const;
   int64_t nflags_ = 0;
+  int64_t perm_n_ = -1;
 };
 
 }  // namespace uh

@@ -421,6 +421,16 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
   const int warp = tid >> 5;
   int nchunk = 0;  // reduced chunks so far: their parity selects the chunk-end buffers
   int np = 0;      // releases handed to the publisher
+  {
+    // This CTA's slice of the permutation, then its release (each warp after its own stores).
+    const int64_t b = blockIdx.x, nb = gridDim.x;
+    const int64_t a = (p.n * b / nb) / EPL * EPL;
+    const int64_t e = b == nb - 1 ? p.n : (p.n * (b + 1) / nb) / EPL * EPL;
+    const T* x = static_cast<const T*>(p.x);
+    T* xp = static_cast<T*>(p.xp);
+    for (int64_t r = a + tid; r < e; r += kStreamConsumers) xp[r] = x[p.perm[r]];
+    publish(bar, pub_ctr, np++, kCounterPermute, p, abort_flag);
+  }
   for (int seq = 0;; ++seq) {
     const int s = seq % kStages;
     const uint32_t parity = static_cast<uint32_t>(seq / kStages) & 1u;
@@ -464,11 +474,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
 #pragma unroll
       for (int e = 0; e < EPL; ++e) acc[e] = T{0, 0};
     }
-    if (kind == kPermute) {
-      const T* x = static_cast<const T*>(p.x);
-      T* xp = static_cast<T*>(p.xp);
-      for (int r = tid; r < h; r += kStreamConsumers) xp[dst + r] = x[p.perm[dst + r]];
-    } else if (lane < need) {
+    if (lane < need) {
       const T* tile = reinterpret_cast<const T*>(st) + lane * EPL;
       const T* vin = reinterpret_cast<const T*>(st) + static_cast<size_t>(nc) * hp;  // inputs after the tile
       int c = g;
@@ -498,48 +504,46 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(&bar.empty[s]);
     if (flags & kItemLast) {
-      if (kind != kPermute) {
-        // Column groups in one warp (lanes < 32: groups g and g ^ (m / lanes) share a warp):
-        // butterfly over the group bits of the lane index, fixed order.
-        for (int m = lanes; m < 32; m <<= 1) {
+      // Column groups in one warp (lanes < 32: groups g and g ^ (m / lanes) share a warp):
+      // butterfly over the group bits of the lane index, fixed order.
+      for (int m = lanes; m < 32; m <<= 1) {
 #pragma unroll
-          for (int e = 0; e < EPL; ++e) acc[e] = cadd(acc[e], shfl_xor(acc[e], m));
-        }
-        // One partial per warp (lanes <= 32) or per group (lanes >= 32): at most 8 of them.
-        const int parts = lanes < 32 ? kStreamConsumerWarps : groups;
-        const int part = lanes < 32 ? warp : g;
-        if (lanes >= 32 || (tid & 31) < lanes) {
-#pragma unroll
-          for (int e = 0; e < EPL; ++e) sred[part * hpl + lane * EPL + e] = acc[e];
-        }
-        consumer_sync();
-        if (tid < h) {
-          T v = sred[tid];
-          for (int q = 1; q < parts; ++q) v = cadd(v, sred[q * hpl + tid]);
-          if (flags & kItemBase) v = cadd(v, base);
-          if (kind == kToY) {
-            static_cast<T*>(p.y)[out_idx] = v;
-          } else if (kind == kScatterZ1 || kind == kScatterZ2) {
-            svals[tid] = v;
-          } else {
-            T* z = static_cast<T*>(kind == kToZ1 ? p.z1 : kind == kToZ2 ? p.z2 : p.z3);
-            z[dst + tid] = v;
-          }
-        }
-        if (kind == kScatterZ1 || kind == kScatterZ2) {
-          consumer_sync();  // svals written
-          // (entry, row) pairs over all consumer threads: each entry's rows are consecutive
-          T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : p.z2);
-          for (int w = tid; w < naux * h; w += kStreamConsumers) {
-            const int k = w / h, r = w - k * h;
-            const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];
-            if (r >= e.lo && r < e.hi) z[e.dst + r - e.lo] = svals[r];
-          }
-        }
-        // sred, svals and sscat of this parity are next written two chunks on, after the next
-        // chunk end's barrier.
-        ++nchunk;
+        for (int e = 0; e < EPL; ++e) acc[e] = cadd(acc[e], shfl_xor(acc[e], m));
       }
+      // One partial per warp (lanes <= 32) or per group (lanes >= 32): at most 8 of them.
+      const int parts = lanes < 32 ? kStreamConsumerWarps : groups;
+      const int part = lanes < 32 ? warp : g;
+      if (lanes >= 32 || (tid & 31) < lanes) {
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) sred[part * hpl + lane * EPL + e] = acc[e];
+      }
+      consumer_sync();
+      if (tid < h) {
+        T v = sred[tid];
+        for (int q = 1; q < parts; ++q) v = cadd(v, sred[q * hpl + tid]);
+        if (flags & kItemBase) v = cadd(v, base);
+        if (kind == kToY) {
+          static_cast<T*>(p.y)[out_idx] = v;
+        } else if (kind == kScatterZ1 || kind == kScatterZ2) {
+          svals[tid] = v;
+        } else {
+          T* z = static_cast<T*>(kind == kToZ1 ? p.z1 : kind == kToZ2 ? p.z2 : p.z3);
+          z[dst + tid] = v;
+        }
+      }
+      if (kind == kScatterZ1 || kind == kScatterZ2) {
+        consumer_sync();  // svals written
+        // (entry, row) pairs over all consumer threads: each entry's rows are consecutive
+        T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : p.z2);
+        for (int w = tid; w < naux * h; w += kStreamConsumers) {
+          const int k = w / h, r = w - k * h;
+          const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];
+          if (r >= e.lo && r < e.hi) z[e.dst + r - e.lo] = svals[r];
+        }
+      }
+      // sred, svals and sscat of this parity are next written two chunks on, after the next
+      // chunk end's barrier.
+      ++nchunk;
       // On failure the abort flag is set; the leader's next wait then ends the loop for all.
       if (counter >= 0)
         publish(bar, pub_ctr, np++, counter == kCounterFlag ? kFlagBase + naux : counter, p, abort_flag);

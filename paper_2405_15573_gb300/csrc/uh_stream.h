@@ -17,9 +17,11 @@
 // publisher warp, fed through a ring of mbarriers, so that its wait for the chunk's stores is off
 // the consumers' path.
 //
-// Work is placed in two parts. The static part (permutation, forward transform, the first half of
-// the near field, coupling) is a list per CTA, ordered by group; a group there only waits on
-// earlier groups. The pool (the second half of the near field, then the backward chunks) is one
+// Every CTA first permutes its slice of x into cluster order (xp), at entry, without descriptors:
+// positions [a_b, a_{b+1}) with a_b = floor(n b / grid) rounded down to 16 bytes, and publishes the
+// permutation counter (one release per CTA). Work is then placed in two parts. The static part
+// (forward transform, the first half of the near field, coupling) is a list per CTA, ordered by
+// group; a group there only waits on earlier groups. The pool (the second half of the near field, then the backward chunks) is one
 // list of chunks in a fixed order that the CTAs take from, one chunk per ticket of a global
 // counter, once their static list is issued. A CTA whose static part ran slowly takes fewer pool
 // chunks: the end times of the CTAs differ by about one pool chunk. A backward chunk adds its row
@@ -94,13 +96,12 @@ constexpr int kCounterFlag = 15;
 constexpr int kTicketIndex = kNumCounters;
 constexpr int kFlagBase = kNumCounters + 1;
 
-// Chunk outputs: kToZ1..kToZ3 write z[dst + r]; kToY writes y[perm[dst + r]]; kPermute fills
-// xp[dst + r] = x[perm[dst + r]] (no tile, no inputs); kScatterZ1 / kScatterZ2 write output r to
+// Chunk outputs: kToZ1..kToZ3 write z[dst + r]; kToY writes y[perm[dst + r]]; kScatterZ1 / kScatterZ2 write output r to
 // z[e.dst + r - e.lo] for every scatter entry e with e.lo <= r < e.hi (the chunk's entries are
 // scatter[aux .. aux + naux)): each consumer chunk then finds its inputs in one contiguous run.
 // counter >= 0: the chunk's completion is added to that group counter.
 // kEnd: written by a CTA's producer after its last item (never packed).
-enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kPermute = 4, kScatterZ1 = 5, kScatterZ2 = 6, kEnd = 7 };
+enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kScatterZ1 = 5, kScatterZ2 = 6, kEnd = 7 };
 
 struct Scatter {
   int32_t dst;
@@ -114,7 +115,7 @@ struct alignas(16) WorkItem {
   int32_t hp;        // rows of the tile = padded chunk height
   int32_t ncols;     // tile columns = staged input values (sum of the run lengths)
   int32_t h;         // the chunk's height
-  int16_t kind;      // the chunk's output kind (kTo*, kPermute)
+  int16_t kind;      // the chunk's output kind (kTo*, kScatter*)
   int16_t counter;   // the chunk's group counter, or -1
   int16_t nruns;
   int16_t flags;     // kItem* | dependency bits
@@ -155,6 +156,7 @@ struct StreamParams {
   unsigned long long flag_need;    // a flag is set in this call when it is >= flag_need
   const void* M;             // packed tiles
   const void* x;             // input, original ordering
+  int64_t n;                 // positions permuted into xp (all operators of the program)
   void* y;                   // output, original ordering
   const int32_t* perm;       // position -> original index
   const Scatter* scatter;    // scatter entries of the scatter kinds
