@@ -36,6 +36,9 @@ namespace {
 // streaming and ~1 us per chunk end).
 constexpr int64_t kItemCost = 4096;
 constexpr int64_t kChunkCost = 49152;
+// Consecutive pool chunks are handed out by one ticket until their cost reaches this (a ticket
+// costs the producer about 2 us of latency, hidden only behind enough staged work).
+constexpr int64_t kPoolUnitCost = 131072;
 int counter_of_source(int src) {
   return src == kSrcXp ? kCounterPermute : src == kSrcZ1 ? kCounterForward : src == kSrcZ2 ? kCounterCoupling : -1;
 }
@@ -176,7 +179,7 @@ const char* ProgramBuilder::finalize() {
   std::vector<int64_t> load(ncta_, 0);
   cta_of_.assign(nchunk, -1);
   pool_pos_.assign(nchunk, -1);
-  std::vector<int> pool_order;
+  std::vector<int> pool_order, order_pos(nchunk, -1);
   using Entry = std::pair<int64_t, int>;  // (load, cta), smallest first
   for (int g = 0; g < kNumGroups; ++g) {
     std::vector<int> ids;
@@ -189,11 +192,11 @@ const char* ProgramBuilder::finalize() {
       // (so that it is likely complete when the chunk is taken).
       auto key = [&](int c) -> int64_t {
         const int b = base_of_[c];
-        return b >= 0 && pool_pos_[b] >= 0 ? 1 + pool_pos_[b] : 0;
+        return b >= 0 && order_pos[b] >= 0 ? 1 + order_pos[b] : 0;
       };
       std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return key(a) < key(b); });
       for (int c : ids) {
-        pool_pos_[c] = static_cast<int>(pool_order.size());
+        order_pos[c] = static_cast<int>(pool_order.size());
         pool_order.push_back(c);
       }
       continue;
@@ -246,10 +249,20 @@ const char* ProgramBuilder::finalize() {
   }
   cta_begin[ncta_] = static_cast<int32_t>(items.size());
   pool.clear();
-  for (int c : pool_order) {
+  first_item_.assign(nchunk, -1);
+  for (int32_t k = 0; k < cta_begin[ncta_]; ++k)
+    if (items[k].flags & kItemFirst) first_item_[items[k].chunk] = k;
+  for (size_t k = 0; k < pool_order.size();) {
     PoolRange r{};
     r.begin = static_cast<int32_t>(items.size());
-    emit(c);
+    int64_t cost = 0;
+    while (k < pool_order.size() && cost < kPoolUnitCost) {
+      const int c = pool_order[k++];
+      pool_pos_[c] = static_cast<int>(pool.size());
+      cost += bytes_[c];
+      first_item_[c] = static_cast<int32_t>(items.size());
+      emit(c);
+    }
     r.end = static_cast<int32_t>(items.size());
     pool.push_back(r);
   }
@@ -319,8 +332,10 @@ const char* ProgramBuilder::self_check() const {
           }
           if (!cov) return "near-field base neither flagged nor published by a later group";
         }
-        // the flag's chunk is static, or handed out before this one; static chunks wait on no flag
-        if (pos < 0 || pool_pos_[bc] >= pos) return "near-field base handed out after its reader";
+        // the flag's chunk is static, or handed out before this one (or earlier by the same
+        // ticket: the same consumers finish it first); static chunks wait on no flag
+        if (pos < 0 || pool_pos_[bc] > pos) return "near-field base handed out after its reader";
+        if (pool_pos_[bc] == pos && first_item_[bc] > first_item_[it.chunk]) return "near-field base after its reader";
         if (run.start < 0 || run.start + static_cast<int64_t>(run.len) > src_len_[kSrcZ3]) return "base outside z3";
       } else {
         if (run.src < 0 || run.src > 2 || run.len <= 0 || run.len % A_ || run.start < 0 || run.start % A_ ||
@@ -366,21 +381,26 @@ const char* ProgramBuilder::self_check() const {
     }
     if (open_chunk >= 0) return "chunk not closed in its CTA";
   }
-  // pool: consecutive ranges after the static items, one chunk each
+  // pool: consecutive ranges after the static items, each one or more whole chunks
   int32_t at = cta_begin[ncta_];
   for (size_t t = 0; t < pool.size(); ++t) {
     const PoolRange& r = pool[t];
     if (r.begin != at || r.end <= r.begin) return "pool ranges";
     at = r.end;
-    const int c = items[r.begin].chunk;
-    if (c < 0 || c >= nchunk || pool_pos_[c] != static_cast<int>(t) || seen[c]) return "pool chunk";
-    seen[c] = 1;
+    int open_chunk = -1;
     for (int32_t k = r.begin; k < r.end; ++k) {
       const WorkItem& it = items[k];
+      if (it.chunk < 0 || it.chunk >= nchunk || pool_pos_[it.chunk] != static_cast<int>(t)) return "pool chunk";
       if (const char* e = check_item(it, static_cast<int>(t))) return e;
-      if (it.chunk != c || ((it.flags & kItemFirst) != 0) != (k == r.begin) || ((it.flags & kItemLast) != 0) != (k == r.end - 1))
-        return "pool chunk items";
+      if (it.flags & kItemFirst) {
+        if (open_chunk >= 0 || seen[it.chunk]) return "pool chunk items not contiguous";
+        open_chunk = it.chunk;
+        seen[it.chunk] = 1;
+      }
+      if (open_chunk != it.chunk) return "item outside its pool chunk";
+      if (it.flags & kItemLast) open_chunk = -1;
     }
+    if (open_chunk >= 0) return "pool chunk not closed in its range";
   }
   if (at != static_cast<int32_t>(items.size())) return "items after the pool";
   for (int c = 0; c < nchunk; ++c) {

@@ -84,7 +84,8 @@ class ProgramBuilder {
   // Results.
   std::vector<WorkItem> items;        // by CTA
   std::vector<int32_t> cta_begin;     // ncta + 1 (static items)
-  std::vector<PoolRange> pool;        // pool chunks in ticket order (items after the static ones)
+  std::vector<PoolRange> pool;        // pool tickets in order: each one or more whole chunks (items
+                                      // after the static ones)
   std::vector<OutChunk> chunks;
   std::vector<cd> M;                  // packed tiles (converted to the element type at upload)
   std::vector<Scatter> scatter;       // scatter entries
@@ -98,6 +99,7 @@ class ProgramBuilder {
   int64_t A_;   // elements per 16 bytes
   int eb_;      // bytes per element
   std::vector<int> group_, base_of_, cta_of_, pool_pos_;
+  std::vector<int32_t> first_item_;  // index of each chunk's first item
   std::vector<int64_t> bytes_;
   std::vector<std::vector<WorkItem>> chunk_items_;
   int64_t counter_total_[kNumCounters] = {0, 0, 0};

@@ -316,10 +316,10 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
     }
   }
 
-  // ---- pool: a CTA takes chunks by ticket until its first ticket past the end. The next ticket is
-  // taken three items before the end of the current chunk and resolved after its last item is
-  // issued (the atomic's latency is hidden behind those items); descriptors are fetched into the
-  // ring one segment ahead.
+  // ---- pool: a CTA takes tickets (each one or more whole chunks) until its first ticket past the
+  // end. The next ticket is taken three items before the end of the current one and resolved after
+  // its last item is issued (the atomic's latency is hidden behind those items); descriptors are
+  // fetched into the ring one segment ahead.
   unsigned long long* ticket = p.group_done + kTicketIndex;
   const unsigned long long P = static_cast<unsigned long long>(p.pool_chunks);
   int fetched = 0, landed = 0;  // pool segments fetched / waited for

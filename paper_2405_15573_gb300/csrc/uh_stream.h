@@ -139,13 +139,14 @@ struct OutChunk {
 };
 
 struct PoolRange {
-  int32_t begin, end;  // items of a pool chunk: [begin, end)
+  int32_t begin, end;  // items of a pool ticket: [begin, end), one or more whole chunks
 };
 
 struct StreamParams {
   const WorkItem* items;
   const int32_t* cta_begin;  // static items of CTA b: [cta_begin[b], cta_begin[b + 1])
-  const PoolRange* pool;     // [pool_chunks], in the order the tickets hand them out
+  const PoolRange* pool;     // [pool_chunks] item ranges (one or more whole chunks each), in the
+                             // order the tickets hand them out
   int64_t pool_chunks;
   unsigned long long* group_done;  // counters, monotonic over calls: [kNumCounters] group counters,
                                    // [kTicketIndex] the pool ticket (every call adds pool_chunks +
