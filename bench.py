@@ -603,9 +603,8 @@ def gpu_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
         "data": "synthetic",
-        "config": {"workload": f"UH matvec, unit-sphere Helmholtz collocation N={w.n} k={w.wavenumber:g} "
-                               f"leaf {w.leaf} eta {w.eta:g} eps {w.eps:g}, complex64 storage, FP32 "
-                               f"accumulation, 1 RHS",
+        "config": {"workload": workload_name(w),
+                   "precision": "complex64 storage, FP32 accumulation",
                    "l2": "inputs larger than L2: the packed operator is "
                          f"{st['packed_bytes'] / 2**20:.0f} MiB, every step streams all of it; no flush",
                    "parallelism": f"replicas x{world}", "operator_build_s": round(build_s, 2)},
@@ -648,6 +647,12 @@ def gpu_arm(args):
 # ----------------------------------------------------------------------------- reference arm
 
 
+def workload_name(w):
+    """The benchmark workload, named the same way by both arms."""
+    return (f"UH matvec, unit-sphere Helmholtz collocation N={w.n} k={w.wavenumber:g} leaf {w.leaf} "
+            f"eta {w.eta:g} eps {w.eps:g}, 1 RHS")
+
+
 def reference_arm(args):
     """The oracle (FP64 NumPy, one BLAS thread) timed on the benchmark workload: the operator is
     made by the library's host builder (no GPU), written out, and each step is one full oracle UH
@@ -670,11 +675,12 @@ def reference_arm(args):
         import shutil
         shutil.rmtree(tmpdir, ignore_errors=True)
     ms = 1e3 * secs / reps
-    out = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0, "steps": reps,
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    out = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world, "steps": reps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"UH matvec (FP64 oracle), unit-sphere Helmholtz collocation "
-                                  f"N={w.n} k={w.wavenumber:g} leaf {w.leaf} eta {w.eta:g} eps {w.eps:g}, 1 RHS",
+           "config": {"workload": workload_name(w),
+                      "precision": "complex128, the FP64 oracle on the host (no GPU work)",
                       "operator_build_s": round(build_s, 1)},
            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{reps} full FP64 oracle UH matvecs of the N={w.n} operator "
