@@ -3,12 +3,13 @@
 //
 // Roles in a CTA of 320 threads:
 //  - producer (lane 0 of warp 8): streams the CTA's item descriptors into a shared-memory ring
-//    (its static list in batches, then pool chunks taken by ticket, in segments); per item waits
+//    (its static list in batches, then pool tickets, in segments); per item waits
 //    for its stage to be free, arms the stage's full barrier with the byte count, copies the tile
 //    with one TMA bulk copy and, once every group the item's runs read from is complete (checked
 //    once per group and call, then remembered), each input run with one more bulk copy into the
 //    stage's input area. After its last item it marks the next ring slot as the end.
-//  - consumers (warps 0-7): per item, wait for the stage, multiply the tile by the staged inputs
+//  - consumers (warps 0-7): first gather the CTA's slice of x into cluster order and release the
+//    permutation counter; then per item, wait for the stage, multiply the tile by the staged inputs
 //    into per-thread accumulators (thread = 16-byte row slice x column group), release the
 //    stage; at the end of a chunk reduce the column groups in a fixed tree order, add the staged
 //    near-field partial if the chunk has one, write the outputs and, for chunks other CTAs wait on,

@@ -9,26 +9,27 @@
 // (cp.async.bulk, mbarrier transaction counts); eight consumer warps multiply and accumulate, and
 // at the end of a chunk reduce the column groups and write the chunk's outputs.
 //
-// Dependencies are per phase group: an item that reads x in cluster order, xhat, yhat or a
-// near-field partial waits (in its producer, before copying those runs) until every chunk of the
-// group that writes that vector has finished in this call, counted by a monotonic 64-bit counter
-// per group. A producer checks a group once per call and then remembers it. The release that
-// publishes a finished chunk to the other CTAs (red.release on the group counter) is issued by a
-// publisher warp, fed through a ring of mbarriers, so that its wait for the chunk's stores is off
-// the consumers' path.
+// Dependencies are per phase group: an item that reads x in cluster order, xhat or yhat waits (in
+// its producer, before copying those runs) until every chunk of the group that writes that vector
+// has finished in this call, counted by a monotonic 64-bit counter per group. A producer checks a
+// group once per call and then remembers it. The release that publishes a finished chunk to the
+// other CTAs (red.release on the group counter) is issued by a publisher warp, fed through a ring
+// of mbarriers, so that its wait for the chunk's stores is off the consumers' path.
 //
 // Every CTA first permutes its slice of x into cluster order (xp), at entry, without descriptors:
 // positions [a_b, a_{b+1}) with a_b = floor(n b / grid) rounded down to 16 bytes, and publishes the
 // permutation counter (one release per CTA). Work is then placed in two parts. The static part
 // (forward transform, the first half of the near field, coupling) is a list per CTA, ordered by
-// group; a group there only waits on earlier groups. The pool (the second half of the near field, then the backward chunks) is one
-// list of chunks in a fixed order that the CTAs take from, one chunk per ticket of a global
-// counter, once their static list is issued. A CTA whose static part ran slowly takes fewer pool
-// chunks: the end times of the CTAs differ by about one pool chunk. A backward chunk adds its row
-// tile's near-field partial, written by any CTA: every near-field chunk that writes a partial
-// releases a flag of its own, and the backward chunk stages the partial like an input run once
-// that flag is set in this call. A pool chunk only waits on static groups and on flags of chunks
-// handed out before it, so every wait ends.
+// group; a group there only waits on earlier groups. The pool (the second half of the near field,
+// then the backward chunks) is one list of tickets in a fixed order, each one or more whole chunks,
+// that the CTAs take from through a global counter once their static list is issued. A CTA whose
+// static part ran slowly takes fewer tickets: the end times of the CTAs differ by about one
+// ticket. A backward chunk adds its row tile's near-field partial, written by any CTA: every
+// near-field chunk that writes a partial releases a flag of its own, and the backward chunk stages
+// the partial like an input run once that flag is set in this call (or without a flag, when the
+// partial's CTA published it through a later chunk of a group the backward chunk waits for). A
+// pool chunk only waits on static groups and on flags of chunks handed out before it (or earlier
+// in its own ticket), so every wait ends.
 #pragma once
 
 #include <stdint.h>
