@@ -30,8 +30,11 @@
  *    op owns, and return; the caller keeps ownership of its arrays and may free them afterwards.
  *  - Product calls take DEVICE pointers owned by the caller and are asynchronous on the given
  *    cudaStream_t (passed as void*, NULL = legacy default stream). Scratch memory belongs to the
- *    op; calls on one op must be ordered (same stream, or synchronised between streams), since
- *    they share that scratch.
+ *    op. Calls on one op may come from several streams and host threads: the library runs them
+ *    in the order they are made (a call on another stream than the op's previous call waits,
+ *    on the device, for that call's work), since they share the op's scratch and its per-call
+ *    counters. Two products of one op could not overlap anyway: each one fills the GPU. Calls on
+ *    different ops are independent. Inside a CUDA-graph stream capture, keep an op on one stream.
  */
 #ifndef UH_H
 #define UH_H
@@ -254,8 +257,9 @@ int uh_batch_stats(const uh_batch* batch, uh_stats_t* out);
  * Gram-Schmidt, two passes), the norms and the update x += V y run in FP64 on the GPU. A solve
  * ends as converged only when the recomputed residual of the returned x satisfies
  * ||b - A x|| <= tol ||b||. Its arithmetic does not depend on the other solves running with it.
- * The server uses the device current at uh_server_create and its own stream; the ops it is
- * given must live on that device, outlive their solves, and not be used elsewhere meanwhile.
+ * The server uses the device current at uh_server_create and streams of its own; the ops it is
+ * given must live on that device and outlive their solves. Products the caller runs on the same
+ * ops meanwhile are ordered with the solves' products, like any calls on one op.
  */
 typedef struct uh_server uh_server;
 

@@ -21,6 +21,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -222,6 +223,15 @@ struct OpBase {
   void* d_pz1 = nullptr;
   void* d_pz2 = nullptr;
   uh_stats_t st{};
+  // Calls on one op run in the order they are made, from any streams and host threads: they
+  // share the op's scratch and its per-call counters, and two products of one op could not run
+  // at the same time anyway (each fills the GPU). `mu` serialises the host side; every call
+  // records `order_ev` on its stream after its work, and a call on another stream than the
+  // previous one first waits for that event.
+  std::mutex mu;
+  bool called = false;
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t order_ev = nullptr;
 };
 
 void free_op(OpBase* o) {
@@ -231,6 +241,22 @@ void free_op(OpBase* o) {
                   o->d_ptiles, o->d_pitems, o->d_pbegin, o->d_pxp, o->d_pz1, o->d_pz2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (o->order_ev) cudaEventDestroy(o->order_ev);
+}
+
+// Orders a call on stream s after the op's previous call (the caller holds o->mu).
+int order_call(OpBase* o, cudaStream_t s) {
+  if (!o->order_ev) CUDA_TRY(cudaEventCreateWithFlags(&o->order_ev, cudaEventDisableTiming));
+  if (o->called && s != o->last_stream) CUDA_TRY(cudaStreamWaitEvent(s, o->order_ev, 0));
+  return UH_OK;
+}
+
+// Marks the end of a call's work on stream s (the caller holds o->mu).
+int call_done(OpBase* o, cudaStream_t s) {
+  CUDA_TRY(cudaEventRecord(o->order_ev, s));
+  o->called = true;
+  o->last_stream = s;
+  return UH_OK;
 }
 
 template <typename T>
@@ -307,6 +333,10 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   const char* xa = static_cast<const char*>(x);
   const char* ya = static_cast<const char*>(y);
   if (xa < ya + o->n * eb && ya < xa + o->n * eb) return fail(UH_EINVAL, "x and y overlap");
+  std::lock_guard<std::mutex> lock(o->mu);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc;
+  if ((rc = order_call(o, s))) return rc;
   ++o->epoch;
   uh::StreamParams p{};
   p.items = o->d_items;
@@ -334,13 +364,19 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   p.z3 = o->d_z3;
   p.status = o->d_status;
   p.timeout_cycles = timeout;
-  cudaError_t e = uh::stream_launch(o->c128, p, o->ncta, static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return fail(UH_ECUDA, "streaming kernel launch: %s", cudaGetErrorString(e));
-  return UH_OK;
+  cudaError_t e = uh::stream_launch(o->c128, p, o->ncta, s);
+  if (e != cudaSuccess) {
+    --o->epoch;  // nothing launched: the counters did not move
+    return fail(UH_ECUDA, "streaming kernel launch: %s", cudaGetErrorString(e));
+  }
+  return call_done(o, s);
 }
 
 int check_status(OpBase* o, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(o->mu);
+  int rc;
+  if ((rc = order_call(o, s))) return rc;
   uint32_t v = 0;
   CUDA_TRY(cudaMemcpyAsync(&v, o->d_status, sizeof v, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -1203,6 +1239,8 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
   if (op->mm_mode != mode)
     return fail(UH_EINVAL, "matmat mode %d needs an op created with precision %s", mode,
                 mode == UH_MM_TF32 ? "UH_PREC_C64_TF32" : "UH_PREC_C64_BF16X3");
+  std::lock_guard<std::mutex> lock(op->mu);
+  if ((rc = order_call(op, static_cast<cudaStream_t>(stream)))) return rc;
   for (int32_t rhs0 = 0; rhs0 < nrhs; rhs0 += uh::kPanelR) {
     const int32_t nb = std::min<int32_t>(uh::kPanelR, nrhs - rhs0);
     if ((rc = uh::panel_gather(X, ldx, op->n, op->d_perm, rhs0, nb, op->d_pxp, stream))) return rc;
@@ -1227,7 +1265,7 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
       if ((rc = uh::panel_launch(p, op->panel_ncta, stream))) return rc;
     }
   }
-  return UH_OK;
+  return call_done(op, static_cast<cudaStream_t>(stream));
 }
 int uh_reserve(uh_op* op, int32_t max_nrhs) {
   if (!op) return fail(UH_EINVAL, "null op");

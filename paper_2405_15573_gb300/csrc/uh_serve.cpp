@@ -104,7 +104,6 @@ struct uh_server {
   int queue_cap = 64;
   std::vector<cudaStream_t> streams;          // one per running solve (slots)
   std::vector<char> slot_used;
-  std::map<uh_op*, cudaEvent_t> op_done;      // the last product launched per op
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Solve*> pending;
@@ -210,29 +209,16 @@ int start_solve(uh_server* sv, Solve* s, cudaStream_t st) {
 
 // out = A v (complex128 out; for complex64 ops through v32 / y32). With out null, a complex64 op
 // leaves its product in y32 for the caller to widen; v32_ready: v32 already holds complex64(v).
-// The per-op event that orders that op's products across the solves' streams.
-thread_local std::map<uh_op*, cudaEvent_t>* g_op_done = nullptr;
-
-int ordered_matvec(uh_op* op, const void* x, void* y, cudaStream_t st) {
-  cudaEvent_t& ev = (*g_op_done)[op];
-  if (!ev) {
-    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return UH_ECUDA;
-  } else if (cudaStreamWaitEvent(st, ev, 0) != cudaSuccess) {
-    return UH_ECUDA;
-  }
-  const int rc = uh_matvec(op, x, y, st);
-  if (rc) return rc;
-  return cudaEventRecord(ev, st) == cudaSuccess ? UH_OK : UH_ECUDA;
-}
-
+// Products of one op issued from different solves' streams run in call order: uh_matvec orders
+// the calls on an op.
 int apply_op(Solve* s, const void* v, void* out, cudaStream_t st, bool v32_ready = false) {
   int rc;
   if (s->c64) {
     if (!v32_ready && (rc = uh::vec_d2f(v, s->v32, s->n, st))) return rc;
-    if ((rc = ordered_matvec(s->op, s->v32, s->y32, st))) return rc;
+    if ((rc = uh_matvec(s->op, s->v32, s->y32, st))) return rc;
     return out ? uh::vec_f2d(s->y32, out, s->n, st) : UH_OK;
   }
-  return ordered_matvec(s->op, v, out, st);
+  return uh_matvec(s->op, v, out, st);
 }
 
 // Kernels of the start of a cycle: V_0 = (b - A x) / ||b - A x|| (and its complex64 copy for the
@@ -374,7 +360,6 @@ void after(Solve* s) {
 
 void worker_main(uh_server* sv) {
   cudaSetDevice(sv->device);
-  g_op_done = &sv->op_done;
   for (;;) {
     std::vector<Solve*> round;
     {
@@ -506,8 +491,6 @@ int uh_server_destroy(uh_server* sv) {
   sv->cv.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
   for (cudaStream_t st : sv->streams) cudaStreamDestroy(st);
-  for (auto& kv : sv->op_done)
-    if (kv.second) cudaEventDestroy(kv.second);
   delete sv;
   return UH_OK;
 }

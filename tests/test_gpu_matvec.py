@@ -50,6 +50,37 @@ WORKLOADS = {
 }
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_calls_on_two_streams_run_in_call_order(U, prec):
+    """Products of one op issued alternately on two streams, with no synchronisation between the
+    streams and the first stream held back by a sleep kernel, equal bit for bit the same products
+    issued on one stream: the library runs calls on one op in the order they are made (they share
+    the op's scratch and per-call counters)."""
+    import torch
+    pts, tree, hf, h, uh = oracle_ops(*WORKLOADS["sphere2048"])
+    op = U.UHOp.from_arrays(uh_arrays(uh), prec)
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    xs = [torch.from_numpy(I.complex_normal(tree.n, 100 + k)).to("cuda", dt) for k in range(8)]
+    ref = []
+    for x in xs:
+        y = torch.empty_like(x)
+        op.matvec(x, y)
+        ref.append(y)
+    ys = [torch.full_like(x, complex(float("nan"), float("nan"))) for x in xs]
+    torch.cuda.synchronize()
+    op.check()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    if hasattr(torch.cuda, "_sleep"):
+        with torch.cuda.stream(streams[0]):
+            torch.cuda._sleep(40_000_000)  # about 20 ms: the first product starts late
+    for k, x in enumerate(xs):
+        op.matvec(x, ys[k], stream=streams[k & 1])
+    torch.cuda.synchronize()
+    op.check()
+    for k in range(len(xs)):
+        assert torch.equal(ys[k], ref[k]), k
+
+
 @pytest.mark.parametrize("name", list(WORKLOADS))
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 def test_uh_matvec_parity(U, name, prec):
