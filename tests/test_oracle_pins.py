@@ -356,3 +356,171 @@ def test_compression_invariant_under_refactorisation(ops512):
     assert uhm.ranks() == uh.ranks()
     A1, A2 = O.uh_to_dense(uh), O.uh_to_dense(uhm)
     assert np.linalg.norm(A1 - A2) <= 1e-10 * np.linalg.norm(A1)
+
+
+# ---------------------------------------------------------------- two-sided pins (Def. 2.5,
+# Section 2.3, Theorem 5.1, Lemma 2.6): each equality fails on a one-index or missing-factor slip
+
+
+def test_sparsity_constant_hand_counted():
+    """Def. 2.5 on block lists written out by hand. row(1) = {2, 3}, row(4) = {2, 5, 6},
+    row(7) = {2}; col(2) = {1, 4, 7}, col(3) = {1}, col(5) = {4}, col(6) = {4}: c_sp = 3,
+    reached by a row set and by a column set. The second list reaches its maximum only on the
+    column side, the third only on the row side."""
+    adm = [(1, 2), (1, 3), (4, 2), (4, 5), (4, 6), (7, 2)]
+    assert O.sparsity_constant(adm) == 3
+    # col(9) = {1, 2, 3, 4}, every row set has one or two members: c_sp = 4 (columns only)
+    adm_c = [(1, 9), (2, 9), (3, 9), (4, 9), (1, 8)]
+    assert O.sparsity_constant(adm_c) == 4
+    # row(5) = {1, 2, 3, 4, 6}, every column set has one member: c_sp = 5 (rows only)
+    adm_r = [(5, 1), (5, 2), (5, 3), (5, 4), (5, 6)]
+    assert O.sparsity_constant(adm_r) == 5
+    # a repeated cluster number on the two sides is still two different sets
+    assert O.sparsity_constant([(1, 1), (2, 1), (1, 2)]) == 2
+    assert O.sparsity_constant([]) == 0
+
+
+def test_sparsity_constant_brute_force_on_block_tree(tree1000):
+    """The same count taken from the exact cover of I x J: for every cluster, the number of
+    distinct admissible blocks whose row (column) index set is exactly that cluster's."""
+    _, t = tree1000
+    adm, _ = O.block_tree(t, 1.0)
+    per_row, per_col = {}, {}
+    for (a, b) in adm:
+        key_r = tuple(t.indices(a))
+        key_c = tuple(t.indices(b))
+        per_row[key_r] = per_row.get(key_r, 0) + 1
+        per_col[key_c] = per_col.get(key_c, 0) + 1
+    assert O.sparsity_constant(adm) == max(list(per_row.values()) + list(per_col.values()))
+
+
+def test_truncate_h_error_is_first_dropped_singular_value(ops512):
+    """Section 2.3: truncating a block to the singular values > eps sigma_1 leaves a spectral
+    error of exactly sigma_{k+1}, and the kept rank k satisfies the rule on both sides."""
+    _, tree, hf, sv, _, _ = ops512
+    eps = 1e-4
+    h = O.truncate_h(hf, sv, eps)
+    checked = 0
+    for b in hf.adm[::3]:
+        X, Y = hf.lowrank[b]
+        Xt, Yt = h.lowrank[b]
+        full = X @ Y.conj().T
+        s = np.linalg.svd(full, compute_uv=False)  # the block's own singular values
+        k = Xt.shape[1]
+        assert k >= 1 and s[k - 1] > eps * s[0]
+        if k < len(s):
+            assert s[k] <= eps * s[0]
+        err = np.linalg.norm(full - Xt @ Yt.conj().T, 2)
+        expect = s[k] if k < len(s) else 0.0
+        assert abs(err - expect) <= 1e-9 * expect + 1e-13 * s[0]
+        checked += 1
+    assert checked > 20
+    # some blocks really lose rank at this eps
+    assert any(h.lowrank[b][0].shape[1] < hf.lowrank[b][0].shape[1] for b in hf.adm)
+
+
+def _cluster_projection_errors(hf, uh):
+    """e_tau = |A_tau - U_tau U_tau^* A_tau|_2 with A_tau = [X_b Y_b^*]_{sigma in row(tau)}
+    assembled explicitly, and likewise e_sigma for the column blocks (proof of Theorem 5.1)."""
+    row, col = O.row_sets(hf.adm)
+    e_row, e_col = {}, {}
+    for t in row:
+        At = np.concatenate([hf.lowrank[(t, s)][0] @ hf.lowrank[(t, s)][1].conj().T
+                             for s in row[t]], axis=1)
+        U = uh.U[t]
+        e_row[t] = np.linalg.norm(At - U @ (U.conj().T @ At), 2)
+    for s in col:
+        Bs = np.concatenate([(hf.lowrank[(t, s)][0] @ hf.lowrank[(t, s)][1].conj().T).conj().T
+                             for t in col[s]], axis=1)
+        V = uh.V[s]
+        e_col[s] = np.linalg.norm(Bs - V @ (V.conj().T @ Bs), 2)
+    return e_row, e_col
+
+
+def test_theorem51_terms_are_next_singular_values(ops512):
+    """Theorem 5.1's terms: e_tau equals sigma_{l_tau+1}(X_tau) (two-sided), and the bound is
+    sqrt(2) sqrt(sum e_tau^2 + sum e_sigma^2) of the explicitly assembled projections."""
+    _, tree, hf, _, uh, _ = ops512
+    e_row, e_col = _cluster_projection_errors(hf, uh)
+    for t, e in e_row.items():
+        s, ell = uh.row_sv[t], uh.U[t].shape[1]
+        expect = s[ell] if ell < len(s) else 0.0
+        assert abs(e - expect) <= 1e-9 * expect + 1e-13 * s[0]
+    for c, e in e_col.items():
+        s, ell = uh.col_sv[c], uh.V[c].shape[1]
+        expect = s[ell] if ell < len(s) else 0.0
+        assert abs(e - expect) <= 1e-9 * expect + 1e-13 * s[0]
+    explicit = math.sqrt(2.0) * math.sqrt(sum(e * e for e in e_row.values())
+                                          + sum(e * e for e in e_col.values()))
+    assert explicit > 0
+    assert abs(O.theorem51_bound(uh) - explicit) <= 1e-9 * explicit
+
+
+def test_theorem51_single_block_is_eckart_young():
+    """One admissible block with distinct singular values: U_tau and V_sigma are its leading
+    singular vectors, so A^UH|_b is the best rank-l approximation (Eckart-Young) with spectral
+    error sigma_{l+1}, e_tau = e_sigma = sigma_{l+1}, and the bound of eq. (5.1) is exactly
+    sqrt(2) * sqrt(2) * sigma_{l+1} = 2 sigma_{l+1}: attained up to the factor 2."""
+    pts = np.stack([np.arange(40.0), np.zeros(40), np.zeros(40)], axis=1)
+    tree = O.ClusterTree(pts, 20)  # root and two leaves of 20 points
+    a, b = tree.children[0]
+    rng = np.random.default_rng(11)
+    P, _ = np.linalg.qr(rng.standard_normal((20, 20)) + 1j * rng.standard_normal((20, 20)))
+    Q, _ = np.linalg.qr(rng.standard_normal((20, 20)) + 1j * rng.standard_normal((20, 20)))
+    s = 10.0 ** (-0.5 * np.arange(20))  # 1, 0.316, 0.1, ... distinct
+    Ab = (P * s) @ Q.conj().T
+    for eps, ell in ((0.05, 3), (2e-4, 8), (0.0, 20)):
+        h = O.HMatrix(tree, [(a, b)], [], {(a, b): (P * s, Q)}, {})
+        uh = O.uniform_compression(h, eps)
+        assert uh.U[a].shape[1] == ell and uh.V[b].shape[1] == ell
+        blk = uh.U[a] @ uh.S[(a, b)] @ uh.V[b].conj().T
+        best = (P[:, :ell] * s[:ell]) @ Q[:, :ell].conj().T
+        assert np.linalg.norm(blk - best) <= 1e-13
+        err = np.linalg.norm(Ab - blk, 2)
+        nxt = s[ell] if ell < 20 else 0.0
+        assert abs(err - nxt) <= 1e-12
+        assert abs(O.theorem51_bound(uh) - 2.0 * nxt) <= 1e-12
+
+
+def test_storage_bounds_formula_by_hand():
+    """Lemma 2.6 evaluated by hand on a balanced tree: 64 points on a line, leaf 8, so
+    L = 4 levels and n_min = 8. Blocks are listed by hand with c_sp = 3 (row(1) has three
+    members), k_max = 5 and l_max = 7:
+      (2.2a)  c_sp k_max (L|I| + L|J|)                      = 3 * 5 * (256 + 256) = 7680,
+      (2.2b)  l_max (L|I| + L|J|) + l_max^2 2 c_sp |I|/n_min = 7 * 512 + 49 * 2 * 3 * 8 = 5936."""
+    pts = np.stack([np.arange(64.0), np.zeros(64), np.zeros(64)], axis=1)
+    tree = O.ClusterTree(pts, 8)
+    assert tree.depth() == 4 and min(tree.size) == 8 and tree.n == 64
+    adm = [(1, 2), (1, 3), (1, 4), (5, 2)]
+    ranks = {(1, 2): 5, (1, 3): 2, (1, 4): 4, (5, 2): 1}
+    low = {b: (np.zeros((tree.size[b[0]], k)), np.zeros((tree.size[b[1]], k)))
+           for b, k in ranks.items()}
+    h = O.HMatrix(tree, adm, [], low, {})
+    U = {1: np.zeros((tree.size[1], 7)), 5: np.zeros((tree.size[5], 3))}
+    V = {2: np.zeros((tree.size[2], 6)), 3: np.zeros((tree.size[3], 2)),
+         4: np.zeros((tree.size[4], 1))}
+    uh = O.UHMatrix(tree, adm, [], U, V, {}, {}, {}, {})
+    bnd = O.storage_bounds(h, uh)
+    assert (bnd["csp"], bnd["kmax"], bnd["lmax"], bnd["L"], bnd["nmin"]) == (3, 5, 7, 4, 8)
+    assert bnd["H"] == 7680
+    assert bnd["UH"] == 5936
+
+
+def test_frobenius_tail_equals_explicit_projection_errors(ops512):
+    """The Frobenius estimate of Section 5 term by term: for every cluster,
+    |A_tau - U U^* A_tau|_F^2 equals the sum of the dropped sigma_i(X_tau)^2 (two-sided)."""
+    _, tree, hf, _, uh, _ = ops512
+    row, col = O.row_sets(hf.adm)
+    tot = 0.0
+    for t in row:
+        At = np.concatenate([hf.lowrank[(t, s)][0] @ hf.lowrank[(t, s)][1].conj().T
+                             for s in row[t]], axis=1)
+        U = uh.U[t]
+        tot += np.linalg.norm(At - U @ (U.conj().T @ At)) ** 2
+    for s in col:
+        Bs = np.concatenate([(hf.lowrank[(t, s)][0] @ hf.lowrank[(t, s)][1].conj().T).conj().T
+                             for t in col[s]], axis=1)
+        V = uh.V[s]
+        tot += np.linalg.norm(Bs - V @ (V.conj().T @ Bs)) ** 2
+    assert tot > 0
+    assert abs(O.frobenius_tail(uh) - tot) <= 1e-8 * tot
