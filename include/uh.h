@@ -342,7 +342,7 @@ int h_stats(const h_op* op, uh_stats_t* out);
  * memory handed out by its own arena or a framework's allocator. It allocates nothing: the
  * intermediate vectors live in a fixed device array inside the library (266,240 bytes, held on
  * every GPU that loads the library until the process exits).
- *  m, n      block size |tau| x |sigma|, >= 1
+ *  m, n      block size |tau| x |sigma|, each in [1, (2^31 - 1) * 256]; UH_EINVAL outside
  *  lt, ls    ranks l_tau, l_sigma, each in [0, 256] (the limit set by the fixed array; larger
  *            ranks are rejected with UH_EINVAL) and lt <= m, ls <= n
  *  U         device, m x lt column-major, leading dimension ldu >= m

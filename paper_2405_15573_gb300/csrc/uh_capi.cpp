@@ -1243,7 +1243,12 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
   if ((rc = order_call(op, static_cast<cudaStream_t>(stream)))) return rc;
   for (int32_t rhs0 = 0; rhs0 < nrhs; rhs0 += uh::kPanelR) {
     const int32_t nb = std::min<int32_t>(uh::kPanelR, nrhs - rhs0);
-    if ((rc = uh::panel_gather(X, ldx, op->n, op->d_perm, rhs0, nb, op->d_pxp, stream))) return rc;
+    // on a failed launch, still mark the call's end so that the next call is ordered after the
+    // panels already queued (they share the op's panel scratch)
+    if ((rc = uh::panel_gather(X, ldx, op->n, op->d_perm, rhs0, nb, op->d_pxp, stream))) {
+      call_done(op, static_cast<cudaStream_t>(stream));
+      return rc;
+    }
     for (int phase = 0; phase < 3; ++phase) {
       uh::PanelParams p{};
       p.items = op->d_pitems;
@@ -1262,7 +1267,10 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
       p.mode = op->panel_mode;
       p.status = op->d_status;
       p.timeout_cycles = kTimeoutCycles;
-      if ((rc = uh::panel_launch(p, op->panel_ncta, stream))) return rc;
+      if ((rc = uh::panel_launch(p, op->panel_ncta, stream))) {
+        call_done(op, static_cast<cudaStream_t>(stream));
+        return rc;
+      }
     }
   }
   return call_done(op, static_cast<cudaStream_t>(stream));

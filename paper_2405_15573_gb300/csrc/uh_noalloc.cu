@@ -14,6 +14,9 @@ namespace {
 constexpr int kNaMaxRank = 256;     // largest l_tau and l_sigma accepted
 constexpr int kNaMaxChunks = 64;    // row chunks of the forward step (partial sums per column)
 constexpr int kNaMaxDevices = 64;
+// Largest block height or width: keeps the backward grid ((m + 255) / 256 blocks) inside the
+// 2^31 - 1 limit of a grid's x dimension.
+constexpr int64_t kNaMaxRows = static_cast<int64_t>(0x7fffffff) * 256;
 // Partial sums [kNaMaxChunks][kNaMaxRank] and yhat [kNaMaxRank], complex128-sized slots.
 constexpr size_t kNaScratchBytes = static_cast<size_t>(kNaMaxChunks + 1) * kNaMaxRank * 16;
 
@@ -145,6 +148,9 @@ extern "C" int uh_block_apply_noalloc(int64_t m, int64_t n, int32_t lt, int32_t 
     return uh::set_error(UH_EINVAL, "uh_block_apply_noalloc: precision %d not supported", precision);
   if (m < 1 || n < 1) return uh::set_error(UH_EINVAL, "uh_block_apply_noalloc: m = %lld, n = %lld must be >= 1",
                                            (long long)m, (long long)n);
+  if (m > kNaMaxRows || n > kNaMaxRows)
+    return uh::set_error(UH_EINVAL, "uh_block_apply_noalloc: m = %lld, n = %lld above the limit %lld",
+                         (long long)m, (long long)n, (long long)kNaMaxRows);
   if (lt < 0 || ls < 0 || lt > kNaMaxRank || ls > kNaMaxRank)
     return uh::set_error(UH_EINVAL,
                          "uh_block_apply_noalloc: ranks l_tau = %d, l_sigma = %d outside [0, %d], the limit of the "

@@ -294,17 +294,46 @@ class _Op:
             pass
 
 
+def _check_block_args(U, S, V, x, y):
+    """Raises ValueError unless the five tensors describe one block product the library can run
+    without touching memory outside them: one complex dtype, consistent sizes, column-major
+    matrices, contiguous vectors, and every tensor on the current CUDA device."""
+    import torch
+    if x.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError(f"x must be complex64 or complex128, not {x.dtype}")
+    for name, t in (("U", U), ("S", S), ("V", V), ("y", y)):
+        if t.dtype != x.dtype:
+            raise ValueError(f"{name} has dtype {t.dtype}, x has {x.dtype}")
+    for name, t in (("U", U), ("S", S), ("V", V)):
+        if t.dim() != 2:
+            raise ValueError(f"{name} must be a matrix")
+    for name, t in (("x", x), ("y", y)):
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous vector")
+    m, lt = U.shape
+    n, ls = V.shape
+    if tuple(S.shape) != (lt, ls):
+        raise ValueError(f"S is {tuple(S.shape)}, expected ({lt}, {ls}) from U and V")
+    if x.numel() != n or y.numel() != m:
+        raise ValueError(f"x has {x.numel()} values (needs {n}), y has {y.numel()} (needs {m})")
+    for name, t, rows in (("U", U, m), ("S", S, lt), ("V", V, n)):
+        if t.numel() and (t.stride(0) != 1 or t.stride(1) < rows):
+            raise ValueError(f"{name} must be column-major (stride (1, >= {rows}))")
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for name, t in (("U", U), ("S", S), ("V", V), ("x", x), ("y", y)):
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
+
+
 def block_apply_noalloc(U, S, V, x, y, stream=None):
     """y = U (S (V^* x)) for one UH block without any allocation by the library (uh.h,
     uh_block_apply_noalloc). U (m x lt), S (lt x ls), V (n x ls) are column-major CUDA tensors
     (tensor.T contiguous), x (n) and y (m) contiguous; all complex128 or all complex64."""
+    _check_block_args(U, S, V, x, y)
     import torch
     c128 = x.dtype == torch.complex128
     m, lt = U.shape
     n, ls = V.shape
-    for name, t in (("U", U), ("S", S), ("V", V)):
-        if t.dim() != 2 or t.stride(0) != 1 or t.dtype != x.dtype or not t.is_cuda:
-            raise ValueError(f"{name} must be a column-major CUDA matrix of {x.dtype}")
     check(lib.uh_block_apply_noalloc(m, n, lt, ls, U.data_ptr(), max(U.stride(1), m), S.data_ptr(),
                                      max(S.stride(1), lt), V.data_ptr(), max(V.stride(1), n),
                                      x.data_ptr(), y.data_ptr(),

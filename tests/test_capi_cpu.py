@@ -188,3 +188,39 @@ def test_server_argument_checks(uh):
     t = C.c_uint64()
     assert uh.lib.uh_solve_submit(None, None, None, 1e-6, 30, 100, C.byref(t)) == uh.UH_EINVAL
     assert uh.lib.uh_solve_poll(None, 1, None, None) == uh.UH_EINVAL
+
+
+def test_block_apply_noalloc_argument_checks(uh):
+    """The binding rejects every inconsistent block product before the library is called, and
+    the C entry point rejects sizes its grid cannot cover; neither needs a GPU to do so."""
+    import torch
+    cd = torch.complex128
+    m, n, lt, ls = 40, 30, 5, 4
+
+    def good():
+        return dict(U=torch.zeros(lt, m, dtype=cd).T, S=torch.zeros(ls, lt, dtype=cd).T,
+                    V=torch.zeros(ls, n, dtype=cd).T, x=torch.zeros(n, dtype=cd),
+                    y=torch.zeros(m, dtype=cd))
+
+    bad = [
+        ("x", lambda a: a["x"].to(torch.float64), "complex64 or complex128"),
+        ("y", lambda a: a["y"].to(torch.complex64), "y has dtype"),
+        ("S", lambda a: a["S"].to(torch.complex64), "S has dtype"),
+        ("U", lambda a: a["U"][:, 0].contiguous(), "U must be a matrix"),
+        ("x", lambda a: torch.zeros(n + 1, dtype=cd), "x has 31 values"),
+        ("y", lambda a: torch.zeros(m - 1, dtype=cd), "y has 39"),
+        ("y", lambda a: torch.zeros(2 * m, dtype=cd)[::2], "contiguous vector"),
+        ("S", lambda a: torch.zeros(ls, lt + 1, dtype=cd).T, r"S is \(6, 4\)"),
+        ("U", lambda a: torch.zeros(m, lt, dtype=cd), "U must be column-major"),
+        ("V", lambda a: a["V"], "must be a CUDA tensor"),  # all consistent, but on the host
+    ]
+    for name, make, match in bad:
+        a = good()
+        a[name] = make(a)
+        with pytest.raises(ValueError, match=match):
+            uh.block_apply_noalloc(a["U"], a["S"], a["V"], a["x"], a["y"])
+    big = (0x7FFFFFFF * 256) + 1
+    for mm, nn in ((big, 8), (8, big)):
+        rc = uh.lib.uh_block_apply_noalloc(mm, nn, 1, 1, 16, mm, 16, 1, 16, nn, 16, 16,
+                                           uh.UH_PREC_C128, None)
+        assert rc == uh.UH_EINVAL and "above the limit" in uh.lib.uh_last_error().decode()
