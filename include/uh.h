@@ -162,6 +162,19 @@ int uh_destroy(uh_op* op);
 int uh_matvec(uh_op* op, const void* x, void* y, void* stream);
 
 /*
+ * y = A^UH x with the op's complex64 storage and extended-precision arithmetic: x and y are
+ * complex128 device arrays of n values in ORIGINAL ordering (not overlapping); every product
+ * and sum of Algorithm 6 (Section 4.4) is carried in pairs of FP32 values (hi + lo, exact
+ * products by fma and Knuth's two-sum), about 48 significant bits, so y is the product of the
+ * STORED complex64 operator with x to about 1e-13 relative, not the FP32-accumulated product of
+ * uh_matvec. It is the residual product of mixed-precision iterative refinement (r = b - A x).
+ * For ops created with UH_PREC_C64, UH_PREC_C64_TF32 or UH_PREC_C64_BF16X3 (whose scratch for
+ * it is allocated by uh_create: 16 bytes per intermediate value); UH_EINVAL for complex128 ops.
+ * Ordered with the op's other calls like uh_matvec; asynchronous on `stream`.
+ */
+int uh_matvec_mixed(uh_op* op, const void* x, void* y, void* stream);
+
+/*
  * Waits for `stream` and reports whether a bounded device-side wait of this op's products ran
  * out since the last check (UH_ETIMEOUT, status then cleared) - which only happens if the GPU
  * could not run all of the product's CTAs at once. UH_OK otherwise.

@@ -37,9 +37,9 @@ using cd = std::complex<double>;
 using cf = std::complex<float>;
 
 namespace uh {
-cudaError_t stream_prepare(bool c128);
-cudaError_t stream_occupancy(bool c128, int* blocks_per_sm);
-cudaError_t stream_launch(bool c128, const StreamParams& p, int grid, cudaStream_t stream);
+cudaError_t stream_prepare(int variant);
+cudaError_t stream_occupancy(int variant, int* blocks_per_sm);
+cudaError_t stream_launch(int variant, const StreamParams& p, int grid, cudaStream_t stream);
 }  // namespace uh
 
 namespace {
@@ -212,6 +212,8 @@ struct OpBase {
   void* d_z1 = nullptr;
   void* d_z2 = nullptr;
   void* d_z3 = nullptr;
+  // uh_matvec_mixed (complex64 UH ops): xp, z1, z2, z3 at 16 bytes per value
+  void* d_xm[4] = {};
   // tensor-core uh_matmat (UH_PREC_C64_TF32 / UH_PREC_C64_BF16X3 ops)
   int mm_mode = -1;       // UH_MM_TF32 or UH_MM_BF16X3
   int panel_mode = 0;     // uh::kPanelTF32 or uh::kPanelBF16X3
@@ -238,7 +240,8 @@ void free_op(OpBase* o) {
   if (!o) return;
   void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_scatter, o->d_pool, o->d_status,
                   o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3,
-                  o->d_ptiles, o->d_pitems, o->d_pbegin, o->d_pxp, o->d_pz1, o->d_pz2};
+                  o->d_ptiles, o->d_pitems, o->d_pbegin, o->d_pxp, o->d_pz1, o->d_pz2,
+                  o->d_xm[0], o->d_xm[1], o->d_xm[2], o->d_xm[3]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (o->order_ev) cudaEventDestroy(o->order_ev);
@@ -279,16 +282,24 @@ int query_ncta(bool c128, int* ncta, int* device) {
   CUDA_TRY(cudaGetDevice(device));
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, *device));
-  CUDA_TRY(uh::stream_prepare(c128));
+  const int variant = c128 ? uh::kVarC128 : uh::kVarC64;
+  CUDA_TRY(uh::stream_prepare(variant));
   int per = 0;
-  CUDA_TRY(uh::stream_occupancy(c128, &per));
+  CUDA_TRY(uh::stream_occupancy(variant, &per));
   if (per < 1) return fail(UH_ECUDA, "streaming kernel does not fit on an SM");
   *ncta = sms * per;
+  if (!c128) {
+    // the extended-precision variant runs the same program on the same grid
+    CUDA_TRY(uh::stream_prepare(uh::kVarMixed));
+    int pm = 0;
+    CUDA_TRY(uh::stream_occupancy(uh::kVarMixed, &pm));
+    if (pm < per) return fail(UH_ECUDA, "extended-precision streaming kernel does not fit the grid");
+  }
   return UH_OK;
 }
 
 // Finalize, self-check and upload the program; allocate the scratch vectors.
-int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T) {
+int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T, bool mixed_vectors = false) {
   if (const char* e = P.finalize()) return fail(UH_EINVAL, "packing: %s", e);
   if (const char* e = P.self_check()) return fail(UH_EINVAL, "internal packing error: %s", e);
   int rc;
@@ -317,19 +328,28 @@ int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T) {
   for (int k = 0; k < 4; ++k)
     if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(P.src_len_[k], 2)) * eb, z[k])))
       return rc;
+  if (mixed_vectors)
+    for (int k = 0; k < 4; ++k)
+      if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(P.src_len_[k], 2)) * 16,
+                       &o->d_xm[k])))
+        return rc;
   o->st.packed_bytes = P.tile_bytes_total + P.input_bytes_total;
   o->st.device_bytes = static_cast<int64_t>(P.M.size() * eb + P.items.size() * sizeof(uh::WorkItem) +
                                             P.chunks.size() * (sizeof(uh::OutChunk) + 4) + T.n * 4) +
                        (P.src_len_[0] + P.src_len_[1] + P.src_len_[2] + P.src_len_[3]) * static_cast<int64_t>(eb);
+  if (mixed_vectors)
+    o->st.device_bytes += (P.src_len_[0] + P.src_len_[1] + P.src_len_[2] + P.src_len_[3]) * int64_t{16};
   o->st.n_launches = 1;
   o->st.n_items = static_cast<int64_t>(P.items.size());
   return UH_OK;
 }
 
 int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeout = kTimeoutCycles,
-               bool stall = false) {
+               bool stall = false, bool mixed = false) {
   if (!x || !y) return fail(UH_EINVAL, "x and y must be device pointers");
-  const size_t eb = o->c128 ? 16 : 8;
+  if (mixed && (o->c128 || !o->d_xm[0]))
+    return fail(UH_EINVAL, "the extended-precision product needs a complex64 UH op");
+  const size_t eb = o->c128 || mixed ? 16 : 8;
   const char* xa = static_cast<const char*>(x);
   const char* ya = static_cast<const char*>(y);
   if (xa < ya + o->n * eb && ya < xa + o->n * eb) return fail(UH_EINVAL, "x and y overlap");
@@ -358,13 +378,14 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   p.y = y;
   p.perm = o->d_perm;
   p.scatter = o->d_scatter;
-  p.xp = o->d_xp;
-  p.z1 = o->d_z1;
-  p.z2 = o->d_z2;
-  p.z3 = o->d_z3;
+  p.xp = mixed ? o->d_xm[0] : o->d_xp;
+  p.z1 = mixed ? o->d_xm[1] : o->d_z1;
+  p.z2 = mixed ? o->d_xm[2] : o->d_z2;
+  p.z3 = mixed ? o->d_xm[3] : o->d_z3;
   p.status = o->d_status;
   p.timeout_cycles = timeout;
-  cudaError_t e = uh::stream_launch(o->c128, p, o->ncta, s);
+  const int variant = mixed ? uh::kVarMixed : o->c128 ? uh::kVarC128 : uh::kVarC64;
+  cudaError_t e = uh::stream_launch(variant, p, o->ncta, s);
   if (e != cudaSuccess) {
     --o->epoch;  // nothing launched: the counters did not move
     return fail(UH_ECUDA, "streaming kernel launch: %s", cudaGetErrorString(e));
@@ -874,7 +895,7 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   o->n = T.n;
   o->ncta = ncta;
   o->device = device;
-  if ((rc = upload_program(o, P, T))) { free_op(o); delete o; return rc; }
+  if ((rc = upload_program(o, P, T, !c128))) { free_op(o); delete o; return rc; }
   const uh_stats_t packed = o->st;  // packing figures filled by the upload
   uh_fill_stats(u, precision, c128 ? 16 : 8, &o->st);
   o->st.packed_bytes = packed.packed_bytes;
@@ -905,6 +926,11 @@ int uh_destroy(uh_op* op) {
 int uh_matvec(uh_op* op, const void* x, void* y, void* stream) {
   if (!op) return fail(UH_EINVAL, "null op");
   return run_matvec(op, x, y, stream);
+}
+
+int uh_matvec_mixed(uh_op* op, const void* x, void* y, void* stream) {
+  if (!op) return fail(UH_EINVAL, "null op");
+  return run_matvec(op, x, y, stream, kTimeoutCycles, false, true);
 }
 
 int uh_check(uh_op* op, void* stream) {

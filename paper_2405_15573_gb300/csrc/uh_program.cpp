@@ -350,6 +350,9 @@ const char* ProgramBuilder::self_check() const {
     if (it.ncols < 0 || it.ncols > kStreamMaxCols || static_cast<int64_t>(it.ncols) * it.hp * eb_ > kTileBytes ||
         (static_cast<int64_t>(it.ncols) * it.hp + staged) * eb_ > kStageBytes)
       return "item tile size";
+    // the extended-precision variant stages the same complex64 tile with 16-byte inputs
+    if (eb_ == 8 && static_cast<int64_t>(it.ncols) * it.hp * 8 + staged * 16 > kStageBytesMixed)
+      return "item tile size (extended-precision stage)";
     if (it.tile_off < 0 || (it.tile_off * eb_) % 16 || it.tile_off + static_cast<int64_t>(it.ncols) * it.hp > msize)
       return "item tile outside the packed buffer or misaligned";
     if (((static_cast<uint32_t>(it.flags) >> kDepShift) & ((1u << kNumCounters) - 1u)) != deps ||

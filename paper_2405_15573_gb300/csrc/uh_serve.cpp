@@ -10,10 +10,11 @@
 // scratch and its per-call group counters. A solve
 // is restarted GMRES with its matrix-vector products in the operator's precision (complex64
 // storage, FP32 accumulation for UH_PREC_C64 ops) and everything else in FP64 on the GPU: the
-// true residual r = b - A x at every restart, classical Gram-Schmidt applied twice for the
+// true residual r = b - A x at every restart (its product in extended precision on the
+// complex128 x for complex64 ops, uh_matvec_mixed), classical Gram-Schmidt applied twice for the
 // Arnoldi basis, the norms and the solution update x += V y. The restarts with the recomputed
-// FP64 residual are the refinement: a solve only stops as converged when the true residual of
-// the returned x is below the tolerance. The kernel sequence of a solve depends only on its own
+// residual are the mixed-precision refinement: a solve only stops as converged when the true
+// residual of the returned x against the stored operator is below the tolerance. The kernel sequence of a solve depends only on its own
 // data, so its result is the same whether it runs alone or among other solves.
 #include <algorithm>
 #include <chrono>
@@ -228,8 +229,15 @@ int issue_start(Solve* s, cudaStream_t st) {
   if (s->x_zero) {
     if (cudaMemcpyAsync(s->V, s->db, s->n * 16, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return UH_ECUDA;
   } else {
-    if ((rc = apply_op(s, s->x, s->c64 ? nullptr : s->w, st))) return rc;
-    if ((rc = uh::vec_residual(s->db, s->c64 ? s->y32 : s->w, s->c64, s->V, s->n, st))) return rc;
+    // The true residual of the current x against the stored operator: for complex64 ops the
+    // product runs in extended precision on the complex128 x (uh_matvec_mixed), so the restart
+    // sees b - A x to about 1e-13, not the FP32-accumulated product of the Arnoldi steps.
+    if (s->c64) {
+      if ((rc = uh_matvec_mixed(s->op, s->x, s->w, st))) return rc;
+    } else if ((rc = apply_op(s, s->x, s->w, st))) {
+      return rc;
+    }
+    if ((rc = uh::vec_residual(s->db, s->w, false, s->V, s->n, st))) return rc;
   }
   if ((rc = uh::vec_norm(s->V, s->n, s->part, s->scal, nullptr, st))) return rc;
   if ((rc = uh::vec_scale_f(s->V, s->scal, s->V, s->c64 ? s->v32 : nullptr, s->n, st))) return rc;

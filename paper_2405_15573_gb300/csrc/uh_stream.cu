@@ -25,9 +25,27 @@
 namespace uh {
 namespace {
 
-template <typename R> struct Cx;
-template <> struct Cx<float> { using T = float2; };
-template <> struct Cx<double> { using T = double2; };
+// Variants (uh_stream.h): TM = tile element, TV = element of the intermediate vectors, of the
+// staged inputs and of the accumulators, TX = element of x and y, L = shared-memory layout.
+struct KC64 {
+  using TM = float2;
+  using TV = float2;
+  using TX = float2;
+  using L = StreamSmemStd;
+};
+struct KC128 {
+  using TM = double2;
+  using TV = double2;
+  using TX = double2;
+  using L = StreamSmemStd;
+};
+// TV = (re_hi, im_hi, re_lo, im_lo): the value re_hi + re_lo + i (im_hi + im_lo).
+struct KMixed {
+  using TM = float2;
+  using TV = float4;
+  using TX = double2;
+  using L = StreamSmemMixed;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -93,11 +111,67 @@ __device__ __forceinline__ void cfma(double2& a, double2 m, double2 v) {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
+// Extended precision from FP32 pairs. The round-to-nearest intrinsics keep the compiler from
+// contracting a product and a sum into one fma, which would break the error-free transforms.
+// (h, l) += p + pl, where p is a rounded value and pl a small correction: Knuth's two-sum gives
+// the exact rounding error e of h + p, and the correction and e are added to the low word.
+__device__ __forceinline__ void ff_acc(float& h, float& l, float p, float pl) {
+  const float s = __fadd_rn(h, p);
+  const float z = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(p, z));
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(e, pl));
+}
+// a += m * v, m a complex64 tile element, v and a extended: each of the four real products
+// m_i * v_hi is split exactly into its rounded value and error (fma), and m_i * v_lo joins the error.
+__device__ __forceinline__ void cfma(float4& a, float2 m, float4 v) {
+  float p = __fmul_rn(m.x, v.x);
+  ff_acc(a.x, a.z, p, fmaf(m.x, v.z, fmaf(m.x, v.x, -p)));
+  const float my = -m.y;
+  p = __fmul_rn(my, v.y);
+  ff_acc(a.x, a.z, p, fmaf(my, v.w, fmaf(my, v.y, -p)));
+  p = __fmul_rn(m.x, v.y);
+  ff_acc(a.y, a.w, p, fmaf(m.x, v.w, fmaf(m.x, v.y, -p)));
+  p = __fmul_rn(m.y, v.x);
+  ff_acc(a.y, a.w, p, fmaf(m.y, v.z, fmaf(m.y, v.x, -p)));
+}
+// (h, l) normalised: h = round(h + l), l the exact rest.
+__device__ __forceinline__ void ff_norm(float& h, float& l) {
+  const float s = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(s, h));
+  h = s;
+}
+__device__ __forceinline__ float4 cadd(float4 a, float4 b) {
+  ff_acc(a.x, a.z, b.x, b.z);
+  ff_acc(a.y, a.w, b.y, b.w);
+  ff_norm(a.x, a.z);
+  ff_norm(a.y, a.w);
+  return a;
+}
+// Conversions between the x / y element and the vector element.
+__device__ __forceinline__ float2 to_v(float2 a, float2*) { return a; }
+__device__ __forceinline__ double2 to_v(double2 a, double2*) { return a; }
+__device__ __forceinline__ float4 to_v(double2 a, float4*) {
+  const float rh = __double2float_rn(a.x), ih = __double2float_rn(a.y);
+  return make_float4(rh, ih, __double2float_rn(a.x - static_cast<double>(rh)),
+                     __double2float_rn(a.y - static_cast<double>(ih)));
+}
+__device__ __forceinline__ float2 to_x(float2 a, float2*) { return a; }
+__device__ __forceinline__ double2 to_x(double2 a, double2*) { return a; }
+__device__ __forceinline__ double2 to_x(float4 a, double2*) {
+  return make_double2(static_cast<double>(a.x) + static_cast<double>(a.z),
+                      static_cast<double>(a.y) + static_cast<double>(a.w));
+}
+
 __device__ __forceinline__ float2 shfl_xor(float2 v, int m) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 __device__ __forceinline__ double2 shfl_xor(double2 v, int m) {
   return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ __forceinline__ float4 shfl_xor(float4 v, int m) {
+  return make_float4(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m),
+                     __shfl_xor_sync(0xffffffffu, v.z, m), __shfl_xor_sync(0xffffffffu, v.w, m));
 }
 
 __device__ __forceinline__ void lds16(const float2* p, float2 (&m)[2]) {
@@ -132,10 +206,11 @@ struct Bars {
   uint64_t* pub_empty;  // the publisher has taken the slot (1 arrival)
   uint64_t* pool;       // pool descriptor segment landed [2] (1 arrival + bytes)
 };
+template <class L>
 __device__ __forceinline__ Bars bars_of(unsigned char* smem) {
-  uint64_t* b = reinterpret_cast<uint64_t*>(smem + kSmemBars);
-  uint64_t* q = b + 2 * kStages + kDescBatches;
-  return Bars{b, b + kStages, b + 2 * kStages, q, q + kPubRing, q + 2 * kPubRing};
+  uint64_t* b = reinterpret_cast<uint64_t*>(smem + L::bars);
+  uint64_t* q = b + 2 * L::stages + kDescBatches;
+  return Bars{b, b + L::stages, b + 2 * L::stages, q, q + kPubRing, q + 2 * kPubRing};
 }
 
 // Consumers: hand counter `counter` (index in group_done, or -1: no more) to the publisher as
@@ -161,10 +236,11 @@ __device__ __forceinline__ bool publish(const Bars& bar, int* pub_ctr, int np, i
 }
 
 // Publisher: releases until the consumers hand over -1 (or the CTA aborts).
+template <class L>
 __device__ void publisher(const StreamParams& p, unsigned char* smem) {
-  const Bars bar = bars_of(smem);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
-  const volatile int* pub_ctr = reinterpret_cast<const volatile int*>(smem + kSmemPub);
+  const Bars bar = bars_of<L>(smem);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::misc);
+  const volatile int* pub_ctr = reinterpret_cast<const volatile int*>(smem + L::pub);
   for (int j = 0;; ++j) {
     const int k = j % kPubRing;
     if (!wait_parity(&bar.pub_full[k], static_cast<uint32_t>(j / kPubRing) & 1u, p.timeout_cycles, abort_flag)) {
@@ -195,14 +271,16 @@ __device__ __forceinline__ void drain(uint64_t* bar, uint32_t parity, long long 
   }
 }
 
-template <typename R>
+template <class K>
 __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* smem) {
-  using T = typename Cx<R>::T;
+  using TM = typename K::TM;
+  using TV = typename K::TV;
+  using L = typename K::L;
   unsigned char* stages = smem;
-  WorkItem* ring = reinterpret_cast<WorkItem*>(smem + kSmemDesc);
-  const Bars bar = bars_of(smem);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
-  const T* M = static_cast<const T*>(p.M);
+  WorkItem* ring = reinterpret_cast<WorkItem*>(smem + L::desc);
+  const Bars bar = bars_of<L>(smem);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::misc);
+  const TM* M = static_cast<const TM*>(p.M);
   const int n = i1 - i0;
   int batches = 0;  // static descriptor batches issued
   auto issue_batch = [&](int batch) {
@@ -227,8 +305,8 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
 
   // Waits for the stage of item `sq` to be free.
   auto stage_free = [&](int sq) -> bool {
-    const uint32_t k = static_cast<uint32_t>(sq / kStages);
-    if (k > 0 && !wait_parity(&bar.empty[sq % kStages], (k - 1) & 1u, p.timeout_cycles, abort_flag)) {
+    const uint32_t k = static_cast<uint32_t>(sq / L::stages);
+    if (k > 0 && !wait_parity(&bar.empty[sq % L::stages], (k - 1) & 1u, p.timeout_cycles, abort_flag)) {
       atomicOr(p.status, 2u);
       return false;
     }
@@ -246,13 +324,13 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
 #pragma unroll
       for (int k = 0; k < static_cast<int>(sizeof(WorkItem) / 16); ++k) w[k] = src[k];
     }
-    const int s = sq % kStages;
-    unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
-    const uint32_t tile_bytes = static_cast<uint32_t>(it.ncols) * static_cast<uint32_t>(it.hp) * sizeof(T);
+    const int s = sq % L::stages;
+    unsigned char* st = stages + static_cast<size_t>(s) * L::stage_bytes;
+    const uint32_t tile_bytes = static_cast<uint32_t>(it.ncols) * static_cast<uint32_t>(it.hp) * sizeof(TM);
     uint32_t bytes = tile_bytes;
 #pragma unroll
     for (int r = 0; r < kMaxRuns; ++r)
-      if (r < it.nruns) bytes += static_cast<uint32_t>(it.runs[r].len) * sizeof(T);
+      if (r < it.nruns) bytes += static_cast<uint32_t>(it.runs[r].len) * sizeof(TV);
     mbar_arrive_expect_tx(&bar.full[s], bytes);
     if (tile_bytes) bulk_g2s_hint(st, M + it.tile_off, tile_bytes, &bar.full[s], stream_once);
     const uint32_t deps = (static_cast<uint32_t>(it.flags) >> kDepShift) & ((1u << kNumCounters) - 1u);
@@ -281,8 +359,8 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
     for (int r = 0; r < kMaxRuns; ++r) {
       if (r >= it.nruns) break;
       const Run run = it.runs[r];
-      bulk_g2s_hint(st + tile_bytes + col * sizeof(T), static_cast<const T*>(src_ptr(p, run.src)) + run.start,
-                    static_cast<uint32_t>(run.len) * sizeof(T), &bar.full[s], keep);
+      bulk_g2s_hint(st + tile_bytes + col * sizeof(TV), static_cast<const TV*>(src_ptr(p, run.src)) + run.start,
+                    static_cast<uint32_t>(run.len) * sizeof(TV), &bar.full[s], keep);
       col += static_cast<uint32_t>(run.len);
     }
     return done;
@@ -389,30 +467,33 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
   // ---- end mark: the next ring slot says kEnd; its stage's full barrier completes without bytes
   if (ok && stage_free(seq)) {
     reinterpret_cast<volatile int16_t*>(&ring[seq % kDescRing].kind)[0] = kEnd;
-    mbar_arrive(&bar.full[seq % kStages]);
+    mbar_arrive(&bar.full[seq % L::stages]);
     return;
   }
   *abort_flag = 1;
   // Let every bulk copy already issued land before the CTA can exit: bounded waits on the stages
   // of the last kStages armed items and on the descriptor copies in flight.
-  for (int q = seq >= kStages ? seq - kStages : 0; q < seq; ++q)
-    drain(&bar.full[q % kStages], static_cast<uint32_t>(q / kStages) & 1u, p.timeout_cycles);
+  for (int q = seq >= L::stages ? seq - L::stages : 0; q < seq; ++q)
+    drain(&bar.full[q % L::stages], static_cast<uint32_t>(q / L::stages) & 1u, p.timeout_cycles);
   for (int b = waited; b < batches; ++b)
     drain(&bar.desc[b % kDescBatches], static_cast<uint32_t>(b / kDescBatches) & 1u, p.timeout_cycles);
   for (int f = landed; f < fetched; ++f)
     drain(&bar.pool[f & 1], static_cast<uint32_t>(f >> 1) & 1u, p.timeout_cycles);
 }
 
-template <typename R>
+template <class K>
 __device__ void consumers(const StreamParams& p, unsigned char* smem) {
-  using T = typename Cx<R>::T;
-  constexpr int EPL = 16 / sizeof(T);
+  using TM = typename K::TM;
+  using T = typename K::TV;
+  using TX = typename K::TX;
+  using L = typename K::L;
+  constexpr int EPL = 16 / sizeof(TM);  // tile elements per 16-byte row slice
   const int tid = threadIdx.x;
   unsigned char* stages = smem;
-  const WorkItem* ring = reinterpret_cast<const WorkItem*>(smem + kSmemDesc);
-  int* pub_ctr = reinterpret_cast<int*>(smem + kSmemPub);
-  const Bars bar = bars_of(smem);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kSmemMisc);
+  const WorkItem* ring = reinterpret_cast<const WorkItem*>(smem + L::desc);
+  int* pub_ctr = reinterpret_cast<int*>(smem + L::pub);
+  const Bars bar = bars_of<L>(smem);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::misc);
   volatile int* go = abort_flag + 1;  // go[0], go[1]: leader's decision, by item parity
 
   T acc[EPL];
@@ -424,17 +505,18 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
   int np = 0;      // releases handed to the publisher
   {
     // This CTA's slice of the permutation, then its release (each warp after its own stores).
+    constexpr int64_t EPV = 16 / sizeof(T) > 0 ? 16 / sizeof(T) : 1;  // vector elements per 16 bytes
     const int64_t b = blockIdx.x, nb = gridDim.x;
-    const int64_t a = (p.n * b / nb) / EPL * EPL;
-    const int64_t e = b == nb - 1 ? p.n : (p.n * (b + 1) / nb) / EPL * EPL;
-    const T* x = static_cast<const T*>(p.x);
+    const int64_t a = (p.n * b / nb) / EPV * EPV;
+    const int64_t e = b == nb - 1 ? p.n : (p.n * (b + 1) / nb) / EPV * EPV;
+    const TX* x = static_cast<const TX*>(p.x);
     T* xp = static_cast<T*>(p.xp);
-    for (int64_t r = a + tid; r < e; r += kStreamConsumers) xp[r] = x[p.perm[r]];
+    for (int64_t r = a + tid; r < e; r += kStreamConsumers) xp[r] = to_v(x[p.perm[r]], static_cast<T*>(nullptr));
     publish(bar, pub_ctr, np++, kCounterPermute, p, abort_flag);
   }
   for (int seq = 0;; ++seq) {
-    const int s = seq % kStages;
-    const uint32_t parity = static_cast<uint32_t>(seq / kStages) & 1u;
+    const int s = seq % L::stages;
+    const uint32_t parity = static_cast<uint32_t>(seq / L::stages) & 1u;
     if (tid == 0) {
       const bool ok = wait_parity(&bar.full[s], parity, p.timeout_cycles, abort_flag);
       if (!ok && !*abort_flag) {
@@ -453,11 +535,11 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
     const int hp = sl.hp, nc = sl.ncols;
     const int kind = sl.kind, h = sl.h, counter = sl.counter, aux = sl.aux, naux = sl.naux;
     const int64_t dst = sl.dst;
-    const unsigned char* st = stages + static_cast<size_t>(s) * kStageBytes;
+    const unsigned char* st = stages + static_cast<size_t>(s) * L::stage_bytes;
     const int rb = nchunk & 1;
-    T* sred = reinterpret_cast<T*>(smem + kSmemRed) + rb * (kStreamConsumers * EPL);
-    Scatter* sscat = reinterpret_cast<Scatter*>(smem + kSmemScat) + rb * 256;
-    T* svals = reinterpret_cast<T*>(smem + kSmemVals) + rb * (64 * EPL);
+    T* sred = reinterpret_cast<T*>(smem + L::red) + rb * (kStreamConsumers * EPL);
+    Scatter* sscat = reinterpret_cast<Scatter*>(smem + L::scat) + rb * 256;
+    T* svals = reinterpret_cast<T*>(smem + L::vals) + rb * 64;
     if ((flags & kItemFirst) && (kind == kScatterZ1 || kind == kScatterZ2)) {
       // the chunk's scatter entries, used at its end
       for (int k = tid; k < naux && k < 256; k += kStreamConsumers) sscat[k] = p.scatter[aux + k];
@@ -475,12 +557,14 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
 #pragma unroll
       for (int e = 0; e < EPL; ++e) acc[e] = T{0, 0};
     }
+    // the staged inputs, after the tile
+    const T* vin = reinterpret_cast<const T*>(st + static_cast<size_t>(nc) * hp * sizeof(TM));
     if (lane < need) {
-      const T* tile = reinterpret_cast<const T*>(st) + lane * EPL;
-      const T* vin = reinterpret_cast<const T*>(st) + static_cast<size_t>(nc) * hp;  // inputs after the tile
+      const TM* tile = reinterpret_cast<const TM*>(st) + lane * EPL;
       int c = g;
       for (; c + 7 * groups < nc; c += 8 * groups) {
-        T m[8][EPL], v[8];
+        TM m[8][EPL];
+        T v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           lds16(tile + (c + u * groups) * hp, m[u]);
@@ -492,7 +576,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
           for (int e = 0; e < EPL; ++e) cfma(acc[e], m[u][e], v[u]);
       }
       for (; c < nc; c += groups) {
-        T m0[EPL];
+        TM m0[EPL];
         lds16(tile + c * hp, m0);
         const T v0 = vin[c];
 #pragma unroll
@@ -500,7 +584,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
       }
     }
     // the near-field partial of this row tile, staged after the inputs
-    if ((flags & kItemBase) && tid < h) base = reinterpret_cast<const T*>(st)[static_cast<size_t>(nc) * hp + nc + tid];
+    if ((flags & kItemBase) && tid < h) base = vin[nc + tid];
     // The stage (tile, inputs, slot) has been read: release it to the producer.
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(&bar.empty[s]);
@@ -524,7 +608,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
         for (int q = 1; q < parts; ++q) v = cadd(v, sred[q * hpl + tid]);
         if (flags & kItemBase) v = cadd(v, base);
         if (kind == kToY) {
-          static_cast<T*>(p.y)[out_idx] = v;
+          static_cast<TX*>(p.y)[out_idx] = to_x(v, static_cast<TX*>(nullptr));
         } else if (kind == kScatterZ1 || kind == kScatterZ2) {
           svals[tid] = v;
         } else {
@@ -554,13 +638,14 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
   if (__shfl_sync(0xffffffffu, *abort_flag ? 0 : 1, 0)) publish(bar, pub_ctr, np, -1, p, abort_flag);
 }
 
-template <typename R>
+template <class K>
 __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamParams p) {
+  using L = typename K::L;
   extern __shared__ __align__(128) unsigned char smem[];
-  const Bars bar = bars_of(smem);
-  volatile int* misc = reinterpret_cast<volatile int*>(smem + kSmemMisc);
+  const Bars bar = bars_of<L>(smem);
+  volatile int* misc = reinterpret_cast<volatile int*>(smem + L::misc);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < L::stages; ++s) {
       mbar_init(&bar.full[s], 1);
       mbar_init(&bar.empty[s], kStreamConsumerWarps);
     }
@@ -575,36 +660,46 @@ __global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamP
   }
   __syncthreads();
   if (threadIdx.x >= kStreamConsumers + 32) {
-    if (threadIdx.x == kStreamConsumers + 32) publisher(p, smem);
+    if (threadIdx.x == kStreamConsumers + 32) publisher<L>(p, smem);
   } else if (threadIdx.x >= kStreamConsumers) {
-    if (threadIdx.x == kStreamConsumers) producer<R>(p, p.cta_begin[blockIdx.x], p.cta_begin[blockIdx.x + 1], smem);
+    if (threadIdx.x == kStreamConsumers) producer<K>(p, p.cta_begin[blockIdx.x], p.cta_begin[blockIdx.x + 1], smem);
   } else {
-    consumers<R>(p, smem);
+    consumers<K>(p, smem);
   }
   __syncthreads();
 }
 
 }  // namespace
 
-cudaError_t stream_prepare(bool c128) {
-  return c128 ? cudaFuncSetAttribute(stream_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kStreamSmemBytes)
-              : cudaFuncSetAttribute(stream_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kStreamSmemBytes);
+const void* stream_fn(int variant, int* smem_bytes) {
+  switch (variant) {
+    case kVarC64: *smem_bytes = KC64::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC64>);
+    case kVarC128: *smem_bytes = KC128::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC128>);
+    case kVarMixed: *smem_bytes = KMixed::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KMixed>);
+    default: *smem_bytes = 0; return nullptr;
+  }
 }
 
-cudaError_t stream_occupancy(bool c128, int* blocks_per_sm) {
-  return c128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stream_kernel<double>, kStreamThreads,
-                                                              kStreamSmemBytes)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stream_kernel<float>, kStreamThreads,
-                                                              kStreamSmemBytes);
+cudaError_t stream_prepare(int variant) {
+  int smem = 0;
+  const void* fn = stream_fn(variant, &smem);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-cudaError_t stream_launch(bool c128, const StreamParams& p, int grid, cudaStream_t stream) {
+cudaError_t stream_occupancy(int variant, int* blocks_per_sm) {
+  int smem = 0;
+  const void* fn = stream_fn(variant, &smem);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kStreamThreads, smem);
+}
+
+cudaError_t stream_launch(int variant, const StreamParams& p, int grid, cudaStream_t stream) {
+  int smem = 0;
+  const void* fn = stream_fn(variant, &smem);
+  if (!fn) return cudaErrorInvalidValue;
   void* args[] = {const_cast<StreamParams*>(&p)};
-  const void* fn = c128 ? reinterpret_cast<const void*>(stream_kernel<double>)
-                        : reinterpret_cast<const void*>(stream_kernel<float>);
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kStreamThreads), args, kStreamSmemBytes, stream);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kStreamThreads), args, smem, stream);
 }
 
 }  // namespace uh

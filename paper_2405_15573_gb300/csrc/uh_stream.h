@@ -59,18 +59,41 @@ constexpr int kDescRing = kDescBatch * kDescBatches;
 static_assert(kStages < kDescBatch, "consumers must be past a batch when it is refilled");
 static_assert(2 * kPoolSeg + kStages <= kDescRing, "a fetched pool segment must not overwrite live descriptors");
 
-// Shared-memory layout of the kernel (bytes). The chunk-end buffers are double-buffered by chunk
-// parity, so a chunk end needs no barrier after its last use of them.
-constexpr int kSmemRed = kStages * kStageBytes;                  // group reduction [2], one 16 B slot per consumer thread
-constexpr int kSmemDesc = kSmemRed + 2 * kStreamConsumers * 16;  // descriptor ring, 96 B each
-constexpr int kSmemScat = kSmemDesc + kDescRing * 96;            // scatter entries of a chunk [2] (256 x 8 B)
-constexpr int kSmemVals = kSmemScat + 2 * 256 * 8;                // a chunk's outputs before they are scattered [2]
-constexpr int kSmemBars = kSmemVals + 2 * 64 * 16;                // full, empty [kStages], desc [kDescBatches],
+// The kernel comes in three variants over the same device program:
+//  kVarC64    complex64 tiles, vectors and accumulation in FP32;
+//  kVarC128   complex128 tiles, vectors and accumulation in FP64;
+//  kVarMixed  complex64 tiles of a complex64 program, x and y in complex128, the intermediate
+//             vectors and the accumulation in extended precision from pairs of FP32 values
+//             (value = hi + lo, error-free transforms), 16 bytes per complex value. Its inputs
+//             take twice the bytes of the complex64 ones, so it runs two stages of
+//             kStageBytesMixed: a complex64 item with ncols columns and s staged values uses
+//             ncols * hp * 8 + s * 8 <= kStageBytes bytes, hence ncols * hp * 8 + s * 16 <=
+//             kStageBytes + 8 * (kStreamMaxCols + kStreamHpMax) = kStageBytesMixed.
+enum StreamVariant : int { kVarC64 = 0, kVarC128 = 1, kVarMixed = 2 };
+constexpr int kStageBytesMixed = kStageBytes + 8 * (kStreamMaxCols + kStreamHpMax);
+constexpr int kStagesMixed = 2;
+
+// Shared-memory layout of the kernel (bytes) for `Stages` stages of `StageBytes` and a per-thread
+// reduction slot of `RedSlot` bytes. The chunk-end buffers are double-buffered by chunk parity,
+// so a chunk end needs no barrier after its last use of them.
+template <int Stages, int StageBytes, int RedSlot>
+struct StreamSmem {
+  static constexpr int stages = Stages;
+  static constexpr int stage_bytes = StageBytes;
+  static constexpr int red = Stages * StageBytes;                // group reduction [2], one slot per consumer thread
+  static constexpr int desc = red + 2 * kStreamConsumers * RedSlot;  // descriptor ring, 96 B each
+  static constexpr int scat = desc + kDescRing * 96;             // scatter entries of a chunk [2] (256 x 8 B)
+  static constexpr int vals = scat + 2 * 256 * 8;                 // a chunk's outputs before they are scattered [2]
+  static constexpr int bars = vals + 2 * 64 * 16;                 // full, empty [Stages], desc [kDescBatches],
                                                                   // pub_full, pub_empty [kPubRing], pool [2]
-constexpr int kSmemMisc = kSmemBars + (2 * kStages + kDescBatches + 2 * kPubRing + 2) * 8;  // abort flag, decision words
-constexpr int kSmemPub = kSmemMisc + 32;                          // group counter of each release [kPubRing]
-constexpr int kStreamSmemBytes = kSmemPub + kPubRing * 4;
-static_assert(kStreamSmemBytes <= 227 * 1024, "shared memory of one CTA");
+  static constexpr int misc = bars + (2 * Stages + kDescBatches + 2 * kPubRing + 2) * 8;  // abort flag, decision words
+  static constexpr int pub = misc + 32;                           // group counter of each release [kPubRing]
+  static constexpr int bytes = pub + kPubRing * 4;
+  static_assert(Stages <= kStages, "descriptor ring sized for at most kStages stages");
+  static_assert(bytes <= 227 * 1024, "shared memory of one CTA");
+};
+using StreamSmemStd = StreamSmem<kStages, kStageBytes, 16>;
+using StreamSmemMixed = StreamSmem<kStagesMixed, kStageBytesMixed, 32>;
 
 // Input vectors a run can read.
 enum : int8_t { kSrcXp = 0, kSrcZ1 = 1, kSrcZ2 = 2, kSrcZ3 = 3 };
@@ -157,9 +180,9 @@ struct StreamParams {
   unsigned long long ticket_base;  // ticket value at the start of this call
   unsigned long long flag_need;    // a flag is set in this call when it is >= flag_need
   const void* M;             // packed tiles
-  const void* x;             // input, original ordering
+  const void* x;             // input, original ordering (complex128 in the mixed variant)
   int64_t n;                 // positions permuted into xp (all operators of the program)
-  void* y;                   // output, original ordering
+  void* y;                   // output, original ordering (complex128 in the mixed variant)
   const int32_t* perm;       // position -> original index
   const Scatter* scatter;    // scatter entries of the scatter kinds
   void* xp;                  // x in cluster order (kSrcXp)

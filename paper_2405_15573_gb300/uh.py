@@ -89,6 +89,7 @@ for _name, _args in [
     ("uh_debug_stalled_matvec", [_p, _p, _p, C.c_longlong, _p]),
     ("h_pack_check", [C.POINTER(HDesc), _i32, _i32]),
     ("h_check", [_p, _p]),
+    ("uh_matvec_mixed", [_p, _p, _p, _p]),
     ("uh_block_apply_noalloc", [_i64, _i64, _i32, _i32, _p, _i64, _p, _i64, _p, _i64, _p, _p, _i32, _p]),
     ("uh_batch_create", [C.POINTER(C.POINTER(UHDesc)), _i32, _i32, C.POINTER(_p)]),
     ("uh_batch_destroy", [_p]),
@@ -356,6 +357,24 @@ class UHOp(_Op):
     def from_arrays(cls, arrays: dict, precision: str = "c64"):
         desc, keep = uh_desc_from_arrays(arrays)
         return cls(desc, precision)
+
+    def matvec_mixed(self, x, y=None, stream=None):
+        """y = A x with the complex64-stored operator in extended-precision arithmetic
+        (uh_matvec_mixed): x and y are contiguous complex128 CUDA tensors of length n."""
+        import torch
+        if self.c128:
+            raise ValueError("matvec_mixed needs an op with complex64 storage")
+        for name, t in (("x", x), ("y", y)):
+            if t is None:
+                continue
+            if not t.is_cuda or t.dtype != torch.complex128 or t.dim() != 1 or t.shape[0] != self.n \
+                    or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CUDA tensor of {self.n} complex128")
+        if y is None:
+            y = torch.empty_like(x)
+        check(lib.uh_matvec_mixed(self.handle, x.data_ptr(), y.data_ptr(), _stream_handle(stream)),
+              "uh_matvec_mixed")
+        return y
 
 
 def _desc_array(descs):

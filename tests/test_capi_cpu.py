@@ -203,7 +203,7 @@ def test_block_apply_noalloc_argument_checks(uh):
                     y=torch.zeros(m, dtype=cd))
 
     bad = [
-        ("x", lambda a: a["x"].to(torch.float64), "complex64 or complex128"),
+        ("x", lambda a: torch.zeros(n, dtype=torch.float64), "complex64 or complex128"),
         ("y", lambda a: a["y"].to(torch.complex64), "y has dtype"),
         ("S", lambda a: a["S"].to(torch.complex64), "S has dtype"),
         ("U", lambda a: a["U"][:, 0].contiguous(), "U must be a matrix"),

@@ -106,3 +106,11 @@ def relerr(a, b) -> float:
     a = np.asarray(a)
     b = np.asarray(b)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def stored_c64(uh: O.UHMatrix) -> O.UHMatrix:
+    """The operator a complex64 op stores: every entry of U, V, S and the dense blocks rounded to
+    complex64 (round to nearest), held in complex128 so the oracle applies it in FP64."""
+    r = lambda d: {k: v.astype(np.complex64).astype(np.complex128) for k, v in d.items()}  # noqa: E731
+    return O.UHMatrix(uh.tree, uh.adm, uh.dense, r(uh.U), r(uh.V), r(uh.S), r(uh.near),
+                      uh.row_sv, uh.col_sv)
