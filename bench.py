@@ -312,8 +312,7 @@ def matmat_figures(model, n, steps, torch, peak_bf16):
             y = Y.cpu().numpy().astype(np.complex128)
             err = max(float(np.linalg.norm(y[:, j] - yref[:, j]) / np.linalg.norm(yref[:, j]))
                       for j in range(nrhs))
-            products = 3 if mode == "bf16x3" else 1
-            flops = products * 2 * 128 * 64 * st["panel_bytes"] / 256  # M = 128, K = 64 per 256 n bytes
+            flops = st["panel_mma_flops"]  # every MMA of one pass: 2 M N K (3 products in BF16x3)
             tf = flops / (ms * 1e-3) / 1e12
             out[f"{mode}_R{nrhs}"] = {
                 "ms": ms, "rhs_matvec_per_s": nrhs * 1e3 / ms,

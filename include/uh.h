@@ -216,6 +216,7 @@ typedef struct {
   int32_t matmat_mode;        /* tensor-core uh_matmat mode of the op (UH_MM_TF32 / UH_MM_BF16X3), or -1 */
   int64_t panel_bytes;        /* its packed operator: bytes streamed per pass of 64 right-hand sides */
   int64_t panel_items;        /* its work items per pass */
+  int64_t panel_mma_flops;    /* its tensor-core flops per pass (2 * M * N * K of every MMA) */
 } uh_stats_t;
 
 int uh_stats(const uh_op* op, uh_stats_t* out);

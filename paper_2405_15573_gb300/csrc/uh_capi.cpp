@@ -218,6 +218,10 @@ struct OpBase {
   int mm_mode = -1;       // UH_MM_TF32 or UH_MM_BF16X3
   int panel_mode = 0;     // uh::kPanelTF32 or uh::kPanelBF16X3
   int panel_ncta = 0;
+  int64_t panel_xp_rows = 0;  // rows of XP, its zero block included
+  unsigned long long* d_pdone = nullptr;  // [2] Z1 / Z2 chunk counters of the passes, monotonic
+  int64_t panel_zchunks[2] = {0, 0};
+  unsigned long long panel_epoch = 0;     // passes launched since the counters were last reset
   unsigned char* d_ptiles = nullptr;
   uh::PanelItem* d_pitems = nullptr;
   int32_t* d_pbegin = nullptr;
@@ -241,7 +245,7 @@ void free_op(OpBase* o) {
   void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_scatter, o->d_pool, o->d_status,
                   o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3,
                   o->d_ptiles, o->d_pitems, o->d_pbegin, o->d_pxp, o->d_pz1, o->d_pz2,
-                  o->d_xm[0], o->d_xm[1], o->d_xm[2], o->d_xm[3]};
+                  o->d_xm[0], o->d_xm[1], o->d_xm[2], o->d_xm[3], o->d_pdone};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (o->order_ev) cudaEventDestroy(o->order_ev);
@@ -405,8 +409,10 @@ int check_status(OpBase* o, void* stream) {
     // A call that ran out left its group counters short: restart the counting.
     CUDA_TRY(cudaMemsetAsync(o->d_status, 0, sizeof(uint32_t), s));
     CUDA_TRY(cudaMemsetAsync(o->d_done, 0, o->done_len * sizeof(unsigned long long), s));
+    if (o->d_pdone) CUDA_TRY(cudaMemsetAsync(o->d_pdone, 0, 2 * sizeof(unsigned long long), s));
     CUDA_TRY(cudaStreamSynchronize(s));
     o->epoch = 0;
+    o->panel_epoch = 0;
     return fail(UH_ETIMEOUT, "a bounded device-side wait ran out (code %u)", v);
   }
   return UH_OK;
@@ -451,14 +457,26 @@ int build_panel(OpBase* o, const uh_desc* d, const Tree& T, const std::vector<Ti
                 const std::vector<char>& is_col, const std::vector<std::vector<int64_t>>& row_blocks,
                 const std::vector<std::vector<int64_t>>& col_blocks, int mm_mode, int ncta) {
   const int mode = mm_mode == UH_MM_BF16X3 ? uh::kPanelBF16X3 : uh::kPanelTF32;
-  uh::PanelBuilder B(mode, ncta);
+  // Panels in operand-A layout: whole blocks of C rows; XP has one more, always zero, block.
+  const int64_t C = uh::panel_block_rows(mode);
+  auto up = [&](int64_t v) { return (v + C - 1) / C * C; };
+  const int64_t xp_rows = up(T.n) + C;
+  uh::PanelBuilder B(mode, ncta, up(T.n));
   auto live = [&](int64_t b) { return d->row_rank[d->adm_row[b]] > 0 && d->col_rank[d->adm_col[b]] > 0; };
+  // xhat_sigma and yhat_tau each start a block
   std::vector<int64_t> xo(T.ncl, -1), yo(T.ncl, -1);
   int64_t nx = 0, ny = 0;
   for (int32_t c = 0; c < T.ncl; ++c) {
-    if (is_col[c] && d->col_rank[c] > 0) { xo[c] = nx; nx += d->col_rank[c]; }
-    if (is_row[c] && d->row_rank[c] > 0) { yo[c] = ny; ny += d->row_rank[c]; }
+    if (is_col[c] && d->col_rank[c] > 0) { xo[c] = nx; nx += up(d->col_rank[c]); }
+    if (is_row[c] && d->row_rank[c] > 0) { yo[c] = ny; ny += up(d->row_rank[c]); }
   }
+  // Splits l outputs into chunks of at most kPanelMaxH rows that start on block boundaries.
+  auto pieces = [&](int32_t l) {
+    std::vector<int32_t> cut;
+    const int32_t k = static_cast<int32_t>((l + (uh::kPanelMaxH - C) - 1) / (uh::kPanelMaxH - C));
+    for (int32_t q = 0; q <= k; ++q) cut.push_back(q == k ? l : static_cast<int32_t>(up(static_cast<int64_t>(l) * q / k)));
+    return cut;
+  };
   const Src V{d->V_data, d->data_type}, S{d->S_data, d->data_type}, U{d->U_data, d->data_type};
   const Src D{d->dense.data, d->data_type};
   for (int32_t s = 0; s < T.ncl; ++s) {
@@ -468,9 +486,9 @@ int build_panel(OpBase* o, const uh_desc* d, const Tree& T, const std::vector<Ti
     if (!used) continue;
     const int32_t l = d->col_rank[s];
     const int64_t m = T.size[s];
-    const int k = (l + uh::kPanelMaxH - 1) / uh::kPanelMaxH;
-    for (int q = 0; q < k; ++q) {
-      const int j0 = l * q / k, j1 = l * (q + 1) / k;
+    const std::vector<int32_t> cut = pieces(l);
+    for (size_t q = 0; q + 1 < cut.size(); ++q) {
+      const int j0 = cut[q], j1 = cut[q + 1];
       B.add_chunk(0, uh::kPOutZ1, xo[s] + j0, j1 - j0,
                   {ColSpec{uh::kPSrcXP, T.begin[s], m, &V, true, d->col_off[s] + j0 * m, 1, m}});
     }
@@ -479,9 +497,9 @@ int build_panel(OpBase* o, const uh_desc* d, const Tree& T, const std::vector<Ti
   for (int32_t t = 0; t < T.ncl; ++t) {
     if (yo[t] < 0) continue;
     const int32_t l = d->row_rank[t];
-    const int k = (l + uh::kPanelMaxH - 1) / uh::kPanelMaxH;
-    for (int q = 0; q < k; ++q) {
-      const int i0 = l * q / k, i1 = l * (q + 1) / k;
+    const std::vector<int32_t> cut = pieces(l);
+    for (size_t q = 0; q + 1 < cut.size(); ++q) {
+      const int i0 = cut[q], i1 = cut[q + 1];
       cols.clear();
       for (int64_t b : row_blocks[t]) {
         if (!live(b)) continue;
@@ -509,7 +527,8 @@ int build_panel(OpBase* o, const uh_desc* d, const Tree& T, const std::vector<Ti
     B.add_chunk(2, uh::kPOutY, p0, static_cast<int>(tiles[ti].h), cols);
   }
   if (const char* e = B.finalize()) return fail(UH_EINVAL, "multi-RHS packing: %s", e);
-  const int64_t src_rows[3] = {T.n, nx, ny}, out_rows[3] = {nx, ny, T.n};
+  const int64_t src_rows[3] = {xp_rows, std::max<int64_t>(nx, C), std::max<int64_t>(ny, C)},
+                out_rows[3] = {nx, ny, T.n};
   if (const char* e = B.self_check(src_rows, out_rows)) return fail(UH_EINVAL, "internal multi-RHS packing error: %s", e);
   if (!o) return UH_OK;
   int rc;
@@ -518,21 +537,24 @@ int build_panel(OpBase* o, const uh_desc* d, const Tree& T, const std::vector<Ti
   if ((rc = upload(B.items.data(), B.items.size() * sizeof(uh::PanelItem), &o->d_pitems))) return rc;
   if ((rc = upload(B.begin.data(), B.begin.size() * sizeof(int32_t), &o->d_pbegin))) return rc;
   const size_t row = uh::kPanelRowBytes;
-  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(T.n) * row, &o->d_pxp))) return rc;
-  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(nx, 1)) * row, &o->d_pz1)))
-    return rc;
-  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(ny, 1)) * row, &o->d_pz2)))
-    return rc;
+  // zero-filled: the padding rows of every block stay zero (the epilogues write whole blocks of
+  // zeros past a chunk's rows, the gather zeros past n)
+  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(src_rows[0]) * row, &o->d_pxp))) return rc;
+  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(src_rows[1]) * row, &o->d_pz1))) return rc;
+  if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(src_rows[2]) * row, &o->d_pz2))) return rc;
+  if ((rc = upload(static_cast<const void*>(nullptr), 2 * sizeof(unsigned long long), &o->d_pdone))) return rc;
   o->mm_mode = mm_mode;
   o->panel_mode = mode;
   o->panel_ncta = ncta;
+  o->panel_xp_rows = xp_rows;
+  o->panel_zchunks[0] = B.z_chunks[0];
+  o->panel_zchunks[1] = B.z_chunks[1];
   o->st.matmat_mode = mm_mode;
-  int64_t streamed = 0;
-  for (const uh::PanelItem& it : B.items) streamed += 256 * static_cast<int64_t>(it.n);
-  o->st.panel_bytes = streamed;
+  o->st.panel_bytes = B.streamed_bytes;
+  o->st.panel_mma_flops = B.mma_flops;
   o->st.panel_items = static_cast<int64_t>(B.items.size());
   o->st.device_bytes += static_cast<int64_t>(B.tiles.size() + B.items.size() * sizeof(uh::PanelItem)) +
-                        (T.n + std::max<int64_t>(nx, 1) + std::max<int64_t>(ny, 1)) * static_cast<int64_t>(row);
+                        (src_rows[0] + src_rows[1] + src_rows[2]) * static_cast<int64_t>(row);
   return UH_OK;
 }
 
@@ -1271,14 +1293,19 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
     const int32_t nb = std::min<int32_t>(uh::kPanelR, nrhs - rhs0);
     // on a failed launch, still mark the call's end so that the next call is ordered after the
     // panels already queued (they share the op's panel scratch)
-    if ((rc = uh::panel_gather(X, ldx, op->n, op->d_perm, rhs0, nb, op->d_pxp, stream))) {
+    if ((rc = uh::panel_gather(X, ldx, op->n, op->panel_xp_rows, op->d_perm, rhs0, nb, op->panel_mode, op->d_pxp,
+                               stream))) {
       call_done(op, static_cast<cudaStream_t>(stream));
       return rc;
     }
-    for (int phase = 0; phase < 3; ++phase) {
+    {
       uh::PanelParams p{};
+      ++op->panel_epoch;
+      for (int k = 0; k < 2; ++k)
+        p.need[k] = op->panel_epoch * static_cast<unsigned long long>(op->panel_zchunks[k]);
+      p.done = op->d_pdone;
       p.items = op->d_pitems;
-      p.cta_begin = op->d_pbegin + phase * (op->panel_ncta + 1);
+      p.cta_begin = op->d_pbegin;
       p.tiles = op->d_ptiles;
       p.src[0] = op->d_pxp;
       p.src[1] = op->d_pz1;
@@ -1294,6 +1321,7 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
       p.status = op->d_status;
       p.timeout_cycles = kTimeoutCycles;
       if ((rc = uh::panel_launch(p, op->panel_ncta, stream))) {
+        --op->panel_epoch;  // nothing launched: the counters did not move
         call_done(op, static_cast<cudaStream_t>(stream));
         return rc;
       }

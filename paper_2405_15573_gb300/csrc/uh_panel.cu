@@ -1,22 +1,33 @@
-// Tensor-core multi-RHS product (sm_103a): one phase of a pass per launch, one CTA per SM.
-// Layout of the work and of the operands: uh_panel.h.
+// Tensor-core multi-RHS product (sm_103a): one persistent cooperative launch per pass of 64
+// right-hand sides, one CTA per SM. Layout of the work and of the operands: uh_panel.h.
 //
 // Roles in a CTA of 320 threads:
-//  - producer (lane 0 of warp 0): streams the CTA's item descriptors into a shared-memory ring
-//    (TMA bulk copies of 8); per item waits for a free stage, copies the descriptor into the
-//    stage's slot, and copies the item's B operand (one bulk copy) and its panel rows (one bulk
-//    copy per run) into the stage.
+//  - B producer (lane 0 of warp 0): streams the CTA's item descriptors into a shared-memory ring
+//    (TMA bulk copies of 8) and copies operand B of each item (the packed operator, from HBM)
+//    into a byte ring of 120 KB, as far ahead as the ring and the 16 item slots allow; at a
+//    chunk's last item it hands the chunk's output record to the epilogue through a ring of
+//    mbarriers. Operator tiles keep streaming while an operand A waits for the previous phase.
+//  - A producers (lane 0 of warps 11 and 12, alternate items): copy operand A of each item (runs
+//    of panel blocks, already in the MMA's layout, from L2) into one of 3 fixed buffers, once
+//    the item's panel is complete in this pass (Z1 / Z2 counters). A thread issues about two
+//    barrier-armed bulk copies per microsecond whatever their size, so the copies of one item
+//    stream are spread over three threads.
 //  - MMA issuer (lane 0 of warp 1; warp 1 also allocates and frees the tensor memory): per item
-//    waits for the converted A operand, issues the item's tcgen05.mma instructions into the
-//    chunk's accumulator (two accumulators of 128 columns alternate between chunks) and commits
-//    them to the barriers that free the stage and, at a chunk's end, the accumulator for the
-//    epilogue.
-//  - converters (warps 2-9; thread = one A-operand row x one half of K): per item read the
-//    staged panel rows into registers and overwrite them with operand A (TF32 rounding, or a
-//    BF16 hi/lo split) in the swizzled K-major layout, so a stage holds the item's two operands
-//    and nothing else; after the first item of the next chunk has been handed to the MMA
-//    issuer, read the finished accumulator (tcgen05.ld; each warp its 32-lane quarter and half
-//    of the column blocks), combine the real products into complex outputs and write them.
+//    waits for its slot, issues the item's tcgen05.mma instructions into the chunk's accumulator
+//    (two accumulators of 128 columns alternate between chunks) and commits them to the barriers
+//    that free the slot (its B bytes and A buffer) and, at a chunk's end, the accumulator for
+//    the epilogue.
+//  - epilogue (warps 2-9, each on its own): per chunk reads its part of the finished accumulator
+//    (tcgen05.ld; warp w reads the 32-lane quarter w % 4 and half of the column blocks), combines
+//    the real products into complex outputs and writes them: Z1 / Z2 in the operand-A layout of
+//    the next phase (TF32, or BF16 hi and lo), Y as complex64 in original ordering. Each warp
+//    releases the accumulator on its own (an mbarrier of 8 arrivals), so no epilogue warp waits
+//    for another and none of them stalls the producer or the MMA issuer. After its part of a Z1
+//    or Z2 chunk is stored, each warp arrives on the chunk's entry of a publication ring.
+//  - publisher (lane 0 of warp 10): per Z1 / Z2 chunk, once all 8 epilogue warps have arrived,
+//    adds 1 to the pass's counter of that panel with red.release.gpu. The release waits for the
+//    stores to be performed (about a microsecond under full HBM load); that wait is here, not on
+//    the epilogue warps' path.
 // Every wait is bounded (timeout_cycles); when one runs out the CTA records it in `status`, stops,
 // lets its copies and MMAs in flight finish, frees the tensor memory and returns.
 #include <cuda_bf16.h>
@@ -29,39 +40,71 @@
 namespace uh {
 namespace {
 
-constexpr int kThreads = 320;
-constexpr int kConverters = 256;
+constexpr int kAProducers = 3;          // copy-worker threads (one per warp)
+constexpr int kBAhead = 6;              // a worker's B copies run at most this many items past its A
+// B producer, MMA issuer, 8 epilogue warps, publisher, A producers
+constexpr int kThreads = 32 * (11 + kAProducers);
+constexpr int kPubRing = 16;            // Z1 / Z2 chunk publications in flight
+constexpr int kEpiWarps = 8;
 constexpr int kDescBatch = 8;
 constexpr int kDescRing = 2 * kDescBatch;
+constexpr int kRecRing = 4;            // chunk records in flight from the producer to the epilogue
 constexpr int kAccCols = 128;          // one accumulator: N <= 128 FP32 columns
 constexpr uint32_t kTmemCols = 2 * kAccCols;
+constexpr int kSlots = 16;             // items in flight: descriptor, B offset, full / empty barriers
+constexpr int kASlots = 3;             // operand-A buffers
+constexpr int kBRing = 120 * 1024;     // operand-B byte ring (B sizes are multiples of 2 KB)
 
 // Shared memory (bytes from a 1024-aligned base).
-constexpr int kStageTile = 0;                                   // B operand
-constexpr int kStagePanel = kPanelTileMax;                      // staged panel rows, then operand A
-constexpr int kStageBytes = kPanelTileMax + kPanelRawMax;       // 64 KB
-static_assert(kPanelRawMax == kPanelABytes, "operand A replaces the staged panel rows");
-constexpr int kOffSlots = kPanelStages * kStageBytes;           // item descriptor per stage
-constexpr int kOffRing = kOffSlots + kPanelStages * 96;         // descriptor ring
-constexpr int kOffBars = kOffRing + kDescRing * 96;
-// barriers: full[S], empty[S], afull[S], accfull[2], accempty[2], desc[2], done
-constexpr int kNumBars = 3 * kPanelStages + 2 + 2 + 2 + 1;
-constexpr int kOffMisc = kOffBars + kNumBars * 8;              // tmem base, abort, go words
+constexpr int kOffA = 0;                                        // operand A [kASlots]
+constexpr int kOffB = kASlots * kPanelABytes;                   // operand-B ring (1024-aligned)
+constexpr int kOffSlots = kOffB + kBRing;                       // item descriptors [kSlots]
+constexpr int kOffBoff = kOffSlots + kSlots * 96;               // B offset in the ring [kSlots]
+constexpr int kOffDeps = kOffBoff + kSlots * 4;                 // panels read by the item [kSlots]
+constexpr int kOffRing = kOffDeps + kSlots * 4;                 // descriptor ring
+constexpr int kOffRec = kOffRing + kDescRing * 96;              // chunk records [kRecRing]
+constexpr int kOffPub = kOffRec + kRecRing * 16;                // panel of each publication [kPubRing]
+constexpr int kOffBars = kOffPub + kPubRing * 4;
+// barriers: bfull[kSlots], afull[kSlots], sready[kSlots], empty[kSlots], accfull[2], accempty[2],
+// desc[2], recfull[R], recempty[R], done, pubfull[P], pubempty[P]
+constexpr int kNumBars = 4 * kSlots + 2 + 2 + 2 + 2 * kRecRing + 1 + 2 * kPubRing;
+static_assert(kOffB % 1024 == 0 && kBRing % 2048 == 0, "operand-B ring alignment");
+// After a wrap the skipped tail (< one B) and the new B must fit together in the empty ring.
+static_assert(kBRing >= 2 * kPanelTileMax, "operand-B ring too small for every wrap");
+static_assert(kASlots >= kAProducers && kASlots < kSlots, "operand-A buffers");
+// A slot's barriers are reused 16 items on: a drained B copy (item j - kASlots - kAProducers up
+// to j + kBAhead + kAProducers) must not alias an item of the same slot.
+static_assert(kASlots + 2 * kAProducers + kBAhead < kSlots, "slots");
+constexpr int kOffMisc = kOffBars + kNumBars * 8;              // tmem base, abort flag
 constexpr int kSmemBytes = kOffMisc + 64 + 1024;               // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory of one CTA");
+static_assert(kOffRec % 16 == 0 && kOffBars % 8 == 0, "alignment");
+
+// A chunk's output, handed from the producer to the epilogue.
+struct ChunkRec {
+  int64_t out;
+  int16_t h, n, kind, pad;
+};
+static_assert(sizeof(ChunkRec) == 16, "ChunkRec layout");
+
 struct Bars {
-  uint64_t *full, *empty, *afull, *accfull, *accempty, *desc, *done;
+  uint64_t *bfull, *afull, *sready, *empty, *accfull, *accempty, *desc, *recfull, *recempty, *done, *pubfull, *pubempty;
 };
 __device__ __forceinline__ Bars bars_of(unsigned char* sm) {
   uint64_t* b = reinterpret_cast<uint64_t*>(sm + kOffBars);
   Bars r;
-  r.full = b;
-  r.empty = b + kPanelStages;
-  r.afull = b + 2 * kPanelStages;
-  r.accfull = r.afull + kPanelStages;
+  r.bfull = b;
+  r.afull = b + kSlots;
+  r.sready = b + 2 * kSlots;
+  r.empty = b + 3 * kSlots;
+  r.accfull = r.empty + kSlots;
   r.accempty = r.accfull + 2;
   r.desc = r.accempty + 2;
-  r.done = r.desc + 2;
+  r.recfull = r.desc + 2;
+  r.recempty = r.recfull + kRecRing;
+  r.done = r.recempty + kRecRing;
+  r.pubfull = r.done + 1;
+  r.pubempty = r.pubfull + kPubRing;
   return r;
 }
 
@@ -83,6 +126,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Non-blocking test of an mbarrier phase (try_wait may hold the thread for a while before it
+// returns false).
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(smem_u32(bar)), "r"(parity)
@@ -123,9 +179,6 @@ __device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32
       "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
 }
-__device__ __forceinline__ void converters_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kConverters) : "memory");
-}
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
@@ -136,6 +189,13 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(1024 >> 4) << 32) |
          (static_cast<uint64_t>(1) << 46) | (static_cast<uint64_t>(2) << 61);
+}
+// Shared-memory matrix descriptor: K-major without swizzle, core matrices of 8 rows x 16 bytes,
+// `kstep` bytes apart along K (leading-dimension offset) and 128 bytes apart along M (stride
+// offset). Checked against a host product for TF32 and BF16 operands.
+__device__ __forceinline__ uint64_t plain_desc(uint32_t saddr, uint32_t kstep) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>((kstep >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>(128 >> 4) << 32) | (static_cast<uint64_t>(1) << 46);
 }
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
@@ -157,12 +217,29 @@ __device__ __forceinline__ uint32_t tf32_rna(float f) {
   return r;
 }
 
-// Producer: descriptors into the ring, per item the descriptor into the stage slot and the
-// operand B and panel rows into the stage.
-__device__ void producer(const PanelParams& p, int i0, int n, unsigned char* sm, const Bars& bar,
-                         volatile int* abort_flag) {
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// Manager (one thread): descriptors into the ring; per item, in order: waits for its slot (item
+// j - kSlots consumed), its descriptor and room in the B ring (freeing the B bytes of consumed
+// items, in order), then writes the slot (descriptor, B offset, panels it reads), hands over the
+// chunk record at a chunk's last item and signals the slot ready to the copy workers. It issues
+// no copy of operands. After the last item an end record (kind -1).
+__device__ void producer_b(const PanelParams& p, int i0, int n, unsigned char* sm, const Bars& bar,
+                           volatile int* abort_flag) {
   PanelItem* ring = reinterpret_cast<PanelItem*>(sm + kOffRing);
   PanelItem* slots = reinterpret_cast<PanelItem*>(sm + kOffSlots);
+  int32_t* boff = reinterpret_cast<int32_t*>(sm + kOffBoff);
+  int32_t* sdeps = reinterpret_cast<int32_t*>(sm + kOffDeps);
+  ChunkRec* recs = reinterpret_cast<ChunkRec*>(sm + kOffRec);
   auto issue_batch = [&](int batch) {
     const int first = batch * kDescBatch;
     if (first >= n) return;
@@ -173,67 +250,194 @@ __device__ void producer(const PanelParams& p, int i0, int n, unsigned char* sm,
   };
   issue_batch(0);
   issue_batch(1);
-  // The operator is streamed once: its lines go first, so the panels (read by many items) stay.
-  uint64_t stream_once, keep;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_once));
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
-  int j = 0;
+  int jb = 0, oldest = 0;   // next item, oldest item whose B bytes are held
+  int landed = 0;           // descriptor batches waited for
+  int chunk = 0;            // chunk records handed over
+  int head = 0, used = 0;   // B ring: next free byte, bytes held (with wrap waste)
+  int charge[kSlots] = {};  // B ring bytes held by the item in each slot
   bool ok = true;
-  for (; j < n; ++j) {
-    const int batch = j / kDescBatch;
-    if (j % kDescBatch == 0 &&
-        !wait_parity(&bar.desc[batch & 1], static_cast<uint32_t>(batch >> 1) & 1u, p.timeout_cycles, abort_flag)) {
+  // Waits until item `oldest` is consumed and frees its bytes.
+  auto free_oldest = [&]() -> bool {
+    if (!wait_parity(&bar.empty[oldest % kSlots], static_cast<uint32_t>(oldest / kSlots) & 1u, p.timeout_cycles,
+                     abort_flag))
+      return false;
+    used -= charge[oldest % kSlots];
+    ++oldest;
+    return true;
+  };
+  auto rec_wait = [&]() -> bool {
+    return chunk < kRecRing || wait_parity(&bar.recempty[chunk % kRecRing],
+                                           static_cast<uint32_t>(chunk / kRecRing - 1) & 1u, p.timeout_cycles, abort_flag);
+  };
+  for (; jb < n && ok; ++jb) {
+    const int batch = jb / kDescBatch;
+    if (batch >= landed) {
+      if (!wait_parity(&bar.desc[batch & 1], static_cast<uint32_t>(batch >> 1) & 1u, p.timeout_cycles, abort_flag)) {
+        ok = false;
+        break;
+      }
+      landed = batch + 1;
+    }
+    while (ok && jb - kSlots >= oldest) ok = free_oldest();  // the slot
+    if (!ok) break;
+    const PanelItem& it = ring[jb % kDescRing];
+    const int sz = it.tile_bytes;
+    if (used == 0) head = 0;  // an empty ring starts over
+    // B goes at head, or at the ring's start when it does not fit before the end (also when
+    // head is exactly at the end); the skipped tail is held with the item.
+    bool wrap = head + sz > kBRing;
+    while (ok && used + (wrap ? kBRing - head : 0) + sz > kBRing) {
+      ok = free_oldest();
+      if (used == 0) {
+        head = 0;
+        wrap = false;
+      }
+    }
+    if (!ok) break;
+    const int waste = wrap ? kBRing - head : 0;
+    const bool last = (it.flags & kPItemLast) != 0;
+    if (last && !rec_wait()) {
       ok = false;
       break;
     }
-    const int s = j % kPanelStages;
-    if (j >= kPanelStages &&
-        !wait_parity(&bar.empty[s], static_cast<uint32_t>(j / kPanelStages - 1) & 1u, p.timeout_cycles, abort_flag)) {
-      ok = false;
-      break;
-    }
-    const PanelItem& it = ring[j % kDescRing];
-    // Descriptor into the stage slot (generic stores, published by the arrive below).
+    const int s = jb % kSlots;
     const uint4* from = reinterpret_cast<const uint4*>(&it);
     uint4* to = reinterpret_cast<uint4*>(slots + s);
 #pragma unroll
     for (int w = 0; w < 6; ++w) to[w] = from[w];
-    unsigned char* st = sm + s * kStageBytes;
-    const uint32_t tile_bytes = 256u * static_cast<uint32_t>(it.n);
-    mbar_arrive_expect_tx(&bar.full[s], tile_bytes + static_cast<uint32_t>(it.nrows) * kPanelRowBytes);
-    bulk_g2s_hint(st + kStageTile, p.tiles + it.tile_off, tile_bytes, &bar.full[s], stream_once);
-    uint32_t row = 0;
-    for (int r = 0; r < it.nruns; ++r) {
-      const PanelRun run = it.runs[r];
-      const unsigned char* src = static_cast<const unsigned char*>(p.src[run.src]);
-      bulk_g2s_hint(st + kStagePanel + row * kPanelRowBytes, src + static_cast<int64_t>(run.start) * kPanelRowBytes,
-                    static_cast<uint32_t>(run.len) * kPanelRowBytes, &bar.full[s], keep);
-      row += static_cast<uint32_t>(run.len);
+    int deps = 0;
+    for (int r = 0; r < it.nruns; ++r)
+      if (it.runs[r].src != kPSrcXP) deps |= 1 << (it.runs[r].src - 1);
+    sdeps[s] = deps;
+    const int off = wrap ? 0 : head;
+    boff[s] = off;
+    head = off + sz;
+    used += waste + sz;
+    charge[s] = waste + sz;
+    if (last) {
+      recs[chunk % kRecRing] = ChunkRec{it.out, it.h, it.n, it.kind, 0};
+      mbar_arrive(&bar.recfull[chunk % kRecRing]);  // release: the record before the epilogue's acquire
+      ++chunk;
     }
-    if (j % kDescBatch == kDescBatch - 1) {
+    mbar_arrive(&bar.sready[s]);  // release: slot, offset and panels before the copy workers' acquire
+    if (jb % kDescBatch == kDescBatch - 1) {
       // Done with this batch's ring entries (read through the generic proxy): refill them.
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue_batch(batch + 2);
     }
   }
-  if (!ok) {
-    if (!*abort_flag) {
-      atomicOr(p.status, 1u);
-      *abort_flag = 1;
-    }
-    // Let the copies already issued land before the CTA can exit.
-    for (int q = (j >= kPanelStages ? j - kPanelStages + 1 : 0); q < j && q < n; ++q)
-      drain(&bar.full[q % kPanelStages], static_cast<uint32_t>(q / kPanelStages) & 1u, p.timeout_cycles);
-    const int b0 = j / kDescBatch;
-    for (int b = b0; b < b0 + 2 && b * kDescBatch < n; ++b)
-      drain(&bar.desc[b & 1], static_cast<uint32_t>(b >> 1) & 1u, p.timeout_cycles);
+  if (ok && rec_wait()) {
+    recs[chunk % kRecRing] = ChunkRec{0, 0, 0, -1, 0};
+    mbar_arrive(&bar.recfull[chunk % kRecRing]);
+    return;
   }
+  if (!*abort_flag) {
+    atomicOr(p.status, 1u);
+    *abort_flag = 1;
+  }
+  // Let the descriptor copies already issued land before the CTA can exit.
+  for (int b = landed; b < landed + 2 && b * kDescBatch < n; ++b)
+    drain(&bar.desc[b & 1], static_cast<uint32_t>(b >> 1) & 1u, p.timeout_cycles);
+}
+
+// Copy worker `a` of kAProducers (one thread each): items j = a, a + kAProducers, ... in order:
+// waits for the slot (manager) and copies operand B onto bfull; then waits for the item's A
+// buffer (item j - kASlots consumed) and, for runs in Z1 / Z2, the panel complete in this pass,
+// and copies the runs onto afull.
+__device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm, const Bars& bar,
+                           volatile int* abort_flag) {
+  const PanelItem* slots = reinterpret_cast<const PanelItem*>(sm + kOffSlots);
+  const int32_t* sdeps = reinterpret_cast<const int32_t*>(sm + kOffDeps);
+  const int32_t* boff = reinterpret_cast<const int32_t*>(sm + kOffBoff);
+  uint64_t keep;  // the panels stay in L2: every item's runs are read again by other items
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+  // The operator is streamed once: its lines go first, so the panels stay.
+  uint64_t stream_once;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream_once));
+  uint32_t ready = 0;  // panels Z1 (bit 0), Z2 (bit 1) known complete in this pass
+  int j = a;
+  bool ok = true;
+  int jbq = a;  // this worker's next B copy
+  auto copy_b = [&](int q) {
+    const int sb = q % kSlots;
+    const PanelItem& ib = slots[sb];
+    mbar_arrive_expect_tx(&bar.bfull[sb], static_cast<uint32_t>(ib.tile_bytes));
+    bulk_g2s_hint(sm + kOffB + boff[sb], p.tiles + ib.tile_off, static_cast<uint32_t>(ib.tile_bytes), &bar.bfull[sb],
+                  stream_once);
+  };
+  // B of this worker's later items whose slots are already written (a test, never a wait: the
+  // manager may be waiting for room that only this worker's A copies free).
+  auto look_ahead = [&]() {
+    while (jbq < n && jbq <= j + kBAhead && mbar_test(&bar.sready[jbq % kSlots], static_cast<uint32_t>(jbq / kSlots) & 1u)) {
+      copy_b(jbq);
+      jbq += kAProducers;
+    }
+  };
+  for (; j < n; j += kAProducers) {
+    const int s = j % kSlots;
+    if (jbq == j) {  // B of this item
+      if (!wait_parity(&bar.sready[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag)) {
+        ok = false;
+        break;
+      }
+      copy_b(j);
+      jbq += kAProducers;
+    }
+    look_ahead();
+    if (j >= kASlots && !wait_parity(&bar.empty[(j - kASlots) % kSlots],
+                                     static_cast<uint32_t>((j - kASlots) / kSlots) & 1u, p.timeout_cycles, abort_flag)) {
+      ok = false;
+      break;
+    }
+    const uint32_t deps = static_cast<uint32_t>(sdeps[s]);
+    if (deps & ~ready) {
+      const long long t0 = clock64();
+      for (;;) {
+        for (int k = 0; k < 2; ++k)
+          if (((deps & ~ready) >> k) & 1u)
+            if (ld_acquire_u64(p.done + k) >= p.need[k]) ready |= 1u << k;
+        if (!(deps & ~ready)) break;
+        if (*abort_flag || clock64() - t0 > p.timeout_cycles) {
+          ok = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+      if (!ok) break;
+      fence_proxy_async();  // the acquires above before the bulk copies that read those panels
+    }
+    const PanelItem& it = slots[s];
+    unsigned char* dst = sm + kOffA + (j % kASlots) * kPanelABytes;
+    mbar_arrive_expect_tx(&bar.afull[s], static_cast<uint32_t>(it.nrows) * kPanelRowBytes);
+    uint32_t row = 0;
+    for (int r = 0; r < it.nruns; ++r) {
+      const PanelRun run = it.runs[r];
+      const unsigned char* src = static_cast<const unsigned char*>(p.src[run.src]);
+      bulk_g2s_hint(dst + row * kPanelRowBytes, src + static_cast<int64_t>(run.start) * kPanelRowBytes,
+                    static_cast<uint32_t>(run.len) * kPanelRowBytes, &bar.afull[s], keep);
+      row += static_cast<uint32_t>(run.len);
+    }
+    look_ahead();
+  }
+  if (ok) return;
+  if (!*abort_flag) {
+    atomicOr(p.status, 64u);
+    *abort_flag = 1;
+  }
+  // The copies of this worker still in flight: A of its items among the last kASlots before j,
+  // B of its items from there up to jbq.
+  for (int q = j - kAProducers; q >= 0 && q >= j - kASlots - kAProducers; q -= kAProducers)
+    drain(&bar.afull[q % kSlots], static_cast<uint32_t>(q / kSlots) & 1u, p.timeout_cycles);
+  // (items before j - kASlots - kAProducers are consumed: the previous item's buffer wait)
+  for (int q = j - kASlots - kAProducers; q < jbq; q += kAProducers)
+    if (q >= 0) drain(&bar.bfull[q % kSlots], static_cast<uint32_t>(q / kSlots) & 1u, p.timeout_cycles);
 }
 
 // MMA issuer (one thread).
 __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const Bars& bar, uint32_t tmem,
                            volatile int* abort_flag) {
   const PanelItem* slots = reinterpret_cast<const PanelItem*>(sm + kOffSlots);
+  const int32_t* boff = reinterpret_cast<const int32_t*>(sm + kOffBoff);
   const uint32_t st_base = smem_u32(sm);
   const bool bf = p.mode == kPanelBF16X3;
   // D FP32; A, B TF32 (2) or BF16 (1); both K-major; M = 128.
@@ -248,14 +452,14 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
     }
   };
   for (int j = 0; j < n; ++j) {
-    const int s = j % kPanelStages;
-    if (!wait_parity(&bar.afull[s], static_cast<uint32_t>(j / kPanelStages) & 1u, p.timeout_cycles, abort_flag) ||
-        !wait_parity(&bar.full[s], static_cast<uint32_t>(j / kPanelStages) & 1u, p.timeout_cycles, abort_flag)) {
+    const int s = j % kSlots;
+    if (!wait_parity(&bar.bfull[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag) ||
+        !wait_parity(&bar.afull[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag)) {
       give_up();
       break;
     }
     const PanelItem& it = slots[s];
-    const int nn = it.n, flags = it.flags;
+    const int nn = it.n, flags = it.flags, nrows = it.nrows;
     const int c = chunks & 1;
     if ((flags & kPItemFirst) && chunks >= 2 &&
         !wait_parity(&bar.accempty[c], static_cast<uint32_t>((chunks >> 1) - 1) & 1u, p.timeout_cycles, abort_flag)) {
@@ -265,28 +469,27 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
     tc_fence_after();
     const uint32_t d = tmem + static_cast<uint32_t>(c * kAccCols);
     const uint32_t idesc = idesc_base | (static_cast<uint32_t>(nn >> 3) << 17);
-    const uint32_t A = st_base + static_cast<uint32_t>(s * kStageBytes + kStagePanel);
-    const uint32_t B = st_base + static_cast<uint32_t>(s * kStageBytes + kStageTile);
+    const uint32_t A = st_base + static_cast<uint32_t>(kOffA + (j % kASlots) * kPanelABytes);
+    const uint32_t B = st_base + static_cast<uint32_t>(kOffB + boff[s]);
     uint32_t acc = (flags & kPItemFirst) ? 0u : 1u;
     if (!bf) {
-      // K = 8 per instruction: 32-byte steps inside a 128-byte segment (32 TF32 values).
-#pragma unroll
-      for (int k0 = 0; k0 < kPanelK; k0 += 8) {
-        const uint32_t ao = static_cast<uint32_t>((k0 / 32) * 128 * 128 + (k0 % 32) * 4);
+      // K = 8 per instruction: two 4-row blocks of A (2 KB apart); B in 32-value segments.
+      for (int k0 = 0; k0 < nrows; k0 += 8) {
         const uint32_t bo = static_cast<uint32_t>((k0 / 32) * nn * 128 + (k0 % 32) * 4);
-        mma_tf32(d, sw128_desc(A + ao), sw128_desc(B + bo), idesc, acc);
+        mma_tf32(d, plain_desc(A + static_cast<uint32_t>(k0) * kPanelRowBytes, 2048), sw128_desc(B + bo), idesc, acc);
         acc = 1u;
       }
     } else {
-      // K = 16 per instruction; hi and lo planes: hi*hi + hi*lo + lo*hi.
-      const uint32_t alo = 128u * 128u, blo = static_cast<uint32_t>(nn) * 128u;
-#pragma unroll
-      for (int k0 = 0; k0 < kPanelK; k0 += 16) {
+      // K = 16 per instruction: two 8-row blocks of A (4 KB apart, lo plane 2 KB into each);
+      // B's hi plane in segment 0, lo plane in segment 1. hi*hi + hi*lo + lo*hi.
+      const uint32_t blo = static_cast<uint32_t>(nn) * 128u;
+      for (int k0 = 0; k0 < nrows; k0 += 16) {
+        const uint32_t a = A + static_cast<uint32_t>(k0) * kPanelRowBytes;
         const uint32_t o = static_cast<uint32_t>(k0 * 2);
-        mma_bf16(d, sw128_desc(A + o), sw128_desc(B + o), idesc, acc);
+        mma_bf16(d, plain_desc(a, 4096), sw128_desc(B + o), idesc, acc);
         acc = 1u;
-        mma_bf16(d, sw128_desc(A + o), sw128_desc(B + blo + o), idesc, 1u);
-        mma_bf16(d, sw128_desc(A + alo + o), sw128_desc(B + o), idesc, 1u);
+        mma_bf16(d, plain_desc(a, 4096), sw128_desc(B + blo + o), idesc, 1u);
+        mma_bf16(d, plain_desc(a + 2048, 4096), sw128_desc(B + o), idesc, 1u);
       }
     }
     issued = true;
@@ -303,153 +506,160 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
   }
 }
 
-template <bool BF>
-__device__ __forceinline__ void convert_item(unsigned char* panel, int nrows, int t) {
-  // Thread t builds half `hf` of row m of A: A[m][k] = component (m & 1) of right-hand side m / 2
-  // in panel row k, i.e. raw[k * 2 kPanelR + m], for k in [32 hf, 32 hf + 32); rows k >= nrows
-  // are zero. A replaces the staged rows in place: every thread reads its values before any
-  // thread writes.
-  const int m = t & 127, hf = t >> 7;
-  const float* raw = reinterpret_cast<const float*>(panel);
-  constexpr int kH = kPanelK / 2;
-  float v[kH];
-#pragma unroll
-  for (int k = 0; k < kH; ++k) {
-    const int kk = hf * kH + k;
-    v[k] = kk < nrows ? raw[kk * 2 * kPanelR + m] : 0.0f;
-  }
-  converters_sync();
-  unsigned char* rowbase = panel + (m / 8) * 1024 + (m % 8) * 128;
-  if (!BF) {
-    // 32 TF32 values = one 128-byte segment (segment hf).
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      unsigned char* dst = rowbase + hf * (128 * 128) + ((c ^ (m % 8)) * 16);
-      *reinterpret_cast<uint4*>(dst) =
-          make_uint4(tf32_rna(v[4 * c]), tf32_rna(v[4 * c + 1]), tf32_rna(v[4 * c + 2]), tf32_rna(v[4 * c + 3]));
-    }
-  } else {
-    // 32 BF16 values = 16-byte chunks 4 hf .. 4 hf + 3 of the hi and lo planes.
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      uint32_t hi[4], lo[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 f = make_float2(v[8 * c + 2 * e], v[8 * c + 2 * e + 1]);
-        const __nv_bfloat162 h = __float22bfloat162_rn(f);
-        const float2 hf2 = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __float22bfloat162_rn(make_float2(f.x - hf2.x, f.y - hf2.y));
-        hi[e] = *reinterpret_cast<const uint32_t*>(&h);
-        lo[e] = *reinterpret_cast<const uint32_t*>(&l);
-      }
-      unsigned char* dst = rowbase + (((4 * hf + c) ^ (m % 8)) * 16);
-      *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<uint4*>(dst + 128 * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    }
-  }
+// Every lane of the warp waits (each acquires the phase itself); false for all if any lane ran out.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, long long budget, volatile int* abort_flag) {
+  const bool ok = wait_parity(bar, parity, budget, abort_flag);
+  return __all_sync(0xffffffffu, ok) != 0;
 }
 
-struct Pending {
-  int64_t out;
-  int h, n, kind, c, use;
-};
-
-// Epilogue of one chunk by the 128 converter threads; false when aborting.
-__device__ bool epilogue(const PanelParams& p, const Pending& ch, const Bars& bar, uint32_t tmem,
-                         volatile int* abort_flag, volatile int* go, int t) {
-  if (t == 0) {
-    const bool ok = wait_parity(&bar.accfull[ch.c], static_cast<uint32_t>(ch.use) & 1u, p.timeout_cycles, abort_flag);
-    if (!ok && !*abort_flag) {
-      atomicOr(p.status, 2u);
-      *abort_flag = 1;
+// Epilogue warp (warps 2-9): chunk after chunk until the end record.
+__device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& bar, uint32_t tmem,
+                         volatile int* abort_flag) {
+  const ChunkRec* recs = reinterpret_cast<const ChunkRec*>(sm + kOffRec);
+  volatile int* pub = reinterpret_cast<volatile int*>(sm + kOffPub);
+  int np = 0;  // publications handed to the publisher
+  // Hands panel `kind` (or -1: no more) to the publisher as publication np; after this warp's
+  // stores (the warp barrier orders its lanes' stores before lane 0's arrive).
+  auto publish = [&](int kind) -> bool {
+    const int k = np % kPubRing;
+    __syncwarp();
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+      if (np >= kPubRing)
+        ok = wait_parity(&bar.pubempty[k], static_cast<uint32_t>(np / kPubRing - 1) & 1u, p.timeout_cycles, abort_flag);
+      if (ok) {
+        pub[k] = kind;
+        mbar_arrive(&bar.pubfull[k]);
+      } else if (!*abort_flag) {
+        atomicOr(p.status, 16u);
+        *abort_flag = 1;
+      }
     }
-    go[2] = ok ? 1 : 0;
-  }
-  converters_sync();
-  if (!go[2]) return false;
-  tc_fence_after();
+    ++np;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+  };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3;            // tensor-memory lane quarter of this warp
   const int hf = (warp - 2) >> 2;    // which column blocks: 16 (2 b + hf) .. + 15
-  const int m = 32 * q + lane;       // accumulator row
+  const int m = 32 * q + lane;       // accumulator row = operand-A row of the next phase
   const int r = m >> 1, part = m & 1;
-  int pm0 = 0, pm1 = 0;
-  if (ch.kind == kPOutY) {
-    if (lane < ch.h) pm0 = p.perm[ch.out + lane];
-    if (32 + lane < ch.h) pm1 = p.perm[ch.out + 32 + lane];
-  }
-  const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(ch.c * kAccCols);
-  for (int n0 = 16 * hf; n0 < ch.n; n0 += 32) {
-    uint32_t v[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(tbase + static_cast<uint32_t>(n0))
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int ii = 0; ii < 8; ++ii) {
-      const int i = n0 / 2 + ii;
-      if (i >= ch.h) break;  // uniform over the warp
-      // Re: D[2r][2i] - D[2r+1][2i+1]; Im: D[2r+1][2i] + D[2r][2i+1] (partner lane m ^ 1).
-      const float other = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[2 * ii + 1]), 1);
-      const float val = part ? __uint_as_float(v[2 * ii]) + other : __uint_as_float(v[2 * ii]) - other;
-      if (ch.kind == kPOutY) {
-        const int pi = __shfl_sync(0xffffffffu, i < 32 ? pm0 : pm1, i & 31);
-        if (r < p.nb)
-          static_cast<float*>(p.y)[(static_cast<int64_t>(pi) + static_cast<int64_t>(p.rhs0 + r) * p.ldy) * 2 + part] = val;
-      } else {
-        float* z = static_cast<float*>(p.zout[ch.kind]);
-        z[(ch.out + i) * (2 * kPanelR) + m] = val;
+  const bool bf = p.mode == kPanelBF16X3;
+  for (int k = 0;; ++k) {
+    const int qr = k % kRecRing;
+    if (!warp_wait(&bar.recfull[qr], static_cast<uint32_t>(k / kRecRing) & 1u, p.timeout_cycles, abort_flag)) {
+      if (lane == 0 && !*abort_flag) {
+        atomicOr(p.status, 2u);
+        *abort_flag = 1;
       }
+      return;
     }
-  }
-  tc_fence_before();
-  converters_sync();
-  if (t == 0) mbar_arrive(&bar.accempty[ch.c]);
-  return true;
-}
-
-template <bool BF>
-__device__ void converters(const PanelParams& p, int n, unsigned char* sm, const Bars& bar, uint32_t tmem,
-                           volatile int* abort_flag, volatile int* go) {
-  const int t = threadIdx.x - 64;  // 0 .. 255
-  const PanelItem* slots = reinterpret_cast<const PanelItem*>(sm + kOffSlots);
-  Pending pend{};
-  bool pending = false;
-  int chunks = 0;
-  for (int j = 0; j < n; ++j) {
-    const int s = j % kPanelStages;
-    if (t == 0) {
-      const bool ok = wait_parity(&bar.full[s], static_cast<uint32_t>(j / kPanelStages) & 1u, p.timeout_cycles, abort_flag);
-      if (!ok && !*abort_flag) {
+    const ChunkRec rec = recs[qr];
+    if (rec.kind < 0) {
+      publish(-1);
+      return;
+    }
+    const int c = k & 1;
+    if (!warp_wait(&bar.accfull[c], static_cast<uint32_t>(k >> 1) & 1u, p.timeout_cycles, abort_flag)) {
+      if (lane == 0 && !*abort_flag) {
         atomicOr(p.status, 4u);
         *abort_flag = 1;
       }
-      go[j & 1] = ok ? 1 : 0;
+      return;
     }
-    converters_sync();
-    if (!go[j & 1]) return;
-    // Everything needed from the stage slot, before the stage is released below.
-    const PanelItem& it = slots[s];
-    const int nrows = it.nrows, flags = it.flags;
-    const Pending mine{it.out, it.h, it.n, it.kind, chunks & 1, chunks >> 1};
-    convert_item<BF>(sm + s * kStageBytes + kStagePanel, nrows, t);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A writes before the MMA reads them
-    converters_sync();
-    if (t == 0) mbar_arrive(&bar.afull[s]);
-    if ((flags & kPItemFirst) && pending) {
-      if (!epilogue(p, pend, bar, tmem, abort_flag, go, t)) return;
-      pending = false;
+    tc_fence_after();
+    const int h = rec.h;
+    int pm0 = 0, pm1 = 0;
+    if (rec.kind == kPOutY) {
+      if (lane < h) pm0 = p.perm[rec.out + lane];
+      if (32 + lane < h) pm1 = p.perm[rec.out + 32 + lane];
     }
-    if (flags & kPItemLast) {
-      pend = mine;
-      pending = true;
-      ++chunks;
+    const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(c * kAccCols);
+    for (int n0 = 16 * hf; n0 < rec.n; n0 += 32) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tbase + static_cast<uint32_t>(n0))
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      // Re: D[2r][2i] - D[2r+1][2i+1]; Im: D[2r+1][2i] + D[2r][2i+1] (partner lane m ^ 1).
+      float val[8];
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii) {
+        const float other = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[2 * ii + 1]), 1);
+        val[ii] = part ? __uint_as_float(v[2 * ii]) + other : __uint_as_float(v[2 * ii]) - other;
+      }
+      const int i0 = n0 / 2;  // first output row of these 8 (a multiple of 8)
+      if (rec.kind == kPOutY) {
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+          const int i = i0 + ii;
+          if (i >= h) break;  // uniform over the warp
+          const int pi = __shfl_sync(0xffffffffu, i < 32 ? pm0 : pm1, i & 31);
+          if (r < p.nb)
+            static_cast<float*>(p.y)[(static_cast<int64_t>(pi) + static_cast<int64_t>(p.rhs0 + r) * p.ldy) * 2 + part] =
+                val[ii];
+        }
+      } else {
+        // The next phase's operand A: blocks of C rows from row out + i0 (out and i0 multiples
+        // of C); the zero rows of the accumulator past h complete the last block.
+        unsigned char* z = static_cast<unsigned char*>(p.zout[rec.kind]) + (m / 8) * 128 + (m % 8) * 16;
+        if (!bf) {
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            const int i = i0 + 4 * g;
+            if (i < h)
+              *reinterpret_cast<uint4*>(z + (rec.out + i) * kPanelRowBytes) =
+                  make_uint4(tf32_rna(val[4 * g]), tf32_rna(val[4 * g + 1]), tf32_rna(val[4 * g + 2]),
+                             tf32_rna(val[4 * g + 3]));
+          }
+        } else if (i0 < h) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 f = make_float2(val[2 * e], val[2 * e + 1]);
+            const __nv_bfloat162 hv = __float22bfloat162_rn(f);
+            const float2 hf2 = __bfloat1622float2(hv);
+            const __nv_bfloat162 lv = __float22bfloat162_rn(make_float2(f.x - hf2.x, f.y - hf2.y));
+            hi[e] = *reinterpret_cast<const uint32_t*>(&hv);
+            lo[e] = *reinterpret_cast<const uint32_t*>(&lv);
+          }
+          unsigned char* d = z + (rec.out + i0) * kPanelRowBytes;
+          *reinterpret_cast<uint4*>(d) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(d + 2048) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+      }
     }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&bar.accempty[c]);
+      mbar_arrive(&bar.recempty[qr]);
+    }
+    if (rec.kind != kPOutY && !publish(rec.kind)) return;
   }
-  if (pending) epilogue(p, pend, bar, tmem, abort_flag, go, t);
+}
+
+// Publisher (one thread): one release per Z1 / Z2 chunk, until the epilogue hands over -1.
+__device__ void publisher(const PanelParams& p, unsigned char* sm, const Bars& bar, volatile int* abort_flag) {
+  const volatile int* pub = reinterpret_cast<const volatile int*>(sm + kOffPub);
+  for (int j = 0;; ++j) {
+    const int k = j % kPubRing;
+    if (!wait_parity(&bar.pubfull[k], static_cast<uint32_t>(j / kPubRing) & 1u, p.timeout_cycles, abort_flag)) {
+      if (!*abort_flag) {
+        atomicOr(p.status, 32u);
+        *abort_flag = 1;
+      }
+      return;
+    }
+    const int kind = pub[k];
+    mbar_arrive(&bar.pubempty[k]);
+    if (kind < 0) return;
+    // the epilogue warps' stores happen before their arrives, which this thread has acquired;
+    // the release makes them visible to every CTA that acquires the counter
+    red_release_add(p.done + kind, 1ull);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelParams p) {
@@ -459,20 +669,28 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelParams p)
   volatile int* misc = reinterpret_cast<volatile int*>(sm + kOffMisc);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffMisc + 32);
   volatile int* abort_flag = misc;
-  volatile int* go = misc + 1;  // go[0], go[1] by item parity, go[2] for epilogues
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kPanelStages; ++s) {
-      mbar_init(&bar.full[s], 1);
-      mbar_init(&bar.empty[s], 1);  // MMA commit: both operands read
+    for (int s = 0; s < kSlots; ++s) {
+      mbar_init(&bar.bfull[s], 1);
       mbar_init(&bar.afull[s], 1);
+      mbar_init(&bar.sready[s], 1);
+      mbar_init(&bar.empty[s], 1);  // MMA commit: both operands read
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(&bar.accfull[q], 1);
-      mbar_init(&bar.accempty[q], 1);
+      mbar_init(&bar.accempty[q], kEpiWarps);
       mbar_init(&bar.desc[q], 1);
     }
+    for (int q = 0; q < kRecRing; ++q) {
+      mbar_init(&bar.recfull[q], 1);
+      mbar_init(&bar.recempty[q], kEpiWarps);
+    }
     mbar_init(bar.done, 1);
+    for (int q = 0; q < kPubRing; ++q) {
+      mbar_init(&bar.pubfull[q], kEpiWarps);
+      mbar_init(&bar.pubempty[q], 1);
+    }
     for (int q = 0; q < 4; ++q) misc[q] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -488,13 +706,15 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelParams p)
   const uint32_t tmem = *tmem_slot;
   const int i0 = p.cta_begin[blockIdx.x], n = p.cta_begin[blockIdx.x + 1] - i0;
   if (warp == 0) {
-    if (threadIdx.x == 0) producer(p, i0, n, sm, bar, abort_flag);
+    if (threadIdx.x == 0) producer_b(p, i0, n, sm, bar, abort_flag);
   } else if (warp == 1) {
     if (threadIdx.x == 32) mma_issuer(p, n, sm, bar, tmem, abort_flag);
-  } else if (p.mode == kPanelBF16X3) {
-    converters<true>(p, n, sm, bar, tmem, abort_flag, go);
-  } else {
-    converters<false>(p, n, sm, bar, tmem, abort_flag, go);
+  } else if (warp < 2 + kEpiWarps) {
+    epilogue(p, sm, bar, tmem, abort_flag);
+  } else if (warp == 2 + kEpiWarps) {
+    if (threadIdx.x == 32 * (2 + kEpiWarps)) publisher(p, sm, bar, abort_flag);
+  } else if ((threadIdx.x & 31) == 0) {
+    producer_a(p, n, warp - 3 - kEpiWarps, sm, bar, abort_flag);
   }
   tc_fence_before();
   __syncthreads();
@@ -503,21 +723,60 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelParams p)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-__global__ void gather_kernel(const float2* __restrict__ x, int64_t ldx, int64_t n, const int32_t* __restrict__ perm,
-                              int32_t rhs0, int32_t nb, float2* __restrict__ xp) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * 4 + threadIdx.x / kPanelR;
-  const int r = threadIdx.x % kPanelR;
-  if (i >= n) return;
-  xp[i * kPanelR + r] = r < nb ? x[perm[i] + static_cast<int64_t>(rhs0 + r) * ldx] : make_float2(0.f, 0.f);
+// X (complex64, column-major) -> XP in operand-A layout: one thread per (block g, A row m),
+// 2 blocks per 256 threads; rows >= n and right-hand sides >= nb are zero.
+template <bool BF>
+__global__ void gather_kernel(const float2* __restrict__ x, int64_t ldx, int64_t n, int64_t rows,
+                              const int32_t* __restrict__ perm, int32_t rhs0, int32_t nb, unsigned char* __restrict__ xp) {
+  constexpr int C = BF ? 8 : 4;
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * 2 + (threadIdx.x >> 7);
+  const int m = threadIdx.x & 127;
+  if (g * C >= rows) return;
+  const int r = m >> 1, part = m & 1;
+  float v[C];
+#pragma unroll
+  for (int t = 0; t < C; ++t) {
+    const int64_t j = g * C + t;
+    float f = 0.0f;
+    if (j < n && r < nb) {
+      const float2 z = x[perm[j] + static_cast<int64_t>(rhs0 + r) * ldx];
+      f = part ? z.y : z.x;
+    }
+    v[t] = f;
+  }
+  unsigned char* d = xp + g * C * kPanelRowBytes + (m / 8) * 128 + (m % 8) * 16;
+  if (!BF) {
+    *reinterpret_cast<uint4*>(d) = make_uint4(tf32_rna(v[0]), tf32_rna(v[1]), tf32_rna(v[2]), tf32_rna(v[3]));
+  } else {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = make_float2(v[2 * e], v[2 * e + 1]);
+      const __nv_bfloat162 hv = __float22bfloat162_rn(f);
+      const float2 hf2 = __bfloat1622float2(hv);
+      const __nv_bfloat162 lv = __float22bfloat162_rn(make_float2(f.x - hf2.x, f.y - hf2.y));
+      hi[e] = *reinterpret_cast<const uint32_t*>(&hv);
+      lo[e] = *reinterpret_cast<const uint32_t*>(&lv);
+    }
+    *reinterpret_cast<uint4*>(d) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(d + 2048) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
 }
 
 }  // namespace
 
-int panel_gather(const void* x, int64_t ldx, int64_t n, const int32_t* perm, int32_t rhs0, int32_t nb, void* xp,
-                 void* stream) {
-  const int64_t blocks = (n + 3) / 4;
-  gather_kernel<<<static_cast<unsigned>(blocks), 4 * kPanelR, 0, static_cast<cudaStream_t>(stream)>>>(
-      static_cast<const float2*>(x), ldx, n, perm, rhs0, nb, static_cast<float2*>(xp));
+int panel_gather(const void* x, int64_t ldx, int64_t n, int64_t rows, const int32_t* perm, int32_t rhs0, int32_t nb,
+                 int32_t mode, void* xp, void* stream) {
+  const int C = panel_block_rows(mode);
+  const int64_t blocks = (rows / C + 1) / 2;
+  if (blocks > 0) {
+    if (mode == kPanelBF16X3)
+      gather_kernel<true><<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+          static_cast<const float2*>(x), ldx, n, rows, perm, rhs0, nb, static_cast<unsigned char*>(xp));
+    else
+      gather_kernel<false><<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+          static_cast<const float2*>(x), ldx, n, rows, perm, rhs0, nb, static_cast<unsigned char*>(xp));
+  }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : set_error(UH_ECUDA, "panel gather launch: %s", cudaGetErrorString(e));
 }
@@ -528,8 +787,9 @@ int panel_prepare() {
 }
 
 int panel_launch(const PanelParams& p, int grid, void* stream) {
-  panel_kernel<<<grid, kThreads, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(p);
-  const cudaError_t e = cudaGetLastError();
+  void* args[] = {const_cast<PanelParams*>(&p)};
+  const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(panel_kernel), dim3(grid),
+                                                    dim3(kThreads), args, kSmemBytes, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? 0 : set_error(UH_ECUDA, "panel kernel launch: %s", cudaGetErrorString(e));
 }
 

@@ -44,18 +44,32 @@ size_t swizzled(int row, int k, int rows, int esz) {
          (((byte / 16) ^ (row % 8)) * 16) + byte % 16;
 }
 
-constexpr int64_t kItemOverhead = 8192;  // schedule cost of an item beyond its bytes
+// Schedule cost of an item, in bytes streamed in the same time: its operand B, a quarter of its
+// operand A (read from L2, not HBM), but at least the bytes a CTA streams while the tensor core
+// runs the item's MMAs (measured on GB300: about 0.45 us per item of 64 panel rows in BF16x3,
+// 0.35 us in TF32, against ~45 GB/s of operator per CTA).
+constexpr int64_t kABytesDivisor = 4;
+int64_t item_cost(int mode, int64_t b_bytes, int64_t a_bytes) {
+  const int64_t mma_floor = mode == kPanelTF32 ? 16384 : 20480;
+  return std::max(b_bytes + a_bytes / kABytesDivisor, mma_floor);
+}
 
 }  // namespace
 
 void PanelBuilder::pack_item(PanelItem& it, int h, const std::vector<const ColSpec*>& spec,
                              const std::vector<int64_t>& q) {
   const int n = it.n;
-  const size_t bytes = static_cast<size_t>(256) * n;
+  // TF32: one 128-byte K segment per 32 columns; BF16: the hi and the lo plane (K <= 64).
+  const int nseg = mode_ == kPanelTF32 ? (it.nrows + 31) / 32 : 2;
+  const size_t bytes = static_cast<size_t>(128) * n * nseg;
   it.tile_off = static_cast<int64_t>(tiles.size());
+  it.tile_bytes = static_cast<int32_t>(bytes);
+  streamed_bytes += static_cast<int64_t>(bytes);
+  mma_flops += int64_t{2} * 128 * n * it.nrows * (mode_ == kPanelTF32 ? 1 : 3);
   tiles.resize(tiles.size() + bytes, 0);
   unsigned char* t = tiles.data() + it.tile_off;
   for (int k = 0; k < it.nrows; ++k) {
+    if (!spec[k]) continue;  // zero column
     const ColSpec& c = *spec[k];
     for (int i = 0; i < h; ++i) {
       const int64_t idx = c.rowoff ? c.rowoff[i] + q[k] * c.colstep : c.off + q[k] * c.colstep + i * c.rowstep;
@@ -95,47 +109,85 @@ void PanelBuilder::add_chunk(int phase, int16_t kind, int64_t out, int h, const 
   };
   PanelItem cur = fresh();
   auto flush = [&]() {
+    // K up to a multiple of the MMA's K with a run of the zero block of XP
+    while (cur.nrows % kmma_) {
+      cur.runs[cur.nruns++] = PanelRun{static_cast<int32_t>(zero_row_), static_cast<int16_t>(C_), kPSrcXP, 0};
+      cur.nrows = static_cast<int16_t>(cur.nrows + C_);
+      for (int e = 0; e < C_; ++e) {
+        spec.push_back(nullptr);
+        q.push_back(0);
+      }
+    }
     pack_item(cur, h, spec, q);
-    ch.cost += 256 * static_cast<int64_t>(n) + static_cast<int64_t>(cur.nrows) * kPanelRowBytes + kItemOverhead;
+    ch.cost += item_cost(mode_, cur.tile_bytes, static_cast<int64_t>(cur.nrows) * kPanelRowBytes);
     ch.items.push_back(cur);
     cur = fresh();
     spec.clear();
     q.clear();
   };
-  for (const ColSpec& c : cols) {
-    for (int64_t j = 0; j < c.len; ++j) {
-      const int64_t row = c.start + j;
-      if (cur.nrows == kPanelK) flush();
-      PanelRun* last = cur.nruns ? &cur.runs[cur.nruns - 1] : nullptr;
-      const bool extend = last && last->src == c.src && last->start + last->len == row && last->len < 32767;
-      if (!extend && cur.nruns == kPanelMaxRuns) flush();
-      last = cur.nruns ? &cur.runs[cur.nruns - 1] : nullptr;
-      if (last && last->src == c.src && last->start + last->len == row && last->len < 32767) {
-        last->len++;
-      } else {
-        cur.runs[cur.nruns++] = PanelRun{static_cast<int32_t>(row), 1, static_cast<int8_t>(c.src), 0};
-      }
-      spec.push_back(&c);
-      q.push_back(j);
-      cur.nrows++;
+  // One block of C panel rows [p, p + C) of source src; column e comes from segment specs
+  // covering p + e, or is zero. Room is kept for the zero runs that complete the MMA's K.
+  const int max_data_runs = kPanelMaxRuns - kmma_ / C_ + 1;
+  auto add_block = [&](int src, int64_t p, const std::vector<const ColSpec*>& seg) {
+    if (cur.nrows + C_ > kPanelK) flush();
+    PanelRun* last = cur.nruns ? &cur.runs[cur.nruns - 1] : nullptr;
+    const bool extend = last && last->src == src && last->start + last->len == p && last->len + C_ <= 32767;
+    if (!extend && cur.nruns == max_data_runs) flush();
+    last = cur.nruns ? &cur.runs[cur.nruns - 1] : nullptr;
+    if (last && last->src == src && last->start + last->len == p && last->len + C_ <= 32767) {
+      last->len = static_cast<int16_t>(last->len + C_);
+    } else {
+      cur.runs[cur.nruns++] = PanelRun{static_cast<int32_t>(p), static_cast<int16_t>(C_), static_cast<int8_t>(src), 0};
     }
+    for (int e = 0; e < C_; ++e) {
+      const int64_t pos = p + e;
+      const ColSpec* hit = nullptr;
+      for (const ColSpec* c : seg)
+        if (pos >= c->start && pos < c->start + c->len) {
+          hit = c;
+          break;
+        }
+      spec.push_back(hit);
+      q.push_back(hit ? pos - hit->start : 0);
+    }
+    cur.nrows = static_cast<int16_t>(cur.nrows + C_);
+  };
+  // Consecutive specs that continue each other in the same panel form one segment, widened to
+  // block boundaries.
+  size_t k0 = 0;
+  std::vector<const ColSpec*> seg;
+  while (k0 < cols.size()) {
+    if (cols[k0].len <= 0) {
+      ++k0;
+      continue;
+    }
+    size_t k1 = k0 + 1;
+    while (k1 < cols.size() && cols[k1].len > 0 && cols[k1].src == cols[k0].src &&
+           cols[k1].start == cols[k1 - 1].start + cols[k1 - 1].len)
+      ++k1;
+    seg.clear();
+    for (size_t k = k0; k < k1; ++k) seg.push_back(&cols[k]);
+    const int64_t lo = cols[k0].start, hi = cols[k1 - 1].start + cols[k1 - 1].len;
+    for (int64_t p = lo / C_ * C_; p < hi; p += C_) add_block(cols[k0].src, p, seg);
+    k0 = k1;
   }
   if (cur.nrows > 0 || ch.items.empty()) flush();  // a chunk without columns writes zeros
   ch.items.front().flags |= kPItemFirst;
   ch.items.back().flags |= kPItemLast;
+  if (kind == kPOutZ1 || kind == kPOutZ2) ++z_chunks[kind];
   chunks_.push_back(std::move(ch));
 }
 
 const char* PanelBuilder::finalize() {
   items.clear();
-  begin.assign(3 * (ncta_ + 1), 0);
+  begin.assign(ncta_ + 1, 0);
   using Entry = std::pair<int64_t, int>;
+  std::vector<std::vector<int>> per_cta(ncta_);
   for (int phase = 0; phase < 3; ++phase) {
     std::vector<int> ids;
     for (size_t c = 0; c < chunks_.size(); ++c)
       if (chunks_[c].phase == phase) ids.push_back(static_cast<int>(c));
     std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return chunks_[a].cost > chunks_[b].cost; });
-    std::vector<std::vector<int>> per_cta(ncta_);
     std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> pq;
     for (int b = 0; b < ncta_; ++b) pq.push({0, b});
     for (int c : ids) {
@@ -144,41 +196,55 @@ const char* PanelBuilder::finalize() {
       per_cta[b].push_back(c);
       pq.push({l + chunks_[c].cost, b});
     }
-    for (int b = 0; b < ncta_; ++b) {
-      begin[phase * (ncta_ + 1) + b] = static_cast<int32_t>(items.size());
-      for (int c : per_cta[b]) items.insert(items.end(), chunks_[c].items.begin(), chunks_[c].items.end());
-    }
-    begin[phase * (ncta_ + 1) + ncta_] = static_cast<int32_t>(items.size());
+  }
+  for (int b = 0; b < ncta_; ++b) {
+    begin[b] = static_cast<int32_t>(items.size());
+    for (int c : per_cta[b]) items.insert(items.end(), chunks_[c].items.begin(), chunks_[c].items.end());
     if (items.size() > static_cast<size_t>(INT32_MAX)) return "too many work items";
   }
+  begin[ncta_] = static_cast<int32_t>(items.size());
   return nullptr;
 }
 
 const char* PanelBuilder::self_check(const int64_t src_rows[3], const int64_t out_rows[3]) const {
-  for (int phase = 0; phase < 3; ++phase) {
+  for (int k = 0; k < 3; ++k)
+    if (src_rows[k] % C_) return "panel height not a multiple of the block rows";
+  if (zero_row_ % C_ || zero_row_ + C_ > src_rows[kPSrcXP]) return "zero block outside XP";
+  {
     for (int b = 0; b < ncta_; ++b) {
-      const int32_t i0 = begin[phase * (ncta_ + 1) + b], i1 = begin[phase * (ncta_ + 1) + b + 1];
+      const int32_t i0 = begin[b], i1 = begin[b + 1];
       if (i0 > i1 || i1 > static_cast<int32_t>(items.size())) return "item range";
       bool open = false;
+      // Every wait ends: in a CTA's list, no item reads Z1 (Z2) before its last item that
+      // writes Z1 (Z2), so its own chunks of a panel never wait on the panel.
+      bool read_z[2] = {false, false};
       for (int32_t j = i0; j < i1; ++j) {
         const PanelItem& it = items[j];
+        if (it.kind != kPOutY && read_z[it.kind]) return "a CTA reads a panel before it has written its part";
+        for (int r = 0; r < it.nruns; ++r)
+          if (it.runs[r].src != kPSrcXP) read_z[it.runs[r].src - 1] = true;
         if (it.n < 16 || it.n > 2 * kPanelMaxH || it.n % 16) return "MMA N";
         if (it.h < 1 || it.h > kPanelMaxH || 2 * it.h > it.n) return "chunk height";
-        if (it.tile_off < 0 || it.tile_off % 256 || it.tile_off + 256 * static_cast<int64_t>(it.n) >
-                                                       static_cast<int64_t>(tiles.size()))
-          return "tile outside the packed tiles";
-        if (it.nrows < 0 || it.nrows > kPanelK || it.nruns < 0 || it.nruns > kPanelMaxRuns) return "item size";
+        if (it.nrows < 0 || it.nrows > kPanelK || it.nrows % kmma_ || it.nruns < 0 || it.nruns > kPanelMaxRuns)
+          return "item size";
+        const int nseg = mode_ == kPanelTF32 ? (it.nrows + 31) / 32 : 2;
+        if (it.tile_bytes != 128 * it.n * nseg || it.tile_bytes > kPanelTileMax) return "operand B size";
+        if (it.tile_off < 0 || it.tile_off % 1024 ||
+            it.tile_off + static_cast<int64_t>(it.tile_bytes) > static_cast<int64_t>(tiles.size()))
+          return "tile outside the packed tiles or misaligned";
         int64_t rows = 0;
         for (int r = 0; r < it.nruns; ++r) {
           const PanelRun& run = it.runs[r];
-          if (run.src < 0 || run.src > 2 || run.len < 1 || run.start < 0 ||
+          if (run.src < 0 || run.src > 2 || run.len < C_ || run.len % C_ || run.start < 0 || run.start % C_ ||
               static_cast<int64_t>(run.start) + run.len > src_rows[static_cast<int>(run.src)])
-            return "run outside its panel";
+            return "run outside its panel or not whole blocks";
           rows += run.len;
         }
         if (rows != it.nrows) return "run lengths";
-        if (it.kind < kPOutZ1 || it.kind > kPOutY || it.out < 0 || it.out + it.h > out_rows[it.kind])
-          return "chunk outside its output";
+        if (it.kind < kPOutZ1 || it.kind > kPOutY || it.out < 0) return "chunk output";
+        if (it.kind == kPOutY ? it.out + it.h > out_rows[it.kind]
+                              : (it.out % C_ || it.out + (it.h + C_ - 1) / C_ * C_ > out_rows[it.kind]))
+          return "chunk outside its output or misaligned";
         if ((it.flags & kPItemFirst) == open) return "chunk boundaries";
         open = !(it.flags & kPItemLast);
       }

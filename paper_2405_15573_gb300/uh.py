@@ -63,7 +63,8 @@ class Stats(C.Structure):
                 ("rank_min", _i32), ("rank_max", _i32), ("rank_mean", C.c_double), ("csp", _i32),
                 ("algo_bytes_matvec", _i64), ("device_bytes", _i64), ("packed_bytes", _i64),
                 ("n_launches", _i32), ("n_items", _i64),
-                ("matmat_mode", _i32), ("panel_bytes", _i64), ("panel_items", _i64)]
+                ("matmat_mode", _i32), ("panel_bytes", _i64), ("panel_items", _i64),
+                ("panel_mma_flops", _i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
