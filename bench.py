@@ -230,17 +230,17 @@ def timed_back_to_back(op, x, y, steps, torch):
     return a.elapsed_time(b) / steps
 
 
-# DRAM bytes (read + write) that ncu counted for one launch of stream_kernel<float> on the
+# DRAM bytes (read + write) that ncu counted for one launch of stream_kernel<KC64> on the
 # N=32768 sphere workload (cold L2), and digests of the code (kernel, packer and program
 # construction, comments aside) it was taken on. The figure is reported only while that code is
 # unchanged.
-NCU_TRAFFIC_BYTES = 715598080
+NCU_TRAFFIC_BYTES = 715478016
 NCU_TRAFFIC_SOURCES = {
-    "paper_2405_15573_gb300/csrc/uh_stream.cu": "ba3e4089c6dd725b302a961e625dc292d181504bb9d6f8d6fe0cbbdc3b55330c",
-    "paper_2405_15573_gb300/csrc/uh_stream.h": "870fa17e215236620acee2e727fef6d2316338cf73d75fd26e2b4d6b15a39393",
-    "paper_2405_15573_gb300/csrc/uh_program.cpp": "7cb10337b407df7c02d1f4ac81251b53df0f160f43133c34bf94c6c8ce7a14c1",
+    "paper_2405_15573_gb300/csrc/uh_stream.cu": "4c770e0e0bc62478a09a788c69641a199d4dd519411b5001682f6fadfd82c70b",
+    "paper_2405_15573_gb300/csrc/uh_stream.h": "b2bc216385aba291d6f655d109319333e56ba7f96e4299712056e505855cf2da",
+    "paper_2405_15573_gb300/csrc/uh_program.cpp": "51ae94d2d1ee9cded17798619163bd2c55cb75b142ecb3c263c090d34c6b90f6",
     "paper_2405_15573_gb300/csrc/uh_program.h": "42704035556b0d18b9ece7ebd20370269025cfcdbf90f9385f3810d514ae2c62",
-    "paper_2405_15573_gb300/csrc/uh_capi.cpp": "51c3cd8d14aa6d87d99d0127f38b70363406c0db49b75e5cecc2c17057596703",
+    "paper_2405_15573_gb300/csrc/uh_capi.cpp": "9c5945e17397246318f434c12b18a45ff3c605ce2688993e15000753c2c43f0c",
 }
 
 
@@ -284,7 +284,7 @@ def _colmajor_rhs(torch, n, nrhs, seed0=100):
     return torch.from_numpy(X.astype(np.complex64)).to("cuda").T
 
 
-def matmat_figures(model, n, steps, torch, peak_bf16):
+def matmat_figures(model, n, steps, torch, peak_bf16, sizes=(32, 64)):
     """uh_matmat on the tensor cores (TF32, BF16x3) for 32 and 64 right-hand sides: mean time per
     call (CUDA events, back to back), right-hand-side products per second, bytes of the packed
     operator streamed per second, MMA throughput, and the relative error of each column against
@@ -302,7 +302,7 @@ def matmat_figures(model, n, steps, torch, peak_bf16):
     for mode in ("tf32", "bf16x3"):
         op = model.uh_op("c64_" + mode)
         st = op.stats()
-        for nrhs in (32, 64):
+        for nrhs in sizes:
             X = X64[:, :nrhs]
             Y = torch.empty((nrhs, n), dtype=torch.complex64, device="cuda").T
             for _ in range(3):
@@ -357,7 +357,7 @@ def build_ops(workloads, precision="c64", threads=4):
         return list(ex.map(one, workloads))
 
 
-def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30):
+def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30, true_residual_sample=0):
     """GMRES(restart) solves served from a pool of resident complex64 UH operators (uh_server):
     per arrival rate, `requests` solves with Poisson arrivals, each on a random operator of the
     pool with a seeded right-hand side. Latency = submission to completion (library clock);
@@ -398,6 +398,22 @@ def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30):
     srv.close()
     del ops
     return out
+
+
+def large_matmat_figures(torch, peak_bf16, steps):
+    """The N = 131072 ellipsoid (1, 0.7, 0.4) with 1% radial noise, k = 32, eps 1e-4: uh_matmat
+    with 64 right-hand sides in both tensor-core modes, against its CUDA-core product."""
+    from paper_2405_15573_gb300 import inputs as I
+    from paper_2405_15573_gb300 import uh as U
+    w = I.ELLIPSOID_131072_R64
+    t0 = time.time()
+    model = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca)
+    build_s = time.time() - t0
+    res = matmat_figures(model, w.n, steps, torch, peak_bf16, sizes=(64,))
+    st = model.uh_op("c64").stats()
+    model.close()
+    return {"workload": w.name, "operator_build_s": round(build_s, 1),
+            "algo_bytes_matvec_c64": st["algo_bytes_matvec"], **res}
 
 
 def batched_figures(count, steps):
@@ -480,6 +496,7 @@ def profile_arm(args):
 
 
 def gpu_arm(args):
+    import ctypes as C
     import torch
     from paper_2405_15573_gb300 import inputs as I
     from paper_2405_15573_gb300 import uh as U
@@ -523,6 +540,10 @@ def gpu_arm(args):
         h64.matvec(x, yh)
         uh128.matvec(x128, y128)
     torch.cuda.synchronize()
+    # The timed region runs for at least about one second of wall time: K steps as asked, or more
+    # when K steps would take less (estimated from a short untimed run).
+    ms_est = timed_back_to_back(uh64, x, y, 20, torch)
+    steps_timed = max(args.steps, int(math.ceil(1000.0 / max(ms_est, 1e-3))))
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -532,7 +553,7 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     # The timed region: K UH products back to back. The packed operator (about 720 MB) is several
     # times the L2, and every product streams all of it, so no flush is needed between steps.
-    ms_uh = timed_back_to_back(uh64, x, y, args.steps, torch)
+    ms_uh = timed_back_to_back(uh64, x, y, steps_timed, torch)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -540,6 +561,9 @@ def gpu_arm(args):
     # each step (outside the events).
     ms_h = timed_back_to_back(h64, x, yh, args.steps, torch)
     ms_128 = timed_back_to_back(uh128, x128, y128, max(10, args.steps // 10), torch)
+    fp64 = C.c_double(0.0)
+    U.check(U.lib.uh_debug_dfma_rate(100000, C.byref(fp64), None), "uh_debug_dfma_rate")
+    fp64_tflops = fp64.value
     t_uh_fl = timed_matvecs(uh64, x, y, args.steps, flush, torch)
     # End to end through host buffers: every step copies its x in from pinned host memory, runs
     # the product and copies its y out. Two streams alternate so that a step's copies overlap the
@@ -577,7 +601,15 @@ def gpu_arm(args):
     assert np.array_equal(yhost[(e2e_steps - 1) & 1].numpy(), y.cpu().numpy()), "e2e result differs"
     time.sleep(0.2)
     clk = clocks.stop()
-    serving = None if args.no_serving else serving_figures(8, 16384, (200, 1000, 2000), 200)
+    # Configurations beyond the headline, each a documented subset that keeps its size range:
+    # the N = 131072 ellipsoid's 64-RHS product (whole), 32 of the 256 batched operators (N
+    # log-uniform in [1024, 16384]), and a serving pool of 8 operators with N uniform in
+    # [4096, 65536] at the six arrival rates.
+    large_mm = None if args.no_matmat or args.quick else large_matmat_figures(torch, peak_bf16, 20)
+    batched = None if args.quick else batched_figures(32, 20)
+    serving = None if args.no_serving else serving_figures(
+        8, 65536 if not args.quick else 16384,
+        (50, 100, 200, 500, 1000, 2000) if not args.quick else (200, 1000), 150)
 
     ms_max, t_e2e = replica_times(ms_uh, t_e2e, dist, "cuda")
     if rank != 0:
@@ -610,7 +642,8 @@ def gpu_arm(args):
 
     out = {
         "metric": METRIC, "value": job_value(world, ms_max), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "steps": steps_timed, "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "timed_seconds": ms_max * steps_timed / 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
         "data": "synthetic",
         "config": {"workload": workload_name(w),
@@ -624,15 +657,17 @@ def gpu_arm(args):
                 "d2h_bytes_per_step": int(y.numel() * 8)},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "peak_kind": peak_kind, "traffic": traffic,
-                     "kernel": "stream_kernel<float> (one persistent launch per matvec)",
+                     "kernel": "stream_kernel<KC64> (complex64; one persistent launch per matvec)",
                      "algo_bytes_per_matvec": st["algo_bytes_matvec"],
                      "frac_of_nominal_8000": gbs / 8000.0,
                      "l2_flushed": {"achieved": st["algo_bytes_matvec"] / (statistics.mean(t_uh_fl) * 1e-3) / 1e9,
                                     "frac": st["algo_bytes_matvec"] / (statistics.mean(t_uh_fl) * 1e-3) / 1e9 / peak,
-                                    "note": "same kernel, 2x-L2 write before every matvec (outside the events)"}},
+                                    "frac_median": st["algo_bytes_matvec"] / (statistics.median(t_uh_fl) * 1e-3) / 1e9 / peak,
+                                    "note": "same kernel, 2x-L2 write before every matvec (outside the events); "
+                                            "mean and median over the flushed steps"}},
         "cpu_baseline": cpu,
         "clocks": clk,
-        "gpu_launches": args.steps * st["n_launches"],
+        "gpu_launches": steps_timed * st["n_launches"],
         "uh": {"ms_mean": ms_uh, "GBps": gbs, "relerr_vs_oracle": rel_oracle, "stats": st,
                "flushed": {"ms_mean": statistics.mean(t_uh_fl), "ms_median": statistics.median(t_uh_fl),
                            "ms_min": min(t_uh_fl), "matvec_per_s": 1e3 / statistics.mean(t_uh_fl),
@@ -642,7 +677,13 @@ def gpu_arm(args):
         "uh_matmat": mm,
         "serving": serving,
         "uh_c128": {"matvec_per_s": 1e3 / ms_128, "ms_mean": ms_128, "GBps": gbs_128,
-                    "bound": "fp64 FMA (8 flops per complex multiply-add of a 16-byte element)"},
+                    "bound": "fp64 FMA (8 flops per complex multiply-add of a 16-byte element)",
+                    "fp64_tflops": gbs_128 / 16 * 8 / 1e3,
+                    "fp64_peak_tflops_measured": fp64_tflops,
+                    "fp64_frac": (gbs_128 / 16 * 8 / 1e3) / fp64_tflops,
+                    "peak_note": "uh_debug_dfma_rate: 8 independent DFMA chains per thread, 4 CTAs x 256 per SM"},
+        "uh_matmat_large": large_mm,
+        "batched": batched,
         "storage": {"E_UH": st["E_U"] + st["E_V"] + st["E_S"] + st["E_D"],
                     "E_H": hst["E_U"] + hst["E_V"] + hst["E_D"],
                     "ratio_H_over_UH": (hst["E_U"] + hst["E_V"] + hst["E_D"]) /
@@ -713,6 +754,7 @@ def main():
     ap.add_argument("--profile-op", choices=["uh64", "h64", "uh128", "mm_tf32", "mm_bf16x3"], default=None)
     ap.add_argument("--no-matmat", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the large matmat and the batch, smaller serving pool")
     ap.add_argument("--serve", action="store_true", help="serving sweep only (pool and rates below)")
     ap.add_argument("--pool", type=int, default=64)
     ap.add_argument("--n-hi", type=int, default=65536)

@@ -1,5 +1,6 @@
 /*
- * uh_debug.h - host-only checks of the device program (no CUDA call; for tests).
+ * uh_debug.h - host-only checks of the device program (no CUDA call; for tests), and device
+ * probes used by the benchmark.
  *
  * uh_create / h_create pack a product into a device program (work items, chunks, input runs and
  * their dependency flags, one item list per CTA of the persistent kernel) and check every
@@ -28,6 +29,16 @@ int uh_batch_pack_check(const uh_desc* const* descs, int32_t count, int32_t prec
  * For testing the bounded-wait path without hanging or faulting the GPU.
  */
 int uh_debug_stalled_matvec(uh_op* op, const void* x, void* y, long long timeout_cycles, void* stream);
+
+/*
+ * Measures the FP64 fused multiply-add rate of the current device: one launch of 4 resident
+ * CTAs per SM, each thread running 8 independent chains of `iters` dependent DFMAs (the
+ * instruction mix of the complex128 product's inner loop, without its loads), timed with CUDA
+ * events on `stream`; blocks until done. *tflops = 2 * FMAs / time / 1e12. The ceiling that the
+ * complex128 product (8 flops per 16-byte element) is compared with. UH_EINVAL for
+ * iters < 1000 or a null pointer, UH_ECUDA on a CUDA error.
+ */
+int uh_debug_dfma_rate(int32_t iters, double* tflops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -88,6 +88,7 @@ for _name, _args in [
     ("uh_check", [_p, _p]),
     ("uh_pack_check", [C.POINTER(UHDesc), _i32, _i32]),
     ("uh_debug_stalled_matvec", [_p, _p, _p, C.c_longlong, _p]),
+    ("uh_debug_dfma_rate", [_i32, C.POINTER(C.c_double), _p]),
     ("h_pack_check", [C.POINTER(HDesc), _i32, _i32]),
     ("h_check", [_p, _p]),
     ("uh_matvec_mixed", [_p, _p, _p, _p]),
