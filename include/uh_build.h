@@ -59,6 +59,17 @@ typedef struct uh_model uh_model;
 
 /* Build both operators for n points (row-major n x 3 doubles, host). */
 int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* params, uh_model** out);
+/*
+ * The same construction on the current CUDA device (Section 4.3, Algorithms 3 and 4, with the
+ * admissible blocks from ACA and recompression, Section 2.3): the host builds the two trees; the
+ * device computes, one CTA per block or cluster and all in FP64, every block's ACA (at most 64
+ * terms; UH_EINVAL if a block needs more) and recompression, every cluster basis (column-pivoted
+ * QR stopped at 1e-3 eps of the largest column, then one-sided Jacobi; UH_EINVAL if a numerical
+ * rank exceeds 128), the coupling matrices and the dense blocks; the results are copied into the
+ * model's host arrays, laid out as uhb_build_helmholtz lays them out. nthreads is unused.
+ * Synchronous; device memory is freed before it returns. UH_ENOMEM / UH_ECUDA on device errors.
+ */
+int uhb_build_helmholtz_gpu(int64_t n, const double* points, const uhb_params* params, uh_model** out);
 /* Descriptors into the model's arrays (complex128, UH_DATA_C128). */
 int uhb_uh_desc(const uh_model* m, uh_desc* out);
 int uhb_h_desc(const uh_model* m, h_desc* out);

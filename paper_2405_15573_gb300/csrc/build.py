@@ -22,7 +22,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["uh_stream.cu", "uh_noalloc.cu", "uh_panel.cu", "uh_solve.cu", "uh_probe.cu"]
+CU_SOURCES = ["uh_stream.cu", "uh_noalloc.cu", "uh_panel.cu", "uh_solve.cu", "uh_probe.cu", "uh_gbuild.cu"]
 CPP_SOURCES = ["uh_capi.cpp", "uh_program.cpp", "uh_build.cpp", "uh_panel_pack.cpp", "uh_serve.cpp"]
 
 

@@ -12,9 +12,12 @@
 #include <numeric>
 #include <vector>
 
+#include "uh_build_internal.h"
 #include "uh_internal.h"
 
 using cd = std::complex<double>;
+using uhb::Builder;
+using uhb::Cluster;
 
 namespace {
 
@@ -213,83 +216,6 @@ void qr_thin(int m, int k, const cd* A, std::vector<cd>& Q, std::vector<cd>& R) 
 
 // ------------------------------------------------------------------------- geometry
 
-struct Cluster {
-  int64_t begin, size;
-  int32_t level, parent, child0 = -1, child1 = -1;
-  double lo[3], hi[3];
-};
-
-struct Builder {
-  int64_t n = 0;
-  const double* pts = nullptr;
-  uhb_params prm{};
-  std::vector<Cluster> cl;
-  std::vector<int64_t> perm;  // position -> original index
-
-  void split(int64_t begin, std::vector<int64_t>& idx, int32_t level, int32_t parent) {
-    const int32_t id = static_cast<int32_t>(cl.size());
-    Cluster c{};
-    c.begin = begin;
-    c.size = static_cast<int64_t>(idx.size());
-    c.level = level;
-    c.parent = parent;
-    for (int d = 0; d < 3; ++d) { c.lo[d] = INFINITY; c.hi[d] = -INFINITY; }
-    for (int64_t i : idx)
-      for (int d = 0; d < 3; ++d) {
-        c.lo[d] = std::min(c.lo[d], pts[3 * i + d]);
-        c.hi[d] = std::max(c.hi[d], pts[3 * i + d]);
-      }
-    cl.push_back(c);
-    if (c.size > prm.leaf) {
-      int ax = 0;
-      for (int d = 1; d < 3; ++d)
-        if (c.hi[d] - c.lo[d] > c.hi[ax] - c.lo[ax]) ax = d;
-      std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
-        const double pa = pts[3 * a + ax], pb = pts[3 * b + ax];
-        return pa < pb || (pa == pb && a < b);
-      });
-      const int64_t half = c.size / 2;
-      std::vector<int64_t> left(idx.begin(), idx.begin() + half), right(idx.begin() + half, idx.end());
-      idx.clear();
-      idx.shrink_to_fit();
-      const int32_t c0 = static_cast<int32_t>(cl.size());
-      split(begin, left, level + 1, id);
-      const int32_t c1 = static_cast<int32_t>(cl.size());
-      split(begin + half, right, level + 1, id);
-      cl[id].child0 = c0;
-      cl[id].child1 = c1;
-    } else {
-      for (int64_t q = 0; q < c.size; ++q) perm[begin + q] = idx[q];
-    }
-  }
-
-  double diam(int32_t c) const {
-    double s = 0;
-    for (int d = 0; d < 3; ++d) s += (cl[c].hi[d] - cl[c].lo[d]) * (cl[c].hi[d] - cl[c].lo[d]);
-    return std::sqrt(s);
-  }
-  double dist(int32_t a, int32_t b) const {
-    double s = 0;
-    for (int d = 0; d < 3; ++d) {
-      const double g = std::max(0.0, std::max(cl[b].lo[d] - cl[a].hi[d], cl[a].lo[d] - cl[b].hi[d]));
-      s += g * g;
-    }
-    return std::sqrt(s);
-  }
-
-  // A_ij for original indices i, j.
-  cd entry(int64_t i, int64_t j) const {
-    const double dx = pts[3 * i] - pts[3 * j], dy = pts[3 * i + 1] - pts[3 * j + 1], dz = pts[3 * i + 2] - pts[3 * j + 2];
-    const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
-    cd a = (i == j) ? cd(0.5, 0.0) : cd(0.0, 0.0);
-    if (r > 0) {
-      const double kr = prm.wavenumber * r;
-      a += cd(std::cos(kr), std::sin(kr)) / (static_cast<double>(n) * r);
-    }
-    return a;
-  }
-};
-
 struct LowRank {
   int32_t k = 0;              // rank after recompression at tol_aca
   std::vector<cd> Ub, Yb;     // |tau| x k and |sigma| x k, orthonormal columns
@@ -402,25 +328,6 @@ LowRank aca_block(const Builder& B, const int64_t* rows, int m, const int64_t* c
 
 }  // namespace
 
-struct uh_model {
-  uhb_info_t info{};
-  std::vector<int64_t> perm, cl_begin, cl_size;
-  // UH
-  std::vector<int32_t> row_rank, col_rank;
-  std::vector<int64_t> row_off, col_off;
-  std::vector<cd> U, V, S;
-  std::vector<int32_t> adm_row, adm_col;
-  std::vector<int64_t> S_off;
-  // H
-  std::vector<int32_t> h_rank;
-  std::vector<int64_t> X_off, Y_off;
-  std::vector<cd> X, Y;
-  // near field
-  std::vector<int32_t> dense_row, dense_col;
-  std::vector<int64_t> D_off;
-  std::vector<cd> D;
-};
-
 namespace {
 
 void fill_tree(const uh_model* m, uh_tree_desc* t) {
@@ -442,9 +349,7 @@ void fill_dense(const uh_model* m, uh_dense_desc* d) {
 
 }  // namespace
 
-extern "C" {
-
-int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* prm, uh_model** out) {
+int uhb::check_build_args(int64_t n, const double* points, const uhb_params* prm, uh_model** out) {
   if (!points || !prm || !out) return uh::set_error(UH_EINVAL, "null argument");
   *out = nullptr;
   if (n < 1 || n > INT32_MAX) return uh::set_error(UH_EINVAL, "n = %lld out of range", (long long)n);
@@ -453,40 +358,10 @@ int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* prm, 
                          prm->eps, prm->tol_aca);
   for (int64_t i = 0; i < 3 * n; ++i)
     if (!std::isfinite(points[i])) return uh::set_error(UH_EINVAL, "point coordinate %lld is not finite", (long long)i);
-  if (prm->nthreads > 0) omp_set_num_threads(prm->nthreads);
-  auto* M = new (std::nothrow) uh_model();
-  if (!M) return uh::set_error(UH_ENOMEM, "host allocation");
-  double t0 = now_s();
-  Builder B;
-  B.n = n;
-  B.pts = points;
-  B.prm = *prm;
-  B.perm.assign(n, 0);
-  {
-    std::vector<int64_t> idx(n);
-    std::iota(idx.begin(), idx.end(), 0);
-    B.split(0, idx, 0, -1);
-  }
-  // Block cluster tree leaves.
-  std::vector<std::pair<int32_t, int32_t>> adm, dense;
-  std::vector<std::pair<int32_t, int32_t>> stack = {{0, 0}};
-  while (!stack.empty()) {
-    auto [a, b] = stack.back();
-    stack.pop_back();
-    const double d = B.dist(a, b);
-    // weak (eq. (3.3)): min of the two diameters; strong (eq. (3.2)): max
-    const double dm = prm->strong ? std::max(B.diam(a), B.diam(b)) : std::min(B.diam(a), B.diam(b));
-    if (d > 0 && dm <= prm->eta * d) {
-      adm.push_back({a, b});
-    } else if (B.cl[a].child0 < 0 || B.cl[b].child0 < 0) {
-      dense.push_back({a, b});
-    } else {
-      for (int32_t ca : {B.cl[a].child0, B.cl[a].child1})
-        for (int32_t cb : {B.cl[b].child0, B.cl[b].child1}) stack.push_back({ca, cb});
-    }
-  }
-  std::sort(adm.begin(), adm.end());
-  std::sort(dense.begin(), dense.end());
+  return UH_OK;
+}
+
+void uhb::fill_model_tree(uh_model* M, const Builder& B, const BlockList& adm, const BlockList& dense) {
   const int32_t ncl = static_cast<int32_t>(B.cl.size());
   M->perm = B.perm;
   M->cl_begin.resize(ncl);
@@ -497,6 +372,37 @@ int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* prm, 
     M->cl_size[c] = B.cl[c].size;
     depth = std::max(depth, B.cl[c].level + 1);
   }
+  std::vector<int32_t> rc(ncl, 0), cc(ncl, 0);
+  int32_t csp = 0;
+  for (auto& pr : adm) {
+    csp = std::max(csp, ++rc[pr.first]);
+    csp = std::max(csp, ++cc[pr.second]);
+  }
+  M->info.n = B.n;
+  M->info.n_clusters = ncl;
+  M->info.n_adm = static_cast<int64_t>(adm.size());
+  M->info.n_dense = static_cast<int64_t>(dense.size());
+  M->info.depth = depth;
+  M->info.csp = csp;
+}
+
+extern "C" {
+
+int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* prm, uh_model** out) {
+  int rc;
+  if ((rc = uhb::check_build_args(n, points, prm, out))) return rc;
+  if (prm->nthreads > 0) omp_set_num_threads(prm->nthreads);
+  auto* M = new (std::nothrow) uh_model();
+  if (!M) return uh::set_error(UH_ENOMEM, "host allocation");
+  double t0 = now_s();
+  Builder B;
+  B.n = n;
+  B.pts = points;
+  B.prm = *prm;
+  uhb::BlockList adm, dense;
+  uhb::make_trees(B, &adm, &dense);
+  const int32_t ncl = static_cast<int32_t>(B.cl.size());
+  uhb::fill_model_tree(M, B, adm, dense);
   double t1 = now_s();
   M->info.seconds_tree = t1 - t0;
 
@@ -666,19 +572,6 @@ int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* prm, 
   }
   M->info.seconds_dense = now_s() - t3;
 
-  // Statistics.
-  std::vector<int32_t> rc(ncl, 0), cc(ncl, 0);
-  int32_t csp = 0;
-  for (auto& pr : adm) {
-    csp = std::max(csp, ++rc[pr.first]);
-    csp = std::max(csp, ++cc[pr.second]);
-  }
-  M->info.n = n;
-  M->info.n_clusters = ncl;
-  M->info.n_adm = na;
-  M->info.n_dense = nd;
-  M->info.depth = depth;
-  M->info.csp = csp;
   M->info.kmax_aca = kmax_aca;
   M->info.kmax_h = kmax_h;
   M->info.lmax = lmax;

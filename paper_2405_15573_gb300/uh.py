@@ -538,11 +538,13 @@ class BuildInfo(C.Structure):
 
 
 lib.uhb_build_helmholtz.argtypes = [_i64, _p, C.POINTER(BuildParams), C.POINTER(_p)]
+lib.uhb_build_helmholtz_gpu.argtypes = [_i64, _p, C.POINTER(BuildParams), C.POINTER(_p)]
 lib.uhb_uh_desc.argtypes = [_p, C.POINTER(UHDesc)]
 lib.uhb_h_desc.argtypes = [_p, C.POINTER(HDesc)]
 lib.uhb_info.argtypes = [_p, C.POINTER(BuildInfo)]
 lib.uhb_free.argtypes = [_p]
-for _f in (lib.uhb_build_helmholtz, lib.uhb_uh_desc, lib.uhb_h_desc, lib.uhb_info, lib.uhb_free):
+for _f in (lib.uhb_build_helmholtz, lib.uhb_build_helmholtz_gpu, lib.uhb_uh_desc, lib.uhb_h_desc, lib.uhb_info,
+           lib.uhb_free):
     _f.restype = C.c_int
 
 
@@ -558,13 +560,15 @@ class HelmholtzModel:
     """Synthetic Helmholtz collocation operator built on the host (uh_build.h) in both UH and
     H form. The arrays live in the library; uh_op()/h_op() upload them to the GPU."""
 
-    def __init__(self, points, wavenumber, leaf, eta, eps, tol_aca, nthreads: int = 0, strong: bool = False):
+    def __init__(self, points, wavenumber, leaf, eta, eps, tol_aca, nthreads: int = 0, strong: bool = False,
+                 device: bool = False):
+        """device=True: the construction runs on the current CUDA device (uhb_build_helmholtz_gpu)."""
         pts = np.ascontiguousarray(points, dtype=np.float64)
         prm = BuildParams(float(wavenumber), int(leaf), float(eta), float(eps), float(tol_aca),
                           int(nthreads), 1 if strong else 0)
         h = _p()
-        check(lib.uhb_build_helmholtz(len(pts), pts.ctypes.data, C.byref(prm), C.byref(h)),
-              "uhb_build_helmholtz")
+        fn = lib.uhb_build_helmholtz_gpu if device else lib.uhb_build_helmholtz
+        check(fn(len(pts), pts.ctypes.data, C.byref(prm), C.byref(h)), fn.__name__)
         self.handle = h
         self.n = len(pts)
 
