@@ -333,28 +333,23 @@ class _MatmatStep:
         self.op.matmat(self.X, self.Y, mode=self.mode)
 
 
-def build_models(workloads, threads=8):
-    """Host-side builds of several operators at once (the builder releases the GIL)."""
-    from concurrent.futures import ThreadPoolExecutor
+def build_models(workloads):
+    """Several operators built one after the other on the GPU (uhb_build_helmholtz_gpu)."""
     from paper_2405_15573_gb300 import uh as U
-    with ThreadPoolExecutor(threads) as ex:
-        return list(ex.map(lambda w: U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca,
-                                                      nthreads=2), workloads))
+    return [U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca, device=True)
+            for w in workloads]
 
 
-def build_ops(workloads, precision="c64", threads=4):
-    """Device ops of several operators; each host model is freed as soon as its op is uploaded, so
-    at most `threads` models are held on the host at a time."""
-    from concurrent.futures import ThreadPoolExecutor
+def build_ops(workloads, precision="c64"):
+    """Device ops of several operators, each built on the GPU and uploaded, its host model freed
+    before the next one is built."""
     from paper_2405_15573_gb300 import uh as U
-
-    def one(w):
-        m = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca, nthreads=4)
-        op = m.uh_op(precision)
+    ops = []
+    for w in workloads:
+        m = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca, device=True)
+        ops.append(m.uh_op(precision))
         m.close()
-        return op
-    with ThreadPoolExecutor(threads) as ex:
-        return list(ex.map(one, workloads))
+    return ops
 
 
 def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30, true_residual_sample=0):
@@ -407,12 +402,12 @@ def large_matmat_figures(torch, peak_bf16, steps):
     from paper_2405_15573_gb300 import uh as U
     w = I.ELLIPSOID_131072_R64
     t0 = time.time()
-    model = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca)
+    model = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca, device=True)
     build_s = time.time() - t0
     res = matmat_figures(model, w.n, steps, torch, peak_bf16, sizes=(64,))
     st = model.uh_op("c64").stats()
     model.close()
-    return {"workload": w.name, "operator_build_s": round(build_s, 1),
+    return {"workload": w.name, "operator_build_s": round(build_s, 1), "operator_build": "GPU (uhb_build_helmholtz_gpu)",
             "algo_bytes_matvec_c64": st["algo_bytes_matvec"], **res}
 
 
@@ -512,8 +507,12 @@ def gpu_arm(args):
 
     w = I.SPHERE_32768
     t0 = time.time()
-    model = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca)
+    model = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca, device=True)
     build_s = time.time() - t0
+    build_info = model.info()
+    t0 = time.time()
+    U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca).close()
+    build_host_s = time.time() - t0
     uh64 = model.uh_op("c64")
     h64 = model.h_op("c64")
     uh128 = model.uh_op("c128")
@@ -650,7 +649,8 @@ def gpu_arm(args):
                    "precision": "complex64 storage, FP32 accumulation",
                    "l2": "inputs larger than L2: the packed operator is "
                          f"{st['packed_bytes'] / 2**20:.0f} MiB, every step streams all of it; no flush",
-                   "parallelism": f"replicas x{world}", "operator_build_s": round(build_s, 2)},
+                   "parallelism": f"replicas x{world}", "operator_build_s": round(build_s, 2),
+                   "operator_build": "GPU (uhb_build_helmholtz_gpu, Algorithms 3/4 with ACA on the device)"},
         "e2e": {"value": job_value(world, t_e2e), "unit": UNIT,
                 "note": "uh_matvec on two alternating streams; each step's x in and y out overlap neighbouring products",
                 "h2d_bytes_per_step": int(x.numel() * 8),
@@ -684,6 +684,11 @@ def gpu_arm(args):
                     "peak_note": "uh_debug_dfma_rate: 8 independent DFMA chains per thread, 4 CTAs x 256 per SM"},
         "uh_matmat_large": large_mm,
         "batched": batched,
+        "construction": {"gpu_s": build_s, "host_s": build_host_s, "speedup": build_host_s / build_s,
+                         "gpu_stages_s": {k: build_info[k] for k in ("seconds_tree", "seconds_aca", "seconds_bases",
+                                                                      "seconds_dense")},
+                         "host_cores": os.cpu_count(),
+                         "note": "same operator from both builders (identical trees; ranks and products agree to rounding)"},
         "storage": {"E_UH": st["E_U"] + st["E_V"] + st["E_S"] + st["E_D"],
                     "E_H": hst["E_U"] + hst["E_V"] + hst["E_D"],
                     "ratio_H_over_UH": (hst["E_U"] + hst["E_V"] + hst["E_D"]) /
@@ -732,7 +737,10 @@ def reference_arm(args):
            "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
            "config": {"workload": workload_name(w),
                       "precision": "complex128, the FP64 oracle on the host (no GPU work)",
-                      "operator_build_s": round(build_s, 1)},
+                      "operator_build_s": round(build_s, 1),
+                      "operator": "built by the library's host builder (uhb_build_helmholtz, the oracle's "
+                                  "algorithm in C++; the oracle's own NumPy construction of N=32768 does not fit "
+                                  "the arm's time), then applied by the oracle's FP64 UH product"},
            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{reps} full FP64 oracle UH matvecs of the N={w.n} operator "
                                       f"(NumPy, one BLAS thread) in {secs:.1f} s"},

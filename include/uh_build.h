@@ -65,7 +65,7 @@ int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* param
  * device computes, one CTA per block or cluster and all in FP64, every block's ACA (at most 64
  * terms; UH_EINVAL if a block needs more) and recompression, every cluster basis (column-pivoted
  * QR stopped at 1e-3 eps of the largest column, then one-sided Jacobi; UH_EINVAL if a numerical
- * rank exceeds 128), the coupling matrices and the dense blocks; the results are copied into the
+ * rank exceeds 256), the coupling matrices and the dense blocks; the results are copied into the
  * model's host arrays, laid out as uhb_build_helmholtz lays them out. nthreads is unused.
  * Synchronous; device memory is freed before it returns. UH_ENOMEM / UH_ECUDA on device errors.
  */

@@ -11,8 +11,8 @@
 //   basis_kernel      per row (column) cluster: the stacked matrix [U_b s_b] ([Y_b s_b]) of its
 //                     blocks (Algorithm 3's X_tau), column-pivoted Householder QR stopped once the
 //                     rest is below 1e-3 eps of the largest column, one-sided Jacobi of the small
-//                     triangular factor (the rank-revealing route of Remark 4.2), basis = left
-//                     singular vectors with sigma > eps * sigma_1;
+//                     triangular factor (after one more QR: r x r rotations), the rank-revealing
+//                     route of Remark 4.2; basis = left singular vectors with sigma > eps sigma_1;
 //   coupling_kernel   per block: S_b = (U_tau^* U_b s_b)(V_sigma^* Y_b)^*, the projection of the
 //                     block onto the two bases (Section 4.1);
 //   dense_kernel      the near-field blocks' entries;
@@ -380,7 +380,7 @@ __device__ void cta_jacobi(double2* B, int rows, int cols, int64_t ldb, double2*
 }
 
 // Column norms of B (rows x cols), their order (descending, stable) and the number kept above
-// rel * the largest: sv[] and ord[] in shared memory (cols <= 128). Returns the kept count.
+// rel * the largest: sv[] and ord[] in shared memory (cols <= kRowMax). Returns the kept count.
 __device__ int cta_order(const double2* B, int rows, int cols, int64_t ldb, double rel, double* sv, int* ord) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = warp; c < cols; c += kWarps) {
@@ -412,11 +412,12 @@ __device__ int cta_order(const double2* B, int rows, int cols, int64_t ldb, doub
 }
 
 // A (m x p) <- A (m x p) W (p x q), q <= p, in place row by row (W in shared or global memory,
-// ldw). p <= kRowMax.
-constexpr int kRowMax = 128;
+// ldw). p <= P.
+constexpr int kRowMax = 256;  // largest numerical rank of a cluster's stacked matrix
+template <int P>
 __device__ void cta_rows_times(double2* A, int m, int p, int64_t lda, const double2* W, int64_t ldw, int q) {
   for (int t = threadIdx.x; t < m; t += kThreads) {
-    double2 row[kRowMax];
+    double2 row[P];
     for (int a = 0; a < p; ++a) row[a] = A[t + static_cast<int64_t>(a) * lda];
     for (int c = 0; c < q; ++c) {
       double2 s = make_double2(0.0, 0.0);
@@ -487,8 +488,8 @@ __global__ void __launch_bounds__(kThreads) recompress_kernel(BlockTab T, int64_
       M[i + c * kCap] = J[i + ord[c] * kCap];
     }
     __syncthreads();
-    cta_rows_times(X, m, p1, m, R1, kCap, keep);
-    cta_rows_times(Y, n, p2, n, M, kCap, keep);
+    cta_rows_times<kCap>(X, m, p1, m, R1, kCap, keep);
+    cta_rows_times<kCap>(Y, n, p2, n, M, kCap, keep);
     for (int c = threadIdx.x; c < keep; c += kThreads) sv_out[b * kCap + c] = sv[ord[c]];
     if (threadIdx.x == 0) kb[b] = keep;
     __syncthreads();
@@ -650,8 +651,16 @@ __global__ void __launch_bounds__(kThreads) basis_kernel(const BasisWork* work, 
     }
     __syncthreads();
     cta_form_q(X, m, r, m, tau);
-    cta_jacobi(B, K, r, K, Jm, r, &flag);
-    const int keep = cta_order(B, K, r, K, eps, sv, ord);
+    // B = Q_B R_B (Householder): R_B J = Z' diag(s) gives the same J and s as B J = Z diag(s), and
+    // the rotations run on r x r instead of K x r entries.
+    cta_qr(B, K, r, K, tau, shd);
+    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(r) * r; e += kThreads) {
+      const int i = static_cast<int>(e % r), c = static_cast<int>(e / r);
+      if (i > c) B[i + static_cast<int64_t>(c) * K] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    cta_jacobi(B, r, r, K, Jm, r, &flag);
+    const int keep = cta_order(B, r, r, K, eps, sv, ord);
     // the kept columns of J, in order, at the front of B's first column block (r x keep, ld r)
     double2* Jsel = B;  // B is no longer needed
     for (int e = threadIdx.x; e < r * keep; e += kThreads) {
@@ -659,7 +668,7 @@ __global__ void __launch_bounds__(kThreads) basis_kernel(const BasisWork* work, 
       Jsel[i + static_cast<int64_t>(c) * r] = Jm[i + static_cast<int64_t>(ord[c]) * r];
     }
     __syncthreads();
-    cta_rows_times(X, m, r, m, Jsel, r, keep);
+    cta_rows_times<kRowMax>(X, m, r, m, Jsel, r, keep);
     if (threadIdx.x == 0) ell[w] = keep;
     __syncthreads();
   }
