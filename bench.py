@@ -411,9 +411,11 @@ def large_matmat_figures(torch, peak_bf16, steps):
             "algo_bytes_matvec_c64": st["algo_bytes_matvec"], **res}
 
 
-def batched_figures(count, steps):
+def batched_figures(count, steps, tune_sample=32):
     """One launch for `count` independent complex64 UH operators (uh_batch) against one launch
-    per operator (uh_matvec each), back to back, CUDA events; operator products per second."""
+    per operator (uh_matvec each), back to back, CUDA events; operator products per second. The
+    batch is packed twice: with the default parameters and with the autotuner's choice
+    (uh_batch_tune on an evenly spaced sample of `tune_sample` of the operators)."""
     import torch
     from paper_2405_15573_gb300 import inputs as I
     from paper_2405_15573_gb300 import uh as U
@@ -421,9 +423,14 @@ def batched_figures(count, steps):
     t0 = time.time()
     models = build_models(pool)
     build_s = time.time() - t0
+    descs = [m.uh_desc() for m in models]
     t0 = time.time()
-    batch = U.UHBatch([m.uh_desc() for m in models], "c64")
+    best, tune_best_ms, tune_default_ms = U.UHBatch.tune(descs, "c64", sample=tune_sample, reps=20)
+    tune_s = time.time() - t0
+    t0 = time.time()
+    batch = U.UHBatch(descs, "c64")
     pack_s = time.time() - t0
+    tuned = U.UHBatch(descs, "c64", best)
     ops = [m.uh_op("c64") for m in models]
     for m in models:
         m.close()
@@ -435,12 +442,17 @@ def batched_figures(count, steps):
         def matvec(self, _x, _y):
             for k, op in enumerate(ops):
                 op.matvec(x[off[k]:off[k + 1]], y2[off[k]:off[k + 1]])
+    y3 = torch.empty_like(x)
     for _ in range(3):
         batch.matvec(x, y)
+        tuned.matvec(x, y3)
         Seq().matvec(None, None)
     ms_b = timed_back_to_back(batch, x, y, steps, torch)
+    ms_t = timed_back_to_back(tuned, x, y3, steps, torch)
     ms_s = timed_back_to_back(Seq(), None, None, max(3, steps // 5), torch)
     batch.check()
+    tuned.check()
+    tuned_diff = float(torch.linalg.vector_norm(y3 - y) / torch.linalg.vector_norm(y))
     st = batch.stats()
     yb, ys = y.cpu().numpy().astype(np.complex128), y2.cpu().numpy().astype(np.complex128)
     diff = max(float(np.linalg.norm(yb[off[k]:off[k + 1]] - ys[off[k]:off[k + 1]]) /
@@ -451,7 +463,14 @@ def batched_figures(count, steps):
             "operator_matvecs_per_s": count * 1e3 / ms_b, "operator_matvecs_per_s_separate": count * 1e3 / ms_s,
             "GBps": st["algo_bytes_matvec"] / (ms_b * 1e-3) / 1e9,
             "frac": st["algo_bytes_matvec"] / (ms_b * 1e-3) / 1e9 / peak,
-            "algo_bytes": st["algo_bytes_matvec"], "max_rel_diff_vs_separate": diff}
+            "algo_bytes": st["algo_bytes_matvec"], "max_rel_diff_vs_separate": diff,
+            "tuned": {"params": best.as_dict(), "ms": ms_t, "operator_matvecs_per_s": count * 1e3 / ms_t,
+                      "GBps": st["algo_bytes_matvec"] / (ms_t * 1e-3) / 1e9,
+                      "frac": st["algo_bytes_matvec"] / (ms_t * 1e-3) / 1e9 / peak,
+                      "speedup_vs_default": ms_b / ms_t, "tune_s": round(tune_s, 1),
+                      "tune_sample": min(tune_sample, count),
+                      "tuner_ms_default_on_sample": tune_default_ms, "tuner_ms_best_on_sample": tune_best_ms,
+                      "relative_diff_vs_default": tuned_diff}}
 
 
 def profile_arm(args):

@@ -217,6 +217,10 @@ typedef struct {
   int64_t panel_bytes;        /* its packed operator: bytes streamed per pass of 64 right-hand sides */
   int64_t panel_items;        /* its work items per pass */
   int64_t panel_mma_flops;    /* its tensor-core flops per pass (2 * M * N * K of every MMA) */
+  int64_t pack_tile_bytes;    /* packing of the streaming program (uh_pack_params), as used */
+  int64_t pack_item_cost;
+  int64_t pack_chunk_cost;
+  int64_t pack_pool_unit;
 } uh_stats_t;
 
 int uh_stats(const uh_op* op, uh_stats_t* out);
@@ -239,6 +243,37 @@ typedef struct uh_batch uh_batch;
  * must number at most 2^31 - 1.
  */
 int uh_batch_create(const uh_desc* const* descs, int32_t count, int32_t precision, uh_batch** out);
+
+/*
+ * Packing and scheduling of the streaming program (not in the paper: how the products of
+ * Algorithm 6 are cut into work items and spread over the CTAs). 0 selects the default.
+ *  tile_bytes  largest tile of a work item, 4096 .. 65536 (default 65536)
+ *  item_cost   schedule cost of a work item beyond its bytes (default 4096)
+ *  chunk_cost  schedule cost of a chunk end (default 49152)
+ *  pool_unit   consecutive chunks of the dynamic pool share a ticket until their cost reaches this
+ *              (default 131072)
+ * Costs are in bytes streamed in the same time.
+ */
+typedef struct {
+  int32_t tile_bytes, item_cost, chunk_cost, pool_unit;
+} uh_pack_params;
+
+/* uh_batch_create with packing parameters (NULL: the defaults). */
+int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t precision, const uh_pack_params* params,
+                       uh_batch** out);
+
+/*
+ * Autotuner of the batched product: packs an evenly spaced sample of `sample` of the operators
+ * (all of them for sample <= 0 or >= count) with candidate parameters, times `reps` back-to-back
+ * products of each on `stream` (CUDA events, after 3 warm-up products; zero vectors), and returns
+ * the fastest parameters in *best: one pass of coordinate descent over tile_bytes {16, 32, 64 KB},
+ * item_cost {1, 4, 16 KB}, chunk_cost {12, 48, 192 KB} and pool_unit {32, 128, 512 KB} from the
+ * defaults, a change kept when it is at least 1% faster. *default_ms / *best_ms (optional): the
+ * mean product time with the defaults / with *best. Allocates and frees its own batches and
+ * vectors; blocks until done. Pass *best to uh_batch_create_ex for the whole set.
+ */
+int uh_batch_tune(const uh_desc* const* descs, int32_t count, int32_t precision, int32_t sample, int32_t reps,
+                  uh_pack_params* best, double* best_ms, double* default_ms, void* stream);
 int uh_batch_destroy(uh_batch* batch);
 
 /* offsets[0..count]: operator k's points are positions [offsets[k], offsets[k+1]) of the batch

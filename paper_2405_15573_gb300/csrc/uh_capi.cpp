@@ -924,6 +924,13 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   o->st.device_bytes = packed.device_bytes;
   o->st.n_launches = packed.n_launches;
   o->st.n_items = packed.n_items;
+  {
+    const uh::PackParams d;
+    o->st.pack_tile_bytes = d.tile_bytes;
+    o->st.pack_item_cost = d.item_cost;
+    o->st.pack_chunk_cost = d.chunk_cost;
+    o->st.pack_pool_unit = d.pool_unit;
+  }
   if (mm_mode >= 0) {
     int pn = 0;
     if ((rc = panel_ncta(&pn)) ||
@@ -1118,8 +1125,24 @@ int h_stats(const h_op* op, uh_stats_t* out) {
 }
 
 int uh_batch_create(const uh_desc* const* descs, int32_t count, int32_t precision, uh_batch** out) {
+  return uh_batch_create_ex(descs, count, precision, nullptr, out);
+}
+
+int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t precision, const uh_pack_params* params,
+                       uh_batch** out) {
   g_err.clear();
   if (!descs || !out) return fail(UH_EINVAL, "null argument");
+  uh::PackParams pp;
+  if (params) {
+    if (params->tile_bytes) pp.tile_bytes = params->tile_bytes;
+    if (params->item_cost) pp.item_cost = params->item_cost;
+    if (params->chunk_cost) pp.chunk_cost = params->chunk_cost;
+    if (params->pool_unit) pp.pool_unit = params->pool_unit;
+    if (pp.tile_bytes < 4096 || pp.tile_bytes > uh::kTileBytes || pp.item_cost < 0 || pp.chunk_cost < 0 ||
+        pp.pool_unit < 0)
+      return fail(UH_EINVAL, "pack parameters: tile_bytes %lld (4096..%d), costs >= 0", (long long)pp.tile_bytes,
+                  uh::kTileBytes);
+  }
   *out = nullptr;
   if (count < 1) return fail(UH_EINVAL, "count = %d", count);
   int rc;
@@ -1138,7 +1161,7 @@ int uh_batch_create(const uh_desc* const* descs, int32_t count, int32_t precisio
   const bool c128 = precision == UH_PREC_C128;
   int ncta = g_pack_only_ncta, device = 0;
   if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
-  ProgramBuilder P(c128, total, ncta);
+  ProgramBuilder P(c128, total, ncta, pp);
   const int64_t A = P.align();
   P.set_permutation(total);
   // The batch as one operator on the concatenated vectors: position offsets[k] + i of the
@@ -1208,8 +1231,96 @@ int uh_batch_create(const uh_desc* const* descs, int32_t count, int32_t precisio
   sum.n_launches = packed.n_launches;
   sum.n_items = packed.n_items;
   sum.matmat_mode = -1;
+  sum.pack_tile_bytes = pp.tile_bytes;
+  sum.pack_item_cost = pp.item_cost;
+  sum.pack_chunk_cost = pp.chunk_cost;
+  sum.pack_pool_unit = pp.pool_unit;
   o->st = sum;
   *out = o;
+  return UH_OK;
+}
+
+int uh_batch_tune(const uh_desc* const* descs, int32_t count, int32_t precision, int32_t sample, int32_t reps,
+                  uh_pack_params* best, double* best_ms, double* default_ms, void* stream) {
+  g_err.clear();
+  if (!descs || !best || count < 1 || reps < 1) return fail(UH_EINVAL, "uh_batch_tune: invalid argument");
+  // an evenly spaced sample of the operators
+  std::vector<const uh_desc*> sub;
+  const int32_t ns = sample > 0 && sample < count ? sample : count;
+  for (int32_t i = 0; i < ns; ++i) sub.push_back(descs[static_cast<int64_t>(i) * count / ns]);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void *x = nullptr, *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  int rc = UH_OK;
+  int64_t cap = 0;
+  // Mean time of `reps` back-to-back products of the sample packed with p (ms), or < 0 on error.
+  auto timed = [&](const uh_pack_params& p, double* ms) -> int {
+    uh_batch* b = nullptr;
+    int r = uh_batch_create_ex(sub.data(), ns, precision, &p, &b);
+    if (r) return r;
+    const int64_t need = b->n * (b->c128 ? 16 : 8);
+    if (need > cap) {
+      if (x) cudaFree(x);
+      if (y) cudaFree(y);
+      x = y = nullptr;
+      if (cudaMalloc(&x, need) != cudaSuccess || cudaMalloc(&y, need) != cudaSuccess ||
+          cudaMemsetAsync(x, 0, need, st) != cudaSuccess) {
+        uh_batch_destroy(b);
+        return fail(UH_ENOMEM, "uh_batch_tune: vectors of %lld bytes", (long long)need);
+      }
+      cap = need;
+    }
+    for (int i = 0; i < 3 && !r; ++i) r = uh_batch_matvec(b, x, y, stream);
+    if (!r && cudaEventRecord(e0, st) != cudaSuccess) r = fail(UH_ECUDA, "event");
+    for (int i = 0; i < reps && !r; ++i) r = uh_batch_matvec(b, x, y, stream);
+    if (!r && cudaEventRecord(e1, st) != cudaSuccess) r = fail(UH_ECUDA, "event");
+    float t = 0.0f;
+    if (!r && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+      r = fail(UH_ECUDA, "event timing");
+    if (!r) r = uh_batch_check(b, stream);
+    uh_batch_destroy(b);
+    *ms = t / reps;
+    return r;
+  };
+  uh_pack_params cur{};  // zeros: the defaults
+  uh::PackParams d;
+  cur.tile_bytes = static_cast<int32_t>(d.tile_bytes);
+  cur.item_cost = static_cast<int32_t>(d.item_cost);
+  cur.chunk_cost = static_cast<int32_t>(d.chunk_cost);
+  cur.pool_unit = static_cast<int32_t>(d.pool_unit);
+  double cur_ms = 0.0;
+  rc = timed(cur, &cur_ms);
+  if (default_ms) *default_ms = cur_ms;
+  // coordinate descent over the knobs, one pass; a change is kept if at least 1% faster
+  const int32_t tiles[] = {16384, 32768, 65536}, items[] = {1024, 4096, 16384}, chunks[] = {12288, 49152, 196608},
+                pools[] = {32768, 131072, 524288};
+  int32_t* knob[] = {&cur.tile_bytes, &cur.item_cost, &cur.chunk_cost, &cur.pool_unit};
+  const int32_t* vals[] = {tiles, items, chunks, pools};
+  for (int k = 0; k < 4 && !rc; ++k) {
+    const int32_t keep = *knob[k];
+    int32_t pick = keep;
+    for (int v = 0; v < 3 && !rc; ++v) {
+      if (vals[k][v] == keep) continue;
+      *knob[k] = vals[k][v];
+      double ms = 0.0;
+      rc = timed(cur, &ms);
+      if (!rc && ms < 0.99 * cur_ms) {
+        cur_ms = ms;
+        pick = vals[k][v];
+      }
+      *knob[k] = keep;
+    }
+    *knob[k] = pick;
+  }
+  if (x) cudaFree(x);
+  if (y) cudaFree(y);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  *best = cur;
+  if (best_ms) *best_ms = cur_ms;
   return UH_OK;
 }
 
@@ -1244,10 +1355,15 @@ int uh_batch_stats(const uh_batch* batch, uh_stats_t* out) {
 }
 
 int uh_batch_pack_check(const uh_desc* const* descs, int32_t count, int32_t precision, int32_t ncta) {
+  return uh_batch_pack_check_ex(descs, count, precision, nullptr, ncta);
+}
+
+int uh_batch_pack_check_ex(const uh_desc* const* descs, int32_t count, int32_t precision,
+                           const uh_pack_params* params, int32_t ncta) {
   if (ncta < 1) return fail(UH_EINVAL, "ncta = %d", ncta);
   g_pack_only_ncta = ncta;
   uh_batch* o = nullptr;
-  const int rc = uh_batch_create(descs, count, precision, &o);
+  const int rc = uh_batch_create_ex(descs, count, precision, params, &o);
   g_pack_only_ncta = 0;
   return rc;
 }

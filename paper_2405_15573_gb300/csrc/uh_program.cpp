@@ -8,8 +8,8 @@
 
 namespace uh {
 
-ProgramBuilder::ProgramBuilder(bool c128, int64_t n, int ncta)
-    : c128_(c128), n_(n), ncta_(ncta), A_(c128 ? 1 : 2), eb_(c128 ? 16 : 8) {}
+ProgramBuilder::ProgramBuilder(bool c128, int64_t n, int ncta, const PackParams& params)
+    : c128_(c128), n_(n), ncta_(ncta), prm_(params), A_(c128 ? 1 : 2), eb_(c128 ? 16 : 8) {}
 
 int ProgramBuilder::add_chunk(int kind, int64_t dst, int h, int group, int counter) {
   OutChunk c{};
@@ -31,14 +31,11 @@ int ProgramBuilder::add_chunk(int kind, int64_t dst, int h, int group, int count
 }
 
 namespace {
-// Scheduling costs of an item and of a chunk end, in bytes streamed in the same time (GB300
-// traces: a CTA streams ~45 GB/s; consumers spend ~0.1 us of fixed cost per item beyond the
-// streaming and ~1 us per chunk end).
-constexpr int64_t kItemCost = 4096;
-constexpr int64_t kChunkCost = 49152;
-// Consecutive pool chunks are handed out by one ticket until their cost reaches this (a ticket
-// costs the producer about 2 us of latency, hidden only behind enough staged work).
-constexpr int64_t kPoolUnitCost = 131072;
+// The default scheduling costs (PackParams) of an item and of a chunk end are bytes streamed in
+// the same time (GB300 traces: a CTA streams ~45 GB/s; consumers spend ~0.1 us of fixed cost per
+// item beyond the streaming and ~1 us per chunk end); consecutive pool chunks share a ticket up
+// to pool_unit (a ticket costs the producer about 2 us of latency, hidden only behind enough
+// staged work).
 int counter_of_source(int src) {
   return src == kSrcXp ? kCounterPermute : src == kSrcZ1 ? kCounterForward : src == kSrcZ2 ? kCounterCoupling : -1;
 }
@@ -48,7 +45,7 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
   const int h = chunks[chunk].h;
   const int64_t hp = std::max<int64_t>(A_, round_up(h, A_));
   // an item's tile (hp x ncols) and its inputs (ncols) share one stage buffer
-  int64_t maxcols = std::min<int64_t>(kStreamMaxCols, std::min<int64_t>(kTileBytes / (hp * eb_), kStageBytes / ((hp + 1) * eb_)));
+  int64_t maxcols = std::min<int64_t>(kStreamMaxCols, std::min<int64_t>(prm_.tile_bytes / (hp * eb_), kStageBytes / ((hp + 1) * eb_)));
   maxcols = maxcols / A_ * A_;
   auto& out = chunk_items_[chunk];
   WorkItem cur{};
@@ -63,7 +60,7 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
   auto close_item = [&]() {
     if (!open) return;
     out.push_back(cur);
-    bytes_[chunk] += static_cast<int64_t>(cur.ncols) * (hp + 1) * eb_ + kItemCost;
+    bytes_[chunk] += static_cast<int64_t>(cur.ncols) * (hp + 1) * eb_ + prm_.item_cost;
     tile_bytes_total += static_cast<int64_t>(cur.ncols) * hp * eb_;
     input_bytes_total += static_cast<int64_t>(cur.ncols) * eb_;
     open = false;
@@ -150,7 +147,7 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
   }
   out.front().flags |= kItemFirst;
   out.back().flags |= kItemLast;
-  bytes_[chunk] += kChunkCost;
+  bytes_[chunk] += prm_.chunk_cost;
 }
 
 bool ProgramBuilder::covered_by_cta(int reader, const std::vector<int>& list, int base_pos) const {
@@ -256,7 +253,7 @@ const char* ProgramBuilder::finalize() {
     PoolRange r{};
     r.begin = static_cast<int32_t>(items.size());
     int64_t cost = 0;
-    while (k < pool_order.size() && cost < kPoolUnitCost) {
+    while (k < pool_order.size() && cost < prm_.pool_unit) {
       const int c = pool_order[k++];
       pool_pos_[c] = static_cast<int>(pool.size());
       cost += bytes_[c];

@@ -42,9 +42,19 @@ enum Group { kGroupPermute = 0, kGroupForward = 1, kGroupNearA = 2, kGroupCoupli
              kGroupBackward = 5, kNumGroups = 6 };
 constexpr int kFirstPoolGroup = kGroupNearB;
 
+// Packing and scheduling parameters (the defaults were chosen by sweeps on the N = 32768 sphere):
+// the largest tile of an item, the schedule's cost of an item and of a chunk end in bytes
+// streamed in the same time, and the cost that consecutive pool chunks share a ticket up to.
+struct PackParams {
+  int64_t tile_bytes = kTileBytes;
+  int64_t item_cost = 4096;
+  int64_t chunk_cost = 49152;
+  int64_t pool_unit = 131072;
+};
+
 class ProgramBuilder {
  public:
-  ProgramBuilder(bool c128, int64_t n, int ncta);
+  ProgramBuilder(bool c128, int64_t n, int ncta, const PackParams& params = PackParams());
 
   int64_t align() const { return A_; }
   static int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -96,6 +106,7 @@ class ProgramBuilder {
   bool c128_;
   int64_t n_;
   int ncta_;
+  PackParams prm_;
   int64_t A_;   // elements per 16 bytes
   int eb_;      // bytes per element
   std::vector<int> group_, base_of_, cta_of_, pool_pos_;

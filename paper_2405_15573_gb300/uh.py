@@ -64,7 +64,16 @@ class Stats(C.Structure):
                 ("algo_bytes_matvec", _i64), ("device_bytes", _i64), ("packed_bytes", _i64),
                 ("n_launches", _i32), ("n_items", _i64),
                 ("matmat_mode", _i32), ("panel_bytes", _i64), ("panel_items", _i64),
-                ("panel_mma_flops", _i64)]
+                ("panel_mma_flops", _i64), ("pack_tile_bytes", _i64), ("pack_item_cost", _i64),
+                ("pack_chunk_cost", _i64), ("pack_pool_unit", _i64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PackParams(C.Structure):
+    """uh_pack_params: packing and scheduling of the streaming program (0 = default)."""
+    _fields_ = [("tile_bytes", _i32), ("item_cost", _i32), ("chunk_cost", _i32), ("pool_unit", _i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,12 +103,16 @@ for _name, _args in [
     ("uh_matvec_mixed", [_p, _p, _p, _p]),
     ("uh_block_apply_noalloc", [_i64, _i64, _i32, _i32, _p, _i64, _p, _i64, _p, _i64, _p, _p, _i32, _p]),
     ("uh_batch_create", [C.POINTER(C.POINTER(UHDesc)), _i32, _i32, C.POINTER(_p)]),
+    ("uh_batch_create_ex", [C.POINTER(C.POINTER(UHDesc)), _i32, _i32, C.POINTER(PackParams), C.POINTER(_p)]),
+    ("uh_batch_tune", [C.POINTER(C.POINTER(UHDesc)), _i32, _i32, _i32, _i32, C.POINTER(PackParams),
+                       C.POINTER(C.c_double), C.POINTER(C.c_double), _p]),
     ("uh_batch_destroy", [_p]),
     ("uh_batch_offsets", [_p, C.POINTER(_i64)]),
     ("uh_batch_matvec", [_p, _p, _p, _p]),
     ("uh_batch_check", [_p, _p]),
     ("uh_batch_stats", [_p, C.POINTER(Stats)]),
     ("uh_batch_pack_check", [C.POINTER(C.POINTER(UHDesc)), _i32, _i32, _i32]),
+    ("uh_batch_pack_check_ex", [C.POINTER(C.POINTER(UHDesc)), _i32, _i32, C.POINTER(PackParams), _i32]),
     ("uh_server_create", [_i32, _i64, _i32, C.POINTER(_p)]),
     ("uh_server_destroy", [_p]),
     ("uh_solve_submit", [_p, _p, _p, C.c_double, _i32, _i32, C.POINTER(C.c_uint64)]),
@@ -387,13 +400,14 @@ class UHBatch:
     """Many independent UH operators applied in one launch (uh.h, uh_batch_*). x and y of
     matvec() hold the operators' vectors back to back: operator k at offsets[k]:offsets[k+1]."""
 
-    def __init__(self, descs, precision: str = "c64"):
+    def __init__(self, descs, precision: str = "c64", params: "PackParams | None" = None):
         self.precision = precision
         self.c128 = precision == "c128"
         self.count = len(descs)
         h = _p()
-        check(lib.uh_batch_create(_desc_array(descs), self.count, _PREC[precision], C.byref(h)),
-              "uh_batch_create")
+        check(lib.uh_batch_create_ex(_desc_array(descs), self.count, _PREC[precision],
+                                     C.byref(params) if params is not None else None, C.byref(h)),
+              "uh_batch_create_ex")
         self.handle = h
         off = (_i64 * (self.count + 1))()
         check(lib.uh_batch_offsets(self.handle, off), "uh_batch_offsets")
@@ -401,9 +415,18 @@ class UHBatch:
         self.n = int(self.offsets[-1])
 
     @classmethod
-    def from_arrays(cls, arrays_list, precision: str = "c64"):
+    def from_arrays(cls, arrays_list, precision: str = "c64", params: "PackParams | None" = None):
         built = [uh_desc_from_arrays(a) for a in arrays_list]
-        return cls([d for d, _ in built], precision)
+        return cls([d for d, _ in built], precision, params)
+
+    @staticmethod
+    def tune(descs, precision: str = "c64", sample: int = 0, reps: int = 20, stream=None):
+        """uh_batch_tune: (best PackParams, best ms, default ms) for this set of operators."""
+        best = PackParams()
+        bms, dms = C.c_double(0.0), C.c_double(0.0)
+        check(lib.uh_batch_tune(_desc_array(descs), len(descs), _PREC[precision], sample, reps, C.byref(best),
+                                C.byref(bms), C.byref(dms), _stream_handle(stream)), "uh_batch_tune")
+        return best, bms.value, dms.value
 
     def stats(self) -> dict:
         s = Stats()

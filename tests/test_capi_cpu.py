@@ -161,6 +161,30 @@ def test_batch_packing_self_check_passes(uh, prec, ncta):
     assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()
 
 
+# every value the autotuner (uh_batch_tune) can choose, one knob at a time, and all at extremes
+TUNER_PARAMS = [(16384, 0, 0, 0), (32768, 0, 0, 0), (0, 1024, 0, 0), (0, 16384, 0, 0), (0, 0, 12288, 0),
+                (0, 0, 196608, 0), (0, 0, 0, 32768), (0, 0, 0, 524288), (16384, 1024, 12288, 32768),
+                (16384, 16384, 196608, 524288)]
+
+
+@pytest.mark.parametrize("params", TUNER_PARAMS)
+@pytest.mark.parametrize("ncta", [152, 7])
+def test_batch_packing_with_tuner_parameters(uh, params, ncta):
+    built = [uh.uh_desc_from_arrays(a) for a in _batch_arrays()]
+    arr = uh._desc_array([d for d, _ in built])
+    pp = uh.PackParams(*params)
+    rc = uh.lib.uh_batch_pack_check_ex(arr, len(built), 1, pp, ncta)
+    assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()
+
+
+def test_batch_rejects_bad_pack_parameters(uh):
+    built = [uh.uh_desc_from_arrays(a) for a in _batch_arrays()]
+    arr = uh._desc_array([d for d, _ in built])
+    for bad in [(1024, 0, 0, 0), (131072, 0, 0, 0), (0, -1, 0, 0)]:
+        rc = uh.lib.uh_batch_pack_check_ex(arr, len(built), 1, uh.PackParams(*bad), 7)
+        assert rc == uh.UH_EINVAL and "pack parameters" in uh.lib.uh_last_error().decode()
+
+
 def test_batch_rejects_bad_operator_and_precision(uh):
     arrays = _batch_arrays()
     bad = dict(arrays[2])

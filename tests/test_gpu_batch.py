@@ -56,3 +56,53 @@ def test_batch_matches_oracle_and_single(U, prec):
     assert st["E_D"] == sum(op.counts()["E_D"] for op in ops)
     assert st["n_launches"] == 1
     batch.close()
+
+
+TUNER_PARAMS = [(16384, 0, 0, 0), (32768, 0, 0, 0), (0, 1024, 0, 0), (0, 16384, 0, 0), (0, 0, 12288, 0),
+                (0, 0, 196608, 0), (0, 0, 0, 32768), (0, 0, 0, 524288), (16384, 16384, 196608, 524288)]
+
+
+@pytest.mark.parametrize("params", TUNER_PARAMS)
+def test_batch_with_every_tuner_choice(U, params):
+    """Every packing the autotuner can choose gives the same per-operator products (complex64)."""
+    import torch
+    ops = [oracle_ops(*c)[4] for c in CASES]
+    arrays = [uh_arrays(op) for op in ops]
+    batch = U.UHBatch.from_arrays(arrays, "c64", U.PackParams(*params))
+    st = batch.stats()
+    expect = [v if v else d for v, d in zip(params, (65536, 4096, 49152, 131072))]
+    assert [st["pack_tile_bytes"], st["pack_item_cost"], st["pack_chunk_cost"], st["pack_pool_unit"]] == expect
+    off = batch.offsets
+    xs = [I.complex_normal(op.tree.n, 10 + k) for k, op in enumerate(ops)]
+    x = torch.from_numpy(np.concatenate(xs)).to("cuda", torch.complex64)
+    y = batch.matvec(x)
+    batch.check()
+    yb = y.cpu().numpy().astype(np.complex128)
+    for k, op in enumerate(ops):
+        assert relerr(yb[off[k]:off[k + 1]], O.uh_matvec(op, xs[k])) <= TOL["c64"], k
+    batch.close()
+
+
+def test_autotuner_picks_a_candidate_and_stays_correct(U):
+    """uh_batch_tune times candidate packings of the set and returns one of them; the batch
+    created with its choice is as correct as the default one and no slower than it was timed."""
+    import torch
+    ops = [oracle_ops(*c)[4] for c in CASES]
+    arrays = [uh_arrays(op) for op in ops]
+    built = [U.uh_desc_from_arrays(a) for a in arrays]
+    descs = [d for d, _ in built]
+    best, best_ms, default_ms = U.UHBatch.tune(descs, "c64", sample=0, reps=10)
+    assert best.tile_bytes in (16384, 32768, 65536)
+    assert best.item_cost in (1024, 4096, 16384)
+    assert best.chunk_cost in (12288, 49152, 196608)
+    assert best.pool_unit in (32768, 131072, 524288)
+    assert 0 < best_ms <= default_ms
+    batch = U.UHBatch(descs, "c64", best)
+    off = batch.offsets
+    xs = [I.complex_normal(op.tree.n, 30 + k) for k, op in enumerate(ops)]
+    y = batch.matvec(torch.from_numpy(np.concatenate(xs)).to("cuda", torch.complex64))
+    batch.check()
+    yb = y.cpu().numpy().astype(np.complex128)
+    for k, op in enumerate(ops):
+        assert relerr(yb[off[k]:off[k + 1]], O.uh_matvec(op, xs[k])) <= TOL["c64"], k
+    batch.close()
