@@ -29,7 +29,12 @@ Readings where the paper is silent or garbled (each also listed in the design no
      sigma_{l+1}(X_tau) <= eps * sigma_1(X_tau) (relative spectral, Remark 6.1);
   R6 the second inner loop of Algorithm 6 runs over sigma in row(tau);
   R7 the UH operator is the general (non-symmetric) form, with separate row and column bases and
-     a dense coefficient matrix S_b = S_{X,b} S_{Y,b}^* per admissible block.
+     a dense coefficient matrix S_b = S_{X,b} S_{Y,b}^* per admissible block;
+  R11 the factored storage option (Section 4.2 keeps S_{X,b}, S_{Y,b}, k_b (l_tau + l_sigma)
+     elements): the pair of Algorithm 2 has the inner rank of the fine block, so it is first
+     recompressed at eps like an admissible block (Section 2.3: QR of both factors, SVD of the
+     product of the triangles, keep s_j > eps * s_1), and a block keeps the factored form only
+     where k_b (l_tau + l_sigma) < l_tau l_sigma.
 """
 from __future__ import annotations
 
@@ -375,24 +380,37 @@ class UHMatrix:
     Also keeps, per cluster, all singular values of the stacked matrix X_tau (rows) or Y_sigma
     (columns) and the chosen rank, which the error bounds of Section 5 are written in."""
 
-    def __init__(self, tree, adm, dense, U, V, S, near, row_sv, col_sv):
+    def __init__(self, tree, adm, dense, U, V, S, near, row_sv, col_sv, F=None, pairs=None):
         self.tree = tree
         self.adm = adm
         self.dense = dense
         self.U = U  # {tau: (|tau| x l_tau)}
         self.V = V  # {sigma: (|sigma| x l_sigma)}
-        self.S = S  # {(tau, sigma): (l_tau x l_sigma)}
+        self.S = S  # {(tau, sigma): (l_tau x l_sigma)}, the blocks stored dense
         self.near = near  # {(tau, sigma): (|tau| x |sigma|)}
         self.row_sv = row_sv  # {tau: all singular values of X_tau}
         self.col_sv = col_sv  # {sigma: all singular values of Y_sigma}
+        # blocks stored factored (Section 4.2): {(tau, sigma): (S_X (l_tau x k_b), S_Y (l_sigma x k_b))}
+        self.F = F if F is not None else {}
+        # the coefficient pairs (S_X, S_Y) of Algorithm 2 (inner rank k_b of the fine block)
+        self.pairs = pairs if pairs is not None else {}
 
     def counts(self) -> dict:
-        """Stored element counts E_V, E_U, E_S, E_D."""
+        """Stored element counts E_V, E_U, E_S (dense l_tau l_sigma, factored k_b (l_tau + l_sigma)),
+        E_D, and K = sum of the inner ranks k_b of the factored blocks."""
         return dict(
             E_U=sum(u.size for u in self.U.values()),
             E_V=sum(v.size for v in self.V.values()),
-            E_S=sum(s.size for s in self.S.values()),
-            E_D=sum(d.size for d in self.near.values()))
+            E_S=sum(s.size for s in self.S.values()) + sum(x.size + y.size for x, y in self.F.values()),
+            E_D=sum(d.size for d in self.near.values()),
+            K=sum(x.shape[1] for x, _ in self.F.values()))
+
+    def coupling(self, b) -> np.ndarray:
+        """S_b as a dense l_tau x l_sigma matrix, whichever form it is stored in."""
+        if b in self.F:
+            X, Y = self.F[b]
+            return X @ Y.conj().T
+        return self.S[b]
 
     def ranks(self):
         return ({t: u.shape[1] for t, u in self.U.items()},
@@ -452,23 +470,54 @@ def uniform_compression(h: HMatrix, eps: float) -> UHMatrix:
         for t, P in zip(col[s], parts):
             SY[(t, s)] = P
     S = {b: SX[b] @ SY[b].conj().T for b in h.adm}
-    return UHMatrix(h.tree, h.adm, h.dense, U, V, S, dict(h.near), row_sv, col_sv)
+    pairs = {b: (SX[b], SY[b]) for b in h.adm}
+    return UHMatrix(h.tree, h.adm, h.dense, U, V, S, dict(h.near), row_sv, col_sv, pairs=pairs)
+
+
+def factor_coupling(uh: UHMatrix, eps: float, force: bool = False) -> UHMatrix:
+    """Factored coefficient storage S_b = S_{X,b} S_{Y,b}^* (Section 4.2), reading R11.
+
+    For each admissible block, the pair (S_X, S_Y) of Algorithm 2 (or, when the operator carries
+    no pairs, (S_b, I)) is recompressed at eps as in Section 2.3 (recompress: QR of both factors,
+    SVD of R_X R_Y^*, keep s_j > eps * s_1), giving S_X = Q_X W_k diag(s_1..s_k) and
+    S_Y = Q_Y Z_k. The block is stored factored when k_b (l_tau + l_sigma) < l_tau l_sigma (always
+    with force), else its dense S_b is kept unchanged. Bases and dense blocks are shared."""
+    S, F = {}, {}
+    for b, Sb in uh.S.items():
+        lt, ls = Sb.shape
+        if b in uh.pairs:
+            X, Y = uh.pairs[b]
+        else:
+            X, Y = Sb, np.eye(ls, dtype=np.complex128)
+        Ub, sb, Vb = recompress(X, np.conj(Y), eps)
+        k = len(sb)
+        if force or k * (lt + ls) < lt * ls:
+            F[b] = (Ub * sb[None, :], Vb)
+        else:
+            S[b] = Sb
+    return UHMatrix(uh.tree, uh.adm, uh.dense, uh.U, uh.V, S, uh.near, uh.row_sv, uh.col_sv,
+                    F=F, pairs=uh.pairs)
 
 
 def uh_matvec(uh: UHMatrix, x: np.ndarray) -> np.ndarray:
     """Algorithm 6 run on one thread (reading R6), x and result in original ordering.
 
-    Phase 1: xhat_sigma = V_sigma^* x|_sigma. Coupling: yhat_tau = sum_{sigma in row(tau)}
-    S_b xhat_sigma. Phase 2: w|_tau += U_tau yhat_tau. Then w|_tau += A|_b x|_sigma for dense b."""
+    Phase 1: xhat_sigma = V_sigma^* x|_sigma, and for a factored block t_b = S_{Y,b}^* xhat_sigma.
+    Coupling: yhat_tau = sum_{sigma in row(tau)} S_b xhat_sigma (dense S_b) or S_{X,b} t_b
+    (factored). Phase 2: w|_tau += U_tau yhat_tau. Then w|_tau += A|_b x|_sigma for dense b."""
     tree = uh.tree
     xp = x[tree.perm]
     xhat = {}
     for s, V in uh.V.items():
         b = tree.begin[s]
         xhat[s] = V.conj().T @ xp[b:b + tree.size[s]]
+    tb = {b: Y.conj().T @ xhat[b[1]] for b, (_, Y) in uh.F.items()}
     yhat = {}
     for (t, s), S in uh.S.items():
         contrib = S @ xhat[s]
+        yhat[t] = contrib if t not in yhat else yhat[t] + contrib
+    for (t, s), (X, _) in uh.F.items():
+        contrib = X @ tb[(t, s)]
         yhat[t] = contrib if t not in yhat else yhat[t] + contrib
     yp = np.zeros(xp.shape, dtype=np.complex128)
     for t, U in uh.U.items():
@@ -488,6 +537,8 @@ def uh_to_dense(uh: UHMatrix) -> np.ndarray:
     A = np.zeros((tree.n, tree.n), dtype=np.complex128)
     for (t, s), S in uh.S.items():
         A[np.ix_(tree.indices(t), tree.indices(s))] = uh.U[t] @ S @ uh.V[s].conj().T
+    for (t, s), (X, Y) in uh.F.items():
+        A[np.ix_(tree.indices(t), tree.indices(s))] = (uh.U[t] @ X) @ (uh.V[s] @ Y).conj().T
     for (t, s), D in uh.near.items():
         A[np.ix_(tree.indices(t), tree.indices(s))] = D
     return A

@@ -524,3 +524,98 @@ def test_frobenius_tail_equals_explicit_projection_errors(ops512):
         tot += np.linalg.norm(Bs - V @ (V.conj().T @ Bs)) ** 2
     assert tot > 0
     assert abs(O.frobenius_tail(uh) - tot) <= 1e-8 * tot
+
+
+# ---------------------------------------------------------------- factored coefficients (Section 4.2)
+
+
+def test_factored_truncation_is_eckart_young(ops512):
+    """Reading R11: each factored block keeps the singular values of S_b above eps * s_1 (checked
+    both ways against a plain SVD of the dense S_b), and its error is exactly the first dropped
+    singular value (Eckart-Young), so a wrong rank, a lost diag(s) or a factor left unconjugated
+    fails."""
+    *_, uh, _ = ops512
+    for eps in (1e-2, 1e-3):
+        f = O.factor_coupling(uh, eps, force=True)
+        assert not f.S and set(f.F) == set(uh.S)
+        nontrivial = 0
+        for b, (X, Y) in f.F.items():
+            Sb = uh.S[b]
+            s = np.linalg.svd(Sb, compute_uv=False)
+            k = X.shape[1]
+            assert Y.shape == (Sb.shape[1], k) and X.shape == (Sb.shape[0], k)
+            assert k >= 1 and s[k - 1] > eps * s[0]
+            nxt = s[k] if k < len(s) else 0.0
+            assert nxt <= eps * s[0]
+            err = np.linalg.norm(Sb - X @ Y.conj().T, 2)
+            assert abs(err - nxt) <= 1e-9 * s[0]
+            nontrivial += nxt > 0
+        assert nontrivial > len(f.F) // 2
+
+
+def test_factored_storage_rule_both_ways(ops512):
+    """A block is stored factored exactly when k_b (l_tau + l_sigma) < l_tau l_sigma, with k_b the
+    rank rule of a plain SVD of S_b; E_S counts the elements of both forms."""
+    *_, uh, _ = ops512
+    eps = 3e-4  # between the bases' eps and the ranks of these small blocks: both forms occur
+    f = O.factor_coupling(uh, eps)
+    es = 0
+    for b, Sb in uh.S.items():
+        s = np.linalg.svd(Sb, compute_uv=False)
+        k = int(np.sum(s > eps * s[0]))
+        lt, ls = Sb.shape
+        small = k * (lt + ls) < lt * ls
+        assert (b in f.F) == small and (b in f.S) == (not small)
+        es += k * (lt + ls) if small else lt * ls
+    assert f.F and f.S
+    c = f.counts()
+    assert c["E_S"] == es and c["K"] == sum(X.shape[1] for X, _ in f.F.values())
+
+
+def test_factored_product_exact_without_truncation(ops512):
+    """With eps = 0 every nonzero singular value is kept: the factored product (t_b = S_Y^* xhat,
+    yhat += S_X t_b) equals the dense-S product of Algorithm 6 up to rounding."""
+    *_, uh, _ = ops512
+    f = O.factor_coupling(uh, 0.0, force=True)
+    X = I.complex_normal(512, 11, nrhs=2)
+    y0 = O.uh_matvec(uh, X)
+    assert np.linalg.norm(O.uh_matvec(f, X) - y0) <= 1e-13 * np.linalg.norm(y0)
+    assert np.allclose(O.uh_to_dense(f), O.uh_to_dense(uh), rtol=0, atol=1e-13)
+
+
+def test_factored_product_error_within_dropped_values(ops512):
+    """|y_f - y| <= sum_b s_{k_b+1}(S_b) |x_sigma| (the bases are orthonormal), and the factored
+    product agrees with its own block assembly."""
+    _, tree, _, _, uh, _ = ops512
+    eps = 1e-3
+    f = O.factor_coupling(uh, eps, force=True)
+    x = I.complex_normal(512, 12)
+    d = O.uh_matvec(f, x) - O.uh_matvec(uh, x)
+    xp = x[tree.perm]
+    bound = 0.0
+    for (t, s), (Xf, _) in f.F.items():
+        sv = np.linalg.svd(uh.S[(t, s)], compute_uv=False)
+        k = Xf.shape[1]
+        if k < len(sv):
+            bound += sv[k] * np.linalg.norm(xp[tree.begin[s]:tree.begin[s] + tree.size[s]])
+    assert 0 < np.linalg.norm(d) <= bound * (1 + 1e-9)
+    assert np.allclose(O.uh_matvec(f, x), O.uh_to_dense(f) @ x, rtol=0, atol=1e-13)
+
+
+def test_factored_rank_one_coupling_closed_form():
+    """A rank-one S_b = a c^* is stored as one column pair that reproduces it exactly, and a zero
+    S_b as an empty pair (k_b = 0)."""
+    a = np.array([1.0 + 2.0j, -0.5j, 3.0])
+    c = np.array([2.0, 1.0 - 1.0j])
+    Sb = np.outer(a, c.conj())
+    tree = O.ClusterTree(I.fibonacci_sphere(8), 8)
+    U = {0: np.eye(8, 3, dtype=np.complex128)}
+    V = {0: np.eye(8, 2, dtype=np.complex128)}
+    uh = O.UHMatrix(tree, [(0, 0)], [], U, V, {(0, 0): Sb}, {}, {}, {})
+    f = O.factor_coupling(uh, 1e-12)
+    X, Y = f.F[(0, 0)]
+    assert X.shape == (3, 1) and Y.shape == (2, 1)
+    assert np.allclose(X @ Y.conj().T, Sb, rtol=0, atol=1e-14)
+    assert abs(np.linalg.norm(X) - np.linalg.norm(a) * np.linalg.norm(c)) <= 1e-13
+    z = O.factor_coupling(O.UHMatrix(tree, [(0, 0)], [], U, V, {(0, 0): 0 * Sb}, {}, {}, {}), 1e-12)
+    assert z.F[(0, 0)][0].shape == (3, 0)
