@@ -333,6 +333,34 @@ class _MatmatStep:
         self.op.matmat(self.X, self.Y, mode=self.mode)
 
 
+def factored_figures(w, x, y_dense, steps, peak, torch):
+    """The same workload with the coefficient matrices stored factored where smaller (Section
+    4.2; uhb_params.factored, built on the GPU): bytes and product time beside the dense-S form."""
+    from paper_2405_15573_gb300 import uh as U
+    t0 = time.time()
+    m = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca, device=True, factored=True)
+    build_s = time.time() - t0
+    op = m.uh_op("c64")
+    m.close()
+    st = op.stats()
+    y = torch.empty_like(x)
+    for _ in range(3):
+        op.matvec(x, y)
+    torch.cuda.synchronize()
+    ms = timed_back_to_back(op, x, y, steps, torch)
+    op.check()
+    gbs = st["algo_bytes_matvec"] / (ms * 1e-3) / 1e9
+    rel = float(torch.linalg.vector_norm(y - y_dense) / torch.linalg.vector_norm(y_dense))
+    out = {"matvec_per_s": 1e3 / ms, "ms_mean": ms, "steps": steps, "algo_bytes_per_matvec": st["algo_bytes_matvec"],
+           "packed_bytes": st["packed_bytes"], "E_S": st["E_S"], "n_factored": st["n_factored"],
+           "n_adm": st["n_adm"], "sum_factored_rank": st["sum_factored_rank"], "n_items": st["n_items"],
+           "GBps": gbs, "frac": gbs / peak, "build_s": build_s, "relerr_vs_dense_S": rel,
+           "note": "S_b = S_X S_Y^* where k (l_tau + l_sigma) < l_tau l_sigma after recompressing the pair at eps; "
+                   "t_b = S_Y^* xhat_sigma as its own phase group before the coupling"}
+    op.close()
+    return out
+
+
 def build_models(workloads):
     """Several operators built one after the other on the GPU (uhb_build_helmholtz_gpu)."""
     from paper_2405_15573_gb300 import uh as U
@@ -624,6 +652,7 @@ def gpu_arm(args):
     # log-uniform in [1024, 16384]), and a serving pool of 8 operators with N uniform in
     # [4096, 65536] at the six arrival rates.
     large_mm = None if args.no_matmat or args.quick else large_matmat_figures(torch, peak_bf16, 20)
+    factored = factored_figures(w, x, y, max(args.steps, 200), _peaks()[0], torch)
     batched = None if args.quick else batched_figures(32, 20)
     serving = None if args.no_serving else serving_figures(
         8, 65536 if not args.quick else 16384,
@@ -702,6 +731,9 @@ def gpu_arm(args):
                     "fp64_frac": (gbs_128 / 16 * 8 / 1e3) / fp64_tflops,
                     "peak_note": "uh_debug_dfma_rate: 8 independent DFMA chains per thread, 4 CTAs x 256 per SM"},
         "uh_matmat_large": large_mm,
+        "uh_factored": dict(factored, ms_dense=ms_uh, bytes_dense=st["algo_bytes_matvec"],
+                            speedup_vs_dense=ms_uh / factored["ms_mean"],
+                            bytes_ratio=factored["algo_bytes_per_matvec"] / st["algo_bytes_matvec"]),
         "batched": batched,
         "construction": {"gpu_s": build_s, "host_s": build_host_s, "speedup": build_host_s / build_s,
                          "gpu_stages_s": {k: build_info[k] for k in ("seconds_tree", "seconds_aca", "seconds_bases",

@@ -115,6 +115,15 @@ typedef struct {
  *  col bases  V_sigma = V_data + col_off[sigma], |sigma| x col_rank[sigma] column-major;
  *  coupling   S_b     = S_data + S_off[i], row_rank[tau] x col_rank[sigma] column-major, for the
  *             admissible block b = (adm_row[i], adm_col[i]);
+ *             or, where S_rank is not NULL and k = S_rank[i] >= 0, stored factored as
+ *             S_b = S_X,b S_Y,b^* (Section 4.2): S_X,b = S_data + S_off[i], row_rank[tau] x k
+ *             column-major, then S_Y,b = S_data + S_off[i] + row_rank[tau] * k, col_rank[sigma] x k
+ *             column-major; k lies in [0, min(row_rank[tau], col_rank[sigma])]. S_rank[i] = -1
+ *             (or S_rank NULL) is the dense form. The product then computes
+ *             t_b = S_Y,b^* xhat_sigma and adds S_X,b t_b to yhat_tau (Algorithm 6 with the
+ *             factored coefficients), streaming k (l_tau + l_sigma) elements instead of
+ *             l_tau l_sigma; the tensor-core uh_matmat assembles S_b from its factors when it
+ *             packs its operator;
  *  near field as in uh_dense_desc.
  * Ranks may be 0 (the block then contributes nothing). A cluster that is not the row cluster of
  * an admissible block may carry row_rank 0 and any offset (likewise for columns).
@@ -137,6 +146,7 @@ typedef struct {
   const void* S_data;
   int64_t S_len;
   uh_dense_desc dense;
+  const int32_t* S_rank;    /* [n_adm] inner rank k of a factored S_b, -1 = dense; NULL = all dense */
 } uh_desc;
 
 typedef struct uh_op uh_op;
@@ -203,12 +213,13 @@ typedef struct {
   int32_t precision;
   int32_t elem_bytes;         /* 16 (C128) or 8 (C64) */
   int64_t n_row_bases, n_col_bases, n_adm, n_dense;
-  int64_t E_U, E_V, E_S, E_D; /* stored complex element counts */
+  int64_t E_U, E_V, E_S, E_D; /* stored complex element counts (E_S: l_tau l_sigma per dense S_b,
+                                 k (l_tau + l_sigma) per factored one) */
   int64_t sum_row_rank, sum_col_rank;
   int32_t rank_min, rank_max; /* over all row and column bases with rank > 0 */
   double rank_mean;
   int32_t csp;                /* sparsity constant c_sp (Def. 2.5) */
-  int64_t algo_bytes_matvec;  /* elem_bytes*(E_U+E_V+E_S+E_D + 2n + 2(sum ranks)) */
+  int64_t algo_bytes_matvec;  /* elem_bytes*(E_U+E_V+E_S+E_D + 2n + 2(sum ranks) + 2 K) */
   int64_t device_bytes;       /* device memory held by the op (packed operator, indices, scratch) */
   int64_t packed_bytes;       /* bytes streamed per matvec: packed matrices + column indices */
   int32_t n_launches;         /* kernel launches per uh_matvec */
@@ -221,6 +232,8 @@ typedef struct {
   int64_t pack_item_cost;
   int64_t pack_chunk_cost;
   int64_t pack_pool_unit;
+  int64_t n_factored;         /* coupling matrices stored factored (uh_desc.S_rank >= 0) */
+  int64_t sum_factored_rank;  /* K: sum of their inner ranks k */
 } uh_stats_t;
 
 int uh_stats(const uh_op* op, uh_stats_t* out);

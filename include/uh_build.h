@@ -19,7 +19,8 @@
  *    > eps * sigma_1; the singular vectors come from a column-pivoted QR stopped once the
  *    remainder is below 1e-3 * eps * (largest column norm), followed by a one-sided Jacobi SVD
  *    of the small triangular factor (the rank-revealing alternative of Remark 4.2);
- *    S_b = (U_tau^* U_b Sigma_b)(V_sigma^* V_b)^*, the optimal coefficient of Section 4.1.
+ *    S_b = (U_tau^* U_b Sigma_b)(V_sigma^* V_b)^*, the optimal coefficient of Section 4.1, or
+ *    with params.factored that pair recompressed at eps and stored factored where smaller.
  * All arithmetic is complex128 on the host, parallel over blocks and clusters with OpenMP.
  *
  * The model owns every array its descriptors point to; they stay valid until uhb_free.
@@ -43,6 +44,10 @@ typedef struct {
   int32_t nthreads;   /* OpenMP threads; <= 0: the OpenMP default */
   int32_t strong;     /* 0: weak admissibility min(diam) <= eta dist (eq. (3.3));
                          1: strong admissibility max(diam) <= eta dist (eq. (3.2)) */
+  int32_t factored;   /* 0: every S_b dense; 1: the coefficient pair (U_tau^* U_b Sigma_b,
+                         V_sigma^* V_b) recompressed at eps (Section 2.3) and S_b stored factored,
+                         S_b = S_X,b S_Y,b^* (Section 4.2, uh_desc.S_rank), where its rank k gives
+                         k (l_tau + l_sigma) < l_tau l_sigma */
 } uhb_params;
 
 typedef struct {

@@ -222,6 +222,54 @@ struct LowRank {
   std::vector<double> s;      // singular values, descending
 };
 
+// Algebraic recompression (Section 2.3) of X Y^* (X m x k, Y nn x k): QR of both factors, SVD of
+// R1 R2^* by one-sided Jacobi, keep the singular values > tol * s_1. Returns U_b = Q1 W, Y_b = Q2 Z
+// and s with X Y^* ~ U_b diag(s) Y_b^*.
+LowRank recompress_pair(int m, int nn, int k, const cd* X, const cd* Y, double tol) {
+  LowRank out;
+  if (k == 0) return out;
+  std::vector<cd> Q1, R1, Q2, R2;
+  qr_thin(m, k, X, Q1, R1);
+  qr_thin(nn, k, Y, Q2, R2);
+  const int p1 = std::min(m, k), p2 = std::min(nn, k);
+  std::vector<cd> Mx(static_cast<size_t>(p1) * p2, 0.0);  // R1 R2^*
+  for (int b = 0; b < p2; ++b)
+    for (int q = 0; q < k; ++q) {
+      const cd w = std::conj(R2[static_cast<size_t>(q) * p2 + b]);
+      if (w == 0.0) continue;
+      for (int a = 0; a < p1; ++a) Mx[static_cast<size_t>(b) * p1 + a] += R1[static_cast<size_t>(q) * p1 + a] * w;
+    }
+  std::vector<cd> J(static_cast<size_t>(p2) * p2);
+  jacobi(p1, p2, Mx.data(), J.data());  // Mx J = W Sigma
+  std::vector<double> sv(p2);
+  for (int q = 0; q < p2; ++q) sv[q] = std::sqrt(colnorm2(p1, &Mx[static_cast<size_t>(q) * p1]));
+  std::vector<int> ord(p2);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sv[a] > sv[b]; });
+  if (sv[ord[0]] == 0.0) return out;
+  int keep = 0;
+  while (keep < p2 && sv[ord[keep]] > tol * sv[ord[0]]) ++keep;
+  out.k = keep;
+  out.s.resize(keep);
+  out.Ub.assign(static_cast<size_t>(m) * keep, 0.0);
+  out.Yb.assign(static_cast<size_t>(nn) * keep, 0.0);
+  for (int q = 0; q < keep; ++q) {
+    const int col = ord[q];
+    out.s[q] = sv[col];
+    // left vector w = Mx[:, col] / sigma; U_b = Q1 w
+    for (int a = 0; a < p1; ++a) {
+      const cd w = Mx[static_cast<size_t>(col) * p1 + a] / sv[col];
+      for (int t = 0; t < m; ++t) out.Ub[static_cast<size_t>(q) * m + t] += Q1[static_cast<size_t>(a) * m + t] * w;
+    }
+    // right vector = J[:, col]; Y_b = Q2 J[:, col]
+    for (int b = 0; b < p2; ++b) {
+      const cd w = J[static_cast<size_t>(col) * p2 + b];
+      for (int t = 0; t < nn; ++t) out.Yb[static_cast<size_t>(q) * nn + t] += Q2[static_cast<size_t>(b) * nn + t] * w;
+    }
+  }
+  return out;
+}
+
 // Partially pivoted ACA of block (rows, cols) followed by recompression (Section 2.3).
 LowRank aca_block(const Builder& B, const int64_t* rows, int m, const int64_t* cols, int nn, double tol) {
   std::vector<std::vector<cd>> us, vs;
@@ -275,55 +323,15 @@ LowRank aca_block(const Builder& B, const int64_t* rows, int m, const int64_t* c
     if (nxt < 0) break;
     i = nxt;
   }
-  LowRank out;
   const int k = static_cast<int>(us.size());
-  if (k == 0) return out;
-  // A ~ U V^T = X Y^* with X = U, Y = conj(V): QR both, SVD of R1 R2^*.
+  if (k == 0) return LowRank();
+  // A ~ U V^T = X Y^* with X = U, Y = conj(V).
   std::vector<cd> X(static_cast<size_t>(m) * k), Y(static_cast<size_t>(nn) * k);
   for (int q = 0; q < k; ++q) {
     std::copy(us[q].begin(), us[q].end(), &X[static_cast<size_t>(q) * m]);
     for (int t = 0; t < nn; ++t) Y[static_cast<size_t>(q) * nn + t] = std::conj(vs[q][t]);
   }
-  std::vector<cd> Q1, R1, Q2, R2;
-  qr_thin(m, k, X.data(), Q1, R1);
-  qr_thin(nn, k, Y.data(), Q2, R2);
-  const int p1 = std::min(m, k), p2 = std::min(nn, k);
-  std::vector<cd> Mx(static_cast<size_t>(p1) * p2, 0.0);  // R1 R2^*
-  for (int b = 0; b < p2; ++b)
-    for (int q = 0; q < k; ++q) {
-      const cd w = std::conj(R2[static_cast<size_t>(q) * p2 + b]);
-      if (w == 0.0) continue;
-      for (int a = 0; a < p1; ++a) Mx[static_cast<size_t>(b) * p1 + a] += R1[static_cast<size_t>(q) * p1 + a] * w;
-    }
-  std::vector<cd> J(static_cast<size_t>(p2) * p2);
-  jacobi(p1, p2, Mx.data(), J.data());  // Mx J = W Sigma
-  std::vector<double> sv(p2);
-  for (int q = 0; q < p2; ++q) sv[q] = std::sqrt(colnorm2(p1, &Mx[static_cast<size_t>(q) * p1]));
-  std::vector<int> ord(p2);
-  std::iota(ord.begin(), ord.end(), 0);
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sv[a] > sv[b]; });
-  if (sv[ord[0]] == 0.0) return out;
-  int keep = 0;
-  while (keep < p2 && sv[ord[keep]] > tol * sv[ord[0]]) ++keep;
-  out.k = keep;
-  out.s.resize(keep);
-  out.Ub.assign(static_cast<size_t>(m) * keep, 0.0);
-  out.Yb.assign(static_cast<size_t>(nn) * keep, 0.0);
-  for (int q = 0; q < keep; ++q) {
-    const int col = ord[q];
-    out.s[q] = sv[col];
-    // left vector w = Mx[:, col] / sigma; U_b = Q1 w
-    for (int a = 0; a < p1; ++a) {
-      const cd w = Mx[static_cast<size_t>(col) * p1 + a] / sv[col];
-      for (int t = 0; t < m; ++t) out.Ub[static_cast<size_t>(q) * m + t] += Q1[static_cast<size_t>(a) * m + t] * w;
-    }
-    // right vector = J[:, col]; Y_b = Q2 J[:, col]
-    for (int b = 0; b < p2; ++b) {
-      const cd w = J[static_cast<size_t>(col) * p2 + b];
-      for (int t = 0; t < nn; ++t) out.Yb[static_cast<size_t>(q) * nn + t] += Q2[static_cast<size_t>(b) * nn + t] * w;
-    }
-  }
-  return out;
+  return recompress_pair(m, nn, k, X.data(), Y.data(), tol);
 }
 
 }  // namespace
@@ -356,6 +364,9 @@ int uhb::check_build_args(int64_t n, const double* points, const uhb_params* prm
   if (prm->leaf < 1 || !(prm->eta > 0) || !(prm->eps >= 0 && prm->eps < 1) || !(prm->tol_aca > 0 && prm->tol_aca < 1))
     return uh::set_error(UH_EINVAL, "invalid parameters (leaf %d, eta %g, eps %g, tol_aca %g)", prm->leaf, prm->eta,
                          prm->eps, prm->tol_aca);
+  if (prm->strong != 0 && prm->strong != 1) return uh::set_error(UH_EINVAL, "strong = %d (0 or 1)", prm->strong);
+  if (prm->factored != 0 && prm->factored != 1)
+    return uh::set_error(UH_EINVAL, "factored = %d (0 or 1)", prm->factored);
   for (int64_t i = 0; i < 3 * n; ++i)
     if (!std::isfinite(points[i])) return uh::set_error(UH_EINVAL, "point coordinate %lld is not finite", (long long)i);
   return UH_OK;
@@ -508,19 +519,17 @@ int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* prm, 
     std::copy(Ub[c].begin(), Ub[c].end(), M->U.begin() + M->row_off[c]);
     std::copy(Vb[c].begin(), Vb[c].end(), M->V.begin() + M->col_off[c]);
   }
-  M->S_off.resize(na);
-  int64_t ps = 0;
-  for (int64_t q = 0; q < na; ++q) {
-    M->S_off[q] = ps;
-    ps += static_cast<int64_t>(lrow[adm[q].first]) * lcol[adm[q].second];
-  }
-  M->S.assign(ps, 0.0);
+  // Coupling matrices by projection: P = U_tau^* U_b Sigma_b, R = V_sigma^* V_b, S_b = P R^*. With
+  // prm->factored the pair (P, R) is recompressed at eps (Section 2.3) and, where
+  // k (l_tau + l_sigma) < l_tau l_sigma, stored as S_X = Q1 W diag(s), S_Y = Q2 Z (Section 4.2).
+  std::vector<std::vector<cd>> Sq(na);
+  M->S_rank.assign(prm->factored ? na : 0, -1);
 #pragma omp parallel for schedule(dynamic, 8)
   for (int64_t q = 0; q < na; ++q) {
     const int32_t a = adm[q].first, b = adm[q].second;
     const int64_t m = B.cl[a].size, nn = B.cl[b].size;
     const int la = lrow[a], lb = lcol[b], k = lr[q].k;
-    if (la == 0 || lb == 0 || k == 0) continue;
+    if (la == 0 || lb == 0) continue;
     const LowRank& L = lr[q];
     std::vector<cd> P(static_cast<size_t>(la) * k, 0.0), R(static_cast<size_t>(lb) * k, 0.0);
     for (int j = 0; j < k; ++j) {
@@ -539,12 +548,38 @@ int uhb_build_helmholtz(int64_t n, const double* points, const uhb_params* prm, 
         R[static_cast<size_t>(j) * lb + i] = s;
       }
     }
-    cd* S = &M->S[M->S_off[q]];  // S = P R^*  (la x lb)
+    if (prm->factored) {
+      const LowRank f = recompress_pair(la, lb, k, P.data(), R.data(), prm->eps);
+      if (static_cast<int64_t>(f.k) * (la + lb) < static_cast<int64_t>(la) * lb) {
+        std::vector<cd>& out = Sq[q];
+        out.assign(static_cast<size_t>(f.k) * (la + lb), 0.0);
+        for (int j = 0; j < f.k; ++j) {
+          for (int i = 0; i < la; ++i) out[static_cast<size_t>(j) * la + i] = f.Ub[static_cast<size_t>(j) * la + i] * f.s[j];
+          for (int i = 0; i < lb; ++i)
+            out[static_cast<size_t>(la) * f.k + static_cast<size_t>(j) * lb + i] = f.Yb[static_cast<size_t>(j) * lb + i];
+        }
+        M->S_rank[q] = f.k;
+        continue;
+      }
+    }
+    std::vector<cd>& S = Sq[q];  // S = P R^*  (la x lb)
+    S.assign(static_cast<size_t>(la) * lb, 0.0);
     for (int jb = 0; jb < lb; ++jb)
       for (int j = 0; j < k; ++j) {
         const cd w = std::conj(R[static_cast<size_t>(j) * lb + jb]);
         for (int i = 0; i < la; ++i) S[static_cast<size_t>(jb) * la + i] += P[static_cast<size_t>(j) * la + i] * w;
       }
+  }
+  M->S_off.resize(na);
+  int64_t ps = 0;
+  for (int64_t q = 0; q < na; ++q) {
+    M->S_off[q] = ps;
+    ps += static_cast<int64_t>(Sq[q].size());
+  }
+  M->S.resize(ps);
+  for (int64_t q = 0; q < na; ++q) {
+    std::copy(Sq[q].begin(), Sq[q].end(), M->S.begin() + M->S_off[q]);
+    std::vector<cd>().swap(Sq[q]);
   }
   double t3 = now_s();
   M->info.seconds_bases = t3 - t2;
@@ -598,6 +633,7 @@ int uhb_uh_desc(const uh_model* m, uh_desc* d) {
   d->S_off = m->S_off.data();
   d->S_data = m->S.data();
   d->S_len = static_cast<int64_t>(m->S.size());
+  d->S_rank = m->S_rank.empty() ? nullptr : m->S_rank.data();
   fill_dense(m, &d->dense);
   return UH_OK;
 }

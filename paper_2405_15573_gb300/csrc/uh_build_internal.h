@@ -136,6 +136,7 @@ struct uh_model {
   std::vector<uhb::cd> U, V, S;
   std::vector<int32_t> adm_row, adm_col;
   std::vector<int64_t> S_off;
+  std::vector<int32_t> S_rank;  // inner rank of each factored S_b (-1: dense); empty: all dense
   // H
   std::vector<int32_t> h_rank;
   std::vector<int64_t> X_off, Y_off;

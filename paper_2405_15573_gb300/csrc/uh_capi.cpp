@@ -212,8 +212,9 @@ struct OpBase {
   void* d_z1 = nullptr;
   void* d_z2 = nullptr;
   void* d_z3 = nullptr;
-  // uh_matvec_mixed (complex64 UH ops): xp, z1, z2, z3 at 16 bytes per value
-  void* d_xm[4] = {};
+  void* d_z4 = nullptr;
+  // uh_matvec_mixed (complex64 UH ops): xp, z1, z2, z3, z4 at 16 bytes per value
+  void* d_xm[uh::kNumSources] = {};
   // tensor-core uh_matmat (UH_PREC_C64_TF32 / UH_PREC_C64_BF16X3 ops)
   int mm_mode = -1;       // UH_MM_TF32 or UH_MM_BF16X3
   int panel_mode = 0;     // uh::kPanelTF32 or uh::kPanelBF16X3
@@ -243,7 +244,7 @@ struct OpBase {
 void free_op(OpBase* o) {
   if (!o) return;
   void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_scatter, o->d_pool, o->d_status,
-                  o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3,
+                  o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3, o->d_z4, o->d_xm[4],
                   o->d_ptiles, o->d_pitems, o->d_pbegin, o->d_pxp, o->d_pz1, o->d_pz2,
                   o->d_xm[0], o->d_xm[1], o->d_xm[2], o->d_xm[3], o->d_pdone};
   for (void* p : ptrs)
@@ -328,21 +329,22 @@ int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T, bool mixed_vecto
   for (int c = 0; c < uh::kNumCounters; ++c) o->counter_total[c] = P.counter_total(c);
   if ((rc = upload(static_cast<const void*>(nullptr), sizeof(uint32_t), &o->d_status))) return rc;
   if ((rc = upload(T.perm.data(), T.perm.size() * sizeof(int32_t), &o->d_perm))) return rc;
-  void** z[4] = {&o->d_xp, &o->d_z1, &o->d_z2, &o->d_z3};
-  for (int k = 0; k < 4; ++k)
+  void** z[uh::kNumSources] = {&o->d_xp, &o->d_z1, &o->d_z2, &o->d_z3, &o->d_z4};
+  int64_t vec_len = 0;
+  for (int k = 0; k < uh::kNumSources; ++k) vec_len += P.src_len_[k];
+  for (int k = 0; k < uh::kNumSources; ++k)
     if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(P.src_len_[k], 2)) * eb, z[k])))
       return rc;
   if (mixed_vectors)
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < uh::kNumSources; ++k)
       if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(P.src_len_[k], 2)) * 16,
                        &o->d_xm[k])))
         return rc;
   o->st.packed_bytes = P.tile_bytes_total + P.input_bytes_total;
   o->st.device_bytes = static_cast<int64_t>(P.M.size() * eb + P.items.size() * sizeof(uh::WorkItem) +
                                             P.chunks.size() * (sizeof(uh::OutChunk) + 4) + T.n * 4) +
-                       (P.src_len_[0] + P.src_len_[1] + P.src_len_[2] + P.src_len_[3]) * static_cast<int64_t>(eb);
-  if (mixed_vectors)
-    o->st.device_bytes += (P.src_len_[0] + P.src_len_[1] + P.src_len_[2] + P.src_len_[3]) * int64_t{16};
+                       vec_len * static_cast<int64_t>(eb);
+  if (mixed_vectors) o->st.device_bytes += vec_len * int64_t{16};
   o->st.n_launches = 1;
   o->st.n_items = static_cast<int64_t>(P.items.size());
   return UH_OK;
@@ -386,6 +388,7 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   p.z1 = mixed ? o->d_xm[1] : o->d_z1;
   p.z2 = mixed ? o->d_xm[2] : o->d_z2;
   p.z3 = mixed ? o->d_xm[3] : o->d_z3;
+  p.z4 = mixed ? o->d_xm[4] : o->d_z4;
   p.status = o->d_status;
   p.timeout_cycles = timeout;
   const int variant = mixed ? uh::kVarMixed : o->c128 ? uh::kVarC128 : uh::kVarC64;
@@ -462,7 +465,9 @@ int build_panel(OpBase* o, const uh_desc* d, const Tree& T, const std::vector<Ti
   auto up = [&](int64_t v) { return (v + C - 1) / C * C; };
   const int64_t xp_rows = up(T.n) + C;
   uh::PanelBuilder B(mode, ncta, up(T.n));
-  auto live = [&](int64_t b) { return d->row_rank[d->adm_row[b]] > 0 && d->col_rank[d->adm_col[b]] > 0; };
+  auto live = [&](int64_t b) {
+    return d->row_rank[d->adm_row[b]] > 0 && d->col_rank[d->adm_col[b]] > 0 && !(d->S_rank && d->S_rank[b] == 0);
+  };
   // xhat_sigma and yhat_tau each start a block
   std::vector<int64_t> xo(T.ncl, -1), yo(T.ncl, -1);
   int64_t nx = 0, ny = 0;
@@ -479,6 +484,26 @@ int build_panel(OpBase* o, const uh_desc* d, const Tree& T, const std::vector<Ti
   };
   const Src V{d->V_data, d->data_type}, S{d->S_data, d->data_type}, U{d->U_data, d->data_type};
   const Src D{d->dense.data, d->data_type};
+  // Coefficient matrices stored factored are assembled here, S_b = S_X,b S_Y,b^* in FP64 from the
+  // stored factors, and packed like the dense ones.
+  std::vector<std::complex<double>> sfull;
+  std::vector<int64_t> sfull_off(d->n_adm, -1);
+  for (int64_t b = 0; b < d->n_adm; ++b) {
+    const int32_t k = d->S_rank ? d->S_rank[b] : -1;
+    if (k <= 0 || !live(b)) continue;
+    const int64_t lt = d->row_rank[d->adm_row[b]], ls = d->col_rank[d->adm_col[b]];
+    sfull_off[b] = static_cast<int64_t>(sfull.size());
+    sfull.resize(sfull.size() + static_cast<size_t>(lt * ls));
+    std::complex<double>* out = sfull.data() + sfull_off[b];
+    const int64_t x0 = d->S_off[b], y0 = d->S_off[b] + lt * k;
+    for (int64_t j = 0; j < ls; ++j)
+      for (int64_t i = 0; i < lt; ++i) {
+        std::complex<double> v = 0;
+        for (int64_t r = 0; r < k; ++r) v += S.at(x0 + r * lt + i) * std::conj(S.at(y0 + r * ls + j));
+        out[j * lt + i] = v;
+      }
+  }
+  const Src SF{sfull.data(), UH_DATA_C128};
   for (int32_t s = 0; s < T.ncl; ++s) {
     if (xo[s] < 0) continue;
     bool used = false;
@@ -504,7 +529,10 @@ int build_panel(OpBase* o, const uh_desc* d, const Tree& T, const std::vector<Ti
       for (int64_t b : row_blocks[t]) {
         if (!live(b)) continue;
         const int32_t s = d->adm_col[b];
-        cols.push_back(ColSpec{uh::kPSrcZ1, xo[s], d->col_rank[s], &S, false, d->S_off[b] + i0, l, 1});
+        if (sfull_off[b] >= 0)
+          cols.push_back(ColSpec{uh::kPSrcZ1, xo[s], d->col_rank[s], &SF, false, sfull_off[b] + i0, l, 1});
+        else
+          cols.push_back(ColSpec{uh::kPSrcZ1, xo[s], d->col_rank[s], &S, false, d->S_off[b] + i0, l, 1});
       }
       B.add_chunk(1, uh::kPOutZ2, yo[t] + i0, i1 - i0, cols);
     }
@@ -580,14 +608,16 @@ int matmat_by_columns(OpBase* o, int32_t nrhs, const void* X, int64_t ldx, void*
 
 
 // Near-field chunks of the row tiles, alternating between the two near-field groups (static,
-// before the coupling; and the first part of the pool). A tile with a backward part writes its z3
+// before the coupling; and the first part of the pool); with `split`, the static half is itself
+// shared between the group before the t_b chunks and the group after them. A tile with a backward part writes its z3
 // slot (the backward chunk adds it), otherwise y directly. Returns, per tile, the near-field chunk
 // writing z3 (or -1).
 // offN: position of the operator's first point in the program's vectors; z3pos: next free z3 slot
 // (advanced; when null the slots start at 0 and the z3 length is set here).
 std::vector<int> add_near_field(ProgramBuilder& P, const Tree& T, const uh_dense_desc& d, const Src& D,
                                 const std::vector<Tile>& tiles, const std::vector<char>& has_back,
-                                std::vector<char>* has_near, int64_t offN = 0, int64_t* z3pos = nullptr) {
+                                std::vector<char>* has_near, int64_t offN = 0, int64_t* z3pos = nullptr,
+                                bool split = false) {
   const int64_t A = P.align();
   std::vector<std::vector<int64_t>> per_tile(tiles.size());
   for (int64_t i = 0; i < d.n_dense; ++i)
@@ -609,7 +639,8 @@ std::vector<int> add_near_field(ProgramBuilder& P, const Tree& T, const uh_dense
   std::vector<ColSpec> cols;
   for (size_t t = 0; t < tiles.size(); ++t) {
     if (per_tile[t].empty()) continue;
-    const int group = (parity++ & 1) ? uh::kGroupNearB : uh::kGroupNearA;
+    const int par = parity++;
+    const int group = (par & 1) ? uh::kGroupNearB : (split && (par & 2)) ? uh::kGroupNearA2 : uh::kGroupNearA;
     const int c = slot[t] >= 0 ? P.add_chunk(uh::kToZ3, slot[t], tiles[t].h, group)
                                : P.add_chunk(uh::kToY, offN + tiles[t].p0, tiles[t].h, group);
     if (slot[t] >= 0) zchunk[t] = c;
@@ -677,7 +708,11 @@ int prepare_uh(const uh_desc* d, UHPrep* u) {
     }
   }
   for (int64_t i = 0; i < d->n_adm; ++i) {
-    const int64_t cnt = static_cast<int64_t>(d->row_rank[d->adm_row[i]]) * d->col_rank[d->adm_col[i]];
+    const int32_t lt = d->row_rank[d->adm_row[i]], ls = d->col_rank[d->adm_col[i]];
+    const int32_t k = d->S_rank ? d->S_rank[i] : -1;
+    if (k < -1 || k > std::min(lt, ls))
+      return fail(UH_EINVAL, "S_rank[%lld] = %d outside [-1, %d]", (long long)i, k, std::min(lt, ls));
+    const int64_t cnt = k < 0 ? static_cast<int64_t>(lt) * ls : static_cast<int64_t>(k) * (lt + ls);
     if ((rc = check_range(d->S_off[i], cnt, d->S_len, "coupling matrix", i))) return rc;
   }
   std::vector<int32_t> brow, bcol;
@@ -704,15 +739,15 @@ int prepare_uh(const uh_desc* d, UHPrep* u) {
 }
 
 // Vector offsets of one operator inside a program that may hold several (a batch): its points
-// start at position n in xp and y; its z1, z2 and z3 parts start at x, y, z3 (all advanced past
-// what the operator uses).
+// start at position n in xp and y; its z1, z2, z3 and z4 parts start at x, y, z3, t (all advanced
+// past what the operator uses).
 struct Offsets {
-  int64_t n = 0, x = 0, y = 0, z3 = 0;
+  int64_t n = 0, x = 0, y = 0, z3 = 0, t = 0;
 };
 
 // The forward, near-field, coupling and backward chunks of one UH operator (Algorithm 6), with
-// the scatter layout of z1 / z2 (see the file comment). The permutation chunks and the source
-// lengths are the caller's.
+// the scatter layout of z1 / z2 (see the file comment), and for coefficient matrices stored
+// factored the t_b chunks into z4. The permutation chunks and the source lengths are the caller's.
 void add_uh_program(ProgramBuilder& P, const UHPrep& u, Offsets* off) {
   const uh_desc* d = u.d;
   const Tree& T = u.T;
@@ -722,18 +757,46 @@ void add_uh_program(ProgramBuilder& P, const UHPrep& u, Offsets* off) {
   const auto& col_blocks = u.col_blocks;
   const auto& tile_rows = u.tile_rows;
   const int64_t on = off->n;
-  auto live = [&](int64_t b) { return d->row_rank[d->adm_row[b]] > 0 && d->col_rank[d->adm_col[b]] > 0; };
-  // z1: per row cluster tau, the coupling inputs [xhat_sigma]_{sigma in row(tau)} back to back
-  // (the forward chunks scatter each xhat_sigma into every segment that uses it).
-  std::vector<int64_t> xin(T.ncl, -1), xpos(d->n_adm, -1);
+  // inner rank k_b of a coefficient matrix stored factored (Section 4.2), -1 for a dense S_b
+  auto frank = [&](int64_t b) { return d->S_rank ? d->S_rank[b] : -1; };
+  auto live = [&](int64_t b) {
+    return d->row_rank[d->adm_row[b]] > 0 && d->col_rank[d->adm_col[b]] > 0 && frank(b) != 0;
+  };
+  auto dense_s = [&](int64_t b) { return live(b) && frank(b) < 0; };
+  auto fact_s = [&](int64_t b) { return live(b) && frank(b) > 0; };
+  // z1: per row cluster tau, the coupling inputs [xhat_sigma] of its dense-S blocks back to back
+  // (the forward chunks scatter each xhat_sigma into every segment that uses it); then, per column
+  // cluster sigma with factored blocks, one more copy of xhat_sigma at xs[sigma], the input of t_b.
+  std::vector<int64_t> xin(T.ncl, -1), xpos(d->n_adm, -1), xs(T.ncl, -1);
   int64_t nx = off->x;
   for (int32_t t = 0; t < T.ncl; ++t) {
     if (!u.is_row[t] || d->row_rank[t] == 0) continue;
     xin[t] = nx;
     int64_t pos = 0;
     for (int64_t b : row_blocks[t])
-      if (live(b)) { xpos[b] = pos; pos += d->col_rank[d->adm_col[b]]; }
+      if (dense_s(b)) { xpos[b] = pos; pos += d->col_rank[d->adm_col[b]]; }
     nx += ProgramBuilder::round_up(std::max<int64_t>(pos, 1), A);
+  }
+  for (int32_t s = 0; s < T.ncl; ++s) {
+    if (!u.is_col[s] || d->col_rank[s] == 0) continue;
+    bool f = false;
+    for (int64_t b : col_blocks[s]) f = f || fact_s(b);
+    if (f) { xs[s] = nx; nx += ProgramBuilder::round_up(d->col_rank[s], A); }
+  }
+  // z4: per row cluster tau, [t_b] of its factored blocks back to back (the t_b chunks scatter
+  // each block's rows there), so the coupling chunk of tau reads them as one run.
+  std::vector<int64_t> tin(T.ncl, -1), tpos(d->n_adm, -1);
+  int64_t nt = off->t;
+  bool any_factored = false;
+  for (int32_t t = 0; t < T.ncl; ++t) {
+    if (!u.is_row[t] || d->row_rank[t] == 0) continue;
+    int64_t pos = 0;
+    for (int64_t b : row_blocks[t])
+      if (fact_s(b)) { tpos[b] = pos; pos += frank(b); }
+    if (pos == 0) continue;
+    tin[t] = nt;
+    nt += ProgramBuilder::round_up(pos, A);
+    any_factored = true;
   }
   std::vector<char> has_back(tiles.size(), 0);
   // z2: per row tile, the backward inputs [yhat_tau]_{tau contains the tile} back to back (the
@@ -756,8 +819,8 @@ void add_uh_program(ProgramBuilder& P, const UHPrep& u, Offsets* off) {
     if (!u.is_col[s] || d->col_rank[s] == 0) continue;
     std::vector<int64_t> users;
     for (int64_t b : col_blocks[s])
-      if (live(b)) users.push_back(b);
-    if (users.empty()) continue;
+      if (dense_s(b)) users.push_back(b);
+    if (users.empty() && xs[s] < 0) continue;
     const int32_t l = d->col_rank[s];
     const int64_t m = T.size[s];
     const int k = (l + uh::kStreamHpMax - 1) / uh::kStreamHpMax;
@@ -765,13 +828,54 @@ void add_uh_program(ProgramBuilder& P, const UHPrep& u, Offsets* off) {
       const int j0 = l * q / k, j1 = l * (q + 1) / k;
       const int c = P.add_chunk(uh::kScatterZ1, 0, j1 - j0, uh::kGroupForward, uh::kCounterForward);
       for (int64_t b : users) P.add_scatter(c, xin[d->adm_row[b]] + xpos[b] + j0, 0, j1 - j0);
+      if (xs[s] >= 0) P.add_scatter(c, xs[s] + j0, 0, j1 - j0);
       P.add_columns(c, {ColSpec{uh::kSrcXp, on + T.begin[s], m, &V, true, d->col_off[s] + j0 * m, 1, m}});
     }
   }
   std::vector<char> has_near;
-  const std::vector<int> zchunk = add_near_field(P, T, d->dense, D, tiles, has_back, &has_near, on, &off->z3);
-  // Coupling: per row cluster tau (chunks of at most 64 rows), columns [S_b]_{sigma in row(tau)},
-  // inputs one run of z1; outputs scattered to the tiles inside tau.
+  const std::vector<int> zchunk =
+      add_near_field(P, T, d->dense, D, tiles, has_back, &has_near, on, &off->z3, any_factored);
+  // t_b = S_Y,b^* xhat_sigma: per column cluster sigma, the rows conj(S_Y,b[:, j]) of its factored
+  // blocks stacked (blocks in increasing row cluster) and cut into tall chunks of at most
+  // kStreamHpTall rows, input
+  // the copy of xhat_sigma at xs[sigma]; each block's rows are scattered to its place in z4.
+  std::vector<int64_t> rowoff;
+  std::vector<std::pair<int64_t, int32_t>> rowblk;  // (block, j) of each stacked row
+  for (int32_t s = 0; s < T.ncl; ++s) {
+    if (xs[s] < 0) continue;
+    const int32_t ls = d->col_rank[s];
+    rowoff.clear();
+    rowblk.clear();
+    for (int64_t b : col_blocks[s]) {
+      if (!fact_s(b)) continue;
+      const int64_t lt = d->row_rank[d->adm_row[b]];
+      const int32_t k = frank(b);
+      for (int32_t j = 0; j < k; ++j) {
+        rowoff.push_back(d->S_off[b] + lt * k + static_cast<int64_t>(j) * ls);
+        rowblk.emplace_back(b, j);
+      }
+    }
+    const int64_t rows = static_cast<int64_t>(rowoff.size());
+    const int64_t nq = (rows + uh::kStreamHpTall - 1) / uh::kStreamHpTall;
+    for (int64_t q = 0; q < nq; ++q) {
+      const int64_t r0 = rows * q / nq, r1 = rows * (q + 1) / nq;
+      const int c = P.add_chunk(uh::kScatterZ4, 0, static_cast<int>(r1 - r0), uh::kGroupCouplingY, uh::kCounterCouplingY);
+      for (int64_t r = r0; r < r1;) {
+        const int64_t b = rowblk[r].first;
+        int64_t e = r;
+        while (e < r1 && rowblk[e].first == b) ++e;
+        P.add_scatter(c, tin[d->adm_row[b]] + tpos[b] + rowblk[r].second, static_cast<int>(r - r0),
+                      static_cast<int>(e - r0));
+        r = e;
+      }
+      ColSpec cs{uh::kSrcZ1, xs[s], ls, &S, true, 0, 1, 0};
+      cs.rowoff = rowoff.data() + r0;
+      P.add_columns(c, {cs});
+    }
+  }
+  // Coupling: per row cluster tau (chunks of at most 64 rows), columns [S_b] of its dense-S blocks
+  // (inputs one run of z1), then [S_X,b] of its factored blocks (inputs one run of z4); outputs
+  // scattered to the tiles inside tau.
   std::vector<ColSpec> cols;
   for (int32_t t = 0; t < T.ncl; ++t) {
     if (!u.is_row[t] || d->row_rank[t] == 0) continue;
@@ -787,10 +891,12 @@ void add_uh_program(ProgramBuilder& P, const UHPrep& u, Offsets* off) {
       });
       cols.clear();
       for (int64_t b : row_blocks[t]) {
-        if (!live(b)) continue;
+        if (!dense_s(b)) continue;
         const int32_t s = d->adm_col[b];
         cols.push_back(ColSpec{uh::kSrcZ1, xin[t] + xpos[b], d->col_rank[s], &S, false, d->S_off[b] + i0, l, 1});
       }
+      for (int64_t b : row_blocks[t])
+        if (fact_s(b)) cols.push_back(ColSpec{uh::kSrcZ4, tin[t] + tpos[b], frank(b), &S, false, d->S_off[b] + i0, l, 1});
       P.add_columns(c, cols);
     }
   }
@@ -816,6 +922,7 @@ void add_uh_program(ProgramBuilder& P, const UHPrep& u, Offsets* off) {
   off->n += T.n;
   off->x = nx;
   off->y = ny;
+  off->t = nt;
 }
 
 // Sizes of one UH operator and of its product (uh_stats_t); elem_bytes s.
@@ -833,10 +940,19 @@ void uh_fill_stats(const UHPrep& u, int32_t precision, int s, uh_stats_t* st) {
   int32_t rmin = INT32_MAX, rmax = 0;
   int64_t rsum = 0, rcnt = 0;
   std::vector<int32_t> rowc(T.ncl, 0), colc(T.ncl, 0);
+  int64_t nf = 0, kf = 0;
   for (int64_t i = 0; i < d->n_adm; ++i) {
     rowc[d->adm_row[i]]++;
     colc[d->adm_col[i]]++;
-    es += static_cast<int64_t>(d->row_rank[d->adm_row[i]]) * d->col_rank[d->adm_col[i]];
+    const int64_t lt = d->row_rank[d->adm_row[i]], ls = d->col_rank[d->adm_col[i]];
+    const int32_t k = d->S_rank ? d->S_rank[i] : -1;
+    if (k < 0) {
+      es += lt * ls;
+    } else {
+      es += k * (lt + ls);
+      nf++;
+      kf += k;
+    }
   }
   int32_t csp = 0;
   for (int32_t c = 0; c < T.ncl; ++c) {
@@ -862,7 +978,9 @@ void uh_fill_stats(const UHPrep& u, int32_t precision, int s, uh_stats_t* st) {
   st->rank_max = rmax;
   st->rank_mean = rcnt ? static_cast<double>(rsum) / rcnt : 0.0;
   st->csp = csp;
-  st->algo_bytes_matvec = s * (eu + ev + es + ed + 2 * T.n + 2 * (srr + scr));
+  st->n_factored = nf;
+  st->sum_factored_rank = kf;
+  st->algo_bytes_matvec = s * (eu + ev + es + ed + 2 * T.n + 2 * (srr + scr) + 2 * kf);
   st->matmat_mode = -1;
 }
 
@@ -901,6 +1019,7 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   P.set_source_len(uh::kSrcZ1, off.x);
   P.set_source_len(uh::kSrcZ2, off.y);
   P.set_source_len(uh::kSrcZ3, off.z3);
+  P.set_source_len(uh::kSrcZ4, off.t);
 
   const int mm_mode = precision == UH_PREC_C64_TF32 ? UH_MM_TF32 : precision == UH_PREC_C64_BF16X3 ? UH_MM_BF16X3 : -1;
   if (g_pack_only_ncta) {
@@ -1182,6 +1301,7 @@ int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t preci
   P.set_source_len(uh::kSrcZ1, off.x);
   P.set_source_len(uh::kSrcZ2, off.y);
   P.set_source_len(uh::kSrcZ3, off.z3);
+  P.set_source_len(uh::kSrcZ4, off.t);
   if (g_pack_only_ncta) {
     if (const char* e = P.finalize()) return fail(UH_EINVAL, "packing: %s", e);
     if (const char* e = P.self_check()) return fail(UH_EINVAL, "internal packing error: %s", e);
@@ -1211,6 +1331,8 @@ int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t preci
     sum.E_V += st.E_V;
     sum.E_S += st.E_S;
     sum.E_D += st.E_D;
+    sum.n_factored += st.n_factored;
+    sum.sum_factored_rank += st.sum_factored_rank;
     sum.sum_row_rank += st.sum_row_rank;
     sum.sum_col_rank += st.sum_col_rank;
     if (st.rank_max > 0) sum.rank_min = std::min(sum.rank_min, st.rank_min);

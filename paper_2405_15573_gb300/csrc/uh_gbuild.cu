@@ -680,15 +680,18 @@ struct CouplingWork {
   int64_t urow;   // X scratch offset of the row basis (|tau| x l_tau, ld |tau|)
   int64_t vcol;   // X scratch offset of the column basis (|sigma| x l_sigma)
   int64_t soff;   // S_b (l_tau x l_sigma, column-major) in the compact S
+  int64_t poff;   // the pair (factored option): P at Pg + poff (l_tau x kCap), conj(R) at Rg + roff
+  int64_t roff;   // (l_sigma x kCap)
   int32_t lt, ls;
 };
 
 // S_b = (U_tau^* U_b s_b)(V_sigma^* Y_b)^* per block (grid-stride); P (lt x k) and R (ls x k)
-// in per-CTA scratch (kRowMax x kCap each).
+// in per-CTA scratch (kRowMax x kCap each). With Pg != nullptr the pair is also stored, P and
+// conj(R) column-major with leading dimensions lt and ls, for its recompression (Section 2.3).
 __global__ void __launch_bounds__(kThreads) coupling_kernel(const CouplingWork* work, BlockTab T, int64_t nblocks,
                                                             const double2* Xs, const double2* U, const double2* V,
                                                             const double* sv_in, const int32_t* kb, double2* small,
-                                                            double2* S) {
+                                                            double2* S, double2* Pg, double2* Rg) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double2* P = small + static_cast<int64_t>(blockIdx.x) * 2 * kRowMax * kCap;
   double2* R = P + kRowMax * kCap;
@@ -726,6 +729,10 @@ __global__ void __launch_bounds__(kThreads) coupling_kernel(const CouplingWork* 
       double2 s = make_double2(0.0, 0.0);
       for (int j = 0; j < k; ++j) s = cadd(s, cmul(P[i + j * kRowMax], cconj(R[c + j * kRowMax])));
       S[W.soff + e] = s;
+    }
+    if (Pg) {
+      for (int e = threadIdx.x; e < lt * k; e += kThreads) Pg[W.poff + e] = P[e % lt + (e / lt) * kRowMax];
+      for (int e = threadIdx.x; e < ls * k; e += kThreads) Rg[W.roff + e] = cconj(R[e % ls + (e / ls) * kRowMax]);
     }
     __syncthreads();
   }
@@ -1062,26 +1069,95 @@ extern "C" int uhb_build_helmholtz_gpu(int64_t n, const double* points, const uh
     }
     GTRY(download(side == 0 ? M->U : M->V, reinterpret_cast<const cd*>(dst), total));
   }
-  // coupling matrices, in block order
-  M->S_off.resize(na);
+  // coupling matrices, in block order; with the factored option the pairs too, recompressed at
+  // eps, and each block keeps the smaller form
+  const bool factored = prm->factored != 0;
   std::vector<CouplingWork> cw(na);
-  int64_t ps = 0;
+  std::vector<int64_t> dense_off(na);
+  std::vector<int32_t> plt(na), pls(na);
+  int64_t ps = 0, pp = 0, pr = 0;
   for (int64_t b = 0; b < na; ++b) {
     const int32_t a = adm[b].first, c = adm[b].second;
-    M->S_off[b] = ps;
-    cw[b] = CouplingWork{std::max<int64_t>(xrow[a], 0), std::max<int64_t>(xcol[c], 0), ps, lrow[a], lcol[c]};
+    dense_off[b] = ps;
+    plt[b] = lrow[a];
+    pls[b] = lcol[c];
+    cw[b] = CouplingWork{std::max<int64_t>(xrow[a], 0), std::max<int64_t>(xcol[c], 0), ps, pp, pr, lrow[a], lcol[c]};
     ps += static_cast<int64_t>(lrow[a]) * lcol[c];
+    if (factored) {
+      pp += static_cast<int64_t>(lrow[a]) * kCap;
+      pr += static_cast<int64_t>(lcol[c]) * kCap;
+    }
   }
+  std::vector<cd> Sdense, Pf, Rf;
+  std::vector<int32_t> kf;
+  std::vector<double> sf;
   {
     CouplingWork* d_cw;
-    double2* dS;
+    double2 *dS, *dP = nullptr, *dR = nullptr;
     GTRY(mem.upload(&d_cw, cw));
     GTRY(mem.alloc(&dS, ps));
+    if (factored) {
+      GTRY(mem.alloc(&dP, pp));
+      GTRY(mem.alloc(&dR, pr));
+    }
     if (na > 0) {
-      coupling_kernel<<<grid, kThreads>>>(d_cw, T, na, dXs, dU, dV, d_sv, d_kb, d_small, dS);
+      coupling_kernel<<<grid, kThreads>>>(d_cw, T, na, dXs, dU, dV, d_sv, d_kb, d_small, dS, dP, dR);
       GTRY(cudaGetLastError());
     }
-    GTRY(download(M->S, reinterpret_cast<const cd*>(dS), ps));
+    GTRY(download(Sdense, reinterpret_cast<const cd*>(dS), ps));
+    if (factored && na > 0) {
+      std::vector<int64_t> poff(na), roff(na);
+      std::vector<int32_t> kp(na);  // the pair's inner rank (0 where a basis is empty: no pair)
+      for (int64_t b = 0; b < na; ++b) {
+        poff[b] = cw[b].poff;
+        roff[b] = cw[b].roff;
+        kp[b] = plt[b] > 0 && pls[b] > 0 ? kb[b] : 0;
+      }
+      int64_t *d_poff, *d_roff;
+      int32_t *d_lt, *d_ls, *d_kf, *d_kp;
+      GTRY(mem.upload(&d_kp, kp));
+      double* d_sf;
+      GTRY(mem.upload(&d_poff, poff));
+      GTRY(mem.upload(&d_roff, roff));
+      GTRY(mem.upload(&d_lt, plt));
+      GTRY(mem.upload(&d_ls, pls));
+      GTRY(mem.alloc(&d_kf, na));
+      GTRY(mem.alloc(&d_sf, na * kCap));
+      const BlockTab TP{nullptr, d_lt, nullptr, d_ls, d_poff, d_roff};
+      recompress_kernel<<<grid, kThreads>>>(TP, na, d_kp, prm->eps, dP, dR, d_small, d_sf, d_kf);
+      GTRY(cudaGetLastError());
+      GTRY(download(kf, d_kf, na));
+      GTRY(download(sf, d_sf, na * kCap));
+      GTRY(download(Pf, reinterpret_cast<const cd*>(dP), pp));
+      GTRY(download(Rf, reinterpret_cast<const cd*>(dR), pr));
+    }
+  }
+  M->S_off.resize(na);
+  if (factored) M->S_rank.assign(na, -1);
+  int64_t fs = 0;
+  for (int64_t b = 0; b < na; ++b) {
+    M->S_off[b] = fs;
+    const int64_t lt = plt[b], ls = pls[b];
+    if (factored && lt > 0 && ls > 0 && static_cast<int64_t>(kf[b]) * (lt + ls) < lt * ls) {
+      M->S_rank[b] = kf[b];
+      fs += static_cast<int64_t>(kf[b]) * (lt + ls);
+    } else {
+      fs += lt * ls;
+    }
+  }
+  M->S.resize(fs);
+  for (int64_t b = 0; b < na; ++b) {
+    const int64_t lt = plt[b], ls = pls[b];
+    cd* out = M->S.data() + M->S_off[b];
+    if (factored && M->S_rank[b] >= 0) {
+      // S_X = Q1 W diag(s) (in P's place), S_Y = Q2 Z (in conj(R)'s place)
+      for (int j = 0; j < M->S_rank[b]; ++j) {
+        for (int64_t i = 0; i < lt; ++i) out[j * lt + i] = Pf[cw[b].poff + j * lt + i] * sf[b * kCap + j];
+        for (int64_t i = 0; i < ls; ++i) out[lt * M->S_rank[b] + j * ls + i] = Rf[cw[b].roff + j * ls + i];
+      }
+    } else {
+      std::copy(Sdense.begin() + dense_off[b], Sdense.begin() + dense_off[b] + lt * ls, out);
+    }
   }
   const double t3 = now_s();
   M->info.seconds_bases = t3 - t2;

@@ -37,7 +37,8 @@ namespace {
 // to pool_unit (a ticket costs the producer about 2 us of latency, hidden only behind enough
 // staged work).
 int counter_of_source(int src) {
-  return src == kSrcXp ? kCounterPermute : src == kSrcZ1 ? kCounterForward : src == kSrcZ2 ? kCounterCoupling : -1;
+  return src == kSrcXp ? kCounterPermute : src == kSrcZ1 ? kCounterForward : src == kSrcZ2 ? kCounterCoupling
+       : src == kSrcZ4 ? kCounterCouplingY : -1;
 }
 }  // namespace
 
@@ -230,7 +231,7 @@ const char* ProgramBuilder::finalize() {
       it.h = chunks[c].h;
       it.kind = chunks[c].kind;
       it.counter = chunks[c].counter;
-      if (chunks[c].kind == kScatterZ1 || chunks[c].kind == kScatterZ2) {
+      if (is_scatter(chunks[c].kind)) {
         it.aux = chunks[c].scat0;
         it.naux = chunks[c].nscat;
       }
@@ -298,9 +299,9 @@ const char* ProgramBuilder::self_check() const {
     const OutChunk& ch = chunks[it.chunk];
     if (it.dst != ch.dst || it.h != ch.h || it.kind != ch.kind || it.counter != ch.counter)
       return "item does not carry its chunk's output fields";
-    if ((ch.kind == kScatterZ1 || ch.kind == kScatterZ2) && (it.aux != ch.scat0 || it.naux != ch.nscat))
+    if (is_scatter(ch.kind) && (it.aux != ch.scat0 || it.naux != ch.nscat))
       return "item does not carry its chunk's scatter list";
-    if (it.hp < A_ || it.hp > kStreamHpMax || it.hp % A_ || it.hp < ch.h)
+    if (it.hp < A_ || it.hp > (ch.kind == kScatterZ4 ? kStreamHpTall : kStreamHpMax) || it.hp % A_ || it.hp < ch.h)
       return "item height";
     if (it.nruns < 0 || it.nruns > kMaxRuns) return "item run count";
     const bool has_base = (it.flags & kItemBase) != 0;
@@ -335,7 +336,7 @@ const char* ProgramBuilder::self_check() const {
         if (pool_pos_[bc] == pos && first_item_[bc] > first_item_[it.chunk]) return "near-field base after its reader";
         if (run.start < 0 || run.start + static_cast<int64_t>(run.len) > src_len_[kSrcZ3]) return "base outside z3";
       } else {
-        if (run.src < 0 || run.src > 2 || run.len <= 0 || run.len % A_ || run.start < 0 || run.start % A_ ||
+        if (run.src < 0 || run.src >= kNumSources || run.src == kSrcZ3 || run.len <= 0 || run.len % A_ || run.start < 0 || run.start % A_ ||
             run.start + static_cast<int64_t>(run.len) > src_len_[run.src])
           return "run outside its input vector or misaligned";
         cols += run.len;
@@ -422,8 +423,9 @@ const char* ProgramBuilder::self_check() const {
         if (ch.dst + ch.h > n_) return "chunk outside y";
         break;
       case kScatterZ1:
-      case kScatterZ2: {
-        const int64_t len = src_len_[ch.kind == kScatterZ1 ? kSrcZ1 : kSrcZ2];
+      case kScatterZ2:
+      case kScatterZ4: {
+        const int64_t len = src_len_[ch.kind == kScatterZ1 ? kSrcZ1 : ch.kind == kScatterZ2 ? kSrcZ2 : kSrcZ4];
         if (ch.nscat < 1 || ch.scat0 < 0 || ch.scat0 + static_cast<int64_t>(ch.nscat) > static_cast<int64_t>(scatter.size()))
           return "scatter list";
         for (int k = 0; k < ch.nscat; ++k) {

@@ -34,12 +34,12 @@ struct ColSpec {
   const int64_t* rowoff = nullptr;
 };
 
-// Schedule groups. The first four are static (a list per CTA, in this group order; the permutation
+// Schedule groups. The first six are static (a list per CTA, in this group order; the permutation
 // group has no chunks: every CTA permutes a slice of x at entry); the last two form the pool, in
 // this order, handed out by ticket. An item only waits on counters whose
 // chunks are static and in earlier groups, or earlier in the pool.
-enum Group { kGroupPermute = 0, kGroupForward = 1, kGroupNearA = 2, kGroupCoupling = 3, kGroupNearB = 4,
-             kGroupBackward = 5, kNumGroups = 6 };
+enum Group { kGroupPermute = 0, kGroupForward = 1, kGroupNearA = 2, kGroupCouplingY = 3, kGroupNearA2 = 4,
+             kGroupCoupling = 5, kGroupNearB = 6, kGroupBackward = 7, kNumGroups = 8 };
 constexpr int kFirstPoolGroup = kGroupNearB;
 
 // Packing and scheduling parameters (the defaults were chosen by sweeps on the N = 32768 sphere):
@@ -99,7 +99,7 @@ class ProgramBuilder {
   std::vector<OutChunk> chunks;
   std::vector<cd> M;                  // packed tiles (converted to the element type at upload)
   std::vector<Scatter> scatter;       // scatter entries
-  int64_t src_len_[4] = {0, 0, 0, 0};
+  int64_t src_len_[kNumSources] = {};
   int64_t tile_bytes_total = 0, input_bytes_total = 0;
 
  private:

@@ -195,7 +195,7 @@ __device__ bool wait_parity(uint64_t* bar, uint32_t parity, long long budget, vo
 }
 
 __device__ __forceinline__ const void* src_ptr(const StreamParams& p, int src) {
-  return src == kSrcXp ? p.xp : src == kSrcZ1 ? p.z1 : src == kSrcZ2 ? p.z2 : p.z3;
+  return src == kSrcXp ? p.xp : src == kSrcZ1 ? p.z1 : src == kSrcZ2 ? p.z2 : src == kSrcZ3 ? p.z3 : p.z4;
 }
 
 struct Bars {
@@ -540,7 +540,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
     T* sred = reinterpret_cast<T*>(smem + L::red) + rb * (kStreamConsumers * EPL);
     Scatter* sscat = reinterpret_cast<Scatter*>(smem + L::scat) + rb * 256;
     T* svals = reinterpret_cast<T*>(smem + L::vals) + rb * 64;
-    if ((flags & kItemFirst) && (kind == kScatterZ1 || kind == kScatterZ2)) {
+    if ((flags & kItemFirst) && is_scatter(kind)) {
       // the chunk's scatter entries, used at its end
       for (int k = tid; k < naux && k < 256; k += kStreamConsumers) sscat[k] = p.scatter[aux + k];
     }
@@ -609,17 +609,25 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
         if (flags & kItemBase) v = cadd(v, base);
         if (kind == kToY) {
           static_cast<TX*>(p.y)[out_idx] = to_x(v, static_cast<TX*>(nullptr));
-        } else if (kind == kScatterZ1 || kind == kScatterZ2) {
+        } else if (is_scatter(kind) && h <= kStreamHpMax) {
           svals[tid] = v;
+        } else if (is_scatter(kind)) {
+          // a tall chunk (t_b rows, up to kStreamHpTall): each thread stores its own row to every
+          // scatter entry holding it (few entries: one per block in the chunk)
+          T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : kind == kScatterZ2 ? p.z2 : p.z4);
+          for (int k = 0; k < naux; ++k) {
+            const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];
+            if (tid >= e.lo && tid < e.hi) z[e.dst + tid - e.lo] = v;
+          }
         } else {
           T* z = static_cast<T*>(kind == kToZ1 ? p.z1 : kind == kToZ2 ? p.z2 : p.z3);
           z[dst + tid] = v;
         }
       }
-      if (kind == kScatterZ1 || kind == kScatterZ2) {
+      if (is_scatter(kind) && h <= kStreamHpMax) {
         consumer_sync();  // svals written
         // (entry, row) pairs over all consumer threads: each entry's rows are consecutive
-        T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : p.z2);
+        T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : kind == kScatterZ2 ? p.z2 : p.z4);
         for (int w = tid; w < naux * h; w += kStreamConsumers) {
           const int k = w / h, r = w - k * h;
           const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];

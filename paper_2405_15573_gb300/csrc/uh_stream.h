@@ -19,8 +19,10 @@
 // Every CTA first permutes its slice of x into cluster order (xp), at entry, without descriptors:
 // positions [a_b, a_{b+1}) with a_b = floor(n b / grid) rounded down to 16 bytes, and publishes the
 // permutation counter (one release per CTA). Work is then placed in two parts. The static part
-// (forward transform, the first half of the near field, coupling) is a list per CTA, ordered by
-// group; a group there only waits on earlier groups. The pool (the second half of the near field,
+// (forward transform, the first part of the near field, coupling) is a list per CTA, ordered by
+// group; a group there only waits on earlier groups. Coefficient matrices stored factored,
+// S_b = S_X,b S_Y,b^* (Section 4.2), add a static group between the forward transform and the
+// coupling: t_b = S_Y,b^* xhat_sigma into z4, which the coupling reads with S_X,b. The pool (the second half of the near field,
 // then the backward chunks) is one list of tickets in a fixed order, each one or more whole chunks,
 // that the CTAs take from through a global counter once their static list is issued. A CTA whose
 // static part ran slowly takes fewer tickets: the end times of the CTAs differ by about one
@@ -46,6 +48,10 @@ constexpr int kStreamMaxCols = 512;     // largest column count of an item
 constexpr int kStageBytes = 69632;      // an item's tile and inputs (inputs at the tile's end)
 constexpr int kMaxRuns = 6;
 constexpr int kStreamHpMax = 64;
+// Rows of a chunk of t_b = S_Y,b^* xhat_sigma (kScatterZ4): up to one row per consumer thread, so
+// that the stacked rows of a column cluster fill few chunks (their chunk ends scatter directly).
+constexpr int kStreamHpTall = 256;
+static_assert(kStreamHpTall <= kStreamConsumers, "one output row per consumer thread");
 // Pool descriptors are fetched into the ring in segments of at most kPoolSeg items, one segment
 // ahead of the items being issued.
 constexpr int kPoolSeg = 16;
@@ -96,7 +102,8 @@ using StreamSmemStd = StreamSmem<kStages, kStageBytes, 16>;
 using StreamSmemMixed = StreamSmem<kStagesMixed, kStageBytesMixed, 32>;
 
 // Input vectors a run can read.
-enum : int8_t { kSrcXp = 0, kSrcZ1 = 1, kSrcZ2 = 2, kSrcZ3 = 3 };
+enum : int8_t { kSrcXp = 0, kSrcZ1 = 1, kSrcZ2 = 2, kSrcZ3 = 3, kSrcZ4 = 4 };
+constexpr int kNumSources = 5;
 
 struct Run {
   int32_t start;   // first element (a multiple of the 16-byte element count)
@@ -113,19 +120,27 @@ static_assert(sizeof(Run) == 8, "Run layout");
 // group counters, through a later chunk of those groups), and added to the outputs.
 enum : int16_t { kItemFirst = 1, kItemLast = 2, kItemBase = 4 };
 constexpr int kDepShift = 8;
-enum : int { kCounterPermute = 0, kCounterForward = 1, kCounterCoupling = 2, kNumCounters = 3 };
+enum : int { kCounterPermute = 0, kCounterForward = 1, kCounterCoupling = 2, kCounterCouplingY = 3, kNumCounters = 4 };
 // WorkItem::counter of a chunk that releases its own flag (number naux) instead of a group counter.
 constexpr int kCounterFlag = 15;
 // Layout of the counter array: group counters, the pool ticket, then the flags.
 constexpr int kTicketIndex = kNumCounters;
 constexpr int kFlagBase = kNumCounters + 1;
 
-// Chunk outputs: kToZ1..kToZ3 write z[dst + r]; kToY writes y[perm[dst + r]]; kScatterZ1 / kScatterZ2 write output r to
-// z[e.dst + r - e.lo] for every scatter entry e with e.lo <= r < e.hi (the chunk's entries are
+// Chunk outputs: kToZ1..kToZ3 write z[dst + r]; kToY writes y[perm[dst + r]]; kScatterZ1 / kScatterZ2 /
+// kScatterZ4 write output r to z[e.dst + r - e.lo] for every scatter entry e with e.lo <= r < e.hi (the chunk's entries are
 // scatter[aux .. aux + naux)): each consumer chunk then finds its inputs in one contiguous run.
 // counter >= 0: the chunk's completion is added to that group counter.
 // kEnd: written by a CTA's producer after its last item (never packed).
-enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kScatterZ1 = 5, kScatterZ2 = 6, kEnd = 7 };
+enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kScatterZ1 = 5, kScatterZ2 = 6, kEnd = 7, kScatterZ4 = 8 };
+#ifdef __CUDACC__
+#define UH_HOST_DEVICE __host__ __device__
+#else
+#define UH_HOST_DEVICE
+#endif
+UH_HOST_DEVICE constexpr bool is_scatter(int kind) {
+  return kind == kScatterZ1 || kind == kScatterZ2 || kind == kScatterZ4;
+}
 
 struct Scatter {
   int32_t dst;
@@ -186,9 +201,10 @@ struct StreamParams {
   const int32_t* perm;       // position -> original index
   const Scatter* scatter;    // scatter entries of the scatter kinds
   void* xp;                  // x in cluster order (kSrcXp)
-  void* z1;                  // xhat or t_b (kSrcZ1)
+  void* z1;                  // xhat (UH) or t_b (H) (kSrcZ1)
   void* z2;                  // yhat (kSrcZ2)
   void* z3;                  // near-field partials of row tiles (base of the backward chunks)
+  void* z4;                  // t_b = S_Y,b^* xhat_sigma of the blocks stored factored (kSrcZ4)
   uint32_t* status;          // nonzero after a bounded wait ran out
   long long timeout_cycles;  // bound of every wait, in SM clock cycles
 };

@@ -45,7 +45,7 @@ class UHDesc(C.Structure):
                 ("row_rank", _p), ("row_off", _p), ("U_data", _p), ("U_len", _i64),
                 ("col_rank", _p), ("col_off", _p), ("V_data", _p), ("V_len", _i64),
                 ("n_adm", _i64), ("adm_row", _p), ("adm_col", _p), ("S_off", _p), ("S_data", _p),
-                ("S_len", _i64), ("dense", DenseDesc)]
+                ("S_len", _i64), ("dense", DenseDesc), ("S_rank", _p)]
 
 
 class HDesc(C.Structure):
@@ -65,7 +65,8 @@ class Stats(C.Structure):
                 ("n_launches", _i32), ("n_items", _i64),
                 ("matmat_mode", _i32), ("panel_bytes", _i64), ("panel_items", _i64),
                 ("panel_mma_flops", _i64), ("pack_tile_bytes", _i64), ("pack_item_cost", _i64),
-                ("pack_chunk_cost", _i64), ("pack_pool_unit", _i64)]
+                ("pack_chunk_cost", _i64), ("pack_pool_unit", _i64), ("n_factored", _i64),
+                ("sum_factored_rank", _i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -202,6 +203,8 @@ def uh_desc_from_arrays(arrays: dict):
     d.S_off = _ptr(keep(arrays["S_off"], np.int64))
     S = _data(keep, arrays["S_data"], c128)
     d.S_data, d.S_len = _ptr(S), len(S)
+    if arrays.get("S_rank") is not None:
+        d.S_rank = _ptr(keep(arrays["S_rank"], np.int32))
     _dense(keep, d, arrays, c128)
     return d, keep
 
@@ -547,7 +550,8 @@ class HOp(_Op):
 
 class BuildParams(C.Structure):
     _fields_ = [("wavenumber", C.c_double), ("leaf", _i32), ("eta", C.c_double),
-                ("eps", C.c_double), ("tol_aca", C.c_double), ("nthreads", _i32), ("strong", _i32)]
+                ("eps", C.c_double), ("tol_aca", C.c_double), ("nthreads", _i32), ("strong", _i32),
+                ("factored", _i32)]
 
 
 class BuildInfo(C.Structure):
@@ -584,11 +588,12 @@ class HelmholtzModel:
     H form. The arrays live in the library; uh_op()/h_op() upload them to the GPU."""
 
     def __init__(self, points, wavenumber, leaf, eta, eps, tol_aca, nthreads: int = 0, strong: bool = False,
-                 device: bool = False):
-        """device=True: the construction runs on the current CUDA device (uhb_build_helmholtz_gpu)."""
+                 device: bool = False, factored: bool = False):
+        """device=True: the construction runs on the current CUDA device (uhb_build_helmholtz_gpu).
+        factored=True: coefficient matrices stored factored where smaller (uhb_params.factored)."""
         pts = np.ascontiguousarray(points, dtype=np.float64)
         prm = BuildParams(float(wavenumber), int(leaf), float(eta), float(eps), float(tol_aca),
-                          int(nthreads), 1 if strong else 0)
+                          int(nthreads), 1 if strong else 0, 1 if factored else 0)
         h = _p()
         fn = lib.uhb_build_helmholtz_gpu if device else lib.uhb_build_helmholtz
         check(fn(len(pts), pts.ctypes.data, C.byref(prm), C.byref(h)), fn.__name__)
@@ -644,7 +649,8 @@ class HelmholtzModel:
                  adm_row=_view(d.adm_row, d.n_adm, np.int32),
                  adm_col=_view(d.adm_col, d.n_adm, np.int32),
                  S_off=_view(d.S_off, d.n_adm, np.int64),
-                 S_data=_view(d.S_data, d.S_len, np.complex128))
+                 S_data=_view(d.S_data, d.S_len, np.complex128),
+                 S_rank=_view(d.S_rank, d.n_adm, np.int32) if d.S_rank else None)
         a.update(self._dense_arrays(d.dense))
         return {k: (v.copy() if copy and isinstance(v, np.ndarray) else v) for k, v in a.items()}
 

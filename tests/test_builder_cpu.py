@@ -83,3 +83,64 @@ def test_builder_rejects_bad_parameters(U):
     pts[3, 1] = np.nan
     with pytest.raises(U.UHError, match="not finite"):
         U.HelmholtzModel(pts, 1.0, 16, 1.0, 1e-6, 1e-8)
+
+
+def _factored_view(a):
+    """The factored blocks of a builder's UH arrays: {(tau, sigma): (S_X, S_Y)}."""
+    F = {}
+    for i in np.flatnonzero(a["S_rank"] >= 0):
+        t, s, o, kb = int(a["adm_row"][i]), int(a["adm_col"][i]), int(a["S_off"][i]), int(a["S_rank"][i])
+        lt, ls = int(a["row_rank"][t]), int(a["col_rank"][s])
+        F[(t, s)] = (a["S_data"][o:o + lt * kb].reshape(kb, lt).T,
+                     a["S_data"][o + lt * kb:o + kb * (lt + ls)].reshape(kb, ls).T)
+    return F
+
+
+@pytest.mark.parametrize("case", [(2048, 4.0, 32, 1e-6, (1.0, 1.0, 1.0), 0.0),
+                                  (1000, 6.0, 24, 1e-5, (1.0, 0.7, 0.4), 0.01)],
+                         ids=["sphere2048", "ellipsoid1000"])
+def test_builder_factored_option(U, case):
+    """uhb_params.factored (Section 4.2, reading R11): the same bases and partition as the dense
+    build; each factored block keeps the rank rule of a plain SVD of the dense S_b at eps (within
+    one, a value decided within rounding), has its spectral error within eps s_1 and is stored only
+    where k (l_tau + l_sigma) < l_tau l_sigma; a dense-kept block would not have been smaller at a rank within one of the rule's;
+    the factored operator applies within 10 eps of the oracle's."""
+    n, k, leaf, eps, axes, noise = case
+    pts, tree, hf, h, uh = oracle_ops(n, k, leaf, 1.0, eps, 1e-8, axes, noise)
+    md = U.HelmholtzModel(pts, k, leaf, 1.0, eps, 1e-8, nthreads=2)
+    mf = U.HelmholtzModel(pts, k, leaf, 1.0, eps, 1e-8, nthreads=2, factored=True)
+    ad, af = md.uh_arrays(), mf.uh_arrays()
+    assert ad.get("S_rank") is None and af["S_rank"] is not None
+    for key in ("row_rank", "col_rank", "adm_row", "adm_col", "U_data", "V_data", "D_data"):
+        assert np.array_equal(ad[key], af[key]), key
+    Ub, Vb, Sd, near = _oracle_view(ad)
+    F = _factored_view(af)
+    assert len(F) > len(Sd) // 10
+    for b, Sb in Sd.items():
+        if Sb.size == 0:
+            continue
+        s = np.linalg.svd(Sb, compute_uv=False)
+        kr = int(np.sum(s > eps * s[0])) if s[0] > 0 else 0
+        lt, ls = Sb.shape
+        if b in F:
+            X, Y = F[b]
+            assert abs(X.shape[1] - kr) <= 1 and X.shape[1] * (lt + ls) < lt * ls
+            assert np.linalg.norm(Sb - X @ Y.conj().T, 2) <= 1.01 * eps * s[0] + 1e-15
+        else:
+            assert (kr + 1) * (lt + ls) >= lt * ls
+    built = O.UHMatrix(uh.tree, uh.adm, uh.dense, Ub, Vb, {b: S for b, S in Sd.items() if b not in F}, near,
+                       {}, {}, F=F)
+    x = I.complex_normal(n, 7)
+    assert relerr(O.uh_matvec(built, x), O.uh_matvec(uh, x)) < 10 * eps
+    md.close()
+    mf.close()
+
+
+def test_builder_rejects_bad_factored_flag(U):
+    import ctypes as C
+    pts = np.ascontiguousarray(I.fibonacci_sphere(64))
+    h = C.c_void_p()
+    for strong, factored in ((0, 2), (3, 0)):
+        prm = U.BuildParams(1.0, 16, 1.0, 1e-6, 1e-8, 0, strong, factored)
+        assert U.lib.uhb_build_helmholtz(64, pts.ctypes.data, C.byref(prm), C.byref(h)) == U.UH_EINVAL
+        assert h.value is None

@@ -7,6 +7,7 @@ import re
 import numpy as np
 import pytest
 
+from oracle import uh_oracle as O
 from tests.uh_testutil import h_arrays, oracle_ops, uh_arrays
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -248,3 +249,54 @@ def test_block_apply_noalloc_argument_checks(uh):
         rc = uh.lib.uh_block_apply_noalloc(mm, nn, 1, 1, 16, mm, 16, 1, 16, nn, 16, 16,
                                            uh.UH_PREC_C128, None)
         assert rc == uh.UH_EINVAL and "above the limit" in uh.lib.uh_last_error().decode()
+
+
+def _factored_arrays(n, k, leaf, eps, f=1.0):
+    """An oracle operator with its coefficient matrices stored factored where smaller (Section
+    4.2, recompressed at f * eps), flattened into the descriptor arrays (S_rank set)."""
+    axes, noise = ((1.0, 0.7, 0.4), 0.01) if n == 1000 else ((1.0, 1.0, 1.0), 0.0)
+    _, _, hf, h, op = oracle_ops(n, k, leaf, 1.0, eps, 1e-8, axes, noise)
+    return uh_arrays(O.factor_coupling(op, f * eps))
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("ncta", [152, 7, 1])
+@pytest.mark.parametrize("case", [(2048, 4.0, 32, 1e-6, 1.0), (1000, 6.0, 24, 1e-5, 3.0), (2048, 4.0, 32, 1e-6, 30.0)])
+def test_factored_packing_self_check_passes(uh, prec, ncta, case):
+    """Operators with factored and dense coefficient matrices (the t_b group, z4 and its scatter)
+    are packed and every kernel address checked, for the streaming and the tensor-core programs."""
+    a = _factored_arrays(*case)
+    assert a["S_rank"] is not None and (a["S_rank"] >= 0).any()
+    desc, keep = uh.uh_desc_from_arrays(a)
+    rc = uh.lib.uh_pack_check(C.byref(desc), prec, ncta)
+    assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()
+
+
+@pytest.mark.parametrize("ncta", [152, 7])
+def test_factored_batch_packing_self_check_passes(uh, ncta):
+    """A batch mixing operators with and without factored coefficients."""
+    arrays = _batch_arrays()[:3] + [_factored_arrays(2048, 4.0, 32, 1e-6), _factored_arrays(1000, 6.0, 24, 1e-5, 3.0)]
+    built = [uh.uh_desc_from_arrays(a) for a in arrays]
+    arr = uh._desc_array([d for d, _ in built])
+    for prec in (0, 1):
+        rc = uh.lib.uh_batch_pack_check(arr, len(built), prec, ncta)
+        assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()
+
+
+def test_rejects_bad_factored_ranks(uh):
+    a = _factored_arrays(1000, 6.0, 24, 1e-5, 3.0)
+    i = int(np.flatnonzero(a["S_rank"] > 0)[0])
+    b = dict(a)
+    b["S_rank"] = a["S_rank"].copy()
+    b["S_rank"][i] = -2
+    _expect_einval(uh, b, "S_rank")
+    c = dict(a)
+    c["S_rank"] = a["S_rank"].copy()
+    r = int(a["row_rank"][a["adm_row"][i]])
+    s = int(a["col_rank"][a["adm_col"][i]])
+    c["S_rank"][i] = min(r, s) + 1
+    _expect_einval(uh, c, "S_rank")
+    d = dict(a)
+    d["S_off"] = a["S_off"].copy()
+    d["S_off"][i] = len(a["S_data"]) - 1  # the factors would run past the end of S_data
+    _expect_einval(uh, d, "coupling matrix")

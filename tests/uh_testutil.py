@@ -46,16 +46,24 @@ def uh_arrays(uh: O.UHMatrix, dtype=np.complex128) -> dict:
     a = _tree_arrays(tree)
     a["row_rank"], a["row_off"], a["U_data"] = _pack(uh.U, tree.n_clusters)
     a["col_rank"], a["col_off"], a["V_data"] = _pack(uh.V, tree.n_clusters)
-    keys = sorted(uh.S)
-    offs, parts, pos = [], [], 0
+    keys = sorted(list(uh.S) + list(uh.F))
+    offs, parts, ranks, pos = [], [], [], 0
     for b in keys:
         offs.append(pos)
-        parts.append(uh.S[b].ravel(order="F"))
-        pos += uh.S[b].size
+        if b in uh.F:  # factored: S_X then S_Y, both column-major
+            X, Y = uh.F[b]
+            parts += [X.ravel(order="F"), Y.ravel(order="F")]
+            pos += X.size + Y.size
+            ranks.append(X.shape[1])
+        else:
+            parts.append(uh.S[b].ravel(order="F"))
+            pos += uh.S[b].size
+            ranks.append(-1)
     a["adm_row"] = np.array([b[0] for b in keys], np.int32)
     a["adm_col"] = np.array([b[1] for b in keys], np.int32)
     a["S_off"] = np.array(offs, np.int64)
     a["S_data"] = np.concatenate(parts) if parts else np.zeros(0, np.complex128)
+    a["S_rank"] = np.array(ranks, np.int32) if uh.F else None
     a.update(_dense_arrays(uh.near))
     for k in ("U_data", "V_data", "S_data", "D_data"):
         a[k] = a[k].astype(dtype)
@@ -112,5 +120,6 @@ def stored_c64(uh: O.UHMatrix) -> O.UHMatrix:
     """The operator a complex64 op stores: every entry of U, V, S and the dense blocks rounded to
     complex64 (round to nearest), held in complex128 so the oracle applies it in FP64."""
     r = lambda d: {k: v.astype(np.complex64).astype(np.complex128) for k, v in d.items()}  # noqa: E731
+    F = {b: tuple(m.astype(np.complex64).astype(np.complex128) for m in xy) for b, xy in uh.F.items()}
     return O.UHMatrix(uh.tree, uh.adm, uh.dense, r(uh.U), r(uh.V), r(uh.S), r(uh.near),
-                      uh.row_sv, uh.col_sv)
+                      uh.row_sv, uh.col_sv, F=F)
