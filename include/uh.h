@@ -312,8 +312,10 @@ int uh_batch_stats(const uh_batch* batch, uh_stats_t* out);
  * A server runs GMRES(restart) solves A x = b with resident UH ops (the paper's application of
  * the product: solving the boundary integral equation, Sections 1 and 7). Solves are admitted in
  * submission order while their device workspace ((restart + 4) n complex128 values and a little
- * more) fits in the budget and fewer than max_active run, and are advanced together in rounds
- * (one step of every running solve per round: continuous batching). In a solve the operator's
+ * more) fits in the budget and fewer than max_active run, and run together (continuous
+ * batching): each running solve's next step is queued on the GPU as soon as its previous step
+ * has completed, on a stream of its own, so the steps of different solves overlap and none waits
+ * for another's. In a solve the operator's
  * products run in its precision (complex64 storage with FP32 accumulation for UH_PREC_C64 ops);
  * the residual r = b - A x recomputed at every restart, the Arnoldi orthogonalisation (classical
  * Gram-Schmidt, two passes), the norms and the update x += V y run in FP64 on the GPU. A solve

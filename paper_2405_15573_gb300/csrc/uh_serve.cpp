@@ -1,13 +1,16 @@
 // Serving runtime: GMRES(m) solves A x = b with resident UH operators, admitted by device-memory
 // footprint and advanced together in rounds (continuous batching).
 //
-// One worker thread owns one CUDA stream per running solve. Each round it admits queued solves
-// while the admitted footprint stays within the budget and fewer than max_active are running,
-// then issues ONE step of every active solve (asynchronous, each on its solve's stream, so the
-// small vector kernels of different solves overlap), synchronises, and updates the solves' small
-// host-side state (Givens rotations of the Hessenberg matrix, convergence). The products of one
-// operator are chained across streams by an event in launch order: they share the operator's
-// scratch and its per-call group counters. A solve
+// One worker thread owns one CUDA stream and one completion event per running solve. It admits
+// queued solves while the admitted footprint stays within the budget and fewer than max_active
+// are running, and keeps every running solve's next step queued on the GPU: a solve's step (its
+// product and vector kernels, asynchronous on its own stream, then a small device-to-host copy
+// and its completion event) is issued as soon as the worker sees that solve's previous step
+// complete (event query) and has updated the solve's small host-side state (Givens rotations of
+// the Hessenberg matrix, convergence), independently of the other solves. So the GPU always has
+// the other solves' steps queued while the host handles one, and a slow step holds back only its
+// own solve. The products of one operator are chained across streams by an event in launch
+// order: they share the operator's scratch and its per-call group counters. A solve
 // is restarted GMRES with its matrix-vector products in the operator's precision (complex64
 // storage, FP32 accumulation for UH_PREC_C64 ops) and everything else in FP64 on the GPU: the
 // true residual r = b - A x at every restart (its product in extended precision on the
@@ -76,8 +79,10 @@ struct Solve {
   cd *hh1 = nullptr, *hh2 = nullptr, *hy = nullptr, *hx = nullptr;
   double* hscal = nullptr;
   bool v32_ready = false;  // v32 holds complex64(V_j) for the next Arnoldi step
-  int slot = -1;           // index of the solve's stream
+  int slot = -1;           // index of the solve's stream and event
   cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;  // recorded after each issued step
+  bool inflight = false;     // a step is issued and its event not yet seen complete
   // GMRES state
   Phase phase = kStart;
   bool x_zero = true;
@@ -104,6 +109,7 @@ struct uh_server {
   int64_t budget = 0, used = 0;
   int queue_cap = 64;
   std::vector<cudaStream_t> streams;          // one per running solve (slots)
+  std::vector<cudaEvent_t> events;            // completion of the slot's last issued step
   std::vector<char> slot_used;
   std::mutex mu;
   std::condition_variable cv;
@@ -366,10 +372,41 @@ void after(Solve* s) {
   }
 }
 
+// Issues solve s's next step and records its completion event; a failure ends the solve.
+void issue_step(uh_server* sv, Solve* s) {
+  int rc = UH_OK;
+  if (!s->has_ws) rc = start_solve(sv, s, s->st);
+  if (!rc) rc = issue(s, s->st);
+  if (!rc && cudaEventRecord(s->ev, s->st) != cudaSuccess) rc = UH_ECUDA;
+  if (rc) {
+    s->status = rc;
+    s->phase = kDone;
+    s->inflight = false;
+    return;
+  }
+  s->inflight = true;
+}
+
+// Ends the solves still running when the server stops (after their streams drain).
+void abort_active(uh_server* sv) {
+  for (Solve* s : sv->active) {
+    if (s->st) cudaStreamSynchronize(s->st);
+    release_workspace(sv, s);
+    if (s->phase != kDone) s->status = UH_ECUDA;
+    s->phase = kDone;
+    s->inflight = false;
+  }
+  sv->active.clear();
+  for (Workspace& w : sv->spare) free_workspace(w);
+  sv->spare.clear();
+}
+
 void worker_main(uh_server* sv) {
   cudaSetDevice(sv->device);
+  std::vector<Solve*> running, fresh;
+  int idle = 0;
   for (;;) {
-    std::vector<Solve*> round;
+    fresh.clear();
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       while (!sv->pending.empty() && static_cast<int>(sv->active.size()) < sv->max_active &&
@@ -383,78 +420,71 @@ void worker_main(uh_server* sv) {
             sv->slot_used[k] = 1;
             s->slot = k;
             s->st = sv->streams[k];
+            s->ev = sv->events[k];
             break;
           }
         sv->active.push_back(s);
+        fresh.push_back(s);
+      }
+      if (sv->stop) {
+        abort_active(sv);
+        return;
       }
       if (sv->active.empty()) {
-        if (sv->stop) {
-          for (Workspace& w : sv->spare) free_workspace(w);
-          sv->spare.clear();
-          return;
-        }
         sv->cv.wait_for(lk, std::chrono::milliseconds(20));
         continue;
       }
-      if (sv->stop) {
-        for (Solve* s : sv->active) {
-          release_workspace(sv, s);
-          s->status = UH_ECUDA;
-          s->phase = kDone;
-        }
-        sv->active.clear();
-        for (Workspace& w : sv->spare) free_workspace(w);
-        sv->spare.clear();
-        return;
-      }
-      round = sv->active;
+      running = sv->active;
     }
-    // Allocate new solves' workspaces, then issue one step of every active solve.
-    for (Solve* s : round) {
-      if (s->phase == kDone) continue;
-      if (!s->has_ws) {
-        const int rc = start_solve(sv, s, s->st);
-        if (rc) {
-          s->status = rc;
-          s->phase = kDone;
-          continue;
-        }
-      }
-      const int rc = issue(s, s->st);
-      if (rc) {
-        s->status = rc;
-        s->phase = kDone;
-      }
-    }
-    cudaError_t e = cudaSuccess;
-    for (Solve* s : round) {
-      const cudaError_t es = cudaStreamSynchronize(s->st);
-      if (es != cudaSuccess) e = es;
-    }
-    for (Solve* s : round) {
-      if (e != cudaSuccess && s->phase != kDone) {
+    bool progress = !fresh.empty();
+    // newly admitted solves: workspace, then their first step
+    for (Solve* s : fresh) issue_step(sv, s);
+    // every solve whose step has completed: host-side update, then its next step at once
+    for (Solve* s : running) {
+      if (s->phase == kDone || !s->inflight) continue;
+      const cudaError_t q = cudaEventQuery(s->ev);
+      if (q == cudaErrorNotReady) continue;
+      progress = true;
+      s->inflight = false;
+      if (q != cudaSuccess) {
         s->status = UH_ECUDA;
         s->phase = kDone;
+        continue;
       }
-      if (s->phase == kDone) continue;
       after(s);
-      // A finished solve: did a bounded wait of one of the op's products run out meanwhile (a
-      // GPU that could not run a product's CTAs together)?
-      if (s->phase == kDone && s->status == UH_OK && uh_check(s->op, s->st) != UH_OK) s->status = UH_ETIMEOUT;
-    }
-    std::lock_guard<std::mutex> lk(sv->mu);
-    std::vector<Solve*> still;
-    for (Solve* s : sv->active) {
       if (s->phase == kDone) {
-        s->t_done = now_s();
-        release_workspace(sv, s);
-        sv->used -= s->footprint;
-        if (s->slot >= 0) sv->slot_used[s->slot] = 0;
-      } else {
-        still.push_back(s);
+        // did a bounded wait of one of the op's products run out meanwhile (a GPU that could not
+        // run a product's CTAs together)?
+        if (s->status == UH_OK && uh_check(s->op, s->st) != UH_OK) s->status = UH_ETIMEOUT;
+        continue;
       }
+      issue_step(sv, s);
     }
-    sv->active.swap(still);
+    bool finished = false;
+    for (Solve* s : running) finished = finished || s->phase == kDone;
+    if (finished) {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      std::vector<Solve*> still;
+      for (Solve* s : sv->active) {
+        if (s->phase == kDone) {
+          s->t_done = now_s();
+          release_workspace(sv, s);
+          sv->used -= s->footprint;
+          if (s->slot >= 0) sv->slot_used[s->slot] = 0;
+        } else {
+          still.push_back(s);
+        }
+      }
+      sv->active.swap(still);
+    }
+    // Nothing completed: let the GPU work (yield; after a long idle stretch, a short sleep).
+    if (progress) {
+      idle = 0;
+    } else if (++idle < 2000) {
+      std::this_thread::yield();
+    } else {
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
   }
 }
 
@@ -475,14 +505,18 @@ int uh_server_create(int32_t max_active, int64_t hbm_budget_bytes, int32_t queue
   sv->queue_cap = queue_capacity;
   bool ok = cudaGetDevice(&sv->device) == cudaSuccess;
   sv->streams.assign(max_active, nullptr);
+  sv->events.assign(max_active, nullptr);
   sv->slot_used.assign(max_active, 0);
   for (int k = 0; ok && k < max_active; ++k)
-    ok = cudaStreamCreateWithFlags(&sv->streams[k], cudaStreamNonBlocking) == cudaSuccess;
+    ok = cudaStreamCreateWithFlags(&sv->streams[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&sv->events[k], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     for (cudaStream_t st : sv->streams)
       if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : sv->events)
+      if (ev) cudaEventDestroy(ev);
     delete sv;
-    return fail(UH_ECUDA, "stream creation failed");
+    return fail(UH_ECUDA, "stream or event creation failed");
   }
   sv->worker = std::thread(worker_main, sv);
   *out = sv;
@@ -499,6 +533,7 @@ int uh_server_destroy(uh_server* sv) {
   sv->cv.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
   for (cudaStream_t st : sv->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : sv->events) cudaEventDestroy(ev);
   delete sv;
   return UH_OK;
 }

@@ -499,6 +499,8 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
   T acc[EPL];
   T base = T{0, 0};
   int out_idx = 0;
+  static_assert(kStreamConsumers >= 256, "a chunk's first 256 scatter entries, one per consumer thread");
+  Scatter my_scat{};  // this thread's scatter entry of the current chunk (entry tid, if any)
   int need = 1, lanes = 1, groups = kStreamConsumers, lane = 0, g = tid, hpl = EPL;
   const int warp = tid >> 5;
   int nchunk = 0;  // reduced chunks so far: their parity selects the chunk-end buffers
@@ -540,10 +542,9 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
     T* sred = reinterpret_cast<T*>(smem + L::red) + rb * (kStreamConsumers * EPL);
     Scatter* sscat = reinterpret_cast<Scatter*>(smem + L::scat) + rb * 256;
     T* svals = reinterpret_cast<T*>(smem + L::vals) + rb * 64;
-    if ((flags & kItemFirst) && is_scatter(kind)) {
-      // the chunk's scatter entries, used at its end
-      for (int k = tid; k < naux && k < 256; k += kStreamConsumers) sscat[k] = p.scatter[aux + k];
-    }
+    // The chunk's scatter entries (one per thread), loaded now into a register and stored to
+    // shared memory at the chunk end, so that the load's latency overlaps the chunk's items.
+    if ((flags & kItemFirst) && is_scatter(kind) && tid < naux && tid < 256) my_scat = p.scatter[aux + tid];
     // the output's original index: loaded now, used at the end of the chunk
     if ((flags & kItemFirst) && tid < h && kind == kToY) out_idx = p.perm[dst + tid];
     if (flags & kItemFirst) {
@@ -602,6 +603,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
 #pragma unroll
         for (int e = 0; e < EPL; ++e) sred[part * hpl + lane * EPL + e] = acc[e];
       }
+      if (is_scatter(kind) && tid < naux && tid < 256) sscat[tid] = my_scat;
       consumer_sync();
       if (tid < h) {
         T v = sred[tid];
