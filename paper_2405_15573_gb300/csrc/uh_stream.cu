@@ -541,7 +541,6 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
     const int rb = nchunk & 1;
     T* sred = reinterpret_cast<T*>(smem + L::red) + rb * (kStreamConsumers * EPL);
     Scatter* sscat = reinterpret_cast<Scatter*>(smem + L::scat) + rb * 256;
-    T* svals = reinterpret_cast<T*>(smem + L::vals) + rb * 64;
     // The chunk's scatter entries (one per thread), loaded now into a register and stored to
     // shared memory at the chunk end, so that the load's latency overlaps the chunk's items.
     if ((flags & kItemFirst) && is_scatter(kind) && tid < naux && tid < 256) my_scat = p.scatter[aux + tid];
@@ -605,14 +604,36 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
       }
       if (is_scatter(kind) && tid < naux && tid < 256) sscat[tid] = my_scat;
       consumer_sync();
-      if (tid < h) {
-        T v = sred[tid];
-        for (int q = 1; q < parts; ++q) v = cadd(v, sred[q * hpl + tid]);
+      // Output r of the chunk: its partials summed in a fixed order (at most 8 of them; the loads
+      // are independent and issued together).
+      auto row_sum = [&](int r) -> T {
+        T v = sred[r];
+#pragma unroll
+        for (int q = 1; q < kStreamConsumerWarps; ++q)
+          if (q < parts) v = cadd(v, sred[q * hpl + r]);
+        return v;
+      };
+      if (is_scatter(kind) && h <= kStreamHpMax) {
+        // (entry, row) pairs over all consumer threads, each entry's rows consecutive; a thread
+        // sums the row of each pair it stores, so no second barrier is needed.
+        T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : kind == kScatterZ2 ? p.z2 : p.z4);
+        int k = tid / h, r = tid - k * h;
+        const int dk = kStreamConsumers / h, dr = kStreamConsumers - dk * h;
+        for (int w = tid; w < naux * h; w += kStreamConsumers) {
+          const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];
+          if (r >= e.lo && r < e.hi) z[e.dst + r - e.lo] = row_sum(r);
+          k += dk;
+          r += dr;
+          if (r >= h) {
+            r -= h;
+            ++k;
+          }
+        }
+      } else if (tid < h) {
+        T v = row_sum(tid);
         if (flags & kItemBase) v = cadd(v, base);
         if (kind == kToY) {
           static_cast<TX*>(p.y)[out_idx] = to_x(v, static_cast<TX*>(nullptr));
-        } else if (is_scatter(kind) && h <= kStreamHpMax) {
-          svals[tid] = v;
         } else if (is_scatter(kind)) {
           // a tall chunk (t_b rows, up to kStreamHpTall): each thread stores its own row to every
           // scatter entry holding it (few entries: one per block in the chunk)
@@ -626,18 +647,8 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
           z[dst + tid] = v;
         }
       }
-      if (is_scatter(kind) && h <= kStreamHpMax) {
-        consumer_sync();  // svals written
-        // (entry, row) pairs over all consumer threads: each entry's rows are consecutive
-        T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : kind == kScatterZ2 ? p.z2 : p.z4);
-        for (int w = tid; w < naux * h; w += kStreamConsumers) {
-          const int k = w / h, r = w - k * h;
-          const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];
-          if (r >= e.lo && r < e.hi) z[e.dst + r - e.lo] = svals[r];
-        }
-      }
-      // sred, svals and sscat of this parity are next written two chunks on, after the next
-      // chunk end's barrier.
+      // sred and sscat of this parity are next written two chunks on, after the next chunk end's
+      // barrier.
       ++nchunk;
       // On failure the abort flag is set; the leader's next wait then ends the loop for all.
       if (counter >= 0)

@@ -89,8 +89,7 @@ struct StreamSmem {
   static constexpr int red = Stages * StageBytes;                // group reduction [2], one slot per consumer thread
   static constexpr int desc = red + 2 * kStreamConsumers * RedSlot;  // descriptor ring, 96 B each
   static constexpr int scat = desc + kDescRing * 96;             // scatter entries of a chunk [2] (256 x 8 B)
-  static constexpr int vals = scat + 2 * 256 * 8;                 // a chunk's outputs before they are scattered [2]
-  static constexpr int bars = vals + 2 * 64 * 16;                 // full, empty [Stages], desc [kDescBatches],
+  static constexpr int bars = scat + 2 * 256 * 8;                 // full, empty [Stages], desc [kDescBatches],
                                                                   // pub_full, pub_empty [kPubRing], pool [2]
   static constexpr int misc = bars + (2 * Stages + kDescBatches + 2 * kPubRing + 2) * 8;  // abort flag, decision words
   static constexpr int pub = misc + 32;                           // group counter of each release [kPubRing]
