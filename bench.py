@@ -182,7 +182,8 @@ def _oracle_child(npz_path: str, out_path: str, seconds: float, min_reps: int, w
 def dump_operator(model, x: np.ndarray, directory: str) -> None:
     """Write the UH descriptor arrays (and x) as .npy files, straight from the builder's memory."""
     for k, v in model.uh_arrays(copy=False).items():
-        np.save(os.path.join(directory, k + ".npy"), np.asarray(v))
+        if v is not None:  # S_rank is None for dense coefficient matrices
+            np.save(os.path.join(directory, k + ".npy"), np.asarray(v))
     np.save(os.path.join(directory, "x.npy"), x)
 
 
@@ -230,7 +231,7 @@ def timed_back_to_back(op, x, y, steps, torch):
     return a.elapsed_time(b) / steps
 
 
-# DRAM bytes (read + write) that ncu counted for one launch of stream_kernel<KC64> on the
+# DRAM bytes (read + write) that ncu counted for one launch of the complex64 stream kernel on the
 # N=32768 sphere workload (cold L2), and digests of the code (kernel, packer and program
 # construction, comments aside) it was taken on. The figure is reported only while that code is
 # unchanged.
@@ -705,7 +706,9 @@ def gpu_arm(args):
                 "d2h_bytes_per_step": int(y.numel() * 8)},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "peak_kind": peak_kind, "traffic": traffic,
-                     "kernel": "stream_kernel<KC64> (complex64; one persistent launch per matvec)",
+                     "kernel": ("stream_kernel<KC64Dual> (complex64, two CTAs per SM" if st["pack_ctas_per_sm"] == 2
+                                else "stream_kernel<KC64> (complex64, one CTA per SM") +
+                               "; one persistent launch per matvec)",
                      "algo_bytes_per_matvec": st["algo_bytes_matvec"],
                      "frac_of_nominal_8000": gbs / 8000.0,
                      "l2_flushed": {"achieved": st["algo_bytes_matvec"] / (statistics.mean(t_uh_fl) * 1e-3) / 1e9,

@@ -160,6 +160,10 @@ typedef struct uh_op uh_op;
  * Uses the current CUDA device; the op must be used and destroyed with that device current.
  */
 int uh_create(const uh_desc* desc, int32_t precision, uh_op** out);
+/* uh_create with packing parameters for the streaming program (uh_pack_params below; NULL: the
+ * defaults, as uh_create). UH_EINVAL for parameters out of range, or two CTAs per SM with
+ * UH_PREC_C128. */
+int uh_create_ex(const uh_desc* desc, int32_t precision, const struct uh_pack_params_s* params, uh_op** out);
 
 /* Free all device and host memory of the op. NULL is accepted. Synchronises the device. */
 int uh_destroy(uh_op* op);
@@ -232,6 +236,7 @@ typedef struct {
   int64_t pack_item_cost;
   int64_t pack_chunk_cost;
   int64_t pack_pool_unit;
+  int64_t pack_ctas_per_sm;   /* CTAs of the streaming kernel per SM */
   int64_t n_factored;         /* coupling matrices stored factored (uh_desc.S_rank >= 0) */
   int64_t sum_factored_rank;  /* K: sum of their inner ranks k */
 } uh_stats_t;
@@ -267,8 +272,12 @@ int uh_batch_create(const uh_desc* const* descs, int32_t count, int32_t precisio
  *              (default 131072)
  * Costs are in bytes streamed in the same time.
  */
-typedef struct {
+typedef struct uh_pack_params_s {
   int32_t tile_bytes, item_cost, chunk_cost, pool_unit;
+  int32_t ctas_per_sm; /* 1 or 2 CTAs of the streaming kernel per SM (2: complex64 programs only,
+                          tiles up to 24 KB in three 26 KB stages, so that the per-item and
+                          per-chunk latencies of two CTAs overlap on an SM); 0: automatic, two for
+                          complex64 operators streaming at least 256 MiB per product, else one */
 } uh_pack_params;
 
 /* uh_batch_create with packing parameters (NULL: the defaults). */
@@ -279,9 +288,10 @@ int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t preci
  * Autotuner of the batched product: packs an evenly spaced sample of `sample` of the operators
  * (all of them for sample <= 0 or >= count) with candidate parameters, times `reps` back-to-back
  * products of each on `stream` (CUDA events, after 3 warm-up products; zero vectors), and returns
- * the fastest parameters in *best: one pass of coordinate descent over tile_bytes {16, 32, 64 KB},
- * item_cost {1, 4, 16 KB}, chunk_cost {12, 48, 192 KB} and pool_unit {32, 128, 512 KB} from the
- * defaults, a change kept when it is at least 1% faster. *default_ms / *best_ms (optional): the
+ * the fastest parameters in *best: one pass of coordinate descent over ctas_per_sm {1, 2}
+ * (complex64), tile_bytes {16, 32, 64 KB}, item_cost {1, 4, 16 KB}, chunk_cost {12, 48, 192 KB} and
+ * pool_unit {32, 128, 512 KB} from the defaults (ctas_per_sm automatic), a change kept when it is at
+ * least 1% faster. *default_ms / *best_ms (optional): the
  * mean product time with the defaults / with *best. Allocates and frees its own batches and
  * vectors; blocks until done. Pass *best to uh_batch_create_ex for the whole set.
  */

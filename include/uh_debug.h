@@ -22,6 +22,8 @@ int h_pack_check(const h_desc* desc, int32_t precision, int32_t ncta);
 int uh_batch_pack_check(const uh_desc* const* descs, int32_t count, int32_t precision, int32_t ncta);
 int uh_batch_pack_check_ex(const uh_desc* const* descs, int32_t count, int32_t precision,
                            const uh_pack_params* params, int32_t ncta);
+/* uh_pack_check with packing parameters (as uh_create_ex); ncta = SMs x params->ctas_per_sm. */
+int uh_pack_check_ex(const uh_desc* desc, int32_t precision, const uh_pack_params* params, int32_t ncta);
 
 /*
  * Runs one uh_matvec whose dependency waits look for an epoch that no chunk ever publishes, so

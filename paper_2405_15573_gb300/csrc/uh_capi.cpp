@@ -205,6 +205,7 @@ struct OpBase {
   uh::PoolRange* d_pool = nullptr;
   int64_t pool_chunks = 0;
   int64_t perm_n = 0;  // positions of x permuted at the start of a product
+  bool dual = false;   // program packed for two CTAs per SM (uh::kGeomDual)
   int64_t counter_total[uh::kNumCounters] = {};
   uint32_t* d_status = nullptr;
   int32_t* d_perm = nullptr;
@@ -283,24 +284,62 @@ int upload(const void* host, size_t bytes, T** dev) {
 }
 
 // Number of CTAs of the persistent launch (one per SM when the kernel fits once per SM).
-int query_ncta(bool c128, int* ncta, int* device) {
+// Grid of the streaming kernel: SMs x CTAs per SM (dual: the two-CTA variants).
+int query_ncta(bool c128, int* ncta, int* device, bool dual = false) {
   CUDA_TRY(cudaGetDevice(device));
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, *device));
-  const int variant = c128 ? uh::kVarC128 : uh::kVarC64;
+  const int variant = c128 ? uh::kVarC128 : dual ? uh::kVarC64Dual : uh::kVarC64;
   CUDA_TRY(uh::stream_prepare(variant));
   int per = 0;
   CUDA_TRY(uh::stream_occupancy(variant, &per));
-  if (per < 1) return fail(UH_ECUDA, "streaming kernel does not fit on an SM");
+  if (per < (dual ? 2 : 1)) return fail(UH_ECUDA, "streaming kernel does not fit %d CTAs on an SM", dual ? 2 : 1);
+  per = dual ? 2 : 1;
   *ncta = sms * per;
   if (!c128) {
     // the extended-precision variant runs the same program on the same grid
-    CUDA_TRY(uh::stream_prepare(uh::kVarMixed));
+    const int vm = dual ? uh::kVarMixedDual : uh::kVarMixed;
+    CUDA_TRY(uh::stream_prepare(vm));
     int pm = 0;
-    CUDA_TRY(uh::stream_occupancy(uh::kVarMixed, &pm));
+    CUDA_TRY(uh::stream_occupancy(vm, &pm));
     if (pm < per) return fail(UH_ECUDA, "extended-precision streaming kernel does not fit the grid");
   }
   return UH_OK;
+}
+
+// Packing parameters from the C struct (zeros: the defaults), checked.
+int pack_params_from(const uh_pack_params* params, bool c128, uh::PackParams* pp) {
+  if (!params) return UH_OK;
+  if (params->tile_bytes) pp->tile_bytes = params->tile_bytes;
+  if (params->item_cost) pp->item_cost = params->item_cost;
+  if (params->chunk_cost) pp->chunk_cost = params->chunk_cost;
+  if (params->pool_unit) pp->pool_unit = params->pool_unit;
+  pp->ctas_per_sm = params->ctas_per_sm;
+  if (pp->tile_bytes < 4096 || pp->tile_bytes > uh::kTileBytes || pp->item_cost < 0 || pp->chunk_cost < 0 ||
+      pp->pool_unit < 0)
+    return fail(UH_EINVAL, "pack parameters: tile_bytes %lld (4096..%d), costs >= 0", (long long)pp->tile_bytes,
+                uh::kTileBytes);
+  if (pp->ctas_per_sm < 0 || pp->ctas_per_sm > 2)
+    return fail(UH_EINVAL, "pack parameters: ctas_per_sm %lld (0: automatic, 1 or 2)", (long long)pp->ctas_per_sm);
+  if (pp->ctas_per_sm == 2 && c128) return fail(UH_EINVAL, "pack parameters: two CTAs per SM need a complex64 op");
+  return UH_OK;
+}
+
+// The automatic choice of CTAs per SM (ctas_per_sm 0): two for complex64 programs that stream at
+// least kDualMinBytes per product (measured on GB300: 10-23% faster products for operators of
+// 300-720 MB with ranks of 20-60, about neutral at the N = 32768 sphere, 17% slower at 168 MB, where
+// the per-CTA start and phase waits dominate), else one.
+constexpr int64_t kDualMinBytes = int64_t{256} << 20;
+void resolve_ctas(uh::PackParams* pp, bool c128, int64_t algo_bytes) {
+  if (pp->ctas_per_sm == 0) pp->ctas_per_sm = !c128 && algo_bytes >= kDualMinBytes ? 2 : 1;
+}
+
+void fill_pack_stats(const uh::PackParams& pp, const uh::StreamGeometry& g, uh_stats_t* st) {
+  st->pack_tile_bytes = std::min<int64_t>(pp.tile_bytes, g.tile_bytes);
+  st->pack_item_cost = pp.item_cost;
+  st->pack_chunk_cost = pp.chunk_cost;
+  st->pack_pool_unit = pp.pool_unit;
+  st->pack_ctas_per_sm = g.ctas_per_sm;
 }
 
 // Finalize, self-check and upload the program; allocate the scratch vectors.
@@ -391,7 +430,8 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   p.z4 = mixed ? o->d_xm[4] : o->d_z4;
   p.status = o->d_status;
   p.timeout_cycles = timeout;
-  const int variant = mixed ? uh::kVarMixed : o->c128 ? uh::kVarC128 : uh::kVarC64;
+  const int variant = mixed ? (o->dual ? uh::kVarMixedDual : uh::kVarMixed)
+                            : o->c128 ? uh::kVarC128 : o->dual ? uh::kVarC64Dual : uh::kVarC64;
   cudaError_t e = uh::stream_launch(variant, p, o->ncta, s);
   if (e != cudaSuccess) {
     --o->epoch;  // nothing launched: the counters did not move
@@ -997,20 +1037,30 @@ extern "C" {
 const char* uh_last_error(void) { return g_err.c_str(); }
 const char* uh_version(void) { return "uh-gb300 0.2 (sm_103a)"; }
 
-int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
+int uh_create(const uh_desc* d, int32_t precision, uh_op** out) { return uh_create_ex(d, precision, nullptr, out); }
+
+int uh_create_ex(const uh_desc* d, int32_t precision, const uh_pack_params* params, uh_op** out) {
   g_err.clear();
   if (!d || !out) return fail(UH_EINVAL, "null argument");
   *out = nullptr;
   int rc;
   if ((rc = check_precision(precision, true))) return rc;
+  const bool c128 = precision == UH_PREC_C128;
+  uh::PackParams pp;
+  if ((rc = pack_params_from(params, c128, &pp))) return rc;
   UHPrep u;
   if ((rc = prepare_uh(d, &u))) return rc;
   const Tree& T = u.T;
+  {
+    uh_stats_t est{};
+    uh_fill_stats(u, precision, c128 ? 16 : 8, &est);
+    resolve_ctas(&pp, c128, est.algo_bytes_matvec);
+  }
 
-  const bool c128 = precision == UH_PREC_C128;
+  const bool dual = pp.ctas_per_sm == 2;
   int ncta = g_pack_only_ncta, device = 0;
-  if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
-  ProgramBuilder P(c128, T.n, ncta);
+  if (!ncta && (rc = query_ncta(c128, &ncta, &device, dual))) return rc;
+  ProgramBuilder P(c128, T.n, ncta, pp);
   const int64_t A = P.align();
   P.set_permutation(T.n);
   Offsets off;
@@ -1036,6 +1086,7 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   o->n = T.n;
   o->ncta = ncta;
   o->device = device;
+  o->dual = dual;
   if ((rc = upload_program(o, P, T, !c128))) { free_op(o); delete o; return rc; }
   const uh_stats_t packed = o->st;  // packing figures filled by the upload
   uh_fill_stats(u, precision, c128 ? 16 : 8, &o->st);
@@ -1043,13 +1094,7 @@ int uh_create(const uh_desc* d, int32_t precision, uh_op** out) {
   o->st.device_bytes = packed.device_bytes;
   o->st.n_launches = packed.n_launches;
   o->st.n_items = packed.n_items;
-  {
-    const uh::PackParams d;
-    o->st.pack_tile_bytes = d.tile_bytes;
-    o->st.pack_item_cost = d.item_cost;
-    o->st.pack_chunk_cost = d.chunk_cost;
-    o->st.pack_pool_unit = d.pool_unit;
-  }
+  fill_pack_stats(pp, P.geometry(), &o->st);
   if (mm_mode >= 0) {
     int pn = 0;
     if ((rc = panel_ncta(&pn)) ||
@@ -1251,21 +1296,12 @@ int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t preci
                        uh_batch** out) {
   g_err.clear();
   if (!descs || !out) return fail(UH_EINVAL, "null argument");
-  uh::PackParams pp;
-  if (params) {
-    if (params->tile_bytes) pp.tile_bytes = params->tile_bytes;
-    if (params->item_cost) pp.item_cost = params->item_cost;
-    if (params->chunk_cost) pp.chunk_cost = params->chunk_cost;
-    if (params->pool_unit) pp.pool_unit = params->pool_unit;
-    if (pp.tile_bytes < 4096 || pp.tile_bytes > uh::kTileBytes || pp.item_cost < 0 || pp.chunk_cost < 0 ||
-        pp.pool_unit < 0)
-      return fail(UH_EINVAL, "pack parameters: tile_bytes %lld (4096..%d), costs >= 0", (long long)pp.tile_bytes,
-                  uh::kTileBytes);
-  }
   *out = nullptr;
   if (count < 1) return fail(UH_EINVAL, "count = %d", count);
   int rc;
   if ((rc = check_precision(precision, false))) return rc;
+  uh::PackParams pp;
+  if ((rc = pack_params_from(params, precision == UH_PREC_C128, &pp))) return rc;
   std::vector<UHPrep> preps(count);
   int64_t total = 0;
   for (int32_t k = 0; k < count; ++k) {
@@ -1278,8 +1314,18 @@ int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t preci
     if (total > INT32_MAX) return fail(UH_EINVAL, "the batch holds more than 2^31 - 1 points");
   }
   const bool c128 = precision == UH_PREC_C128;
+  {
+    int64_t bytes = 0;
+    for (int32_t k = 0; k < count; ++k) {
+      uh_stats_t est{};
+      uh_fill_stats(preps[k], precision, c128 ? 16 : 8, &est);
+      bytes += est.algo_bytes_matvec;
+    }
+    resolve_ctas(&pp, c128, bytes);
+  }
+  const bool dual = pp.ctas_per_sm == 2;
   int ncta = g_pack_only_ncta, device = 0;
-  if (!ncta && (rc = query_ncta(c128, &ncta, &device))) return rc;
+  if (!ncta && (rc = query_ncta(c128, &ncta, &device, dual))) return rc;
   ProgramBuilder P(c128, total, ncta, pp);
   const int64_t A = P.align();
   P.set_permutation(total);
@@ -1314,6 +1360,7 @@ int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t preci
   o->ncta = ncta;
   o->device = device;
   o->offsets = offsets;
+  o->dual = dual;
   if ((rc = upload_program(o, P, all))) { free_op(o); delete o; return rc; }
   const uh_stats_t packed = o->st;
   uh_stats_t sum{};
@@ -1353,10 +1400,7 @@ int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t preci
   sum.n_launches = packed.n_launches;
   sum.n_items = packed.n_items;
   sum.matmat_mode = -1;
-  sum.pack_tile_bytes = pp.tile_bytes;
-  sum.pack_item_cost = pp.item_cost;
-  sum.pack_chunk_cost = pp.chunk_cost;
-  sum.pack_pool_unit = pp.pool_unit;
+  fill_pack_stats(pp, P.geometry(), &sum);
   o->st = sum;
   *out = o;
   return UH_OK;
@@ -1412,18 +1456,21 @@ int uh_batch_tune(const uh_desc* const* descs, int32_t count, int32_t precision,
   cur.item_cost = static_cast<int32_t>(d.item_cost);
   cur.chunk_cost = static_cast<int32_t>(d.chunk_cost);
   cur.pool_unit = static_cast<int32_t>(d.pool_unit);
+  cur.ctas_per_sm = static_cast<int32_t>(d.ctas_per_sm);
   double cur_ms = 0.0;
   rc = timed(cur, &cur_ms);
   if (default_ms) *default_ms = cur_ms;
-  // coordinate descent over the knobs, one pass; a change is kept if at least 1% faster
-  const int32_t tiles[] = {16384, 32768, 65536}, items[] = {1024, 4096, 16384}, chunks[] = {12288, 49152, 196608},
-                pools[] = {32768, 131072, 524288};
-  int32_t* knob[] = {&cur.tile_bytes, &cur.item_cost, &cur.chunk_cost, &cur.pool_unit};
-  const int32_t* vals[] = {tiles, items, chunks, pools};
-  for (int k = 0; k < 4 && !rc; ++k) {
+  // coordinate descent over the knobs, one pass; a change is kept if at least 1% faster (the CTAs
+  // per SM first: complex64 only; the tile sizes above the two-CTA geometry's cap pack alike)
+  const int32_t ctas[] = {1, 2}, tiles[] = {16384, 32768, 65536}, items[] = {1024, 4096, 16384},
+                chunks[] = {12288, 49152, 196608}, pools[] = {32768, 131072, 524288};
+  int32_t* knob[] = {&cur.ctas_per_sm, &cur.tile_bytes, &cur.item_cost, &cur.chunk_cost, &cur.pool_unit};
+  const int32_t* vals[] = {ctas, tiles, items, chunks, pools};
+  const int nvals[] = {precision == UH_PREC_C128 ? 1 : 2, 3, 3, 3, 3};
+  for (int k = 0; k < 5 && !rc; ++k) {
     const int32_t keep = *knob[k];
     int32_t pick = keep;
-    for (int v = 0; v < 3 && !rc; ++v) {
+    for (int v = 0; v < nvals[k] && !rc; ++v) {
       if (vals[k][v] == keep) continue;
       *knob[k] = vals[k][v];
       double ms = 0.0;
@@ -1586,3 +1633,12 @@ int h_reserve(h_op* op, int32_t max_nrhs) {
 }
 
 }  // extern "C"
+
+extern "C" int uh_pack_check_ex(const uh_desc* desc, int32_t precision, const uh_pack_params* params, int32_t ncta) {
+  if (ncta < 1) return fail(UH_EINVAL, "ncta = %d", ncta);
+  g_pack_only_ncta = ncta;
+  uh_op* o = nullptr;
+  const int rc = uh_create_ex(desc, precision, params, &o);
+  g_pack_only_ncta = 0;
+  return rc;
+}

@@ -9,7 +9,10 @@
 namespace uh {
 
 ProgramBuilder::ProgramBuilder(bool c128, int64_t n, int ncta, const PackParams& params)
-    : c128_(c128), n_(n), ncta_(ncta), prm_(params), A_(c128 ? 1 : 2), eb_(c128 ? 16 : 8) {}
+    : c128_(c128), n_(n), ncta_(ncta), prm_(params), geom_(params.ctas_per_sm == 2 ? kGeomDual : kGeomOne),
+      A_(c128 ? 1 : 2), eb_(c128 ? 16 : 8) {
+  prm_.tile_bytes = std::min<int64_t>(prm_.tile_bytes, geom_.tile_bytes);
+}
 
 int ProgramBuilder::add_chunk(int kind, int64_t dst, int h, int group, int counter) {
   OutChunk c{};
@@ -46,7 +49,7 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
   const int h = chunks[chunk].h;
   const int64_t hp = std::max<int64_t>(A_, round_up(h, A_));
   // an item's tile (hp x ncols) and its inputs (ncols) share one stage buffer
-  int64_t maxcols = std::min<int64_t>(kStreamMaxCols, std::min<int64_t>(prm_.tile_bytes / (hp * eb_), kStageBytes / ((hp + 1) * eb_)));
+  int64_t maxcols = std::min<int64_t>(kStreamMaxCols, std::min<int64_t>(prm_.tile_bytes / (hp * eb_), geom_.stage_bytes / ((hp + 1) * eb_)));
   maxcols = maxcols / A_ * A_;
   auto& out = chunk_items_[chunk];
   WorkItem cur{};
@@ -129,7 +132,7 @@ void ProgramBuilder::add_columns(int chunk, const std::vector<ColSpec>& cols, in
     // when the last one has no room for it).
     const int64_t hb = round_up(h, A_);
     const WorkItem& last = out.back();
-    if (last.nruns == kMaxRuns || (static_cast<int64_t>(last.ncols) * (hp + 1) + hb) * eb_ > kStageBytes) {
+    if (last.nruns == kMaxRuns || (static_cast<int64_t>(last.ncols) * (hp + 1) + hb) * eb_ > geom_.stage_bytes) {
       start_item();
       close_item();
     }
@@ -270,6 +273,7 @@ const char* ProgramBuilder::finalize() {
 
 const char* ProgramBuilder::self_check() const {
   const int nchunk = static_cast<int>(chunks.size());
+  if (geom_.ctas_per_sm == 2 && c128_) return "two CTAs per SM for a complex128 program";
   // the kernel permutes positions [0, perm_n) of x into xp, one slice per CTA, each CTA releasing
   // the permutation counter once
   if (perm_n_ < 0 || perm_n_ > src_len_[kSrcXp] || counter_total_[kCounterPermute] != ncta_)
@@ -345,11 +349,11 @@ const char* ProgramBuilder::self_check() const {
       staged += run.len;
     }
     if (cols != it.ncols) return "item runs do not match its columns";
-    if (it.ncols < 0 || it.ncols > kStreamMaxCols || static_cast<int64_t>(it.ncols) * it.hp * eb_ > kTileBytes ||
-        (static_cast<int64_t>(it.ncols) * it.hp + staged) * eb_ > kStageBytes)
+    if (it.ncols < 0 || it.ncols > kStreamMaxCols || static_cast<int64_t>(it.ncols) * it.hp * eb_ > geom_.tile_bytes ||
+        (static_cast<int64_t>(it.ncols) * it.hp + staged) * eb_ > geom_.stage_bytes)
       return "item tile size";
     // the extended-precision variant stages the same complex64 tile with 16-byte inputs
-    if (eb_ == 8 && static_cast<int64_t>(it.ncols) * it.hp * 8 + staged * 16 > kStageBytesMixed)
+    if (eb_ == 8 && static_cast<int64_t>(it.ncols) * it.hp * 8 + staged * 16 > geom_.stage_bytes_mixed)
       return "item tile size (extended-precision stage)";
     if (it.tile_off < 0 || (it.tile_off * eb_) % 16 || it.tile_off + static_cast<int64_t>(it.ncols) * it.hp > msize)
       return "item tile outside the packed buffer or misaligned";

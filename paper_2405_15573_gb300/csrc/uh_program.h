@@ -43,13 +43,16 @@ enum Group { kGroupPermute = 0, kGroupForward = 1, kGroupNearA = 2, kGroupCoupli
 constexpr int kFirstPoolGroup = kGroupNearB;
 
 // Packing and scheduling parameters (the defaults were chosen by sweeps on the N = 32768 sphere):
-// the largest tile of an item, the schedule's cost of an item and of a chunk end in bytes
-// streamed in the same time, and the cost that consecutive pool chunks share a ticket up to.
+// the largest tile of an item (capped by the geometry's), the schedule's cost of an item and of a
+// chunk end in bytes streamed in the same time, the cost that consecutive pool chunks share a
+// ticket up to, and the CTAs per SM (1: kGeomOne, 2: kGeomDual, complex64 only; 0 = automatic,
+// resolved by the caller before packing).
 struct PackParams {
   int64_t tile_bytes = kTileBytes;
   int64_t item_cost = 4096;
   int64_t chunk_cost = 49152;
   int64_t pool_unit = 131072;
+  int64_t ctas_per_sm = 0;
 };
 
 class ProgramBuilder {
@@ -57,6 +60,7 @@ class ProgramBuilder {
   ProgramBuilder(bool c128, int64_t n, int ncta, const PackParams& params = PackParams());
 
   int64_t align() const { return A_; }
+  const StreamGeometry& geometry() const { return geom_; }
   static int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
   // Input vector lengths (elements, multiples of align()).
@@ -107,6 +111,7 @@ class ProgramBuilder {
   int64_t n_;
   int ncta_;
   PackParams prm_;
+  StreamGeometry geom_;
   int64_t A_;   // elements per 16 bytes
   int eb_;      // bytes per element
   std::vector<int> group_, base_of_, cta_of_, pool_pos_;

@@ -27,17 +27,20 @@ namespace {
 
 // Variants (uh_stream.h): TM = tile element, TV = element of the intermediate vectors, of the
 // staged inputs and of the accumulators, TX = element of x and y, L = shared-memory layout.
+// kMinBlocks: CTAs per SM the variant is compiled for.
 struct KC64 {
   using TM = float2;
   using TV = float2;
   using TX = float2;
   using L = StreamSmemStd;
+  static constexpr int kMinBlocks = 1;
 };
 struct KC128 {
   using TM = double2;
   using TV = double2;
   using TX = double2;
   using L = StreamSmemStd;
+  static constexpr int kMinBlocks = 1;
 };
 // TV = (re_hi, im_hi, re_lo, im_lo): the value re_hi + re_lo + i (im_hi + im_lo).
 struct KMixed {
@@ -45,6 +48,16 @@ struct KMixed {
   using TV = float4;
   using TX = double2;
   using L = StreamSmemMixed;
+  static constexpr int kMinBlocks = 1;
+};
+// The same with two CTAs per SM (programs packed for kGeomDual).
+struct KC64Dual : KC64 {
+  using L = StreamSmemDual;
+  static constexpr int kMinBlocks = 2;
+};
+struct KMixedDual : KMixed {
+  using L = StreamSmemMixedDual;
+  static constexpr int kMinBlocks = 2;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -660,7 +673,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
 }
 
 template <class K>
-__global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const StreamParams p) {
+__global__ void __launch_bounds__(kStreamThreads, K::kMinBlocks) stream_kernel(const StreamParams p) {
   using L = typename K::L;
   extern __shared__ __align__(128) unsigned char smem[];
   const Bars bar = bars_of<L>(smem);
@@ -697,6 +710,10 @@ const void* stream_fn(int variant, int* smem_bytes) {
     case kVarC64: *smem_bytes = KC64::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC64>);
     case kVarC128: *smem_bytes = KC128::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC128>);
     case kVarMixed: *smem_bytes = KMixed::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KMixed>);
+    case kVarC64Dual: *smem_bytes = KC64Dual::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC64Dual>);
+    case kVarMixedDual:
+      *smem_bytes = KMixedDual::L::bytes;
+      return reinterpret_cast<const void*>(stream_kernel<KMixedDual>);
     default: *smem_bytes = 0; return nullptr;
   }
 }

@@ -75,9 +75,28 @@ static_assert(2 * kPoolSeg + kStages <= kDescRing, "a fetched pool segment must 
 //             kStageBytesMixed: a complex64 item with ncols columns and s staged values uses
 //             ncols * hp * 8 + s * 8 <= kStageBytes bytes, hence ncols * hp * 8 + s * 16 <=
 //             kStageBytes + 8 * (kStreamMaxCols + kStreamHpMax) = kStageBytesMixed.
-enum StreamVariant : int { kVarC64 = 0, kVarC128 = 1, kVarMixed = 2 };
+// A complex64 program is packed for one of two geometries: one CTA per SM with kStages stages of
+// kStageBytes (tiles up to kTileBytes), or two CTAs per SM with kStagesDual stages of
+// kStageBytesDual (tiles up to kTileBytesDual). The second suits operators of many small chunks
+// (low ranks, small leaves, batches of small operators), whose per-item and per-chunk latencies
+// then overlap between the two CTAs of an SM; kVarC64Dual and kVarMixedDual run such programs.
+enum StreamVariant : int { kVarC64 = 0, kVarC128 = 1, kVarMixed = 2, kVarC64Dual = 3, kVarMixedDual = 4 };
 constexpr int kStageBytesMixed = kStageBytes + 8 * (kStreamMaxCols + kStreamHpMax);
 constexpr int kStagesMixed = 2;
+constexpr int kStagesDual = 3;
+constexpr int kTileBytesDual = 24576;
+constexpr int kStageBytesDual = 26624;
+constexpr int kStageBytesMixedDual = kStageBytesDual + 8 * (kStreamMaxCols + kStreamHpMax);
+
+// The capacities a program is packed for.
+struct StreamGeometry {
+  int ctas_per_sm;
+  int tile_bytes;          // largest tile of an item
+  int stage_bytes;         // an item's tile and inputs
+  int stage_bytes_mixed;   // the same item in the extended-precision variant
+};
+constexpr StreamGeometry kGeomOne{1, kTileBytes, kStageBytes, kStageBytesMixed};
+constexpr StreamGeometry kGeomDual{2, kTileBytesDual, kStageBytesDual, kStageBytesMixedDual};
 
 // Shared-memory layout of the kernel (bytes) for `Stages` stages of `StageBytes` and a per-thread
 // reduction slot of `RedSlot` bytes. The chunk-end buffers are double-buffered by chunk parity,
@@ -99,6 +118,11 @@ struct StreamSmem {
 };
 using StreamSmemStd = StreamSmem<kStages, kStageBytes, 16>;
 using StreamSmemMixed = StreamSmem<kStagesMixed, kStageBytesMixed, 32>;
+using StreamSmemDual = StreamSmem<kStagesDual, kStageBytesDual, 16>;
+using StreamSmemMixedDual = StreamSmem<kStagesMixed, kStageBytesMixedDual, 32>;
+// two CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+static_assert(2 * (StreamSmemDual::bytes + 1024) <= 228 * 1024, "two CTAs per SM");
+static_assert(2 * (StreamSmemMixedDual::bytes + 1024) <= 228 * 1024, "two CTAs per SM");
 
 // Input vectors a run can read.
 enum : int8_t { kSrcXp = 0, kSrcZ1 = 1, kSrcZ2 = 2, kSrcZ3 = 3, kSrcZ4 = 4 };

@@ -65,7 +65,7 @@ class Stats(C.Structure):
                 ("n_launches", _i32), ("n_items", _i64),
                 ("matmat_mode", _i32), ("panel_bytes", _i64), ("panel_items", _i64),
                 ("panel_mma_flops", _i64), ("pack_tile_bytes", _i64), ("pack_item_cost", _i64),
-                ("pack_chunk_cost", _i64), ("pack_pool_unit", _i64), ("n_factored", _i64),
+                ("pack_chunk_cost", _i64), ("pack_pool_unit", _i64), ("pack_ctas_per_sm", _i64), ("n_factored", _i64),
                 ("sum_factored_rank", _i64)]
 
     def as_dict(self):
@@ -74,7 +74,8 @@ class Stats(C.Structure):
 
 class PackParams(C.Structure):
     """uh_pack_params: packing and scheduling of the streaming program (0 = default)."""
-    _fields_ = [("tile_bytes", _i32), ("item_cost", _i32), ("chunk_cost", _i32), ("pool_unit", _i32)]
+    _fields_ = [("tile_bytes", _i32), ("item_cost", _i32), ("chunk_cost", _i32), ("pool_unit", _i32),
+                ("ctas_per_sm", _i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +85,8 @@ lib.uh_last_error.restype = C.c_char_p
 lib.uh_version.restype = C.c_char_p
 for _name, _args in [
     ("uh_create", [C.POINTER(UHDesc), _i32, C.POINTER(_p)]),
+    ("uh_create_ex", [C.POINTER(UHDesc), _i32, C.POINTER(PackParams), C.POINTER(_p)]),
+    ("uh_pack_check_ex", [C.POINTER(UHDesc), _i32, C.POINTER(PackParams), _i32]),
     ("uh_destroy", [_p]),
     ("uh_matvec", [_p, _p, _p, _p]),
     ("uh_matmat", [_p, _i32, _p, _i64, _p, _i64, _i32, _p]),
@@ -240,11 +243,14 @@ def _stream_handle(stream):
 class _Op:
     _create = _destroy = _matvec = _matmat = _stats = _reserve = _check = None
 
-    def __init__(self, desc, precision: str = "c64"):
+    def __init__(self, desc, precision: str = "c64", params: "PackParams | None" = None):
         self.precision = precision
         self.c128 = precision == "c128"
         h = _p()
-        check(self._create(C.byref(desc), _PREC[precision], C.byref(h)), self._create.__name__)
+        if params is None:
+            check(self._create(C.byref(desc), _PREC[precision], C.byref(h)), self._create.__name__)
+        else:
+            check(lib.uh_create_ex(C.byref(desc), _PREC[precision], C.byref(params), C.byref(h)), "uh_create_ex")
         self.handle = h
         s = Stats()
         check(self._stats(self.handle, C.byref(s)), "stats")
@@ -372,9 +378,9 @@ class UHOp(_Op):
     _check = lib.uh_check
 
     @classmethod
-    def from_arrays(cls, arrays: dict, precision: str = "c64"):
+    def from_arrays(cls, arrays: dict, precision: str = "c64", params: "PackParams | None" = None):
         desc, keep = uh_desc_from_arrays(arrays)
-        return cls(desc, precision)
+        return cls(desc, precision, params)
 
     def matvec_mixed(self, x, y=None, stream=None):
         """y = A x with the complex64-stored operator in extended-precision arithmetic
@@ -615,8 +621,8 @@ class HelmholtzModel:
         check(lib.uhb_h_desc(self.handle, C.byref(d)), "uhb_h_desc")
         return d
 
-    def uh_op(self, precision: str = "c64") -> "UHOp":
-        return UHOp(self.uh_desc(), precision)
+    def uh_op(self, precision: str = "c64", params: "PackParams | None" = None) -> "UHOp":
+        return UHOp(self.uh_desc(), precision, params)
 
     def h_op(self, precision: str = "c64") -> "HOp":
         return HOp(self.h_desc(), precision)

@@ -300,3 +300,33 @@ def test_rejects_bad_factored_ranks(uh):
     d["S_off"] = a["S_off"].copy()
     d["S_off"][i] = len(a["S_data"]) - 1  # the factors would run past the end of S_data
     _expect_einval(uh, d, "coupling matrix")
+
+
+@pytest.mark.parametrize("ncta", [304, 14, 2])
+@pytest.mark.parametrize("case", [(2048, 4.0, 32, 1e-6), (1000, 6.0, 24, 1e-5), (97, 3.0, 16, 1e-6),
+                                  (40, 3.0, 64, 1e-6)])
+def test_two_ctas_per_sm_packing_self_check_passes(uh, ncta, case):
+    """Programs packed for two CTAs per SM (tiles up to 24 KB in 26 KB stages; the extended-
+    precision stage checked as well), single operators, factored coefficients and a batch."""
+    n, k, leaf, eps = case
+    axes, noise = ((1.0, 0.7, 0.4), 0.01) if n == 1000 else ((1.0, 1.0, 1.0), 0.0)
+    _, _, hf, h, op = oracle_ops(n, k, leaf, 1.0, eps, 1e-8, axes, noise)
+    pp = uh.PackParams(0, 0, 0, 0, 2)
+    desc, keep = uh.uh_desc_from_arrays(uh_arrays(op))
+    rc = uh.lib.uh_pack_check_ex(C.byref(desc), 1, C.byref(pp), ncta)
+    assert rc == uh.UH_OK, uh.lib.uh_last_error().decode()
+    if n == 2048:
+        fd, fkeep = uh.uh_desc_from_arrays(_factored_arrays(2048, 4.0, 32, 1e-6))
+        assert uh.lib.uh_pack_check_ex(C.byref(fd), 1, C.byref(pp), ncta) == uh.UH_OK, uh.lib.uh_last_error().decode()
+        built = [uh.uh_desc_from_arrays(a) for a in _batch_arrays()]
+        arr = uh._desc_array([d for d, _ in built])
+        assert uh.lib.uh_batch_pack_check_ex(arr, len(built), 1, pp, ncta) == uh.UH_OK, uh.lib.uh_last_error().decode()
+
+
+def test_two_ctas_per_sm_rejected_for_complex128_and_bad_values(uh):
+    a, _ = _small()
+    desc, keep = uh.uh_desc_from_arrays(a)
+    assert uh.lib.uh_pack_check_ex(C.byref(desc), 0, C.byref(uh.PackParams(0, 0, 0, 0, 2)), 304) == uh.UH_EINVAL
+    assert "complex64" in uh.lib.uh_last_error().decode()
+    assert uh.lib.uh_pack_check_ex(C.byref(desc), 1, C.byref(uh.PackParams(0, 0, 0, 0, 3)), 304) == uh.UH_EINVAL
+    assert "ctas_per_sm" in uh.lib.uh_last_error().decode()

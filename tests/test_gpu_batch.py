@@ -58,8 +58,9 @@ def test_batch_matches_oracle_and_single(U, prec):
     batch.close()
 
 
-TUNER_PARAMS = [(16384, 0, 0, 0), (32768, 0, 0, 0), (0, 1024, 0, 0), (0, 16384, 0, 0), (0, 0, 12288, 0),
-                (0, 0, 196608, 0), (0, 0, 0, 32768), (0, 0, 0, 524288), (16384, 16384, 196608, 524288)]
+TUNER_PARAMS = [(16384, 0, 0, 0, 0), (32768, 0, 0, 0, 0), (0, 1024, 0, 0, 0), (0, 16384, 0, 0, 0),
+                (0, 0, 12288, 0, 0), (0, 0, 196608, 0, 0), (0, 0, 0, 32768, 0), (0, 0, 0, 524288, 0),
+                (16384, 16384, 196608, 524288, 0), (0, 0, 0, 0, 2), (16384, 1024, 12288, 32768, 2)]
 
 
 @pytest.mark.parametrize("params", TUNER_PARAMS)
@@ -70,8 +71,11 @@ def test_batch_with_every_tuner_choice(U, params):
     arrays = [uh_arrays(op) for op in ops]
     batch = U.UHBatch.from_arrays(arrays, "c64", U.PackParams(*params))
     st = batch.stats()
-    expect = [v if v else d for v, d in zip(params, (65536, 4096, 49152, 131072))]
-    assert [st["pack_tile_bytes"], st["pack_item_cost"], st["pack_chunk_cost"], st["pack_pool_unit"]] == expect
+    expect = [v if v else d for v, d in zip(params, (65536, 4096, 49152, 131072, 1))]
+    if expect[4] == 2:
+        expect[0] = min(expect[0], 24576)  # the two-CTA geometry's largest tile
+    assert [st["pack_tile_bytes"], st["pack_item_cost"], st["pack_chunk_cost"], st["pack_pool_unit"],
+            st["pack_ctas_per_sm"]] == expect
     off = batch.offsets
     xs = [I.complex_normal(op.tree.n, 10 + k) for k, op in enumerate(ops)]
     x = torch.from_numpy(np.concatenate(xs)).to("cuda", torch.complex64)
@@ -92,6 +96,7 @@ def test_autotuner_picks_a_candidate_and_stays_correct(U):
     built = [U.uh_desc_from_arrays(a) for a in arrays]
     descs = [d for d, _ in built]
     best, best_ms, default_ms = U.UHBatch.tune(descs, "c64", sample=0, reps=10)
+    assert best.ctas_per_sm in (0, 1, 2)
     assert best.tile_bytes in (16384, 32768, 65536)
     assert best.item_cost in (1024, 4096, 16384)
     assert best.chunk_cost in (12288, 49152, 196608)
@@ -106,3 +111,30 @@ def test_autotuner_picks_a_candidate_and_stays_correct(U):
     for k, op in enumerate(ops):
         assert relerr(yb[off[k]:off[k + 1]], O.uh_matvec(op, xs[k])) <= TOL["c64"], k
     batch.close()
+
+
+@pytest.mark.parametrize("name", ["sphere2048", "ellipsoid1000"])
+def test_two_ctas_per_sm_op_parity(U, name):
+    """A single operator packed for two CTAs per SM (uh_create_ex): the product, the extended-
+    precision product and the factored form agree with the oracle; two calls are bitwise equal."""
+    import torch
+    from tests.test_gpu_matvec import WORKLOADS
+    from tests.uh_testutil import stored_c64
+    pts, tree, hf, h, uh = oracle_ops(*WORKLOADS[name])
+    for arrays, ref in ((uh_arrays(uh), uh), (uh_arrays(O.factor_coupling(uh, 3 * WORKLOADS[name][4])), None)):
+        if ref is None:
+            ref = O.factor_coupling(uh, 3 * WORKLOADS[name][4])
+        op = U.UHOp.from_arrays(arrays, "c64", U.PackParams(0, 0, 0, 0, 2))
+        st = op.stats()
+        assert st["pack_ctas_per_sm"] == 2 and st["pack_tile_bytes"] == 24576
+        x = I.complex_normal(tree.n, 40)
+        xt = torch.from_numpy(x).to("cuda", torch.complex64)
+        y1, y2 = op.matvec(xt), op.matvec(xt)
+        op.check()
+        assert torch.equal(y1, y2)
+        assert relerr(y1.cpu().numpy().astype(np.complex128), O.uh_matvec(stored_c64(ref), x)) <= TOL["c64"]
+        x2 = torch.from_numpy(x).to("cuda")
+        ym = op.matvec_mixed(x2)
+        op.check()
+        assert relerr(ym.cpu().numpy(), O.uh_matvec(stored_c64(ref), x)) <= 1e-11
+        op.close()
