@@ -385,7 +385,9 @@ def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30, tru
     """GMRES(restart) solves served from a pool of resident complex64 UH operators (uh_server):
     per arrival rate, `requests` solves with Poisson arrivals, each on a random operator of the
     pool with a seeded right-hand side. Latency = submission to completion (library clock);
-    throughput = completed solves / wall time from the first submission to the last completion."""
+    throughput = completed solves / wall time from the first submission to the last completion.
+    Each rate runs max(requests, rate / 5) solves, so that at the high rates the start and the
+    drain of the queue take a small part of the wall time."""
     from paper_2405_15573_gb300 import inputs as I
     from paper_2405_15573_gb300 import uh as U
     pool = I.serving_pool(pool_count, n_hi=n_hi)
@@ -398,7 +400,9 @@ def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30, tru
     out = {"pool": pool_count, "n_range": [min(w.n for w in pool), max(w.n for w in pool)],
            "operator_bytes_c64": int(sum(o.stats()["algo_bytes_matvec"] for o in ops)),
            "build_s": round(build_s, 1), "tol": tol, "restart": restart, "rates": {}}
+    base_requests = requests
     for lam in rates:
+        requests = max(base_requests, int(lam / 5))
         arr = I.poisson_arrivals(lam, requests, seed=int(lam))
         which = np.random.default_rng(int(lam) + 1).integers(0, pool_count, size=requests)
         bs = [I.complex_normal(pool[k].n, 100 + i) for i, k in enumerate(which)]
