@@ -313,11 +313,14 @@ def matmat_figures(model, n, steps, torch, peak_bf16, sizes=(32, 64)):
             y = Y.cpu().numpy().astype(np.complex128)
             err = max(float(np.linalg.norm(y[:, j] - yref[:, j]) / np.linalg.norm(yref[:, j]))
                       for j in range(nrhs))
-            flops = st["panel_mma_flops"]  # every MMA of one pass: 2 M N K (3 products in BF16x3)
+            # every MMA of one pass: 2 M N K (3 products in BF16x3), M = 128; a pass of at most 32
+            # right-hand sides issues the same MMAs with M = 64
+            flops = st["panel_mma_flops"] // (2 if nrhs <= 32 else 1)
             tf = flops / (ms * 1e-3) / 1e12
             out[f"{mode}_R{nrhs}"] = {
                 "ms": ms, "rhs_matvec_per_s": nrhs * 1e3 / ms,
                 "operator_GBps": st["panel_bytes"] / (ms * 1e-3) / 1e9,
+                "mma_m": 64 if nrhs <= 32 else 128,
                 "tensor_tflops": tf, "tensor_peak_tflops": peaks[mode], "tensor_frac": tf / peaks[mode],
                 "max_col_relerr_vs_simt": err}
         del op

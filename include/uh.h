@@ -231,7 +231,9 @@ typedef struct {
   int32_t matmat_mode;        /* tensor-core uh_matmat mode of the op (UH_MM_TF32 / UH_MM_BF16X3), or -1 */
   int64_t panel_bytes;        /* its packed operator: bytes streamed per pass of 64 right-hand sides */
   int64_t panel_items;        /* its work items per pass */
-  int64_t panel_mma_flops;    /* its tensor-core flops per pass (2 * M * N * K of every MMA) */
+  int64_t panel_mma_flops;    /* its tensor-core flops per pass of 33-64 right-hand sides (2 M N K of
+                                 every MMA, M = 128); a pass of at most 32 issues them with M = 64,
+                                 half the flops */
   int64_t pack_tile_bytes;    /* packing of the streaming program (uh_pack_params), as used */
   int64_t pack_item_cost;
   int64_t pack_chunk_cost;

@@ -1576,10 +1576,12 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
   if ((rc = order_call(op, static_cast<cudaStream_t>(stream)))) return rc;
   for (int32_t rhs0 = 0; rhs0 < nrhs; rhs0 += uh::kPanelR) {
     const int32_t nb = std::min<int32_t>(uh::kPanelR, nrhs - rhs0);
+    // at most 32 right-hand sides: MMAs of M = 64 on the compact panel layout
+    const int32_t m64 = nb <= uh::kPanelR / 2 ? 1 : 0;
     // on a failed launch, still mark the call's end so that the next call is ordered after the
     // panels already queued (they share the op's panel scratch)
-    if ((rc = uh::panel_gather(X, ldx, op->n, op->panel_xp_rows, op->d_perm, rhs0, nb, op->panel_mode, op->d_pxp,
-                               stream))) {
+    if ((rc = uh::panel_gather(X, ldx, op->n, op->panel_xp_rows, op->d_perm, rhs0, nb, op->panel_mode, m64,
+                               op->d_pxp, stream))) {
       call_done(op, static_cast<cudaStream_t>(stream));
       return rc;
     }
@@ -1602,6 +1604,7 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
       p.perm = op->d_perm;
       p.rhs0 = rhs0;
       p.nb = nb;
+      p.m64 = m64;
       p.mode = op->panel_mode;
       p.status = op->d_status;
       p.timeout_cycles = kTimeoutCycles;

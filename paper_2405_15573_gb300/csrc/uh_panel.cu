@@ -1,17 +1,20 @@
-// Tensor-core multi-RHS product (sm_103a): one persistent cooperative launch per pass of 64
-// right-hand sides, one CTA per SM. Layout of the work and of the operands: uh_panel.h.
+// Tensor-core multi-RHS product (sm_103a): one persistent cooperative launch per pass of up to 64
+// right-hand sides (MMAs of M = 128; of M = 64 on a compact panel layout for up to 32), one CTA
+// per SM. Layout of the work and of the operands: uh_panel.h.
 //
-// Roles in a CTA of 320 threads:
-//  - B producer (lane 0 of warp 0): streams the CTA's item descriptors into a shared-memory ring
-//    (TMA bulk copies of 8) and copies operand B of each item (the packed operator, from HBM)
-//    into a byte ring of 120 KB, as far ahead as the ring and the 16 item slots allow; at a
-//    chunk's last item it hands the chunk's output record to the epilogue through a ring of
-//    mbarriers. Operator tiles keep streaming while an operand A waits for the previous phase.
-//  - A producers (lane 0 of warps 11 and 12, alternate items): copy operand A of each item (runs
-//    of panel blocks, already in the MMA's layout, from L2) into one of 3 fixed buffers, once
+// Roles in a CTA of 448 threads (14 warps):
+//  - manager (lane 0 of warp 0): streams the CTA's item descriptors into a shared-memory ring
+//    (TMA bulk copies of 8); per item it takes one of 16 item slots and room for the item's
+//    operand B in a byte ring of 120 KB, writes the slot and signals it; at a chunk's last item
+//    it hands the chunk's output record to the epilogue through a ring of mbarriers. It issues
+//    no operand copy.
+//  - copy workers (lane 0 of warps 11-13, items in turn): copy operand B of their items (the
+//    packed operator, from HBM) as soon as the slots are written, up to 6 items ahead, so that
+//    operator tiles keep streaming while an operand A waits for the previous phase; and operand A
+//    (runs of panel blocks, already in the MMA's layout, from L2) into one of 3 fixed buffers once
 //    the item's panel is complete in this pass (Z1 / Z2 counters). A thread issues about two
-//    barrier-armed bulk copies per microsecond whatever their size, so the copies of one item
-//    stream are spread over three threads.
+//    barrier-armed bulk copies per microsecond whatever their size, so the copies are spread over
+//    three threads.
 //  - MMA issuer (lane 0 of warp 1; warp 1 also allocates and frees the tensor memory): per item
 //    waits for its slot, issues the item's tcgen05.mma instructions into the chunk's accumulator
 //    (two accumulators of 128 columns alternate between chunks) and commits them to the barriers
@@ -408,13 +411,14 @@ __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm
     }
     const PanelItem& it = slots[s];
     unsigned char* dst = sm + kOffA + (j % kASlots) * kPanelABytes;
-    mbar_arrive_expect_tx(&bar.afull[s], static_cast<uint32_t>(it.nrows) * kPanelRowBytes);
+    const uint32_t rb = panel_row_bytes(p.m64);
+    mbar_arrive_expect_tx(&bar.afull[s], static_cast<uint32_t>(it.nrows) * rb);
     uint32_t row = 0;
     for (int r = 0; r < it.nruns; ++r) {
       const PanelRun run = it.runs[r];
       const unsigned char* src = static_cast<const unsigned char*>(p.src[run.src]);
-      bulk_g2s_hint(dst + row * kPanelRowBytes, src + static_cast<int64_t>(run.start) * kPanelRowBytes,
-                    static_cast<uint32_t>(run.len) * kPanelRowBytes, &bar.afull[s], keep);
+      bulk_g2s_hint(dst + row * rb, src + static_cast<int64_t>(run.start) * rb, static_cast<uint32_t>(run.len) * rb,
+                    &bar.afull[s], keep);
       row += static_cast<uint32_t>(run.len);
     }
     look_ahead();
@@ -440,9 +444,12 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
   const int32_t* boff = reinterpret_cast<const int32_t*>(sm + kOffBoff);
   const uint32_t st_base = smem_u32(sm);
   const bool bf = p.mode == kPanelBF16X3;
-  // D FP32; A, B TF32 (2) or BF16 (1); both K-major; M = 128.
+  // D FP32; A, B TF32 (2) or BF16 (1); both K-major; M = 128, or 64 for a pass of at most 32
+  // right-hand sides (the first 64 operand-A rows, the same layout).
   const uint32_t fmt = bf ? 1u : 2u;
-  const uint32_t idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(128 >> 4) << 24);
+  const uint32_t mdim = p.m64 ? 64u : 128u;
+  const uint32_t rb = panel_row_bytes(p.m64);
+  const uint32_t idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((mdim >> 4) << 24);
   int chunks = 0;
   bool issued = false;
   auto give_up = [&]() {
@@ -473,23 +480,24 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
     const uint32_t B = st_base + static_cast<uint32_t>(kOffB + boff[s]);
     uint32_t acc = (flags & kPItemFirst) ? 0u : 1u;
     if (!bf) {
-      // K = 8 per instruction: two 4-row blocks of A (2 KB apart); B in 32-value segments.
+      // K = 8 per instruction: two 4-row blocks of A (one block, 4 rb bytes, apart); B in 32-value
+      // segments.
       for (int k0 = 0; k0 < nrows; k0 += 8) {
         const uint32_t bo = static_cast<uint32_t>((k0 / 32) * nn * 128 + (k0 % 32) * 4);
-        mma_tf32(d, plain_desc(A + static_cast<uint32_t>(k0) * kPanelRowBytes, 2048), sw128_desc(B + bo), idesc, acc);
+        mma_tf32(d, plain_desc(A + static_cast<uint32_t>(k0) * rb, 4 * rb), sw128_desc(B + bo), idesc, acc);
         acc = 1u;
       }
     } else {
-      // K = 16 per instruction: two 8-row blocks of A (4 KB apart, lo plane 2 KB into each);
+      // K = 16 per instruction: two 8-row blocks of A (8 rb bytes apart, lo plane 4 rb into each);
       // B's hi plane in segment 0, lo plane in segment 1. hi*hi + hi*lo + lo*hi.
       const uint32_t blo = static_cast<uint32_t>(nn) * 128u;
       for (int k0 = 0; k0 < nrows; k0 += 16) {
-        const uint32_t a = A + static_cast<uint32_t>(k0) * kPanelRowBytes;
+        const uint32_t a = A + static_cast<uint32_t>(k0) * rb;
         const uint32_t o = static_cast<uint32_t>(k0 * 2);
-        mma_bf16(d, plain_desc(a, 4096), sw128_desc(B + o), idesc, acc);
+        mma_bf16(d, plain_desc(a, 8 * rb), sw128_desc(B + o), idesc, acc);
         acc = 1u;
-        mma_bf16(d, plain_desc(a, 4096), sw128_desc(B + blo + o), idesc, 1u);
-        mma_bf16(d, plain_desc(a + 2048, 4096), sw128_desc(B + o), idesc, 1u);
+        mma_bf16(d, plain_desc(a, 8 * rb), sw128_desc(B + blo + o), idesc, 1u);
+        mma_bf16(d, plain_desc(a + 4 * rb, 8 * rb), sw128_desc(B + o), idesc, 1u);
       }
     }
     issued = true;
@@ -541,9 +549,13 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3;            // tensor-memory lane quarter of this warp
   const int hf = (warp - 2) >> 2;    // which column blocks: 16 (2 b + hf) .. + 15
-  const int m = 32 * q + lane;       // accumulator row = operand-A row of the next phase
+  // Accumulator row = operand-A row of the next phase: lane 32 q + l holds row 32 q + l (M = 128),
+  // or row 16 q + l for l < 16 (M = 64; lanes 16-31 of a quarter hold no row).
+  const bool live = !p.m64 || lane < 16;
+  const int m = p.m64 ? 16 * q + (lane & 15) : 32 * q + lane;
   const int r = m >> 1, part = m & 1;
   const bool bf = p.mode == kPanelBF16X3;
+  const int64_t rb = panel_row_bytes(p.m64);
   for (int k = 0;; ++k) {
     const int qr = k % kRecRing;
     if (!warp_wait(&bar.recfull[qr], static_cast<uint32_t>(k / kRecRing) & 1u, p.timeout_cycles, abort_flag)) {
@@ -597,7 +609,7 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
           const int i = i0 + ii;
           if (i >= h) break;  // uniform over the warp
           const int pi = __shfl_sync(0xffffffffu, i < 32 ? pm0 : pm1, i & 31);
-          if (r < p.nb)
+          if (live && r < p.nb)
             static_cast<float*>(p.y)[(static_cast<int64_t>(pi) + static_cast<int64_t>(p.rhs0 + r) * p.ldy) * 2 + part] =
                 val[ii];
         }
@@ -609,8 +621,8 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
 #pragma unroll
           for (int g = 0; g < 2; ++g) {
             const int i = i0 + 4 * g;
-            if (i < h)
-              *reinterpret_cast<uint4*>(z + (rec.out + i) * kPanelRowBytes) =
+            if (live && i < h)
+              *reinterpret_cast<uint4*>(z + (rec.out + i) * rb) =
                   make_uint4(tf32_rna(val[4 * g]), tf32_rna(val[4 * g + 1]), tf32_rna(val[4 * g + 2]),
                              tf32_rna(val[4 * g + 3]));
           }
@@ -625,9 +637,11 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
             hi[e] = *reinterpret_cast<const uint32_t*>(&hv);
             lo[e] = *reinterpret_cast<const uint32_t*>(&lv);
           }
-          unsigned char* d = z + (rec.out + i0) * kPanelRowBytes;
-          *reinterpret_cast<uint4*>(d) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(d + 2048) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          unsigned char* d = z + (rec.out + i0) * rb;
+          if (live) {
+            *reinterpret_cast<uint4*>(d) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(d + 4 * rb) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          }
         }
       }
     }
@@ -727,11 +741,13 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelParams p)
 // 2 blocks per 256 threads; rows >= n and right-hand sides >= nb are zero.
 template <bool BF>
 __global__ void gather_kernel(const float2* __restrict__ x, int64_t ldx, int64_t n, int64_t rows,
-                              const int32_t* __restrict__ perm, int32_t rhs0, int32_t nb, unsigned char* __restrict__ xp) {
+                              const int32_t* __restrict__ perm, int32_t rhs0, int32_t nb, int32_t m64,
+                              unsigned char* __restrict__ xp) {
   constexpr int C = BF ? 8 : 4;
   const int64_t g = static_cast<int64_t>(blockIdx.x) * 2 + (threadIdx.x >> 7);
   const int m = threadIdx.x & 127;
-  if (g * C >= rows) return;
+  if (g * C >= rows || (m64 && m >= 64)) return;  // M = 64: the compact layout holds rows 0-63
+  const int64_t rb = panel_row_bytes(m64);
   const int r = m >> 1, part = m & 1;
   float v[C];
 #pragma unroll
@@ -744,7 +760,7 @@ __global__ void gather_kernel(const float2* __restrict__ x, int64_t ldx, int64_t
     }
     v[t] = f;
   }
-  unsigned char* d = xp + g * C * kPanelRowBytes + (m / 8) * 128 + (m % 8) * 16;
+  unsigned char* d = xp + g * C * rb + (m / 8) * 128 + (m % 8) * 16;
   if (!BF) {
     *reinterpret_cast<uint4*>(d) = make_uint4(tf32_rna(v[0]), tf32_rna(v[1]), tf32_rna(v[2]), tf32_rna(v[3]));
   } else {
@@ -759,23 +775,23 @@ __global__ void gather_kernel(const float2* __restrict__ x, int64_t ldx, int64_t
       lo[e] = *reinterpret_cast<const uint32_t*>(&lv);
     }
     *reinterpret_cast<uint4*>(d) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<uint4*>(d + 2048) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    *reinterpret_cast<uint4*>(d + 4 * rb) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
 }
 
 }  // namespace
 
 int panel_gather(const void* x, int64_t ldx, int64_t n, int64_t rows, const int32_t* perm, int32_t rhs0, int32_t nb,
-                 int32_t mode, void* xp, void* stream) {
+                 int32_t mode, int32_t m64, void* xp, void* stream) {
   const int C = panel_block_rows(mode);
   const int64_t blocks = (rows / C + 1) / 2;
   if (blocks > 0) {
     if (mode == kPanelBF16X3)
       gather_kernel<true><<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-          static_cast<const float2*>(x), ldx, n, rows, perm, rhs0, nb, static_cast<unsigned char*>(xp));
+          static_cast<const float2*>(x), ldx, n, rows, perm, rhs0, nb, m64, static_cast<unsigned char*>(xp));
     else
       gather_kernel<false><<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-          static_cast<const float2*>(x), ldx, n, rows, perm, rhs0, nb, static_cast<unsigned char*>(xp));
+          static_cast<const float2*>(x), ldx, n, rows, perm, rhs0, nb, m64, static_cast<unsigned char*>(xp));
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : set_error(UH_ECUDA, "panel gather launch: %s", cudaGetErrorString(e));

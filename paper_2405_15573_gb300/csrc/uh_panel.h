@@ -13,7 +13,9 @@
 // operand B (N = 2h rows: row 2i holds Re, row 2i+1 Im of output row i), with the panel rows its
 // columns multiply (operand A, M = 2 kPanelR rows: row 2r holds Re, row 2r+1 Im of right-hand
 // side r). D = A B^T accumulates in tensor memory (M = 128 lanes x N columns, FP32) over the
-// chunk's items, so that
+// chunk's items; a pass of at most 32 right-hand sides runs MMAs of M = 64 on the first 64 rows
+// of operand A (D row m then sits in lane 32 (m / 16) + m % 16: the lanes 0-15 of each 32-lane
+// quarter), so that
 //   Re Y[i][r] = D[2r][2i] - D[2r+1][2i+1],   Im Y[i][r] = D[2r+1][2i] + D[2r][2i+1],
 // two neighbouring lanes of one warp.
 //
@@ -44,6 +46,17 @@ constexpr int kPanelStages = 3;
 constexpr int kPanelRowBytes = 512;                          // one panel row in operand-A layout
 constexpr int kPanelTileMax = 2 * 128 * 2 * kPanelMaxH;      // B bytes at N = 128, two segments (32 KB)
 constexpr int kPanelABytes = kPanelK * kPanelRowBytes;       // operand A of an item (32 KB)
+// Bytes of a panel row in a pass: M = 128 rows of operand A, or the compact layout of M = 64
+// (the same core-matrix pattern for rows 0-63, blocks of C * 256 bytes) for at most 32
+// right-hand sides.
+#ifndef UH_HOST_DEVICE
+#ifdef __CUDACC__
+#define UH_HOST_DEVICE __host__ __device__
+#else
+#define UH_HOST_DEVICE
+#endif
+#endif
+UH_HOST_DEVICE constexpr int panel_row_bytes(int m64) { return m64 ? kPanelRowBytes / 2 : kPanelRowBytes; }
 
 enum : int { kPanelTF32 = 0, kPanelBF16X3 = 1 };
 // Panel rows per block of the operand-A layout, and the MMA's K per instruction.
@@ -89,6 +102,7 @@ struct PanelParams {
   int32_t rhs0;              // first right-hand side of this pass
   int32_t nb;                // right-hand sides in this pass (<= kPanelR)
   int32_t mode;              // kPanelTF32 or kPanelBF16X3
+  int32_t m64;               // 1: nb <= 32, MMAs of M = 64 on the first 64 operand-A rows
   unsigned long long* done;  // [2] monotonic: +1 per finished Z1 / Z2 chunk
   unsigned long long need[2];  // Z1 / Z2 complete in this pass when done[k] >= need[k]
   uint32_t* status;          // nonzero after a bounded wait ran out
@@ -99,7 +113,7 @@ struct PanelParams {
 // [rhs0, rhs0 + nb) (zero beyond nb), `rows` panel rows (a multiple of the block rows; rows
 // >= n are zero); then one phase of the pass.
 int panel_gather(const void* x, int64_t ldx, int64_t n, int64_t rows, const int32_t* perm, int32_t rhs0,
-                 int32_t nb, int32_t mode, void* xp, void* stream);
+                 int32_t nb, int32_t mode, int32_t m64, void* xp, void* stream);
 int panel_prepare();
 // Cooperative launch of one pass: every CTA must be resident (the phases wait on each other).
 int panel_launch(const PanelParams& p, int grid, void* stream);

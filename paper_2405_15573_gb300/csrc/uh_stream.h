@@ -156,10 +156,12 @@ constexpr int kFlagBase = kNumCounters + 1;
 // counter >= 0: the chunk's completion is added to that group counter.
 // kEnd: written by a CTA's producer after its last item (never packed).
 enum : int16_t { kToZ1 = 0, kToZ2 = 1, kToZ3 = 2, kToY = 3, kScatterZ1 = 5, kScatterZ2 = 6, kEnd = 7, kScatterZ4 = 8 };
+#ifndef UH_HOST_DEVICE
 #ifdef __CUDACC__
 #define UH_HOST_DEVICE __host__ __device__
 #else
 #define UH_HOST_DEVICE
+#endif
 #endif
 UH_HOST_DEVICE constexpr bool is_scatter(int kind) {
   return kind == kScatterZ1 || kind == kScatterZ2 || kind == kScatterZ4;
