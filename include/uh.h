@@ -78,7 +78,10 @@ enum { UH_DATA_C128 = 0, /* complex double, 16 bytes */
 enum { UH_PREC_C128 = 0, UH_PREC_C64 = 1, UH_PREC_C64_TF32 = 2, UH_PREC_C64_BF16X3 = 3 };
 
 /* Arithmetic of uh_matmat / h_matmat.
- *  UH_MM_SIMT:   one product per column on the CUDA cores (any op; the precision of uh_matvec).
+ *  UH_MM_SIMT:   the product on the CUDA cores in the precision of uh_matvec (any op): after
+ *                uh_reserve(op, >= 2) on a complex64 UH op, 4 (or 2) right-hand sides per pass
+ *                over the operator, each column bitwise equal to its uh_matvec; otherwise one
+ *                product per column.
  *  UH_MM_TF32:   tensor cores, TF32 operands, FP32 accumulation (op made with UH_PREC_C64_TF32).
  *  UH_MM_BF16X3: tensor cores, BF16 hi/lo split of both operands, 3 products, FP32 accumulation
  *                (op made with UH_PREC_C64_BF16X3). */
@@ -207,8 +210,11 @@ int uh_check(uh_op* op, void* stream);
 int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy,
               int32_t mode, void* stream);
 
-/* Kept for callers that reserve scratch ahead of uh_matmat: the scratch exists from uh_create on,
- * so this only checks its arguments (max_nrhs >= 1). */
+/* Scratch of the CUDA-core multi-RHS product (UH_MM_SIMT) for complex64 ops: with max_nrhs >= 2,
+ * allocates the product's vectors for 4 right-hand sides per pass (2 for ops of two CTAs per SM,
+ * uh_pack_params.ctas_per_sm), R times the bytes of uh_matvec's vectors. Synchronises the device
+ * when it allocates. Complex128 ops and max_nrhs = 1: nothing to allocate. The tensor-core modes'
+ * scratch exists from uh_create on. UH_EINVAL for max_nrhs < 1. */
 int uh_reserve(uh_op* op, int32_t max_nrhs);
 
 /* Sizes of the stored operator and of one product (Lemma 2.6, Def. 2.5). */

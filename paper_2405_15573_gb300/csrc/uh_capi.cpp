@@ -216,6 +216,11 @@ struct OpBase {
   void* d_z4 = nullptr;
   // uh_matvec_mixed (complex64 UH ops): xp, z1, z2, z3, z4 at 16 bytes per value
   void* d_xm[uh::kNumSources] = {};
+  // CUDA-core multi-RHS product (complex64 UH ops, after uh_reserve): the same vectors with
+  // multi_r values per position
+  int multi_r = 0;
+  void* d_xr[uh::kNumSources] = {};
+  int64_t src_len[uh::kNumSources] = {};
   // tensor-core uh_matmat (UH_PREC_C64_TF32 / UH_PREC_C64_BF16X3 ops)
   int mm_mode = -1;       // UH_MM_TF32 or UH_MM_BF16X3
   int panel_mode = 0;     // uh::kPanelTF32 or uh::kPanelBF16X3
@@ -247,7 +252,8 @@ void free_op(OpBase* o) {
   void* ptrs[] = {o->d_M, o->d_items, o->d_cta, o->d_done, o->d_scatter, o->d_pool, o->d_status,
                   o->d_perm, o->d_xp, o->d_z1, o->d_z2, o->d_z3, o->d_z4, o->d_xm[4],
                   o->d_ptiles, o->d_pitems, o->d_pbegin, o->d_pxp, o->d_pz1, o->d_pz2,
-                  o->d_xm[0], o->d_xm[1], o->d_xm[2], o->d_xm[3], o->d_pdone};
+                  o->d_xm[0], o->d_xm[1], o->d_xm[2], o->d_xm[3], o->d_pdone,
+                  o->d_xr[0], o->d_xr[1], o->d_xr[2], o->d_xr[3], o->d_xr[4]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (o->order_ev) cudaEventDestroy(o->order_ev);
@@ -371,6 +377,7 @@ int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T, bool mixed_vecto
   void** z[uh::kNumSources] = {&o->d_xp, &o->d_z1, &o->d_z2, &o->d_z3, &o->d_z4};
   int64_t vec_len = 0;
   for (int k = 0; k < uh::kNumSources; ++k) vec_len += P.src_len_[k];
+  for (int k = 0; k < uh::kNumSources; ++k) o->src_len[k] = P.src_len_[k];
   for (int k = 0; k < uh::kNumSources; ++k)
     if ((rc = upload(static_cast<const void*>(nullptr), static_cast<size_t>(std::max<int64_t>(P.src_len_[k], 2)) * eb, z[k])))
       return rc;
@@ -389,15 +396,22 @@ int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T, bool mixed_vecto
   return UH_OK;
 }
 
+// One product (nr = 1), or nr = 2 or 4 right-hand sides in one pass over the operator (complex64 UH
+// ops with reserved multi-RHS scratch; x and y n x nr column-major with leading dimensions ldx,
+// ldy).
 int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeout = kTimeoutCycles,
-               bool stall = false, bool mixed = false) {
+               bool stall = false, bool mixed = false, int nr = 1, int64_t ldx = 0, int64_t ldy = 0) {
   if (!x || !y) return fail(UH_EINVAL, "x and y must be device pointers");
   if (mixed && (o->c128 || !o->d_xm[0]))
     return fail(UH_EINVAL, "the extended-precision product needs a complex64 UH op");
   const size_t eb = o->c128 || mixed ? 16 : 8;
   const char* xa = static_cast<const char*>(x);
   const char* ya = static_cast<const char*>(y);
-  if (xa < ya + o->n * eb && ya < xa + o->n * eb) return fail(UH_EINVAL, "x and y overlap");
+  if (nr > 1 && (o->c128 || mixed || nr > o->multi_r || (nr != 2 && nr != 4) || (o->dual && nr > 2)))
+    return fail(UH_EINVAL, "%d right-hand sides per pass need reserved scratch (uh_reserve)", nr);
+  const int64_t xl = (nr - 1) * ldx + o->n, yl = (nr - 1) * ldy + o->n;
+  if (xa < ya + yl * static_cast<int64_t>(eb) && ya < xa + xl * static_cast<int64_t>(eb))
+    return fail(UH_EINVAL, "x and y overlap");
   std::lock_guard<std::mutex> lock(o->mu);
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc;
@@ -423,15 +437,21 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   p.y = y;
   p.perm = o->d_perm;
   p.scatter = o->d_scatter;
-  p.xp = mixed ? o->d_xm[0] : o->d_xp;
-  p.z1 = mixed ? o->d_xm[1] : o->d_z1;
-  p.z2 = mixed ? o->d_xm[2] : o->d_z2;
-  p.z3 = mixed ? o->d_xm[3] : o->d_z3;
-  p.z4 = mixed ? o->d_xm[4] : o->d_z4;
+  void* const* vec = mixed ? o->d_xm : nr > 1 ? o->d_xr : nullptr;
+  p.xp = vec ? vec[0] : o->d_xp;
+  p.z1 = vec ? vec[1] : o->d_z1;
+  p.z2 = vec ? vec[2] : o->d_z2;
+  p.z3 = vec ? vec[3] : o->d_z3;
+  p.z4 = vec ? vec[4] : o->d_z4;
+  p.ldx = ldx;
+  p.ldy = ldy;
   p.status = o->d_status;
   p.timeout_cycles = timeout;
   const int variant = mixed ? (o->dual ? uh::kVarMixedDual : uh::kVarMixed)
-                            : o->c128 ? uh::kVarC128 : o->dual ? uh::kVarC64Dual : uh::kVarC64;
+                      : o->c128 ? uh::kVarC128
+                      : nr == 4 ? uh::kVarC64R4
+                      : nr == 2 ? (o->dual ? uh::kVarC64DualR2 : uh::kVarC64R2)
+                      : o->dual ? uh::kVarC64Dual : uh::kVarC64;
   cudaError_t e = uh::stream_launch(variant, p, o->ncta, s);
   if (e != cudaSuccess) {
     --o->epoch;  // nothing launched: the counters did not move
@@ -635,13 +655,18 @@ int panel_ncta(int* ncta) {
   return UH_OK;
 }
 
-// One matmat by products per column.
+// The CUDA-core multi-RHS product: passes of multi_r right-hand sides (then 2), then one product
+// per remaining column.
 int matmat_by_columns(OpBase* o, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy, void* stream) {
   const size_t eb = o->c128 ? 16 : 8;
-  for (int32_t r = 0; r < nrhs; ++r) {
+  for (int32_t r = 0; r < nrhs;) {
+    const int left = nrhs - r;
+    const int nr = o->multi_r >= 4 && left >= 4 ? 4 : o->multi_r >= 2 && left >= 2 ? 2 : 1;
     const int rc = run_matvec(o, static_cast<const char*>(X) + static_cast<size_t>(r) * ldx * eb,
-                              static_cast<char*>(Y) + static_cast<size_t>(r) * ldy * eb, stream);
+                              static_cast<char*>(Y) + static_cast<size_t>(r) * ldy * eb, stream, kTimeoutCycles,
+                              false, false, nr, ldx, ldy);
     if (rc) return rc;
+    r += nr;
   }
   return UH_OK;
 }
@@ -1620,6 +1645,33 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
 int uh_reserve(uh_op* op, int32_t max_nrhs) {
   if (!op) return fail(UH_EINVAL, "null op");
   if (max_nrhs < 1) return fail(UH_EINVAL, "max_nrhs = %d", max_nrhs);
+  if (op->c128) return UH_OK;
+  // right-hand sides per pass: 4 (one CTA per SM), 2 (two CTAs per SM: the shared memory of the
+  // four-wide stages does not fit twice)
+  const int want = max_nrhs >= 4 && !op->dual ? 4 : max_nrhs >= 2 ? 2 : 1;
+  if (want <= op->multi_r || want < 2) return UH_OK;
+  std::lock_guard<std::mutex> lock(op->mu);
+  CUDA_TRY(cudaDeviceSynchronize());  // no pass may use the old scratch while it is replaced
+  const int variants[] = {op->dual ? uh::kVarC64DualR2 : uh::kVarC64R2, uh::kVarC64R4};
+  const int need = op->dual ? 2 : 1;
+  for (int v = 0; v < (want == 4 ? 2 : 1); ++v) {
+    CUDA_TRY(uh::stream_prepare(variants[v]));
+    int per = 0;
+    CUDA_TRY(uh::stream_occupancy(variants[v], &per));
+    if (per < need) return fail(UH_ECUDA, "multi-RHS streaming kernel does not fit %d CTAs per SM", need);
+  }
+  for (int k = 0; k < uh::kNumSources; ++k) {
+    if (op->d_xr[k]) cudaFree(op->d_xr[k]);
+    op->d_xr[k] = nullptr;
+  }
+  op->multi_r = 0;
+  for (int k = 0; k < uh::kNumSources; ++k) {
+    int rc = upload(static_cast<const void*>(nullptr),
+                    static_cast<size_t>(std::max<int64_t>(op->src_len[k], 2)) * 8 * want, &op->d_xr[k]);
+    if (rc) return rc;
+  }
+  op->multi_r = want;
+  op->st.device_bytes += (op->src_len[0] + op->src_len[1] + op->src_len[2] + op->src_len[3] + op->src_len[4]) * 8 * want;
   return UH_OK;
 }
 int h_matmat(h_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t mode, void* stream) {

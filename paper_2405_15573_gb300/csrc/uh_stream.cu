@@ -27,13 +27,14 @@ namespace {
 
 // Variants (uh_stream.h): TM = tile element, TV = element of the intermediate vectors, of the
 // staged inputs and of the accumulators, TX = element of x and y, L = shared-memory layout.
-// kMinBlocks: CTAs per SM the variant is compiled for.
+// kMinBlocks: CTAs per SM the variant is compiled for; R: right-hand sides of one product.
 struct KC64 {
   using TM = float2;
   using TV = float2;
   using TX = float2;
   using L = StreamSmemStd;
   static constexpr int kMinBlocks = 1;
+  static constexpr int R = 1;
 };
 struct KC128 {
   using TM = double2;
@@ -41,6 +42,7 @@ struct KC128 {
   using TX = double2;
   using L = StreamSmemStd;
   static constexpr int kMinBlocks = 1;
+  static constexpr int R = 1;
 };
 // TV = (re_hi, im_hi, re_lo, im_lo): the value re_hi + re_lo + i (im_hi + im_lo).
 struct KMixed {
@@ -49,6 +51,16 @@ struct KMixed {
   using TX = double2;
   using L = StreamSmemMixed;
   static constexpr int kMinBlocks = 1;
+  static constexpr int R = 1;
+};
+// Several right-hand sides of one complex64 program in one pass over the operator.
+struct KC64R2 : KC64 {
+  using L = StreamSmemR2;
+  static constexpr int R = 2;
+};
+struct KC64R4 : KC64 {
+  using L = StreamSmemR4;
+  static constexpr int R = 4;
 };
 // The same with two CTAs per SM (programs packed for kGeomDual).
 struct KC64Dual : KC64 {
@@ -58,6 +70,10 @@ struct KC64Dual : KC64 {
 struct KMixedDual : KMixed {
   using L = StreamSmemMixedDual;
   static constexpr int kMinBlocks = 2;
+};
+struct KC64DualR2 : KC64Dual {
+  using L = StreamSmemDualR2;
+  static constexpr int R = 2;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -289,6 +305,7 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
   using TM = typename K::TM;
   using TV = typename K::TV;
   using L = typename K::L;
+  constexpr int R = K::R;  // values per vector position
   unsigned char* stages = smem;
   WorkItem* ring = reinterpret_cast<WorkItem*>(smem + L::desc);
   const Bars bar = bars_of<L>(smem);
@@ -343,7 +360,7 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
     uint32_t bytes = tile_bytes;
 #pragma unroll
     for (int r = 0; r < kMaxRuns; ++r)
-      if (r < it.nruns) bytes += static_cast<uint32_t>(it.runs[r].len) * sizeof(TV);
+      if (r < it.nruns) bytes += static_cast<uint32_t>(it.runs[r].len) * sizeof(TV) * R;
     mbar_arrive_expect_tx(&bar.full[s], bytes);
     if (tile_bytes) bulk_g2s_hint(st, M + it.tile_off, tile_bytes, &bar.full[s], stream_once);
     const uint32_t deps = (static_cast<uint32_t>(it.flags) >> kDepShift) & ((1u << kNumCounters) - 1u);
@@ -372,8 +389,9 @@ __device__ void producer(const StreamParams& p, int i0, int i1, unsigned char* s
     for (int r = 0; r < kMaxRuns; ++r) {
       if (r >= it.nruns) break;
       const Run run = it.runs[r];
-      bulk_g2s_hint(st + tile_bytes + col * sizeof(TV), static_cast<const TV*>(src_ptr(p, run.src)) + run.start,
-                    static_cast<uint32_t>(run.len) * sizeof(TV), &bar.full[s], keep);
+      bulk_g2s_hint(st + tile_bytes + col * sizeof(TV) * R,
+                    static_cast<const TV*>(src_ptr(p, run.src)) + static_cast<int64_t>(run.start) * R,
+                    static_cast<uint32_t>(run.len) * sizeof(TV) * R, &bar.full[s], keep);
       col += static_cast<uint32_t>(run.len);
     }
     return done;
@@ -501,6 +519,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
   using TX = typename K::TX;
   using L = typename K::L;
   constexpr int EPL = 16 / sizeof(TM);  // tile elements per 16-byte row slice
+  constexpr int R = K::R;               // right-hand sides: vectors hold R values per position
   const int tid = threadIdx.x;
   unsigned char* stages = smem;
   const WorkItem* ring = reinterpret_cast<const WorkItem*>(smem + L::desc);
@@ -509,8 +528,10 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::misc);
   volatile int* go = abort_flag + 1;  // go[0], go[1]: leader's decision, by item parity
 
-  T acc[EPL];
-  T base = T{0, 0};
+  T acc[EPL][R];
+  T base[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) base[r] = T{0, 0};
   int out_idx = 0;
   static_assert(kStreamConsumers >= 256, "a chunk's first 256 scatter entries, one per consumer thread");
   Scatter my_scat{};  // this thread's scatter entry of the current chunk (entry tid, if any)
@@ -526,7 +547,11 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
     const int64_t e = b == nb - 1 ? p.n : (p.n * (b + 1) / nb) / EPV * EPV;
     const TX* x = static_cast<const TX*>(p.x);
     T* xp = static_cast<T*>(p.xp);
-    for (int64_t r = a + tid; r < e; r += kStreamConsumers) xp[r] = to_v(x[p.perm[r]], static_cast<T*>(nullptr));
+    for (int64_t q = a + tid; q < e; q += kStreamConsumers) {
+      const int64_t src = p.perm[q];
+#pragma unroll
+      for (int r = 0; r < R; ++r) xp[q * R + r] = to_v(x[src + r * p.ldx], static_cast<T*>(nullptr));
+    }
     publish(bar, pub_ctr, np++, kCounterPermute, p, abort_flag);
   }
   for (int seq = 0;; ++seq) {
@@ -552,7 +577,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
     const int64_t dst = sl.dst;
     const unsigned char* st = stages + static_cast<size_t>(s) * L::stage_bytes;
     const int rb = nchunk & 1;
-    T* sred = reinterpret_cast<T*>(smem + L::red) + rb * (kStreamConsumers * EPL);
+    T* sred = reinterpret_cast<T*>(smem + L::red) + rb * (kStreamConsumers * EPL * R);
     Scatter* sscat = reinterpret_cast<Scatter*>(smem + L::scat) + rb * 256;
     // The chunk's scatter entries (one per thread), loaded now into a register and stored to
     // shared memory at the chunk end, so that the load's latency overlaps the chunk's items.
@@ -568,36 +593,46 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
       g = tid / lanes;
       hpl = lanes * EPL;
 #pragma unroll
-      for (int e = 0; e < EPL; ++e) acc[e] = T{0, 0};
+      for (int e = 0; e < EPL; ++e)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[e][r] = T{0, 0};
     }
     // the staged inputs, after the tile
     const T* vin = reinterpret_cast<const T*>(st + static_cast<size_t>(nc) * hp * sizeof(TM));
     if (lane < need) {
       const TM* tile = reinterpret_cast<const TM*>(st) + lane * EPL;
       int c = g;
-      for (; c + 7 * groups < nc; c += 8 * groups) {
-        TM m[8][EPL];
-        T v[8];
+      // columns in flight per iteration: 8, or fewer for several right-hand sides (registers)
+      constexpr int U = R == 1 ? 8 : R == 2 ? 4 : 2;
+      for (; c + (U - 1) * groups < nc; c += U * groups) {
+        TM m[U][EPL];
+        T v[U][R];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < U; ++u) {
           lds16(tile + (c + u * groups) * hp, m[u]);
-          v[u] = vin[c + u * groups];
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[u][r] = vin[(c + u * groups) * R + r];
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < U; ++u)
 #pragma unroll
-          for (int e = 0; e < EPL; ++e) cfma(acc[e], m[u][e], v[u]);
+          for (int e = 0; e < EPL; ++e)
+#pragma unroll
+            for (int r = 0; r < R; ++r) cfma(acc[e][r], m[u][e], v[u][r]);
       }
       for (; c < nc; c += groups) {
         TM m0[EPL];
         lds16(tile + c * hp, m0);
-        const T v0 = vin[c];
 #pragma unroll
-        for (int e = 0; e < EPL; ++e) cfma(acc[e], m0[e], v0);
+        for (int e = 0; e < EPL; ++e)
+#pragma unroll
+          for (int r = 0; r < R; ++r) cfma(acc[e][r], m0[e], vin[c * R + r]);
       }
     }
     // the near-field partial of this row tile, staged after the inputs
-    if ((flags & kItemBase) && tid < h) base = vin[nc + tid];
+    if ((flags & kItemBase) && tid < h)
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[r] = vin[(nc + tid) * R + r];
     // The stage (tile, inputs, slot) has been read: release it to the producer.
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(&bar.empty[s]);
@@ -606,24 +641,29 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
       // butterfly over the group bits of the lane index, fixed order.
       for (int m = lanes; m < 32; m <<= 1) {
 #pragma unroll
-        for (int e = 0; e < EPL; ++e) acc[e] = cadd(acc[e], shfl_xor(acc[e], m));
+        for (int e = 0; e < EPL; ++e)
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[e][r] = cadd(acc[e][r], shfl_xor(acc[e][r], m));
       }
-      // One partial per warp (lanes <= 32) or per group (lanes >= 32): at most 8 of them.
+      // One partial per warp (lanes <= 32) or per group (lanes >= 32): at most 8 of them, each
+      // row's R values together.
       const int parts = lanes < 32 ? kStreamConsumerWarps : groups;
       const int part = lanes < 32 ? warp : g;
       if (lanes >= 32 || (tid & 31) < lanes) {
 #pragma unroll
-        for (int e = 0; e < EPL; ++e) sred[part * hpl + lane * EPL + e] = acc[e];
+        for (int e = 0; e < EPL; ++e)
+#pragma unroll
+          for (int r = 0; r < R; ++r) sred[(part * hpl + lane * EPL + e) * R + r] = acc[e][r];
       }
       if (is_scatter(kind) && tid < naux && tid < 256) sscat[tid] = my_scat;
       consumer_sync();
-      // Output r of the chunk: its partials summed in a fixed order (at most 8 of them; the loads
-      // are independent and issued together).
-      auto row_sum = [&](int r) -> T {
-        T v = sred[r];
+      // Output row `row`, right-hand side r: its partials summed in a fixed order (at most 8 of
+      // them; the loads are independent and issued together).
+      auto row_sum = [&](int row, int r) -> T {
+        T v = sred[row * R + r];
 #pragma unroll
         for (int q = 1; q < kStreamConsumerWarps; ++q)
-          if (q < parts) v = cadd(v, sred[q * hpl + r]);
+          if (q < parts) v = cadd(v, sred[(q * hpl + row) * R + r]);
         return v;
       };
       if (is_scatter(kind) && h <= kStreamHpMax) {
@@ -634,7 +674,9 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
         const int dk = kStreamConsumers / h, dr = kStreamConsumers - dk * h;
         for (int w = tid; w < naux * h; w += kStreamConsumers) {
           const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];
-          if (r >= e.lo && r < e.hi) z[e.dst + r - e.lo] = row_sum(r);
+          if (r >= e.lo && r < e.hi)
+#pragma unroll
+            for (int q = 0; q < R; ++q) z[(static_cast<int64_t>(e.dst) + r - e.lo) * R + q] = row_sum(r, q);
           k += dk;
           r += dr;
           if (r >= h) {
@@ -643,21 +685,30 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
           }
         }
       } else if (tid < h) {
-        T v = row_sum(tid);
-        if (flags & kItemBase) v = cadd(v, base);
+        T v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          v[r] = row_sum(tid, r);
+          if (flags & kItemBase) v[r] = cadd(v[r], base[r]);
+        }
         if (kind == kToY) {
-          static_cast<TX*>(p.y)[out_idx] = to_x(v, static_cast<TX*>(nullptr));
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            static_cast<TX*>(p.y)[out_idx + r * p.ldy] = to_x(v[r], static_cast<TX*>(nullptr));
         } else if (is_scatter(kind)) {
           // a tall chunk (t_b rows, up to kStreamHpTall): each thread stores its own row to every
           // scatter entry holding it (few entries: one per block in the chunk)
           T* z = static_cast<T*>(kind == kScatterZ1 ? p.z1 : kind == kScatterZ2 ? p.z2 : p.z4);
           for (int k = 0; k < naux; ++k) {
             const Scatter e = k < 256 ? sscat[k] : p.scatter[aux + k];
-            if (tid >= e.lo && tid < e.hi) z[e.dst + tid - e.lo] = v;
+            if (tid >= e.lo && tid < e.hi)
+#pragma unroll
+              for (int r = 0; r < R; ++r) z[(static_cast<int64_t>(e.dst) + tid - e.lo) * R + r] = v[r];
           }
         } else {
           T* z = static_cast<T*>(kind == kToZ1 ? p.z1 : kind == kToZ2 ? p.z2 : p.z3);
-          z[dst + tid] = v;
+#pragma unroll
+          for (int r = 0; r < R; ++r) z[(dst + tid) * R + r] = v[r];
         }
       }
       // sred and sscat of this parity are next written two chunks on, after the next chunk end's
@@ -711,6 +762,11 @@ const void* stream_fn(int variant, int* smem_bytes) {
     case kVarC128: *smem_bytes = KC128::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC128>);
     case kVarMixed: *smem_bytes = KMixed::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KMixed>);
     case kVarC64Dual: *smem_bytes = KC64Dual::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC64Dual>);
+    case kVarC64R2: *smem_bytes = KC64R2::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC64R2>);
+    case kVarC64R4: *smem_bytes = KC64R4::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC64R4>);
+    case kVarC64DualR2:
+      *smem_bytes = KC64DualR2::L::bytes;
+      return reinterpret_cast<const void*>(stream_kernel<KC64DualR2>);
     case kVarMixedDual:
       *smem_bytes = KMixedDual::L::bytes;
       return reinterpret_cast<const void*>(stream_kernel<KMixedDual>);

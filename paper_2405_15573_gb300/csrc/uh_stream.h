@@ -80,7 +80,16 @@ static_assert(2 * kPoolSeg + kStages <= kDescRing, "a fetched pool segment must 
 // kStageBytesDual (tiles up to kTileBytesDual). The second suits operators of many small chunks
 // (low ranks, small leaves, batches of small operators), whose per-item and per-chunk latencies
 // then overlap between the two CTAs of an SM; kVarC64Dual and kVarMixedDual run such programs.
-enum StreamVariant : int { kVarC64 = 0, kVarC128 = 1, kVarMixed = 2, kVarC64Dual = 3, kVarMixedDual = 4 };
+// kVarC64R2 / kVarC64R4 / kVarC64DualR2 run a complex64 program for 2 or 4 right-hand sides in one
+// pass over the operator: every vector holds the R values of a position together, and an item's
+// inputs take R times the bytes, so these run two stages of the geometry's stage plus
+// (R - 1) * 8 * (kStreamMaxCols + kStreamHpMax) bytes (an item stages at most
+// kStreamMaxCols + kStreamHpMax values).
+enum StreamVariant : int {
+  kVarC64 = 0, kVarC128 = 1, kVarMixed = 2, kVarC64Dual = 3, kVarMixedDual = 4,
+  kVarC64R2 = 5, kVarC64R4 = 6, kVarC64DualR2 = 7
+};
+constexpr int stage_bytes_rhs(int stage_bytes, int r) { return stage_bytes + (r - 1) * 8 * (kStreamMaxCols + kStreamHpMax); }
 constexpr int kStageBytesMixed = kStageBytes + 8 * (kStreamMaxCols + kStreamHpMax);
 constexpr int kStagesMixed = 2;
 constexpr int kStagesDual = 3;
@@ -121,7 +130,11 @@ using StreamSmemMixed = StreamSmem<kStagesMixed, kStageBytesMixed, 32>;
 using StreamSmemDual = StreamSmem<kStagesDual, kStageBytesDual, 16>;
 using StreamSmemMixedDual = StreamSmem<kStagesMixed, kStageBytesMixedDual, 32>;
 // two CTAs per SM: 228 KB of shared memory per SM, 1 KB of it reserved per CTA
+using StreamSmemR2 = StreamSmem<2, stage_bytes_rhs(kStageBytes, 2), 32>;
+using StreamSmemR4 = StreamSmem<2, stage_bytes_rhs(kStageBytes, 4), 64>;
+using StreamSmemDualR2 = StreamSmem<2, stage_bytes_rhs(kStageBytesDual, 2), 32>;
 static_assert(2 * (StreamSmemDual::bytes + 1024) <= 228 * 1024, "two CTAs per SM");
+static_assert(2 * (StreamSmemDualR2::bytes + 1024) <= 228 * 1024, "two CTAs per SM");
 static_assert(2 * (StreamSmemMixedDual::bytes + 1024) <= 228 * 1024, "two CTAs per SM");
 
 // Input vectors a run can read.
@@ -230,6 +243,8 @@ struct StreamParams {
   void* z2;                  // yhat (kSrcZ2)
   void* z3;                  // near-field partials of row tiles (base of the backward chunks)
   void* z4;                  // t_b = S_Y,b^* xhat_sigma of the blocks stored factored (kSrcZ4)
+  int64_t ldx, ldy;          // several right-hand sides: x and y are n x R column-major, these
+                             // leading dimensions apart (unused for one right-hand side)
   uint32_t* status;          // nonzero after a bounded wait ran out
   long long timeout_cycles;  // bound of every wait, in SM clock cycles
 };

@@ -158,3 +158,32 @@ def test_matmat_argument_errors(U):
     st = opt.stats()
     assert st["matmat_mode"] == U.UH_MM_TF32 and st["panel_items"] > 0
     assert op64.stats()["matmat_mode"] == -1
+
+
+@pytest.mark.parametrize("case", ["one_cta", "two_ctas", "factored"])
+def test_multi_rhs_simt_product_equals_matvec_columns(U, case):
+    """After uh_reserve, the CUDA-core multi-RHS product runs 4 (one CTA per SM) or 2 (two CTAs
+    per SM) right-hand sides per pass over the operator. Each column's arithmetic is that of its
+    single product, so every column equals uh_matvec bit for bit; leading dimensions above n."""
+    import torch
+    pts, tree, hf, h, uh = oracle_ops(*WORKLOADS["ellipsoid1000"])
+    if case == "factored":
+        uh = O.factor_coupling(uh, 3e-5)
+    params = U.PackParams(0, 0, 0, 0, 2) if case == "two_ctas" else None
+    op = U.UHOp.from_arrays(uh_arrays(uh), "c64", params)
+    op.reserve(8)
+    nrhs = 9  # passes of 4 + 4 + 1 (one CTA per SM) or 2 + 2 + 2 + 2 + 1 (two)
+    X = _X(tree.n, nrhs, seed=50)
+    Xd = _colmajor(torch, X, ld=tree.n + 3)
+    Yd = _poisoned(torch, tree.n, nrhs, ld=tree.n + 5)
+    op.matmat(Xd, Yd, mode="simt")
+    for j in range(nrhs):
+        yj = op.matvec(Xd[:, j].contiguous())
+        assert torch.equal(yj, Yd[:, j]), j
+    op.check()
+    Y = Yd.cpu().numpy().astype(np.complex128)
+    for j in range(nrhs):
+        assert relerr(Y[:, j], O.uh_matvec(uh, X[:, j])) <= 5e-6
+    st = op.stats()
+    assert st["pack_ctas_per_sm"] == (2 if case == "two_ctas" else 1)
+    op.close()
