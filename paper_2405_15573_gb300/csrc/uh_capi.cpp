@@ -400,7 +400,8 @@ int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T, bool mixed_vecto
 // ops with reserved multi-RHS scratch; x and y n x nr column-major with leading dimensions ldx,
 // ldy).
 int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeout = kTimeoutCycles,
-               bool stall = false, bool mixed = false, int nr = 1, int64_t ldx = 0, int64_t ldy = 0) {
+               bool stall = false, bool mixed = false, int nr = 1, int64_t ldx = 0, int64_t ldy = 0,
+               bool ranges_checked = false) {
   if (!x || !y) return fail(UH_EINVAL, "x and y must be device pointers");
   if (mixed && (o->c128 || !o->d_xm[0]))
     return fail(UH_EINVAL, "the extended-precision product needs a complex64 UH op");
@@ -410,7 +411,7 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   if (nr > 1 && (o->c128 || mixed || nr > o->multi_r || (nr != 2 && nr != 4) || (o->dual && nr > 2)))
     return fail(UH_EINVAL, "%d right-hand sides per pass need reserved scratch (uh_reserve)", nr);
   const int64_t xl = (nr - 1) * ldx + o->n, yl = (nr - 1) * ldy + o->n;
-  if (xa < ya + yl * static_cast<int64_t>(eb) && ya < xa + xl * static_cast<int64_t>(eb))
+  if (!ranges_checked && xa < ya + yl * static_cast<int64_t>(eb) && ya < xa + xl * static_cast<int64_t>(eb))
     return fail(UH_EINVAL, "x and y overlap");
   std::lock_guard<std::mutex> lock(o->mu);
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1697,3 +1698,24 @@ extern "C" int uh_pack_check_ex(const uh_desc* desc, int32_t precision, const uh
   g_pack_only_ncta = 0;
   return rc;
 }
+
+namespace uh {
+
+int multi_rhs_width(const uh_op* op) { return op && !op->c128 ? op->multi_r : 0; }
+
+int matvec_pair(uh_op* op, const void* x0, const void* x1, void* y0, void* y1, void* stream) {
+  if (!op || !x0 || !x1 || !y0 || !y1) return fail(UH_EINVAL, "null argument");
+  if (op->c128 || op->multi_r < 2) return fail(UH_EINVAL, "a paired product needs a complex64 op with uh_reserve(op, 2)");
+  const int64_t bytes = op->n * 8;
+  const char* v[4] = {static_cast<const char*>(x0), static_cast<const char*>(x1), static_cast<const char*>(y0),
+                      static_cast<const char*>(y1)};
+  // no output overlaps an input or the other output
+  for (int a = 2; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      if (a != b && v[a] < v[b] + bytes && v[b] < v[a] + bytes) return fail(UH_EINVAL, "paired vectors overlap");
+  const std::ptrdiff_t dx = v[1] - v[0], dy = v[3] - v[2];
+  if (dx % 8 || dy % 8) return fail(UH_EINVAL, "paired vectors not element-aligned");
+  return run_matvec(op, x0, y0, stream, kTimeoutCycles, false, false, 2, dx / 8, dy / 8, true);
+}
+
+}  // namespace uh

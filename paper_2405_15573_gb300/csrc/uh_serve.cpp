@@ -83,6 +83,8 @@ struct Solve {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;  // recorded after each issued step
   bool inflight = false;     // a step is issued and its event not yet seen complete
+  bool held = false;         // ready for an Arnoldi step, waiting for a partner of the same op
+  int paired_steps = 0;      // Arnoldi steps whose product shared a pass with another solve's
   // GMRES state
   Phase phase = kStart;
   bool x_zero = true;
@@ -118,6 +120,7 @@ struct uh_server {
   std::map<uint64_t, std::unique_ptr<Solve>> all;  // every solve not yet collected by poll
   std::vector<Workspace> spare;                    // workspaces of finished solves
   uint64_t next_ticket = 1;
+  uint64_t paired = 0;  // Arnoldi steps whose product shared a pass with another solve's
   bool stop = false;
   std::thread worker;
 };
@@ -253,14 +256,15 @@ int issue_start(Solve* s, cudaStream_t st) {
 
 // One Arnoldi step j: w = A V_j, two passes of classical Gram-Schmidt against V_0..V_j,
 // V_{j+1} = w / ||w|| (and its complex64 copy); both coefficient passes and the norm copied to
-// the host in one copy.
-int issue_arnoldi(Solve* s, cudaStream_t st) {
+// the host in one copy. With product = false the product A V_j is already in y32 (a paired
+// product).
+int issue_arnoldi(Solve* s, cudaStream_t st, bool product = true) {
   int rc;
   const int64_t n = s->n;
   const int cnt = s->j + 1;
   const char* Vj = static_cast<const char*>(s->V) + static_cast<size_t>(s->j) * n * 16;
   if (s->c64) {
-    if ((rc = apply_op(s, Vj, nullptr, st, s->v32_ready))) return rc;
+    if (product && (rc = apply_op(s, Vj, nullptr, st, s->v32_ready))) return rc;
     if ((rc = uh::vec_dots_f(s->V, n, cnt, s->y32, s->w, s->part, s->h1, st))) return rc;
   } else {
     if ((rc = apply_op(s, Vj, s->w, st))) return rc;
@@ -387,6 +391,39 @@ void issue_step(uh_server* sv, Solve* s) {
   s->inflight = true;
 }
 
+// Whether solve s's next step is an Arnoldi step whose product can share a pass with another's:
+// complex64 op with two-wide scratch, x in complex64 already (v32).
+bool pairable(const Solve* s) {
+  return s->phase == kArnoldi && s->c64 && s->v32_ready && uh::multi_rhs_width(s->op) >= 2;
+}
+
+// The Arnoldi steps of solves a and b (same op) with one product of two right-hand sides, on a's
+// stream; b's stream waits for it, then each runs its Gram-Schmidt on its own stream. Each result
+// is bitwise that of its own product, so a solve's arithmetic does not depend on its partner.
+void issue_pair(uh_server* sv, Solve* a, Solve* b) {
+  int rc = uh::matvec_pair(a->op, a->v32, b->v32, a->y32, b->y32, a->st);
+  if (!rc && (cudaEventRecord(a->ev, a->st) != cudaSuccess || cudaStreamWaitEvent(b->st, a->ev, 0) != cudaSuccess))
+    rc = UH_ECUDA;
+  if (rc) {  // not issued together: each on its own
+    issue_step(sv, a);
+    issue_step(sv, b);
+    return;
+  }
+  for (Solve* s : {a, b}) {
+    int r = issue_arnoldi(s, s->st, false);
+    if (!r && cudaEventRecord(s->ev, s->st) != cudaSuccess) r = UH_ECUDA;
+    if (r) {
+      s->status = r;
+      s->phase = kDone;
+      s->inflight = false;
+    } else {
+      s->inflight = true;
+      s->paired_steps++;
+    }
+  }
+  sv->paired += 2;
+}
+
 // Ends the solves still running when the server stops (after their streams drain).
 void abort_active(uh_server* sv) {
   for (Solve* s : sv->active) {
@@ -439,7 +476,9 @@ void worker_main(uh_server* sv) {
     bool progress = !fresh.empty();
     // newly admitted solves: workspace, then their first step
     for (Solve* s : fresh) issue_step(sv, s);
-    // every solve whose step has completed: host-side update, then its next step at once
+    // every solve whose step has completed: host-side update; its next step is issued at once,
+    // or held while another solve of the same op has a step in flight and both can share their
+    // next product (one pass of two right-hand sides)
     for (Solve* s : running) {
       if (s->phase == kDone || !s->inflight) continue;
       const cudaError_t q = cudaEventQuery(s->ev);
@@ -458,7 +497,34 @@ void worker_main(uh_server* sv) {
         if (s->status == UH_OK && uh_check(s->op, s->st) != UH_OK) s->status = UH_ETIMEOUT;
         continue;
       }
+      if (pairable(s)) {
+        s->held = true;
+        continue;
+      }
       issue_step(sv, s);
+    }
+    // held solves: in pairs per op; a single one waits only while another solve of its op has a
+    // step in flight (that step ends, so every hold ends)
+    for (size_t i = 0; i < running.size(); ++i) {
+      Solve* a = running[i];
+      if (!a->held) continue;
+      Solve* b = nullptr;
+      bool busy = false;
+      for (size_t k = 0; k < running.size(); ++k) {
+        Solve* c = running[k];
+        if (c == a || c->op != a->op || c->phase == kDone) continue;
+        if (c->held && !b) b = c;
+        if (c->inflight) busy = true;
+      }
+      if (b) {
+        a->held = b->held = false;
+        issue_pair(sv, a, b);
+        progress = true;
+      } else if (!busy) {
+        a->held = false;
+        issue_step(sv, a);
+        progress = true;
+      }
     }
     bool finished = false;
     for (Solve* s : running) finished = finished || s->phase == kDone;
@@ -592,6 +658,7 @@ int uh_solve_poll(uh_server* sv, uint64_t ticket, void* x, uh_solve_info* info) 
     info->rel_residual = s->bnorm > 0 ? s->resid / s->bnorm : 0.0;
     info->queue_s = s->t_admit - s->t_submit;
     info->latency_s = s->t_done - s->t_submit;
+    info->paired_steps = s->paired_steps;
   }
   if (x && s->status == UH_OK) std::memcpy(x, s->result.data(), s->result.size() * sizeof(cd));
   const int status = s->status;

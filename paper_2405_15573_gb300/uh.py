@@ -472,7 +472,8 @@ class UHBatch:
 
 class SolveInfo(C.Structure):
     _fields_ = [("status", _i32), ("converged", _i32), ("iterations", _i32), ("restarts", _i32),
-                ("rel_residual", C.c_double), ("queue_s", C.c_double), ("latency_s", C.c_double)]
+                ("rel_residual", C.c_double), ("queue_s", C.c_double), ("latency_s", C.c_double),
+                ("paired_steps", _i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -97,6 +97,29 @@ def test_same_result_alone_and_in_a_mix(U, ops):
     srv.close()
 
 
+def test_paired_products_change_no_result(U, ops):
+    """With multi-RHS scratch reserved on the op, solves of that op share their Arnoldi products
+    (passes of two right-hand sides). A solve's x is still bitwise that of the same solve alone on
+    an op without pairing, and of the same solve alone on the reserved op."""
+    uh, op_plain, _ = ops["sphere"]
+    op = U.UHOp.from_arrays(uh_arrays(uh), "c64")
+    op.reserve(2)
+    bs = [I.complex_normal(uh.tree.n, 60 + k) for k in range(6)]
+    srv = U.Server(max_active=8)
+    alone = [srv.wait(srv.submit(op_plain, b))[0] for b in bs]
+    x_res, info_res = srv.wait(srv.submit(op, bs[0]))
+    assert info_res["paired_steps"] == 0
+    tickets = [srv.submit(op, b) for b in bs]
+    res = [srv.wait(t) for t in tickets]
+    srv.close()
+    assert np.array_equal(x_res, alone[0])
+    for (x, info), xa in zip(res, alone):
+        assert info["converged"] == 1
+        assert np.array_equal(x, xa)
+    assert sum(info["paired_steps"] for _, info in res) > 0
+    op.close()
+
+
 def test_admission_busy_and_errors(U, ops):
     uh, op64, _ = ops["sphere"]
     b = I.complex_normal(uh.tree.n, 6)
