@@ -339,10 +339,11 @@ int uh_batch_stats(const uh_batch* batch, uh_stats_t* out);
  * Gram-Schmidt, two passes), the norms and the update x += V y run in FP64 on the GPU. A solve
  * ends as converged only when the recomputed residual of the returned x satisfies
  * ||b - A x|| <= tol ||b||. Its arithmetic does not depend on the other solves running with it.
- * Solves of one complex64 op that has multi-RHS scratch (uh_reserve(op, 2)) share their Arnoldi
+ * Solves of one complex64 op that has multi-RHS scratch (uh_reserve) share their Arnoldi
  * products: a solve ready for its next product waits while another solve of the same op has a
- * step in flight, and two such solves run their products as one pass of two right-hand sides
- * (each result bitwise that of its own product, so the results do not change).
+ * step in flight, and the waiting solves run their products as one pass of up to the reserved
+ * width (4, or 2 for ops of two CTAs per SM) right-hand sides (each result bitwise that of its
+ * own product, so the results do not change).
  * The server uses the device current at uh_server_create and streams of its own; the ops it is
  * given must live on that device and outlive their solves. Products the caller runs on the same
  * ops meanwhile are ordered with the solves' products, like any calls on one op.

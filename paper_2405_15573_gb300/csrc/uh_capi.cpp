@@ -397,11 +397,11 @@ int upload_program(OpBase* o, ProgramBuilder& P, const Tree& T, bool mixed_vecto
 }
 
 // One product (nr = 1), or nr = 2 or 4 right-hand sides in one pass over the operator (complex64 UH
-// ops with reserved multi-RHS scratch; x and y n x nr column-major with leading dimensions ldx,
-// ldy).
+// ops with reserved multi-RHS scratch): x = xs[0], y = ys[0], right-hand side r at xs[r] / ys[r]
+// (n values each; the caller checks that no output overlaps an input or another output).
 int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeout = kTimeoutCycles,
-               bool stall = false, bool mixed = false, int nr = 1, int64_t ldx = 0, int64_t ldy = 0,
-               bool ranges_checked = false) {
+               bool stall = false, bool mixed = false, int nr = 1, const void* const* xs = nullptr,
+               void* const* ys = nullptr) {
   if (!x || !y) return fail(UH_EINVAL, "x and y must be device pointers");
   if (mixed && (o->c128 || !o->d_xm[0]))
     return fail(UH_EINVAL, "the extended-precision product needs a complex64 UH op");
@@ -410,8 +410,8 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   const char* ya = static_cast<const char*>(y);
   if (nr > 1 && (o->c128 || mixed || nr > o->multi_r || (nr != 2 && nr != 4) || (o->dual && nr > 2)))
     return fail(UH_EINVAL, "%d right-hand sides per pass need reserved scratch (uh_reserve)", nr);
-  const int64_t xl = (nr - 1) * ldx + o->n, yl = (nr - 1) * ldy + o->n;
-  if (!ranges_checked && xa < ya + yl * static_cast<int64_t>(eb) && ya < xa + xl * static_cast<int64_t>(eb))
+  if (nr > 1 && (!xs || !ys)) return fail(UH_EINVAL, "right-hand side pointers missing");
+  if (nr == 1 && xa < ya + o->n * static_cast<int64_t>(eb) && ya < xa + o->n * static_cast<int64_t>(eb))
     return fail(UH_EINVAL, "x and y overlap");
   std::lock_guard<std::mutex> lock(o->mu);
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -444,8 +444,10 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   p.z2 = vec ? vec[2] : o->d_z2;
   p.z3 = vec ? vec[3] : o->d_z3;
   p.z4 = vec ? vec[4] : o->d_z4;
-  p.ldx = ldx;
-  p.ldy = ldy;
+  for (int r = 0; r < nr && nr > 1; ++r) {
+    p.xr[r] = xs[r];
+    p.yr[r] = ys[r];
+  }
   p.status = o->d_status;
   p.timeout_cycles = timeout;
   const int variant = mixed ? (o->dual ? uh::kVarMixedDual : uh::kVarMixed)
@@ -657,15 +659,19 @@ int panel_ncta(int* ncta) {
 }
 
 // The CUDA-core multi-RHS product: passes of multi_r right-hand sides (then 2), then one product
-// per remaining column.
+// per remaining column (X and Y do not overlap: checked by the caller).
 int matmat_by_columns(OpBase* o, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy, void* stream) {
   const size_t eb = o->c128 ? 16 : 8;
   for (int32_t r = 0; r < nrhs;) {
     const int left = nrhs - r;
     const int nr = o->multi_r >= 4 && left >= 4 ? 4 : o->multi_r >= 2 && left >= 2 ? 2 : 1;
-    const int rc = run_matvec(o, static_cast<const char*>(X) + static_cast<size_t>(r) * ldx * eb,
-                              static_cast<char*>(Y) + static_cast<size_t>(r) * ldy * eb, stream, kTimeoutCycles,
-                              false, false, nr, ldx, ldy);
+    const void* xs[4];
+    void* ys[4];
+    for (int q = 0; q < nr; ++q) {
+      xs[q] = static_cast<const char*>(X) + static_cast<size_t>(r + q) * ldx * eb;
+      ys[q] = static_cast<char*>(Y) + static_cast<size_t>(r + q) * ldy * eb;
+    }
+    const int rc = run_matvec(o, xs[0], ys[0], stream, kTimeoutCycles, false, false, nr, xs, ys);
     if (rc) return rc;
     r += nr;
   }
@@ -1703,19 +1709,23 @@ namespace uh {
 
 int multi_rhs_width(const uh_op* op) { return op && !op->c128 ? op->multi_r : 0; }
 
-int matvec_pair(uh_op* op, const void* x0, const void* x1, void* y0, void* y1, void* stream) {
-  if (!op || !x0 || !x1 || !y0 || !y1) return fail(UH_EINVAL, "null argument");
-  if (op->c128 || op->multi_r < 2) return fail(UH_EINVAL, "a paired product needs a complex64 op with uh_reserve(op, 2)");
+int matvec_group(uh_op* op, int nr, const void* const* xs, void* const* ys, void* stream) {
+  if (!op || !xs || !ys) return fail(UH_EINVAL, "null argument");
+  if (op->c128 || (nr != 2 && nr != 4) || nr > op->multi_r)
+    return fail(UH_EINVAL, "%d products in one pass need a complex64 op with uh_reserve(op, %d)", nr, nr);
   const int64_t bytes = op->n * 8;
-  const char* v[4] = {static_cast<const char*>(x0), static_cast<const char*>(x1), static_cast<const char*>(y0),
-                      static_cast<const char*>(y1)};
-  // no output overlaps an input or the other output
-  for (int a = 2; a < 4; ++a)
-    for (int b = 0; b < 4; ++b)
-      if (a != b && v[a] < v[b] + bytes && v[b] < v[a] + bytes) return fail(UH_EINVAL, "paired vectors overlap");
-  const std::ptrdiff_t dx = v[1] - v[0], dy = v[3] - v[2];
-  if (dx % 8 || dy % 8) return fail(UH_EINVAL, "paired vectors not element-aligned");
-  return run_matvec(op, x0, y0, stream, kTimeoutCycles, false, false, 2, dx / 8, dy / 8, true);
+  for (int a = 0; a < nr; ++a) {
+    if (!xs[a] || !ys[a]) return fail(UH_EINVAL, "null vector");
+    const char* ya = static_cast<const char*>(ys[a]);
+    // no output overlaps an input or another output
+    for (int b = 0; b < nr; ++b) {
+      const char* xb = static_cast<const char*>(xs[b]);
+      const char* yb = static_cast<const char*>(ys[b]);
+      if (ya < xb + bytes && xb < ya + bytes) return fail(UH_EINVAL, "grouped vectors overlap");
+      if (b != a && ya < yb + bytes && yb < ya + bytes) return fail(UH_EINVAL, "grouped outputs overlap");
+    }
+  }
+  return run_matvec(op, xs[0], ys[0], stream, kTimeoutCycles, false, false, nr, xs, ys);
 }
 
 }  // namespace uh

@@ -120,7 +120,6 @@ struct uh_server {
   std::map<uint64_t, std::unique_ptr<Solve>> all;  // every solve not yet collected by poll
   std::vector<Workspace> spare;                    // workspaces of finished solves
   uint64_t next_ticket = 1;
-  uint64_t paired = 0;  // Arnoldi steps whose product shared a pass with another solve's
   bool stop = false;
   std::thread worker;
 };
@@ -397,19 +396,30 @@ bool pairable(const Solve* s) {
   return s->phase == kArnoldi && s->c64 && s->v32_ready && uh::multi_rhs_width(s->op) >= 2;
 }
 
-// The Arnoldi steps of solves a and b (same op) with one product of two right-hand sides, on a's
-// stream; b's stream waits for it, then each runs its Gram-Schmidt on its own stream. Each result
-// is bitwise that of its own product, so a solve's arithmetic does not depend on its partner.
-void issue_pair(uh_server* sv, Solve* a, Solve* b) {
-  int rc = uh::matvec_pair(a->op, a->v32, b->v32, a->y32, b->y32, a->st);
-  if (!rc && (cudaEventRecord(a->ev, a->st) != cudaSuccess || cudaStreamWaitEvent(b->st, a->ev, 0) != cudaSuccess))
-    rc = UH_ECUDA;
+void issue_group(uh_server* sv, const std::vector<Solve*>& g);
+
+// The Arnoldi steps of the solves in g (2 or 4, one op) with one product of that many right-hand
+// sides, on the first solve's stream; the others' streams wait for it, then each runs its
+// Gram-Schmidt on its own stream. Each result is bitwise that of its own product, so a solve's
+// arithmetic does not depend on its partners.
+void issue_group(uh_server* sv, const std::vector<Solve*>& g) {
+  const int nr = static_cast<int>(g.size());
+  Solve* a = g[0];
+  const void* xs[4];
+  void* ys[4];
+  for (int r = 0; r < nr; ++r) {
+    xs[r] = g[r]->v32;
+    ys[r] = g[r]->y32;
+  }
+  int rc = uh::matvec_group(a->op, nr, xs, ys, a->st);
+  if (!rc && cudaEventRecord(a->ev, a->st) != cudaSuccess) rc = UH_ECUDA;
+  for (int r = 1; r < nr && !rc; ++r)
+    if (cudaStreamWaitEvent(g[r]->st, a->ev, 0) != cudaSuccess) rc = UH_ECUDA;
   if (rc) {  // not issued together: each on its own
-    issue_step(sv, a);
-    issue_step(sv, b);
+    for (Solve* s : g) issue_step(sv, s);
     return;
   }
-  for (Solve* s : {a, b}) {
+  for (Solve* s : g) {
     int r = issue_arnoldi(s, s->st, false);
     if (!r && cudaEventRecord(s->ev, s->st) != cudaSuccess) r = UH_ECUDA;
     if (r) {
@@ -421,7 +431,6 @@ void issue_pair(uh_server* sv, Solve* a, Solve* b) {
       s->paired_steps++;
     }
   }
-  sv->paired += 2;
 }
 
 // Ends the solves still running when the server stops (after their streams drain).
@@ -503,28 +512,34 @@ void worker_main(uh_server* sv) {
       }
       issue_step(sv, s);
     }
-    // held solves: in pairs per op; a single one waits only while another solve of its op has a
-    // step in flight (that step ends, so every hold ends)
+    // held solves, per op: as soon as as many are held as one pass takes (2 or 4), or when no
+    // other solve of the op has a step in flight (that step ends, so every hold ends), they go in
+    // groups of 4, 2, then alone
     for (size_t i = 0; i < running.size(); ++i) {
       Solve* a = running[i];
       if (!a->held) continue;
-      Solve* b = nullptr;
+      std::vector<Solve*> held = {a};
       bool busy = false;
       for (size_t k = 0; k < running.size(); ++k) {
         Solve* c = running[k];
         if (c == a || c->op != a->op || c->phase == kDone) continue;
-        if (c->held && !b) b = c;
+        if (c->held) held.push_back(c);
         if (c->inflight) busy = true;
       }
-      if (b) {
-        a->held = b->held = false;
-        issue_pair(sv, a, b);
-        progress = true;
-      } else if (!busy) {
-        a->held = false;
-        issue_step(sv, a);
-        progress = true;
+      const int width = uh::multi_rhs_width(a->op);
+      if (busy && static_cast<int>(held.size()) < width) continue;
+      size_t at = 0;
+      while (at < held.size()) {
+        const size_t left = held.size() - at;
+        const size_t nr = width >= 4 && left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        std::vector<Solve*> g(held.begin() + static_cast<std::ptrdiff_t>(at),
+                              held.begin() + static_cast<std::ptrdiff_t>(at + nr));
+        for (Solve* c : g) c->held = false;
+        if (nr == 1) issue_step(sv, g[0]);
+        else issue_group(sv, g);
+        at += nr;
       }
+      progress = true;
     }
     bool finished = false;
     for (Solve* s : running) finished = finished || s->phase == kDone;

@@ -550,7 +550,8 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
     for (int64_t q = a + tid; q < e; q += kStreamConsumers) {
       const int64_t src = p.perm[q];
 #pragma unroll
-      for (int r = 0; r < R; ++r) xp[q * R + r] = to_v(x[src + r * p.ldx], static_cast<T*>(nullptr));
+      for (int r = 0; r < R; ++r)
+        xp[q * R + r] = to_v((R == 1 ? x : static_cast<const TX*>(p.xr[r]))[src], static_cast<T*>(nullptr));
     }
     publish(bar, pub_ctr, np++, kCounterPermute, p, abort_flag);
   }
@@ -694,7 +695,7 @@ __device__ void consumers(const StreamParams& p, unsigned char* smem) {
         if (kind == kToY) {
 #pragma unroll
           for (int r = 0; r < R; ++r)
-            static_cast<TX*>(p.y)[out_idx + r * p.ldy] = to_x(v[r], static_cast<TX*>(nullptr));
+            static_cast<TX*>(R == 1 ? p.y : p.yr[r])[out_idx] = to_x(v[r], static_cast<TX*>(nullptr));
         } else if (is_scatter(kind)) {
           // a tall chunk (t_b rows, up to kStreamHpTall): each thread stores its own row to every
           // scatter entry holding it (few entries: one per block in the chunk)

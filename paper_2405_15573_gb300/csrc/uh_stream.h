@@ -243,8 +243,8 @@ struct StreamParams {
   void* z2;                  // yhat (kSrcZ2)
   void* z3;                  // near-field partials of row tiles (base of the backward chunks)
   void* z4;                  // t_b = S_Y,b^* xhat_sigma of the blocks stored factored (kSrcZ4)
-  int64_t ldx, ldy;          // several right-hand sides: x and y are n x R column-major, these
-                             // leading dimensions apart (unused for one right-hand side)
+  const void* xr[4];         // several right-hand sides (R > 1): x and y of right-hand side r
+  void* yr[4];               // (x and y above are unused then)
   uint32_t* status;          // nonzero after a bounded wait ran out
   long long timeout_cycles;  // bound of every wait, in SM clock cycles
 };
