@@ -324,6 +324,27 @@ def matmat_figures(model, n, steps, torch, peak_bf16, sizes=(32, 64)):
                 "tensor_tflops": tf, "tensor_peak_tflops": peaks[mode], "tensor_frac": tf / peaks[mode],
                 "max_col_relerr_vs_simt": err}
         del op
+    # the CUDA-core multi-RHS product: 4 right-hand sides per pass (an op of one CTA per SM)
+    # against one product per column
+    from paper_2405_15573_gb300 import uh as U
+    op = model.uh_op("c64", U.PackParams(0, 0, 0, 0, 1))
+    X4 = X64[:, :4]
+    Y4 = torch.empty((4, n), dtype=torch.complex64, device="cuda").T
+    for _ in range(3):
+        op.matmat(X4, Y4, mode="simt")
+    ms_cols = timed_back_to_back(_MatmatStep(op, X4, Y4, "simt"), None, None, steps, torch)
+    yc = Y4.clone()
+    op.reserve(4)
+    for _ in range(3):
+        op.matmat(X4, Y4, mode="simt")
+    ms_r4 = timed_back_to_back(_MatmatStep(op, X4, Y4, "simt"), None, None, steps, torch)
+    op.check()
+    y = Y4.cpu().numpy().astype(np.complex128)
+    out["simt_R4"] = {"ms": ms_r4, "ms_by_columns": ms_cols, "speedup": ms_cols / ms_r4,
+                      "rhs_matvec_per_s": 4e3 / ms_r4, "bitwise_equal_to_columns": bool(torch.equal(yc, Y4)),
+                      "max_col_relerr_vs_simt": max(float(np.linalg.norm(y[:, j] - yref[:, j]) /
+                                                          np.linalg.norm(yref[:, j])) for j in range(4))}
+    del op
     return out
 
 
