@@ -420,7 +420,9 @@ def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30, tru
     build_s = time.time() - t0
     for o in ops:  # solves of one operator share their Arnoldi products (passes of two)
         o.reserve(2)
-    srv = U.Server(max_active=32, hbm_budget=32 << 30, queue_capacity=1 << 20)
+    # up to 128 solves run at once: the more of them share an operator, the more products run in
+    # shared passes
+    srv = U.Server(max_active=128, hbm_budget=48 << 30, queue_capacity=1 << 20)
     for o, w in zip(ops, pool):  # one solve per operator before timing
         srv.wait(srv.submit(o, I.complex_normal(w.n, 7), tol=tol, restart=restart))
     out = {"pool": pool_count, "n_range": [min(w.n for w in pool), max(w.n for w in pool)],
