@@ -79,7 +79,7 @@ enum { UH_PREC_C128 = 0, UH_PREC_C64 = 1, UH_PREC_C64_TF32 = 2, UH_PREC_C64_BF16
 
 /* Arithmetic of uh_matmat / h_matmat.
  *  UH_MM_SIMT:   the product on the CUDA cores in the precision of uh_matvec (any op): after
- *                uh_reserve(op, >= 2) on a complex64 UH op, 4 (or 2) right-hand sides per pass
+ *                uh_reserve / h_reserve(op, >= 2) on a complex64 op, 4 (or 2) right-hand sides per pass
  *                over the operator, each column bitwise equal to its uh_matvec; otherwise one
  *                product per column.
  *  UH_MM_TF32:   tensor cores, TF32 operands, FP32 accumulation (op made with UH_PREC_C64_TF32).
@@ -411,7 +411,8 @@ int h_create(const h_desc* desc, int32_t precision, h_op** out);
 int h_destroy(h_op* op);
 /* y = A^H x, Algorithm 5 (Section 4.4); arguments as for uh_matvec. */
 int h_matvec(h_op* op, const void* x, void* y, void* stream);
-/* Y = A^H X; arguments as for uh_matmat; only UH_MM_SIMT. */
+/* Y = A^H X; arguments as for uh_matmat; only UH_MM_SIMT (in passes of 4 right-hand sides after
+ * h_reserve(op, >= 4) on a complex64 op). */
 int h_matmat(h_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy,
              int32_t mode, void* stream);
 int h_reserve(h_op* op, int32_t max_nrhs);

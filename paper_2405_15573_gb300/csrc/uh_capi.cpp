@@ -1056,6 +1056,40 @@ void uh_fill_stats(const UHPrep& u, int32_t precision, int s, uh_stats_t* st) {
   st->matmat_mode = -1;
 }
 
+// Scratch of the CUDA-core multi-RHS product (uh_reserve / h_reserve).
+int reserve_multi(OpBase* op, int32_t max_nrhs) {
+  if (!op) return fail(UH_EINVAL, "null op");
+  if (max_nrhs < 1) return fail(UH_EINVAL, "max_nrhs = %d", max_nrhs);
+  if (op->c128) return UH_OK;
+  // right-hand sides per pass: 4 (one CTA per SM), 2 (two CTAs per SM: the shared memory of the
+  // four-wide stages does not fit twice)
+  const int want = max_nrhs >= 4 && !op->dual ? 4 : max_nrhs >= 2 ? 2 : 1;
+  if (want <= op->multi_r || want < 2) return UH_OK;
+  std::lock_guard<std::mutex> lock(op->mu);
+  CUDA_TRY(cudaDeviceSynchronize());  // no pass may use the old scratch while it is replaced
+  const int variants[] = {op->dual ? uh::kVarC64DualR2 : uh::kVarC64R2, uh::kVarC64R4};
+  const int need = op->dual ? 2 : 1;
+  for (int v = 0; v < (want == 4 ? 2 : 1); ++v) {
+    CUDA_TRY(uh::stream_prepare(variants[v]));
+    int per = 0;
+    CUDA_TRY(uh::stream_occupancy(variants[v], &per));
+    if (per < need) return fail(UH_ECUDA, "multi-RHS streaming kernel does not fit %d CTAs per SM", need);
+  }
+  for (int k = 0; k < uh::kNumSources; ++k) {
+    if (op->d_xr[k]) cudaFree(op->d_xr[k]);
+    op->d_xr[k] = nullptr;
+  }
+  op->multi_r = 0;
+  for (int k = 0; k < uh::kNumSources; ++k) {
+    int rc = upload(static_cast<const void*>(nullptr),
+                    static_cast<size_t>(std::max<int64_t>(op->src_len[k], 2)) * 8 * want, &op->d_xr[k]);
+    if (rc) return rc;
+  }
+  op->multi_r = want;
+  op->st.device_bytes += (op->src_len[0] + op->src_len[1] + op->src_len[2] + op->src_len[3] + op->src_len[4]) * 8 * want;
+  return UH_OK;
+}
+
 }  // namespace
 
 struct uh_op : OpBase {};
@@ -1649,38 +1683,7 @@ int uh_matmat(uh_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int6
   }
   return call_done(op, static_cast<cudaStream_t>(stream));
 }
-int uh_reserve(uh_op* op, int32_t max_nrhs) {
-  if (!op) return fail(UH_EINVAL, "null op");
-  if (max_nrhs < 1) return fail(UH_EINVAL, "max_nrhs = %d", max_nrhs);
-  if (op->c128) return UH_OK;
-  // right-hand sides per pass: 4 (one CTA per SM), 2 (two CTAs per SM: the shared memory of the
-  // four-wide stages does not fit twice)
-  const int want = max_nrhs >= 4 && !op->dual ? 4 : max_nrhs >= 2 ? 2 : 1;
-  if (want <= op->multi_r || want < 2) return UH_OK;
-  std::lock_guard<std::mutex> lock(op->mu);
-  CUDA_TRY(cudaDeviceSynchronize());  // no pass may use the old scratch while it is replaced
-  const int variants[] = {op->dual ? uh::kVarC64DualR2 : uh::kVarC64R2, uh::kVarC64R4};
-  const int need = op->dual ? 2 : 1;
-  for (int v = 0; v < (want == 4 ? 2 : 1); ++v) {
-    CUDA_TRY(uh::stream_prepare(variants[v]));
-    int per = 0;
-    CUDA_TRY(uh::stream_occupancy(variants[v], &per));
-    if (per < need) return fail(UH_ECUDA, "multi-RHS streaming kernel does not fit %d CTAs per SM", need);
-  }
-  for (int k = 0; k < uh::kNumSources; ++k) {
-    if (op->d_xr[k]) cudaFree(op->d_xr[k]);
-    op->d_xr[k] = nullptr;
-  }
-  op->multi_r = 0;
-  for (int k = 0; k < uh::kNumSources; ++k) {
-    int rc = upload(static_cast<const void*>(nullptr),
-                    static_cast<size_t>(std::max<int64_t>(op->src_len[k], 2)) * 8 * want, &op->d_xr[k]);
-    if (rc) return rc;
-  }
-  op->multi_r = want;
-  op->st.device_bytes += (op->src_len[0] + op->src_len[1] + op->src_len[2] + op->src_len[3] + op->src_len[4]) * 8 * want;
-  return UH_OK;
-}
+int uh_reserve(uh_op* op, int32_t max_nrhs) { return reserve_multi(op, max_nrhs); }
 int h_matmat(h_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_t ldy, int32_t mode, void* stream) {
   if (!op) return fail(UH_EINVAL, "null op");
   int rc;
@@ -1688,11 +1691,7 @@ int h_matmat(h_op* op, int32_t nrhs, const void* X, int64_t ldx, void* Y, int64_
   if (mode != UH_MM_SIMT) return fail(UH_EINVAL, "h_matmat: only UH_MM_SIMT (mode %d)", mode);
   return matmat_by_columns(op, nrhs, X, ldx, Y, ldy, stream);
 }
-int h_reserve(h_op* op, int32_t max_nrhs) {
-  if (!op) return fail(UH_EINVAL, "null op");
-  if (max_nrhs < 1) return fail(UH_EINVAL, "max_nrhs = %d", max_nrhs);
-  return UH_OK;
-}
+int h_reserve(h_op* op, int32_t max_nrhs) { return reserve_multi(op, max_nrhs); }
 
 }  // extern "C"
 

@@ -187,3 +187,24 @@ def test_multi_rhs_simt_product_equals_matvec_columns(U, case):
     st = op.stats()
     assert st["pack_ctas_per_sm"] == (2 if case == "two_ctas" else 1)
     op.close()
+
+
+def test_h_form_multi_rhs_simt_product(U):
+    """The H form (Algorithm 5) in passes of 4 right-hand sides after h_reserve: every column equals
+    h_matvec bit for bit and the oracle's H product to the complex64 tolerance."""
+    import torch
+    from tests.uh_testutil import h_arrays
+    pts, tree, hf, h, uh = oracle_ops(*WORKLOADS["sphere2048"])
+    op = U.HOp.from_arrays(h_arrays(h), "c64")
+    op.reserve(4)
+    X = _X(tree.n, 6, seed=70)
+    Xd = _colmajor(torch, X)
+    Yd = _poisoned(torch, tree.n, 6)
+    op.matmat(Xd, Yd, mode="simt")
+    for j in range(6):
+        assert torch.equal(op.matvec(Xd[:, j].contiguous()), Yd[:, j]), j
+    op.check()
+    Y = Yd.cpu().numpy().astype(np.complex128)
+    for j in range(6):
+        assert relerr(Y[:, j], O.h_matvec(h, X[:, j])) <= 5e-6
+    op.close()
