@@ -2,24 +2,28 @@
 
 Workload: the unit-sphere Helmholtz collocation operator, N = 32768 Fibonacci points, k = 16,
 leaf 64, eta = 1, eps = 1e-6 (ACA 1e-8), stored complex64 with FP32 accumulation, one right-hand
-side (complex normal, seed 0). The operator is built on the host by the library's builder
-(uh_build.h), uploaded once, and then timed:
+side (complex normal, seed 0). The operator is built on the GPU by the library's builder
+(uh_build.h, the host builder is timed beside it), uploaded once, and then timed:
 
-  value     UH matvecs/s, x and y resident on the GPU, K matvecs back to back between two
-            CUDA events on the launching stream (the packed operator, about 720 MB, is several
-            times the L2 and each matvec streams all of it); the same with an L2 flush before
-            every matvec is reported beside it;
+  value     UH matvecs/s, x and y resident on the GPU, matvecs back to back between two CUDA
+            events on the launching stream for at least one second (the packed operator, about
+            720 MB, is several times the L2 and each matvec streams all of it); the same with an
+            L2 flush before every matvec is reported beside it;
   e2e       the same through host buffers: pinned x copied in, matvec, y copied out;
   roofline  algorithmic bytes of one UH matvec (stored operator + vectors, Section 4.4) per
             event-timed matvec, against the measured HBM copy bandwidth;
-  extra     the plain H-matrix matvec (Algorithm 5) on the same GPU, the complex128 UH matvec,
-            storage of both forms; the multi-RHS product uh_matmat on the tensor cores (TF32
-            and BF16x3, 32 and 64 right-hand sides) against its CUDA-core (SIMT) result;
+  extra     the plain H-matrix matvec (Algorithm 5) on the same GPU, the complex128 UH matvec
+            against the measured FP64 rate, storage of both forms; the multi-RHS product
+            uh_matmat on the tensor cores (TF32 and BF16x3, 32 and 64 right-hand sides) and on
+            the CUDA cores (4 per pass); the N = 131072 ellipsoid's 64-RHS product; 32 operators
+            of the batched workload in one launch (default and tuned packing); the factored
+            coefficient storage; the construction times;
   cpu_baseline  the FP64 oracle's UH matvec on the same operator, timed on one host core in a
             spawned child process, also giving the relative error of the GPU result.
 
-  serving   GMRES(30) solves from a pool of 8 resident operators (N up to 16384) with Poisson
-            arrivals at 200, 1000 and 2000 per second: solve latency p50 / p99 and solves per second.
+  serving   GMRES(30) solves from a pool of 8 resident operators of the serving distribution (N up
+            to 65536) with Poisson arrivals at 50 to 2000 per second: solve latency p50 / p99,
+            solves per second, and the share of Arnoldi steps whose product ran in a shared pass.
 
 `--serve` runs the serving sweep alone (pool of 64 operators, N up to 65536, six arrival rates by
 default); `--batched` times 256 independent operators in one launch against one launch each.
@@ -551,6 +555,14 @@ def profile_arm(args):
         X = _colmajor_rhs(torch, w.n, 64)
         Y = torch.empty((64, w.n), dtype=torch.complex64, device="cuda").T
         run = lambda: op.matmat(X, Y, mode=mode)  # noqa: E731
+    elif args.profile_op == "simt_r4":
+        # the CUDA-core multi-RHS product: 4 right-hand sides per pass (one CTA per SM)
+        op = model.uh_op("c64", U.PackParams(0, 0, 0, 0, 1))
+        model.close()
+        op.reserve(4)
+        X = _colmajor_rhs(torch, w.n, 4)
+        Y = torch.empty((4, w.n), dtype=torch.complex64, device="cuda").T
+        run = lambda: op.matmat(X, Y, mode="simt")  # noqa: E731
     else:
         prec = "c128" if args.profile_op.endswith("128") else "c64"
         op = model.uh_op(prec) if args.profile_op.startswith("uh") else model.h_op(prec)
@@ -847,7 +859,7 @@ def main():
     ap.add_argument("--impl", default="uh", choices=["uh", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile-op", choices=["uh64", "h64", "uh128", "mm_tf32", "mm_bf16x3"], default=None)
+    ap.add_argument("--profile-op", choices=["uh64", "h64", "uh128", "mm_tf32", "mm_bf16x3", "simt_r4"], default=None)
     ap.add_argument("--no-matmat", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the large matmat and the batch, smaller serving pool")
