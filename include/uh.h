@@ -282,10 +282,10 @@ int uh_batch_create(const uh_desc* const* descs, int32_t count, int32_t precisio
  */
 typedef struct uh_pack_params_s {
   int32_t tile_bytes, item_cost, chunk_cost, pool_unit;
-  int32_t ctas_per_sm; /* 1 or 2 CTAs of the streaming kernel per SM (2: complex64 programs only,
-                          tiles up to 24 KB in three 26 KB stages, so that the per-item and
-                          per-chunk latencies of two CTAs overlap on an SM); 0: automatic, two for
-                          complex64 operators streaming at least 256 MiB per product, else one */
+  int32_t ctas_per_sm; /* 1 or 2 CTAs of the streaming kernel per SM (2: tiles up to 24 KB in
+                          three 26 KB stages, so that the per-item and per-chunk latencies of two
+                          CTAs overlap on an SM); 0: automatic, two for operators streaming
+                          at least 256 MiB per product, else one */
 } uh_pack_params;
 
 /* uh_batch_create with packing parameters (NULL: the defaults). */

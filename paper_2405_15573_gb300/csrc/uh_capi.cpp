@@ -295,7 +295,7 @@ int query_ncta(bool c128, int* ncta, int* device, bool dual = false) {
   CUDA_TRY(cudaGetDevice(device));
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, *device));
-  const int variant = c128 ? uh::kVarC128 : dual ? uh::kVarC64Dual : uh::kVarC64;
+  const int variant = c128 ? (dual ? uh::kVarC128Dual : uh::kVarC128) : dual ? uh::kVarC64Dual : uh::kVarC64;
   CUDA_TRY(uh::stream_prepare(variant));
   int per = 0;
   CUDA_TRY(uh::stream_occupancy(variant, &per));
@@ -327,17 +327,16 @@ int pack_params_from(const uh_pack_params* params, bool c128, uh::PackParams* pp
                 uh::kTileBytes);
   if (pp->ctas_per_sm < 0 || pp->ctas_per_sm > 2)
     return fail(UH_EINVAL, "pack parameters: ctas_per_sm %lld (0: automatic, 1 or 2)", (long long)pp->ctas_per_sm);
-  if (pp->ctas_per_sm == 2 && c128) return fail(UH_EINVAL, "pack parameters: two CTAs per SM need a complex64 op");
   return UH_OK;
 }
 
-// The automatic choice of CTAs per SM (ctas_per_sm 0): two for complex64 programs that stream at
-// least kDualMinBytes per product (measured on GB300: 10-23% faster products for operators of
+// The automatic choice of CTAs per SM (ctas_per_sm 0): two for programs that stream at least
+// kDualMinBytes per product (measured on GB300: complex64 products 10-23% faster for operators of
 // 300-720 MB with ranks of 20-60, about neutral at the N = 32768 sphere, 17% slower at 168 MB, where
-// the per-CTA start and phase waits dominate), else one.
+// the per-CTA start and phase waits dominate; complex128 2% faster at the N = 32768 sphere), else one.
 constexpr int64_t kDualMinBytes = int64_t{256} << 20;
-void resolve_ctas(uh::PackParams* pp, bool c128, int64_t algo_bytes) {
-  if (pp->ctas_per_sm == 0) pp->ctas_per_sm = !c128 && algo_bytes >= kDualMinBytes ? 2 : 1;
+void resolve_ctas(uh::PackParams* pp, int64_t algo_bytes) {
+  if (pp->ctas_per_sm == 0) pp->ctas_per_sm = algo_bytes >= kDualMinBytes ? 2 : 1;
 }
 
 void fill_pack_stats(const uh::PackParams& pp, const uh::StreamGeometry& g, uh_stats_t* st) {
@@ -451,7 +450,7 @@ int run_matvec(OpBase* o, const void* x, void* y, void* stream, long long timeou
   p.status = o->d_status;
   p.timeout_cycles = timeout;
   const int variant = mixed ? (o->dual ? uh::kVarMixedDual : uh::kVarMixed)
-                      : o->c128 ? uh::kVarC128
+                      : o->c128 ? (o->dual ? uh::kVarC128Dual : uh::kVarC128)
                       : nr == 4 ? uh::kVarC64R4
                       : nr == 2 ? (o->dual ? uh::kVarC64DualR2 : uh::kVarC64R2)
                       : o->dual ? uh::kVarC64Dual : uh::kVarC64;
@@ -1120,7 +1119,7 @@ int uh_create_ex(const uh_desc* d, int32_t precision, const uh_pack_params* para
   {
     uh_stats_t est{};
     uh_fill_stats(u, precision, c128 ? 16 : 8, &est);
-    resolve_ctas(&pp, c128, est.algo_bytes_matvec);
+    resolve_ctas(&pp, est.algo_bytes_matvec);
   }
 
   const bool dual = pp.ctas_per_sm == 2;
@@ -1387,7 +1386,7 @@ int uh_batch_create_ex(const uh_desc* const* descs, int32_t count, int32_t preci
       uh_fill_stats(preps[k], precision, c128 ? 16 : 8, &est);
       bytes += est.algo_bytes_matvec;
     }
-    resolve_ctas(&pp, c128, bytes);
+    resolve_ctas(&pp, bytes);
   }
   const bool dual = pp.ctas_per_sm == 2;
   int ncta = g_pack_only_ncta, device = 0;

@@ -273,7 +273,6 @@ const char* ProgramBuilder::finalize() {
 
 const char* ProgramBuilder::self_check() const {
   const int nchunk = static_cast<int>(chunks.size());
-  if (geom_.ctas_per_sm == 2 && c128_) return "two CTAs per SM for a complex128 program";
   // the kernel permutes positions [0, perm_n) of x into xp, one slice per CTA, each CTA releasing
   // the permutation counter once
   if (perm_n_ < 0 || perm_n_ > src_len_[kSrcXp] || counter_total_[kCounterPermute] != ncta_)

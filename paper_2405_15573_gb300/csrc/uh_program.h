@@ -45,7 +45,7 @@ constexpr int kFirstPoolGroup = kGroupNearB;
 // Packing and scheduling parameters (the defaults were chosen by sweeps on the N = 32768 sphere):
 // the largest tile of an item (capped by the geometry's), the schedule's cost of an item and of a
 // chunk end in bytes streamed in the same time, the cost that consecutive pool chunks share a
-// ticket up to, and the CTAs per SM (1: kGeomOne, 2: kGeomDual, complex64 only; 0 = automatic,
+// ticket up to, and the CTAs per SM (1: kGeomOne, 2: kGeomDual; 0 = automatic,
 // resolved by the caller before packing).
 struct PackParams {
   int64_t tile_bytes = kTileBytes;

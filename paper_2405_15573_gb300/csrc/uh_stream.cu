@@ -71,6 +71,10 @@ struct KMixedDual : KMixed {
   using L = StreamSmemMixedDual;
   static constexpr int kMinBlocks = 2;
 };
+struct KC128Dual : KC128 {
+  using L = StreamSmemDual;
+  static constexpr int kMinBlocks = 2;
+};
 struct KC64DualR2 : KC64Dual {
   using L = StreamSmemDualR2;
   static constexpr int R = 2;
@@ -763,6 +767,9 @@ const void* stream_fn(int variant, int* smem_bytes) {
     case kVarC128: *smem_bytes = KC128::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC128>);
     case kVarMixed: *smem_bytes = KMixed::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KMixed>);
     case kVarC64Dual: *smem_bytes = KC64Dual::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC64Dual>);
+    case kVarC128Dual:
+      *smem_bytes = KC128Dual::L::bytes;
+      return reinterpret_cast<const void*>(stream_kernel<KC128Dual>);
     case kVarC64R2: *smem_bytes = KC64R2::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC64R2>);
     case kVarC64R4: *smem_bytes = KC64R4::L::bytes; return reinterpret_cast<const void*>(stream_kernel<KC64R4>);
     case kVarC64DualR2:

@@ -75,11 +75,12 @@ static_assert(2 * kPoolSeg + kStages <= kDescRing, "a fetched pool segment must 
 //             kStageBytesMixed: a complex64 item with ncols columns and s staged values uses
 //             ncols * hp * 8 + s * 8 <= kStageBytes bytes, hence ncols * hp * 8 + s * 16 <=
 //             kStageBytes + 8 * (kStreamMaxCols + kStreamHpMax) = kStageBytesMixed.
-// A complex64 program is packed for one of two geometries: one CTA per SM with kStages stages of
+// A program is packed for one of two geometries: one CTA per SM with kStages stages of
 // kStageBytes (tiles up to kTileBytes), or two CTAs per SM with kStagesDual stages of
 // kStageBytesDual (tiles up to kTileBytesDual). The second suits operators of many small chunks
 // (low ranks, small leaves, batches of small operators), whose per-item and per-chunk latencies
-// then overlap between the two CTAs of an SM; kVarC64Dual and kVarMixedDual run such programs.
+// then overlap between the two CTAs of an SM; kVarC64Dual, kVarMixedDual and kVarC128Dual run
+// such programs.
 // kVarC64R2 / kVarC64R4 / kVarC64DualR2 run a complex64 program for 2 or 4 right-hand sides in one
 // pass over the operator: every vector holds the R values of a position together, and an item's
 // inputs take R times the bytes, so these run two stages of the geometry's stage plus
@@ -87,7 +88,7 @@ static_assert(2 * kPoolSeg + kStages <= kDescRing, "a fetched pool segment must 
 // kStreamMaxCols + kStreamHpMax values).
 enum StreamVariant : int {
   kVarC64 = 0, kVarC128 = 1, kVarMixed = 2, kVarC64Dual = 3, kVarMixedDual = 4,
-  kVarC64R2 = 5, kVarC64R4 = 6, kVarC64DualR2 = 7
+  kVarC64R2 = 5, kVarC64R4 = 6, kVarC64DualR2 = 7, kVarC128Dual = 8
 };
 constexpr int stage_bytes_rhs(int stage_bytes, int r) { return stage_bytes + (r - 1) * 8 * (kStreamMaxCols + kStreamHpMax); }
 constexpr int kStageBytesMixed = kStageBytes + 8 * (kStreamMaxCols + kStreamHpMax);

@@ -138,3 +138,17 @@ def test_two_ctas_per_sm_op_parity(U, name):
         op.check()
         assert relerr(ym.cpu().numpy(), O.uh_matvec(stored_c64(ref), x)) <= 1e-11
         op.close()
+
+
+def test_two_ctas_per_sm_complex128_parity(U):
+    """A complex128 program on two CTAs per SM: the product agrees with the oracle to 1e-12."""
+    import torch
+    from tests.test_gpu_matvec import WORKLOADS
+    pts, tree, hf, h, uh = oracle_ops(*WORKLOADS["ellipsoid1000"])
+    op = U.UHOp.from_arrays(uh_arrays(uh), "c128", U.PackParams(0, 0, 0, 0, 2))
+    assert op.stats()["pack_ctas_per_sm"] == 2
+    x = I.complex_normal(tree.n, 41)
+    y = op.matvec(torch.from_numpy(x).to("cuda"))
+    op.check()
+    assert relerr(y.cpu().numpy(), O.uh_matvec(uh, x)) <= TOL["c128"]
+    op.close()
