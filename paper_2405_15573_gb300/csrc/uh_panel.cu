@@ -2,30 +2,29 @@
 // right-hand sides (MMAs of M = 128; of M = 64 on a compact panel layout for up to 32), one CTA
 // per SM. Layout of the work and of the operands: uh_panel.h.
 //
-// Roles in a CTA of 448 threads (14 warps):
-//  - manager (lane 0 of warp 0): streams the CTA's item descriptors into a shared-memory ring
-//    (TMA bulk copies of 8); per item it takes one of 16 item slots and room for the item's
-//    operand B in a byte ring of 120 KB, writes the slot and signals it; at a chunk's last item
-//    it hands the chunk's output record to the epilogue through a ring of mbarriers. It issues
-//    no operand copy.
+// Roles in a CTA of 448 threads (14 warps). No thread allocates operand space: the packer has
+// placed every item's operand B in the CTA's B ring and named the item whose consumption frees
+// that room (PanelItem boff, room), and the items' descriptors stream into a ring of 32 that
+// every role reads.
 //  - copy workers (lane 0 of warps 11-13, items in turn): copy operand B of their items (the
-//    packed operator, from HBM) as soon as the slots are written, up to 6 items ahead, so that
-//    operator tiles keep streaming while an operand A waits for the previous phase; and operand A
-//    (runs of panel blocks, already in the MMA's layout, from L2) into one of 3 fixed buffers once
-//    the item's panel is complete in this pass (Z1 / Z2 counters). A thread issues about two
+//    packed operator, from HBM) once the room is free, up to 6 items ahead, so that operator
+//    tiles keep streaming while an operand A waits for the previous phase; and operand A (runs
+//    of panel blocks, already in the MMA's layout, from L2) into one of 3 fixed buffers once the
+//    item's panel is complete in this pass (Z1 / Z2 counters). A thread issues about two
 //    barrier-armed bulk copies per microsecond whatever their size, so the copies are spread over
 //    three threads.
-//  - MMA issuer (lane 0 of warp 1; warp 1 also allocates and frees the tensor memory): per item
-//    waits for its slot, issues the item's tcgen05.mma instructions into the chunk's accumulator
-//    (two accumulators of 128 columns alternate between chunks) and commits them to the barriers
-//    that free the slot (its B bytes and A buffer) and, at a chunk's end, the accumulator for
-//    the epilogue.
+//  - MMA issuer (lane 0 of warp 1; warp 1 also allocates and frees the tensor memory): issues
+//    the descriptor copies (TMA bulk copies of 8, refilled as the items are consumed); per item
+//    waits for its operands, at a chunk's first item for the accumulator (two of 128 columns
+//    alternate between chunks) and hands the chunk's output record to the epilogue, issues the
+//    item's tcgen05.mma instructions and commits them to the barriers that free the slot (its B
+//    bytes and A buffer) and, at a chunk's end, the accumulator for the epilogue.
 //  - epilogue (warps 2-9, each on its own): per chunk reads its part of the finished accumulator
 //    (tcgen05.ld; warp w reads the 32-lane quarter w % 4 and half of the column blocks), combines
 //    the real products into complex outputs and writes them: Z1 / Z2 in the operand-A layout of
 //    the next phase (TF32, or BF16 hi and lo), Y as complex64 in original ordering. Each warp
 //    releases the accumulator on its own (an mbarrier of 8 arrivals), so no epilogue warp waits
-//    for another and none of them stalls the producer or the MMA issuer. After its part of a Z1
+//    for another and none of them stalls the copy workers or the MMA issuer. After its part of a Z1
 //    or Z2 chunk is stored, each warp arrives on the chunk's entry of a publication ring.
 //  - publisher (lane 0 of warp 10): per Z1 / Z2 chunk, once all 8 epilogue warps have arrived,
 //    adds 1 to the pass's counter of that panel with red.release.gpu. The release waits for the
@@ -45,39 +44,37 @@ namespace {
 
 constexpr int kAProducers = 3;          // copy-worker threads (one per warp)
 constexpr int kBAhead = 6;              // a worker's B copies run at most this many items past its A
-// B producer, MMA issuer, 8 epilogue warps, publisher, A producers
+// (warp 0 unused), MMA issuer, 8 epilogue warps, publisher, copy workers
 constexpr int kThreads = 32 * (11 + kAProducers);
 constexpr int kPubRing = 16;            // Z1 / Z2 chunk publications in flight
 constexpr int kEpiWarps = 8;
-constexpr int kDescBatch = 8;
-constexpr int kDescRing = 2 * kDescBatch;
-constexpr int kRecRing = 4;            // chunk records in flight from the producer to the epilogue
+constexpr int kDescBatch = 8;           // descriptors per bulk copy
+constexpr int kDescBatches = 4;         // batches in the descriptor ring
+constexpr int kDescRing = kDescBatches * kDescBatch;
 constexpr int kAccCols = 128;          // one accumulator: N <= 128 FP32 columns
 constexpr uint32_t kTmemCols = 2 * kAccCols;
-constexpr int kSlots = 16;             // items in flight: descriptor, B offset, full / empty barriers
+constexpr int kSlots = kPanelSlots;    // items in flight: full / empty barriers
 constexpr int kASlots = 3;             // operand-A buffers
-constexpr int kBRing = 120 * 1024;     // operand-B byte ring (B sizes are multiples of 2 KB)
+constexpr int kBRing = kPanelBRing;    // operand-B byte ring (B sizes are multiples of 2 KB)
 
 // Shared memory (bytes from a 1024-aligned base).
 constexpr int kOffA = 0;                                        // operand A [kASlots]
 constexpr int kOffB = kASlots * kPanelABytes;                   // operand-B ring (1024-aligned)
-constexpr int kOffSlots = kOffB + kBRing;                       // item descriptors [kSlots]
-constexpr int kOffBoff = kOffSlots + kSlots * 96;               // B offset in the ring [kSlots]
-constexpr int kOffDeps = kOffBoff + kSlots * 4;                 // panels read by the item [kSlots]
-constexpr int kOffRing = kOffDeps + kSlots * 4;                 // descriptor ring
-constexpr int kOffRec = kOffRing + kDescRing * 96;              // chunk records [kRecRing]
-constexpr int kOffPub = kOffRec + kRecRing * 16;                // panel of each publication [kPubRing]
+constexpr int kOffRing = kOffB + kBRing;                        // descriptor ring [kDescRing]
+constexpr int kOffRec = kOffRing + kDescRing * 96;              // chunk records [2], one per accumulator
+constexpr int kOffPub = kOffRec + 2 * 16;                       // panel of each publication [kPubRing]
 constexpr int kOffBars = kOffPub + kPubRing * 4;
-// barriers: bfull[kSlots], afull[kSlots], sready[kSlots], empty[kSlots], accfull[2], accempty[2],
-// desc[2], recfull[R], recempty[R], done, pubfull[P], pubempty[P]
-constexpr int kNumBars = 4 * kSlots + 2 + 2 + 2 + 2 * kRecRing + 1 + 2 * kPubRing;
+// barriers: bfull[kSlots], afull[kSlots], empty[kSlots], accfull[2], accempty[2], desc[kDescBatches],
+// recfull[2], done, pubfull[P], pubempty[P]
+constexpr int kNumBars = 3 * kSlots + 2 + 2 + kDescBatches + 2 + 1 + 2 * kPubRing;
 static_assert(kOffB % 1024 == 0 && kBRing % 2048 == 0, "operand-B ring alignment");
-// After a wrap the skipped tail (< one B) and the new B must fit together in the empty ring.
-static_assert(kBRing >= 2 * kPanelTileMax, "operand-B ring too small for every wrap");
 static_assert(kASlots >= kAProducers && kASlots < kSlots, "operand-A buffers");
 // A slot's barriers are reused 16 items on: a drained B copy (item j - kASlots - kAProducers up
 // to j + kBAhead + kAProducers) must not alias an item of the same slot.
 static_assert(kASlots + 2 * kAProducers + kBAhead < kSlots, "slots");
+// A copy worker at item j has seen item j - kASlots - kAProducers consumed; the descriptors it
+// reads (up to j + kBAhead) must lie in the batches issued by then.
+static_assert(kBAhead + kASlots + kAProducers + 2 * kDescBatch <= kDescRing, "descriptor ring");
 constexpr int kOffMisc = kOffBars + kNumBars * 8;              // tmem base, abort flag
 constexpr int kSmemBytes = kOffMisc + 64 + 1024;               // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory of one CTA");
@@ -91,21 +88,19 @@ struct ChunkRec {
 static_assert(sizeof(ChunkRec) == 16, "ChunkRec layout");
 
 struct Bars {
-  uint64_t *bfull, *afull, *sready, *empty, *accfull, *accempty, *desc, *recfull, *recempty, *done, *pubfull, *pubempty;
+  uint64_t *bfull, *afull, *empty, *accfull, *accempty, *desc, *recfull, *done, *pubfull, *pubempty;
 };
 __device__ __forceinline__ Bars bars_of(unsigned char* sm) {
   uint64_t* b = reinterpret_cast<uint64_t*>(sm + kOffBars);
   Bars r;
   r.bfull = b;
   r.afull = b + kSlots;
-  r.sready = b + 2 * kSlots;
-  r.empty = b + 3 * kSlots;
+  r.empty = b + 2 * kSlots;
   r.accfull = r.empty + kSlots;
   r.accempty = r.accfull + 2;
   r.desc = r.accempty + 2;
-  r.recfull = r.desc + 2;
-  r.recempty = r.recfull + kRecRing;
-  r.done = r.recempty + kRecRing;
+  r.recfull = r.desc + kDescBatches;
+  r.done = r.recfull + 2;
   r.pubfull = r.done + 1;
   r.pubempty = r.pubfull + kPubRing;
   return r;
@@ -231,127 +226,28 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned 
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
-// Manager (one thread): descriptors into the ring; per item, in order: waits for its slot (item
-// j - kSlots consumed), its descriptor and room in the B ring (freeing the B bytes of consumed
-// items, in order), then writes the slot (descriptor, B offset, panels it reads), hands over the
-// chunk record at a chunk's last item and signals the slot ready to the copy workers. It issues
-// no copy of operands. After the last item an end record (kind -1).
-__device__ void producer_b(const PanelParams& p, int i0, int n, unsigned char* sm, const Bars& bar,
-                           volatile int* abort_flag) {
+// Descriptors of items [8 batch, 8 batch + 8) of the CTA's list (from global index i0) into
+// their batch of the descriptor ring.
+__device__ void issue_desc_batch(const PanelParams& p, int i0, int n, int batch, unsigned char* sm, const Bars& bar) {
+  const int first = batch * kDescBatch;
+  if (first >= n) return;
+  const int cnt = n - first < kDescBatch ? n - first : kDescBatch;
   PanelItem* ring = reinterpret_cast<PanelItem*>(sm + kOffRing);
-  PanelItem* slots = reinterpret_cast<PanelItem*>(sm + kOffSlots);
-  int32_t* boff = reinterpret_cast<int32_t*>(sm + kOffBoff);
-  int32_t* sdeps = reinterpret_cast<int32_t*>(sm + kOffDeps);
-  ChunkRec* recs = reinterpret_cast<ChunkRec*>(sm + kOffRec);
-  auto issue_batch = [&](int batch) {
-    const int first = batch * kDescBatch;
-    if (first >= n) return;
-    const int cnt = n - first < kDescBatch ? n - first : kDescBatch;
-    uint64_t* b = &bar.desc[batch & 1];
-    mbar_arrive_expect_tx(b, static_cast<uint32_t>(cnt * sizeof(PanelItem)));
-    bulk_g2s(ring + (batch & 1) * kDescBatch, p.items + i0 + first, static_cast<uint32_t>(cnt * sizeof(PanelItem)), b);
-  };
-  issue_batch(0);
-  issue_batch(1);
-  int jb = 0, oldest = 0;   // next item, oldest item whose B bytes are held
-  int landed = 0;           // descriptor batches waited for
-  int chunk = 0;            // chunk records handed over
-  int head = 0, used = 0;   // B ring: next free byte, bytes held (with wrap waste)
-  int charge[kSlots] = {};  // B ring bytes held by the item in each slot
-  bool ok = true;
-  // Waits until item `oldest` is consumed and frees its bytes.
-  auto free_oldest = [&]() -> bool {
-    if (!wait_parity(&bar.empty[oldest % kSlots], static_cast<uint32_t>(oldest / kSlots) & 1u, p.timeout_cycles,
-                     abort_flag))
-      return false;
-    used -= charge[oldest % kSlots];
-    ++oldest;
-    return true;
-  };
-  auto rec_wait = [&]() -> bool {
-    return chunk < kRecRing || wait_parity(&bar.recempty[chunk % kRecRing],
-                                           static_cast<uint32_t>(chunk / kRecRing - 1) & 1u, p.timeout_cycles, abort_flag);
-  };
-  for (; jb < n && ok; ++jb) {
-    const int batch = jb / kDescBatch;
-    if (batch >= landed) {
-      if (!wait_parity(&bar.desc[batch & 1], static_cast<uint32_t>(batch >> 1) & 1u, p.timeout_cycles, abort_flag)) {
-        ok = false;
-        break;
-      }
-      landed = batch + 1;
-    }
-    while (ok && jb - kSlots >= oldest) ok = free_oldest();  // the slot
-    if (!ok) break;
-    const PanelItem& it = ring[jb % kDescRing];
-    const int sz = it.tile_bytes;
-    if (used == 0) head = 0;  // an empty ring starts over
-    // B goes at head, or at the ring's start when it does not fit before the end (also when
-    // head is exactly at the end); the skipped tail is held with the item.
-    bool wrap = head + sz > kBRing;
-    while (ok && used + (wrap ? kBRing - head : 0) + sz > kBRing) {
-      ok = free_oldest();
-      if (used == 0) {
-        head = 0;
-        wrap = false;
-      }
-    }
-    if (!ok) break;
-    const int waste = wrap ? kBRing - head : 0;
-    const bool last = (it.flags & kPItemLast) != 0;
-    if (last && !rec_wait()) {
-      ok = false;
-      break;
-    }
-    const int s = jb % kSlots;
-    const uint4* from = reinterpret_cast<const uint4*>(&it);
-    uint4* to = reinterpret_cast<uint4*>(slots + s);
-#pragma unroll
-    for (int w = 0; w < 6; ++w) to[w] = from[w];
-    int deps = 0;
-    for (int r = 0; r < it.nruns; ++r)
-      if (it.runs[r].src != kPSrcXP) deps |= 1 << (it.runs[r].src - 1);
-    sdeps[s] = deps;
-    const int off = wrap ? 0 : head;
-    boff[s] = off;
-    head = off + sz;
-    used += waste + sz;
-    charge[s] = waste + sz;
-    if (last) {
-      recs[chunk % kRecRing] = ChunkRec{it.out, it.h, it.n, it.kind, 0};
-      mbar_arrive(&bar.recfull[chunk % kRecRing]);  // release: the record before the epilogue's acquire
-      ++chunk;
-    }
-    mbar_arrive(&bar.sready[s]);  // release: slot, offset and panels before the copy workers' acquire
-    if (jb % kDescBatch == kDescBatch - 1) {
-      // Done with this batch's ring entries (read through the generic proxy): refill them.
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_batch(batch + 2);
-    }
-  }
-  if (ok && rec_wait()) {
-    recs[chunk % kRecRing] = ChunkRec{0, 0, 0, -1, 0};
-    mbar_arrive(&bar.recfull[chunk % kRecRing]);
-    return;
-  }
-  if (!*abort_flag) {
-    atomicOr(p.status, 1u);
-    *abort_flag = 1;
-  }
-  // Let the descriptor copies already issued land before the CTA can exit.
-  for (int b = landed; b < landed + 2 && b * kDescBatch < n; ++b)
-    drain(&bar.desc[b & 1], static_cast<uint32_t>(b >> 1) & 1u, p.timeout_cycles);
+  uint64_t* b = &bar.desc[batch % kDescBatches];
+  mbar_arrive_expect_tx(b, static_cast<uint32_t>(cnt * sizeof(PanelItem)));
+  bulk_g2s(ring + (batch % kDescBatches) * kDescBatch, p.items + i0 + first, static_cast<uint32_t>(cnt * sizeof(PanelItem)), b);
 }
+__device__ __forceinline__ uint64_t* desc_bar(const Bars& bar, int j) { return &bar.desc[(j / kDescBatch) % kDescBatches]; }
+__device__ __forceinline__ uint32_t desc_parity(int j) { return static_cast<uint32_t>(j / kDescBatch / kDescBatches) & 1u; }
 
-// Copy worker `a` of kAProducers (one thread each): items j = a, a + kAProducers, ... in order:
-// waits for the slot (manager) and copies operand B onto bfull; then waits for the item's A
-// buffer (item j - kASlots consumed) and, for runs in Z1 / Z2, the panel complete in this pass,
-// and copies the runs onto afull.
+// Copy worker `a` of kAProducers (one thread each): items j = a, a + kAProducers, ... in order,
+// their descriptors read from the ring: copies operand B to its place in the B ring once the
+// item named by its room is consumed (onto bfull), running up to kBAhead items ahead; then waits
+// for the item's A buffer (item j - kASlots consumed) and, for runs in Z1 / Z2, the panel
+// complete in this pass, and copies the runs onto afull.
 __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm, const Bars& bar,
                            volatile int* abort_flag) {
-  const PanelItem* slots = reinterpret_cast<const PanelItem*>(sm + kOffSlots);
-  const int32_t* sdeps = reinterpret_cast<const int32_t*>(sm + kOffDeps);
-  const int32_t* boff = reinterpret_cast<const int32_t*>(sm + kOffBoff);
+  const PanelItem* ring = reinterpret_cast<const PanelItem*>(sm + kOffRing);
   uint64_t keep;  // the panels stay in L2: every item's runs are read again by other items
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
   // The operator is streamed once: its lines go first, so the panels stay.
@@ -361,29 +257,38 @@ __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm
   int j = a;
   bool ok = true;
   int jbq = a;  // this worker's next B copy
-  auto copy_b = [&](int q) {
+  auto copy_b = [&](const PanelItem& ib, int q) {
     const int sb = q % kSlots;
-    const PanelItem& ib = slots[sb];
-    mbar_arrive_expect_tx(&bar.bfull[sb], static_cast<uint32_t>(ib.tile_bytes));
-    bulk_g2s_hint(sm + kOffB + boff[sb], p.tiles + ib.tile_off, static_cast<uint32_t>(ib.tile_bytes), &bar.bfull[sb],
-                  stream_once);
+    const uint32_t bytes = static_cast<uint32_t>(panel_tile_bytes(p.mode, ib.n, ib.nrows));
+    mbar_arrive_expect_tx(&bar.bfull[sb], bytes);
+    bulk_g2s_hint(sm + kOffB + ib.boff, p.tiles + ib.tile_off, bytes, &bar.bfull[sb], stream_once);
   };
-  // B of this worker's later items whose slots are already written (a test, never a wait: the
-  // manager may be waiting for room that only this worker's A copies free).
+  // B of this worker's later items whose descriptors have landed and whose room is free (tests,
+  // never waits).
   auto look_ahead = [&]() {
-    while (jbq < n && jbq <= j + kBAhead && mbar_test(&bar.sready[jbq % kSlots], static_cast<uint32_t>(jbq / kSlots) & 1u)) {
-      copy_b(jbq);
+    while (jbq < n && jbq <= j + kBAhead && mbar_test(desc_bar(bar, jbq), desc_parity(jbq))) {
+      const PanelItem& ib = ring[jbq % kDescRing];
+      const int room = ib.room;
+      if (room >= 0 && !mbar_test(&bar.empty[room % kSlots], static_cast<uint32_t>(room / kSlots) & 1u)) break;
+      copy_b(ib, jbq);
       jbq += kAProducers;
     }
   };
   for (; j < n; j += kAProducers) {
     const int s = j % kSlots;
+    if (!wait_parity(desc_bar(bar, j), desc_parity(j), p.timeout_cycles, abort_flag)) {
+      ok = false;
+      break;
+    }
+    const PanelItem& it = ring[j % kDescRing];
     if (jbq == j) {  // B of this item
-      if (!wait_parity(&bar.sready[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag)) {
+      const int room = it.room;
+      if (room >= 0 && !wait_parity(&bar.empty[room % kSlots], static_cast<uint32_t>(room / kSlots) & 1u,
+                                    p.timeout_cycles, abort_flag)) {
         ok = false;
         break;
       }
-      copy_b(j);
+      copy_b(it, j);
       jbq += kAProducers;
     }
     look_ahead();
@@ -392,7 +297,7 @@ __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm
       ok = false;
       break;
     }
-    const uint32_t deps = static_cast<uint32_t>(sdeps[s]);
+    const uint32_t deps = static_cast<uint32_t>(it.flags / kPItemDepZ1) & 3u;
     if (deps & ~ready) {
       const long long t0 = clock64();
       for (;;) {
@@ -409,7 +314,6 @@ __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm
       if (!ok) break;
       fence_proxy_async();  // the acquires above before the bulk copies that read those panels
     }
-    const PanelItem& it = slots[s];
     unsigned char* dst = sm + kOffA + (j % kASlots) * kPanelABytes;
     const uint32_t rb = panel_row_bytes(p.m64);
     mbar_arrive_expect_tx(&bar.afull[s], static_cast<uint32_t>(it.nrows) * rb);
@@ -437,11 +341,16 @@ __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm
     if (q >= 0) drain(&bar.bfull[q % kSlots], static_cast<uint32_t>(q / kSlots) & 1u, p.timeout_cycles);
 }
 
-// MMA issuer (one thread).
-__device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const Bars& bar, uint32_t tmem,
+// MMA issuer (one thread): issues the first descriptor batches; per item waits for its operands,
+// at a chunk's first item for its accumulator (and writes the chunk's record for the epilogue),
+// issues the item's tcgen05.mma instructions and commits them to the barriers that free the
+// item's slot (its B bytes and A buffer) and, at a chunk's end, the accumulator; after the last
+// item of a descriptor batch, refills that batch of the ring. After the last item an end record
+// (kind -1).
+__device__ void mma_issuer(const PanelParams& p, int i0, int n, unsigned char* sm, const Bars& bar, uint32_t tmem,
                            volatile int* abort_flag) {
-  const PanelItem* slots = reinterpret_cast<const PanelItem*>(sm + kOffSlots);
-  const int32_t* boff = reinterpret_cast<const int32_t*>(sm + kOffBoff);
+  const PanelItem* ring = reinterpret_cast<const PanelItem*>(sm + kOffRing);
+  ChunkRec* recs = reinterpret_cast<ChunkRec*>(sm + kOffRec);
   const uint32_t st_base = smem_u32(sm);
   const bool bf = p.mode == kPanelBF16X3;
   // D FP32; A, B TF32 (2) or BF16 (1); both K-major; M = 128, or 64 for a pass of at most 32
@@ -450,54 +359,68 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
   const uint32_t mdim = p.m64 ? 64u : 128u;
   const uint32_t rb = panel_row_bytes(p.m64);
   const uint32_t idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((mdim >> 4) << 24);
+  int batches = 0;  // descriptor batches issued
+  for (; batches < kDescBatches && batches * kDescBatch < n; ++batches) issue_desc_batch(p, i0, n, batches, sm, bar);
   int chunks = 0;
-  bool issued = false;
+  bool issued = false, ok = true;
   auto give_up = [&]() {
     if (!*abort_flag) {
       atomicOr(p.status, 8u);
       *abort_flag = 1;
     }
+    ok = false;
+  };
+  // The accumulator of chunk `k` is free (the epilogue is done with chunk k - 2); then record.
+  auto put_record = [&](int k, const ChunkRec& r) -> bool {
+    const int c = k & 1;
+    if (k >= 2 && !wait_parity(&bar.accempty[c], static_cast<uint32_t>((k >> 1) - 1) & 1u, p.timeout_cycles, abort_flag))
+      return false;
+    recs[c] = r;
+    mbar_arrive(&bar.recfull[c]);  // release: the record before the epilogue's acquire
+    return true;
   };
   for (int j = 0; j < n; ++j) {
     const int s = j % kSlots;
-    if (!wait_parity(&bar.bfull[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag) ||
+    if (!wait_parity(desc_bar(bar, j), desc_parity(j), p.timeout_cycles, abort_flag) ||
+        !wait_parity(&bar.bfull[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag) ||
         !wait_parity(&bar.afull[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag)) {
       give_up();
       break;
     }
-    const PanelItem& it = slots[s];
+    const PanelItem& it = ring[j % kDescRing];
     const int nn = it.n, flags = it.flags, nrows = it.nrows;
     const int c = chunks & 1;
-    if ((flags & kPItemFirst) && chunks >= 2 &&
-        !wait_parity(&bar.accempty[c], static_cast<uint32_t>((chunks >> 1) - 1) & 1u, p.timeout_cycles, abort_flag)) {
+    if ((flags & kPItemFirst) && !put_record(chunks, ChunkRec{it.out, it.h, it.n, it.kind, 0})) {
       give_up();
       break;
     }
     tc_fence_after();
     const uint32_t d = tmem + static_cast<uint32_t>(c * kAccCols);
     const uint32_t idesc = idesc_base | (static_cast<uint32_t>(nn >> 3) << 17);
-    const uint32_t A = st_base + static_cast<uint32_t>(kOffA + (j % kASlots) * kPanelABytes);
-    const uint32_t B = st_base + static_cast<uint32_t>(kOffB + boff[s]);
+    // Descriptors of the item's A buffer and B bytes; a K step moves their start addresses (the
+    // low 14 bits, in 16-byte units, which stay within shared memory).
+    const uint64_t da = plain_desc(st_base + static_cast<uint32_t>(kOffA + (j % kASlots) * kPanelABytes), (bf ? 8u : 4u) * rb);
+    const uint64_t db = sw128_desc(st_base + static_cast<uint32_t>(kOffB + it.boff));
     uint32_t acc = (flags & kPItemFirst) ? 0u : 1u;
     if (!bf) {
       // K = 8 per instruction: two 4-row blocks of A (one block, 4 rb bytes, apart); B in 32-value
       // segments.
       for (int k0 = 0; k0 < nrows; k0 += 8) {
-        const uint32_t bo = static_cast<uint32_t>((k0 / 32) * nn * 128 + (k0 % 32) * 4);
-        mma_tf32(d, plain_desc(A + static_cast<uint32_t>(k0) * rb, 4 * rb), sw128_desc(B + bo), idesc, acc);
+        const uint32_t bo = static_cast<uint32_t>((k0 >> 5) * nn * 128 + (k0 & 31) * 4);
+        mma_tf32(d, da + ((static_cast<uint32_t>(k0) * rb) >> 4), db + (bo >> 4), idesc, acc);
         acc = 1u;
       }
     } else {
       // K = 16 per instruction: two 8-row blocks of A (8 rb bytes apart, lo plane 4 rb into each);
       // B's hi plane in segment 0, lo plane in segment 1. hi*hi + hi*lo + lo*hi.
-      const uint32_t blo = static_cast<uint32_t>(nn) * 128u;
+      const uint64_t dblo = db + ((static_cast<uint32_t>(nn) * 128u) >> 4);
+      const uint64_t dalo = da + ((4u * rb) >> 4);
       for (int k0 = 0; k0 < nrows; k0 += 16) {
-        const uint32_t a = A + static_cast<uint32_t>(k0) * rb;
-        const uint32_t o = static_cast<uint32_t>(k0 * 2);
-        mma_bf16(d, plain_desc(a, 8 * rb), sw128_desc(B + o), idesc, acc);
+        const uint64_t ao = (static_cast<uint32_t>(k0) * rb) >> 4, bo = static_cast<uint32_t>(k0 * 2) >> 4;
+        mma_bf16(d, da + ao, db + bo, idesc, acc);
         acc = 1u;
-        mma_bf16(d, plain_desc(a, 8 * rb), sw128_desc(B + blo + o), idesc, 1u);
-        mma_bf16(d, plain_desc(a + 4 * rb, 8 * rb), sw128_desc(B + o), idesc, 1u);
+        mma_bf16(d, da + ao, dblo + bo, idesc, 1u);
+        mma_bf16(d, dalo + ao, db + bo, idesc, 1u);
       }
     }
     issued = true;
@@ -506,7 +429,18 @@ __device__ void mma_issuer(const PanelParams& p, int n, unsigned char* sm, const
       tc_commit(&bar.accfull[c]);
       ++chunks;
     }
+    // Done with this batch's ring entries (the copy workers read them before the copies this
+    // item waited for): refill them with the batch kDescBatches on.
+    if ((j % kDescBatch == kDescBatch - 1) && batches * kDescBatch < n) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_desc_batch(p, i0, n, batches, sm, bar);
+      ++batches;
+    }
   }
+  if (ok && !put_record(chunks, ChunkRec{0, 0, 0, -1, 0})) give_up();
+  // Let the descriptor copies already issued land before the CTA can exit.
+  for (int b = batches > kDescBatches ? batches - kDescBatches : 0; b < batches; ++b)
+    drain(&bar.desc[b % kDescBatches], static_cast<uint32_t>(b / kDescBatches) & 1u, p.timeout_cycles);
   // No MMA may be in flight when the tensor memory is freed.
   if (issued) {
     tc_commit(bar.done);
@@ -557,20 +491,19 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
   const bool bf = p.mode == kPanelBF16X3;
   const int64_t rb = panel_row_bytes(p.m64);
   for (int k = 0;; ++k) {
-    const int qr = k % kRecRing;
-    if (!warp_wait(&bar.recfull[qr], static_cast<uint32_t>(k / kRecRing) & 1u, p.timeout_cycles, abort_flag)) {
+    const int c = k & 1;
+    if (!warp_wait(&bar.recfull[c], static_cast<uint32_t>(k >> 1) & 1u, p.timeout_cycles, abort_flag)) {
       if (lane == 0 && !*abort_flag) {
         atomicOr(p.status, 2u);
         *abort_flag = 1;
       }
       return;
     }
-    const ChunkRec rec = recs[qr];
+    const ChunkRec rec = recs[c];
     if (rec.kind < 0) {
       publish(-1);
       return;
     }
-    const int c = k & 1;
     if (!warp_wait(&bar.accfull[c], static_cast<uint32_t>(k >> 1) & 1u, p.timeout_cycles, abort_flag)) {
       if (lane == 0 && !*abort_flag) {
         atomicOr(p.status, 4u);
@@ -647,10 +580,7 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
     }
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) {
-      mbar_arrive(&bar.accempty[c]);
-      mbar_arrive(&bar.recempty[qr]);
-    }
+    if (lane == 0) mbar_arrive(&bar.accempty[c]);  // the accumulator and the record are free
     if (rec.kind != kPOutY && !publish(rec.kind)) return;
   }
 }
@@ -688,18 +618,14 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelParams p)
     for (int s = 0; s < kSlots; ++s) {
       mbar_init(&bar.bfull[s], 1);
       mbar_init(&bar.afull[s], 1);
-      mbar_init(&bar.sready[s], 1);
       mbar_init(&bar.empty[s], 1);  // MMA commit: both operands read
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(&bar.accfull[q], 1);
       mbar_init(&bar.accempty[q], kEpiWarps);
-      mbar_init(&bar.desc[q], 1);
-    }
-    for (int q = 0; q < kRecRing; ++q) {
       mbar_init(&bar.recfull[q], 1);
-      mbar_init(&bar.recempty[q], kEpiWarps);
     }
+    for (int q = 0; q < kDescBatches; ++q) mbar_init(&bar.desc[q], 1);
     mbar_init(bar.done, 1);
     for (int q = 0; q < kPubRing; ++q) {
       mbar_init(&bar.pubfull[q], kEpiWarps);
@@ -720,9 +646,9 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelParams p)
   const uint32_t tmem = *tmem_slot;
   const int i0 = p.cta_begin[blockIdx.x], n = p.cta_begin[blockIdx.x + 1] - i0;
   if (warp == 0) {
-    if (threadIdx.x == 0) producer_b(p, i0, n, sm, bar, abort_flag);
+    // no role: the operand placement is precomputed by the packer
   } else if (warp == 1) {
-    if (threadIdx.x == 32) mma_issuer(p, n, sm, bar, tmem, abort_flag);
+    if (threadIdx.x == 32) mma_issuer(p, i0, n, sm, bar, tmem, abort_flag);
   } else if (warp < 2 + kEpiWarps) {
     epilogue(p, sm, bar, tmem, abort_flag);
   } else if (warp == 2 + kEpiWarps) {

@@ -42,10 +42,15 @@ constexpr int kPanelR = 64;          // right-hand sides per pass (M = 2 kPanelR
 constexpr int kPanelK = 64;          // panel rows (K) per item
 constexpr int kPanelMaxH = 64;       // outputs per chunk (N <= 128)
 constexpr int kPanelMaxRuns = 8;     // contiguous runs of panel blocks per item
-constexpr int kPanelStages = 3;
 constexpr int kPanelRowBytes = 512;                          // one panel row in operand-A layout
 constexpr int kPanelTileMax = 2 * 128 * 2 * kPanelMaxH;      // B bytes at N = 128, two segments (32 KB)
 constexpr int kPanelABytes = kPanelK * kPanelRowBytes;       // operand A of an item (32 KB)
+// A CTA's operand-B ring in shared memory, and its items in flight (each has a slot of
+// barriers). The packer places every item's B in the ring (PanelItem::boff) and names the item
+// whose consumption frees that room and the item's slot (PanelItem::room), so the copies need
+// no allocator on the device.
+constexpr int kPanelBRing = 120 * 1024;
+constexpr int kPanelSlots = 16;
 // Bytes of a panel row in a pass: M = 128 rows of operand A, or the compact layout of M = 64
 // (the same core-matrix pattern for rows 0-63, blocks of C * 256 bytes) for at most 32
 // right-hand sides.
@@ -65,7 +70,8 @@ constexpr int panel_mma_k(int mode) { return mode == kPanelTF32 ? 8 : 16; }
 // Panel sources and outputs.
 enum : int8_t { kPSrcXP = 0, kPSrcZ1 = 1, kPSrcZ2 = 2 };
 enum : int16_t { kPOutZ1 = 0, kPOutZ2 = 1, kPOutY = 2 };
-enum : int16_t { kPItemFirst = 1, kPItemLast = 2 };
+// kPItemDepZ1 / kPItemDepZ2: the item's operand A reads Z1 / Z2.
+enum : int16_t { kPItemFirst = 1, kPItemLast = 2, kPItemDepZ1 = 4, kPItemDepZ2 = 8 };
 
 struct PanelRun {
   int32_t start;  // first panel row in the source (a multiple of the block rows)
@@ -77,8 +83,10 @@ static_assert(sizeof(PanelRun) == 8, "PanelRun layout");
 
 struct alignas(16) PanelItem {
   int64_t tile_off;    // byte offset of the item's B operand in the packed tiles
-  int64_t out;         // the chunk's first output row (Z1 / Z2 row, or Y position in cluster order)
-  int32_t tile_bytes;  // bytes of B: 128 * n per K segment
+  int32_t out;         // the chunk's first output row (Z1 / Z2 row, or Y position in cluster order)
+  int32_t boff;        // byte offset of B in the CTA's operand-B ring
+  int32_t room;        // B may be copied once the CTA's item `room` (index in its list) is consumed;
+                       // -1: at once
   int16_t n;           // MMA N = 2h rounded up to 16
   int16_t h;           // the chunk's output rows
   int16_t kind;        // kPOut*
@@ -88,6 +96,11 @@ struct alignas(16) PanelItem {
   PanelRun runs[kPanelMaxRuns];
 };
 static_assert(sizeof(PanelItem) == 96, "PanelItem layout");
+// Bytes of an item's operand B: 128 * n per K segment (TF32: one per 32 panel rows; BF16: the hi
+// and the lo plane).
+UH_HOST_DEVICE constexpr int panel_tile_bytes(int mode, int n, int nrows) {
+  return 128 * n * (mode == kPanelTF32 ? (nrows + 31) / 32 : 2);
+}
 
 // A pass (one launch).
 struct PanelParams {

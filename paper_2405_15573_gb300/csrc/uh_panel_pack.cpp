@@ -60,10 +60,10 @@ void PanelBuilder::pack_item(PanelItem& it, int h, const std::vector<const ColSp
                              const std::vector<int64_t>& q) {
   const int n = it.n;
   // TF32: one 128-byte K segment per 32 columns; BF16: the hi and the lo plane (K <= 64).
-  const int nseg = mode_ == kPanelTF32 ? (it.nrows + 31) / 32 : 2;
-  const size_t bytes = static_cast<size_t>(128) * n * nseg;
+  const size_t bytes = static_cast<size_t>(panel_tile_bytes(mode_, n, it.nrows));
   it.tile_off = static_cast<int64_t>(tiles.size());
-  it.tile_bytes = static_cast<int32_t>(bytes);
+  for (int r = 0; r < it.nruns; ++r)
+    if (it.runs[r].src != kPSrcXP) it.flags |= it.runs[r].src == kPSrcZ1 ? kPItemDepZ1 : kPItemDepZ2;
   streamed_bytes += static_cast<int64_t>(bytes);
   mma_flops += int64_t{2} * 128 * n * it.nrows * (mode_ == kPanelTF32 ? 1 : 3);
   tiles.resize(tiles.size() + bytes, 0);
@@ -101,7 +101,7 @@ void PanelBuilder::add_chunk(int phase, int16_t kind, int64_t out, int h, const 
   std::vector<int64_t> q;
   auto fresh = [&]() {
     PanelItem it{};
-    it.out = out;
+    it.out = static_cast<int32_t>(out);
     it.n = n;
     it.h = static_cast<int16_t>(h);
     it.kind = kind;
@@ -119,7 +119,7 @@ void PanelBuilder::add_chunk(int phase, int16_t kind, int64_t out, int h, const 
       }
     }
     pack_item(cur, h, spec, q);
-    ch.cost += item_cost(mode_, cur.tile_bytes, static_cast<int64_t>(cur.nrows) * kPanelRowBytes);
+    ch.cost += item_cost(mode_, panel_tile_bytes(mode_, cur.n, cur.nrows), static_cast<int64_t>(cur.nrows) * kPanelRowBytes);
     ch.items.push_back(cur);
     cur = fresh();
     spec.clear();
@@ -203,6 +203,39 @@ const char* PanelBuilder::finalize() {
     if (items.size() > static_cast<size_t>(INT32_MAX)) return "too many work items";
   }
   begin[ncta_] = static_cast<int32_t>(items.size());
+  // The CTA's operand-B ring, items placed in list order and freed in list order (the MMAs
+  // consume them in order): B goes at the head, or at the ring's start when it does not fit
+  // before the end (the skipped tail is held with the item); an empty ring starts over. Before
+  // its copy, the item waits for the consumption of the last item that has to be freed to make
+  // room, and of the item kPanelSlots before it (whose barriers it reuses): the last item freed
+  // so far, since another copy worker may copy it before the copies of the items before it.
+  std::vector<int> charge;
+  for (int b = 0; b < ncta_; ++b) {
+    const int n = begin[b + 1] - begin[b];
+    PanelItem* its = items.data() + begin[b];
+    charge.assign(static_cast<size_t>(n), 0);
+    int head = 0, used = 0, oldest = 0;
+    for (int j = 0; j < n; ++j) {
+      for (; oldest <= j - kPanelSlots; ++oldest) used -= charge[oldest];
+      const int sz = panel_tile_bytes(mode_, its[j].n, its[j].nrows);
+      if (used == 0) head = 0;
+      bool wrap = head + sz > kPanelBRing;
+      while (used + (wrap ? kPanelBRing - head : 0) + sz > kPanelBRing) {
+        used -= charge[oldest];
+        ++oldest;
+        if (used == 0) {
+          head = 0;
+          wrap = false;
+        }
+      }
+      const int off = wrap ? 0 : head;
+      charge[j] = (wrap ? kPanelBRing - head : 0) + sz;
+      used += charge[j];
+      head = off + sz;
+      its[j].boff = off;
+      its[j].room = oldest - 1;
+    }
+  }
   return nullptr;
 }
 
@@ -227,11 +260,26 @@ const char* PanelBuilder::self_check(const int64_t src_rows[3], const int64_t ou
         if (it.h < 1 || it.h > kPanelMaxH || 2 * it.h > it.n) return "chunk height";
         if (it.nrows < 0 || it.nrows > kPanelK || it.nrows % kmma_ || it.nruns < 0 || it.nruns > kPanelMaxRuns)
           return "item size";
-        const int nseg = mode_ == kPanelTF32 ? (it.nrows + 31) / 32 : 2;
-        if (it.tile_bytes != 128 * it.n * nseg || it.tile_bytes > kPanelTileMax) return "operand B size";
-        if (it.tile_off < 0 || it.tile_off % 1024 ||
-            it.tile_off + static_cast<int64_t>(it.tile_bytes) > static_cast<int64_t>(tiles.size()))
+        const int bytes = panel_tile_bytes(mode_, it.n, it.nrows);
+        if (bytes > kPanelTileMax) return "operand B size";
+        if (it.tile_off < 0 || it.tile_off % 1024 || it.tile_off + static_cast<int64_t>(bytes) > static_cast<int64_t>(tiles.size()))
           return "tile outside the packed tiles or misaligned";
+        // Operand B in the ring: inside it, 1024-aligned, copied only after the item whose
+        // barrier slot it reuses is consumed, and disjoint from every earlier item that can still
+        // hold its bytes (one consumed after this item's room is free).
+        const int jj = j - i0;
+        if (it.boff < 0 || it.boff % 1024 || it.boff + bytes > kPanelBRing) return "operand B outside its ring";
+        if (it.room >= jj || it.room < jj - kPanelSlots || (jj >= kPanelSlots && it.room < 0))
+          return "operand B room";
+        for (int q = std::max(0, it.room + 1); q < jj; ++q) {
+          const PanelItem& o = items[i0 + q];
+          const int ob = panel_tile_bytes(mode_, o.n, o.nrows);
+          if (o.boff < it.boff + bytes && it.boff < o.boff + ob) return "operand B overlaps an item in flight";
+        }
+        int deps = 0;
+        for (int r = 0; r < it.nruns; ++r)
+          if (it.runs[r].src != kPSrcXP) deps |= it.runs[r].src == kPSrcZ1 ? kPItemDepZ1 : kPItemDepZ2;
+        if ((it.flags & (kPItemDepZ1 | kPItemDepZ2)) != deps) return "panel dependencies";
         int64_t rows = 0;
         for (int r = 0; r < it.nruns; ++r) {
           const PanelRun& run = it.runs[r];
@@ -242,8 +290,8 @@ const char* PanelBuilder::self_check(const int64_t src_rows[3], const int64_t ou
         }
         if (rows != it.nrows) return "run lengths";
         if (it.kind < kPOutZ1 || it.kind > kPOutY || it.out < 0) return "chunk output";
-        if (it.kind == kPOutY ? it.out + it.h > out_rows[it.kind]
-                              : (it.out % C_ || it.out + (it.h + C_ - 1) / C_ * C_ > out_rows[it.kind]))
+        if (it.kind == kPOutY ? int64_t{it.out} + it.h > out_rows[it.kind]
+                              : (it.out % C_ || int64_t{it.out} + (it.h + C_ - 1) / C_ * C_ > out_rows[it.kind]))
           return "chunk outside its output or misaligned";
         if ((it.flags & kPItemFirst) == open) return "chunk boundaries";
         open = !(it.flags & kPItemLast);
