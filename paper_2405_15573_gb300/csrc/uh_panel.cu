@@ -9,14 +9,16 @@
 //  - copy workers (lane 0 of warps 11-13, items in turn): copy operand B of their items (the
 //    packed operator, from HBM) once the room is free, up to 6 items ahead, so that operator
 //    tiles keep streaming while an operand A waits for the previous phase; and operand A (runs
-//    of panel blocks, already in the MMA's layout, from L2) into one of 3 fixed buffers once the
-//    item's panel is complete in this pass (Z1 / Z2 counters). A thread issues about two
+//    of panel blocks, already in the MMA's layout, from L2) into one of 3 fixed buffers (6 of half
+//    the size in a pass of M = 64) once the item's panel is complete in this pass (Z1 / Z2
+//    counters). Both copies arrive on the item's one full barrier. A thread issues about two
 //    barrier-armed bulk copies per microsecond whatever their size, so the copies are spread over
 //    three threads.
 //  - MMA issuer (lane 0 of warp 1; warp 1 also allocates and frees the tensor memory): issues
 //    the descriptor copies (TMA bulk copies of 8, refilled as the items are consumed); per item
-//    waits for its operands, at a chunk's first item for the accumulator (two of 128 columns
-//    alternate between chunks) and hands the chunk's output record to the epilogue, issues the
+//    waits for its operands, at a chunk's first item for the accumulator (all 512 columns of
+//    tensor memory, taken in turn by the chunks: four of 128 columns for TF32, two of 256 for
+//    BF16x3) and hands the chunk's output record to the epilogue, issues the
 //    item's tcgen05.mma instructions and commits them to the barriers that free the slot (its B
 //    bytes and A buffer) and, at a chunk's end, the accumulator for the epilogue.
 //  - epilogue (warps 2-9, each on its own): per chunk reads its part of the finished accumulator
@@ -51,30 +53,38 @@ constexpr int kEpiWarps = 8;
 constexpr int kDescBatch = 8;           // descriptors per bulk copy
 constexpr int kDescBatches = 4;         // batches in the descriptor ring
 constexpr int kDescRing = kDescBatches * kDescBatch;
-constexpr int kAccCols = 128;          // one accumulator: N <= 128 FP32 columns
-constexpr uint32_t kTmemCols = 2 * kAccCols;
+constexpr int kAccCols = 128;          // one accumulator of a TF32 pass: N <= 128 FP32 columns
+constexpr int kAccs = 4;               // accumulators, chunk after chunk (all 512 columns)
+constexpr uint32_t kTmemCols = kAccs * kAccCols;
 constexpr int kSlots = kPanelSlots;    // items in flight: full / empty barriers
-constexpr int kASlots = 3;             // operand-A buffers
+constexpr int kASlots = 3;             // operand-A buffers of 32 KB (twice as many of 16 KB at M = 64)
 constexpr int kBRing = kPanelBRing;    // operand-B byte ring (B sizes are multiples of 2 KB)
 
 // Shared memory (bytes from a 1024-aligned base).
 constexpr int kOffA = 0;                                        // operand A [kASlots]
 constexpr int kOffB = kASlots * kPanelABytes;                   // operand-B ring (1024-aligned)
 constexpr int kOffRing = kOffB + kBRing;                        // descriptor ring [kDescRing]
-constexpr int kOffRec = kOffRing + kDescRing * 96;              // chunk records [2], one per accumulator
-constexpr int kOffPub = kOffRec + 2 * 16;                       // panel of each publication [kPubRing]
+constexpr int kOffRec = kOffRing + kDescRing * 96;              // chunk records [kAccs], one per accumulator
+constexpr int kOffPub = kOffRec + kAccs * 16;                   // panel of each publication [kPubRing]
 constexpr int kOffBars = kOffPub + kPubRing * 4;
-// barriers: bfull[kSlots], afull[kSlots], empty[kSlots], accfull[2], accempty[2], desc[kDescBatches],
-// recfull[2], done, pubfull[P], pubempty[P]
-constexpr int kNumBars = 3 * kSlots + 2 + 2 + kDescBatches + 2 + 1 + 2 * kPubRing;
+// barriers: full[kSlots] (operands B and A landed: two arrivals with their bytes), empty[kSlots],
+// accfull[A], accempty[A], desc[kDescBatches], recfull[A], done, pubfull[P], pubempty[P]
+constexpr int kNumBars = 2 * kSlots + 3 * kAccs + kDescBatches + 1 + 2 * kPubRing;
 static_assert(kOffB % 1024 == 0 && kBRing % 2048 == 0, "operand-B ring alignment");
-static_assert(kASlots >= kAProducers && kASlots < kSlots, "operand-A buffers");
-// A slot's barriers are reused 16 items on: a drained B copy (item j - kASlots - kAProducers up
-// to j + kBAhead + kAProducers) must not alias an item of the same slot.
-static_assert(kASlots + 2 * kAProducers + kBAhead < kSlots, "slots");
-// A copy worker at item j has seen item j - kASlots - kAProducers consumed; the descriptors it
-// reads (up to j + kBAhead) must lie in the batches issued by then.
-static_assert(kBAhead + kASlots + kAProducers + 2 * kDescBatch <= kDescRing, "descriptor ring");
+static_assert(kASlots >= 2 && 2 * kASlots < kSlots, "operand-A buffers");
+// A slot's barriers are reused kSlots items on: a drained B copy (item j - nA - kAProducers up
+// to j + kBAhead + kAProducers, nA <= 2 kASlots buffers) must not alias an item of the same slot.
+static_assert(2 * kASlots + 2 * kAProducers + kBAhead < kSlots, "slots");
+// A copy worker at item j has seen item j - nA - kAProducers consumed; the descriptors it reads
+// (up to j + kBAhead) must lie in the batches issued by then.
+static_assert(kBAhead + 2 * kASlots + kAProducers + 2 * kDescBatch <= kDescRing, "descriptor ring");
+// Operand-A buffers of a pass: kASlots of a whole operand A, or at M = 64 (compact panel rows of
+// half the bytes) twice as many in the same space.
+__device__ __forceinline__ int a_buffers(int m64) { return m64 ? 2 * kASlots : kASlots; }
+__device__ __forceinline__ int a_buffer_bytes(int m64) { return m64 ? kPanelABytes / 2 : kPanelABytes; }
+// A BF16x3 pass accumulates hi*[hi; lo] in 2 N columns: two accumulators of 256 columns.
+__device__ __forceinline__ int acc_count(bool bf) { return bf ? kAccs / 2 : kAccs; }
+__device__ __forceinline__ int acc_cols(bool bf) { return bf ? 2 * kAccCols : kAccCols; }
 constexpr int kOffMisc = kOffBars + kNumBars * 8;              // tmem base, abort flag
 constexpr int kSmemBytes = kOffMisc + 64 + 1024;               // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory of one CTA");
@@ -88,19 +98,18 @@ struct ChunkRec {
 static_assert(sizeof(ChunkRec) == 16, "ChunkRec layout");
 
 struct Bars {
-  uint64_t *bfull, *afull, *empty, *accfull, *accempty, *desc, *recfull, *done, *pubfull, *pubempty;
+  uint64_t *full, *empty, *accfull, *accempty, *desc, *recfull, *done, *pubfull, *pubempty;
 };
 __device__ __forceinline__ Bars bars_of(unsigned char* sm) {
   uint64_t* b = reinterpret_cast<uint64_t*>(sm + kOffBars);
   Bars r;
-  r.bfull = b;
-  r.afull = b + kSlots;
-  r.empty = b + 2 * kSlots;
+  r.full = b;
+  r.empty = b + kSlots;
   r.accfull = r.empty + kSlots;
-  r.accempty = r.accfull + 2;
-  r.desc = r.accempty + 2;
+  r.accempty = r.accfull + kAccs;
+  r.desc = r.accempty + kAccs;
   r.recfull = r.desc + kDescBatches;
-  r.done = r.recfull + 2;
+  r.done = r.recfull + kAccs;
   r.pubfull = r.done + 1;
   r.pubempty = r.pubfull + kPubRing;
   return r;
@@ -242,9 +251,10 @@ __device__ __forceinline__ uint32_t desc_parity(int j) { return static_cast<uint
 
 // Copy worker `a` of kAProducers (one thread each): items j = a, a + kAProducers, ... in order,
 // their descriptors read from the ring: copies operand B to its place in the B ring once the
-// item named by its room is consumed (onto bfull), running up to kBAhead items ahead; then waits
-// for the item's A buffer (item j - kASlots consumed) and, for runs in Z1 / Z2, the panel
-// complete in this pass, and copies the runs onto afull.
+// item named by its room is consumed, running up to kBAhead items ahead; then waits for the
+// item's A buffer (item j - nA consumed, nA buffers) and, for runs in Z1 / Z2, the panel complete
+// in this pass, and copies the runs. Both copies arrive on the item's full barrier (two
+// arrivals, with their bytes).
 __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm, const Bars& bar,
                            volatile int* abort_flag) {
   const PanelItem* ring = reinterpret_cast<const PanelItem*>(sm + kOffRing);
@@ -257,11 +267,12 @@ __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm
   int j = a;
   bool ok = true;
   int jbq = a;  // this worker's next B copy
+  const int na = a_buffers(p.m64), abytes = a_buffer_bytes(p.m64);
   auto copy_b = [&](const PanelItem& ib, int q) {
     const int sb = q % kSlots;
     const uint32_t bytes = static_cast<uint32_t>(panel_tile_bytes(p.mode, ib.n, ib.nrows));
-    mbar_arrive_expect_tx(&bar.bfull[sb], bytes);
-    bulk_g2s_hint(sm + kOffB + ib.boff, p.tiles + ib.tile_off, bytes, &bar.bfull[sb], stream_once);
+    mbar_arrive_expect_tx(&bar.full[sb], bytes);
+    bulk_g2s_hint(sm + kOffB + ib.boff, p.tiles + ib.tile_off, bytes, &bar.full[sb], stream_once);
   };
   // B of this worker's later items whose descriptors have landed and whose room is free (tests,
   // never waits).
@@ -292,8 +303,8 @@ __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm
       jbq += kAProducers;
     }
     look_ahead();
-    if (j >= kASlots && !wait_parity(&bar.empty[(j - kASlots) % kSlots],
-                                     static_cast<uint32_t>((j - kASlots) / kSlots) & 1u, p.timeout_cycles, abort_flag)) {
+    if (j >= na && !wait_parity(&bar.empty[(j - na) % kSlots], static_cast<uint32_t>((j - na) / kSlots) & 1u,
+                                p.timeout_cycles, abort_flag)) {
       ok = false;
       break;
     }
@@ -314,15 +325,15 @@ __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm
       if (!ok) break;
       fence_proxy_async();  // the acquires above before the bulk copies that read those panels
     }
-    unsigned char* dst = sm + kOffA + (j % kASlots) * kPanelABytes;
+    unsigned char* dst = sm + kOffA + (j % na) * abytes;
     const uint32_t rb = panel_row_bytes(p.m64);
-    mbar_arrive_expect_tx(&bar.afull[s], static_cast<uint32_t>(it.nrows) * rb);
+    mbar_arrive_expect_tx(&bar.full[s], static_cast<uint32_t>(it.nrows) * rb);
     uint32_t row = 0;
     for (int r = 0; r < it.nruns; ++r) {
       const PanelRun run = it.runs[r];
       const unsigned char* src = static_cast<const unsigned char*>(p.src[run.src]);
       bulk_g2s_hint(dst + row * rb, src + static_cast<int64_t>(run.start) * rb, static_cast<uint32_t>(run.len) * rb,
-                    &bar.afull[s], keep);
+                    &bar.full[s], keep);
       row += static_cast<uint32_t>(run.len);
     }
     look_ahead();
@@ -332,13 +343,12 @@ __device__ void producer_a(const PanelParams& p, int n, int a, unsigned char* sm
     atomicOr(p.status, 64u);
     *abort_flag = 1;
   }
-  // The copies of this worker still in flight: A of its items among the last kASlots before j,
-  // B of its items from there up to jbq.
-  for (int q = j - kAProducers; q >= 0 && q >= j - kASlots - kAProducers; q -= kAProducers)
-    drain(&bar.afull[q % kSlots], static_cast<uint32_t>(q / kSlots) & 1u, p.timeout_cycles);
-  // (items before j - kASlots - kAProducers are consumed: the previous item's buffer wait)
-  for (int q = j - kASlots - kAProducers; q < jbq; q += kAProducers)
-    if (q >= 0) drain(&bar.bfull[q % kSlots], static_cast<uint32_t>(q / kSlots) & 1u, p.timeout_cycles);
+  // The copies of this worker still in flight: its items from j - nA - kAProducers (earlier ones
+  // are consumed: the previous item's buffer wait) up to jbq. Items from j on have their B copy
+  // but no A copy: the missing arrival (without bytes) lets their barrier complete when B lands.
+  for (int q = j; q < jbq; q += kAProducers) mbar_arrive(&bar.full[q % kSlots]);
+  for (int q = j - na - kAProducers; q < jbq; q += kAProducers)
+    if (q >= 0) drain(&bar.full[q % kSlots], static_cast<uint32_t>(q / kSlots) & 1u, p.timeout_cycles);
 }
 
 // MMA issuer (one thread): issues the first descriptor batches; per item waits for its operands,
@@ -359,6 +369,8 @@ __device__ void mma_issuer(const PanelParams& p, int i0, int n, unsigned char* s
   const uint32_t mdim = p.m64 ? 64u : 128u;
   const uint32_t rb = panel_row_bytes(p.m64);
   const uint32_t idesc_base = (1u << 4) | (fmt << 7) | (fmt << 10) | ((mdim >> 4) << 24);
+  const int na = a_buffers(p.m64), abytes = a_buffer_bytes(p.m64);
+  const int nacc = acc_count(bf);
   int batches = 0;  // descriptor batches issued
   for (; batches < kDescBatches && batches * kDescBatch < n; ++batches) issue_desc_batch(p, i0, n, batches, sm, bar);
   int chunks = 0;
@@ -370,10 +382,11 @@ __device__ void mma_issuer(const PanelParams& p, int i0, int n, unsigned char* s
     }
     ok = false;
   };
-  // The accumulator of chunk `k` is free (the epilogue is done with chunk k - 2); then record.
+  // The accumulator of chunk `k` is free (the epilogue is done with chunk k - nacc); then record.
   auto put_record = [&](int k, const ChunkRec& r) -> bool {
-    const int c = k & 1;
-    if (k >= 2 && !wait_parity(&bar.accempty[c], static_cast<uint32_t>((k >> 1) - 1) & 1u, p.timeout_cycles, abort_flag))
+    const int c = k % nacc;
+    if (k >= nacc &&
+        !wait_parity(&bar.accempty[c], static_cast<uint32_t>(k / nacc - 1) & 1u, p.timeout_cycles, abort_flag))
       return false;
     recs[c] = r;
     mbar_arrive(&bar.recfull[c]);  // release: the record before the epilogue's acquire
@@ -381,25 +394,27 @@ __device__ void mma_issuer(const PanelParams& p, int i0, int n, unsigned char* s
   };
   for (int j = 0; j < n; ++j) {
     const int s = j % kSlots;
-    if (!wait_parity(desc_bar(bar, j), desc_parity(j), p.timeout_cycles, abort_flag) ||
-        !wait_parity(&bar.bfull[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag) ||
-        !wait_parity(&bar.afull[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag)) {
+    // (the batch's descriptors land together: one wait per batch)
+    if ((j % kDescBatch == 0 && !wait_parity(desc_bar(bar, j), desc_parity(j), p.timeout_cycles, abort_flag)) ||
+        !wait_parity(&bar.full[s], static_cast<uint32_t>(j / kSlots) & 1u, p.timeout_cycles, abort_flag)) {
       give_up();
       break;
     }
     const PanelItem& it = ring[j % kDescRing];
     const int nn = it.n, flags = it.flags, nrows = it.nrows;
-    const int c = chunks & 1;
-    if ((flags & kPItemFirst) && !put_record(chunks, ChunkRec{it.out, it.h, it.n, it.kind, 0})) {
-      give_up();
-      break;
+    const int c = chunks % nacc;
+    if (flags & kPItemFirst) {
+      if (!put_record(chunks, ChunkRec{it.out, it.h, it.n, it.kind, 0})) {
+        give_up();
+        break;
+      }
+      tc_fence_after();  // the epilogue's reads of this accumulator before these MMAs
     }
-    tc_fence_after();
-    const uint32_t d = tmem + static_cast<uint32_t>(c * kAccCols);
+    const uint32_t d = tmem + static_cast<uint32_t>(c * acc_cols(bf));
     const uint32_t idesc = idesc_base | (static_cast<uint32_t>(nn >> 3) << 17);
     // Descriptors of the item's A buffer and B bytes; a K step moves their start addresses (the
     // low 14 bits, in 16-byte units, which stay within shared memory).
-    const uint64_t da = plain_desc(st_base + static_cast<uint32_t>(kOffA + (j % kASlots) * kPanelABytes), (bf ? 8u : 4u) * rb);
+    const uint64_t da = plain_desc(st_base + static_cast<uint32_t>(kOffA + (j % na) * abytes), (bf ? 8u : 4u) * rb);
     const uint64_t db = sw128_desc(st_base + static_cast<uint32_t>(kOffB + it.boff));
     uint32_t acc = (flags & kPItemFirst) ? 0u : 1u;
     if (!bf) {
@@ -411,15 +426,16 @@ __device__ void mma_issuer(const PanelParams& p, int i0, int n, unsigned char* s
         acc = 1u;
       }
     } else {
-      // K = 16 per instruction: two 8-row blocks of A (8 rb bytes apart, lo plane 4 rb into each);
-      // B's hi plane in segment 0, lo plane in segment 1. hi*hi + hi*lo + lo*hi.
-      const uint64_t dblo = db + ((static_cast<uint32_t>(nn) * 128u) >> 4);
+      // K = 16 per instruction: two 8-row blocks of A (8 rb bytes apart, lo plane 4 rb into each).
+      // B's hi plane (segment 0) and lo plane (segment 1, n rows on) are one K-major operand of
+      // 2 n rows: hi*[hi; lo] into columns [0, 2n), then lo*hi into [0, n); the epilogue adds
+      // column n + i to column i (hi*hi + lo*hi + hi*lo).
+      const uint32_t idesc2 = idesc_base | (static_cast<uint32_t>(nn >> 2) << 17);
       const uint64_t dalo = da + ((4u * rb) >> 4);
       for (int k0 = 0; k0 < nrows; k0 += 16) {
         const uint64_t ao = (static_cast<uint32_t>(k0) * rb) >> 4, bo = static_cast<uint32_t>(k0 * 2) >> 4;
-        mma_bf16(d, da + ao, db + bo, idesc, acc);
+        mma_bf16(d, da + ao, db + bo, idesc2, acc);
         acc = 1u;
-        mma_bf16(d, da + ao, dblo + bo, idesc, 1u);
         mma_bf16(d, dalo + ao, db + bo, idesc, 1u);
       }
     }
@@ -489,10 +505,11 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
   const int m = p.m64 ? 16 * q + (lane & 15) : 32 * q + lane;
   const int r = m >> 1, part = m & 1;
   const bool bf = p.mode == kPanelBF16X3;
+  const int nacc = acc_count(bf);
   const int64_t rb = panel_row_bytes(p.m64);
   for (int k = 0;; ++k) {
-    const int c = k & 1;
-    if (!warp_wait(&bar.recfull[c], static_cast<uint32_t>(k >> 1) & 1u, p.timeout_cycles, abort_flag)) {
+    const int c = k % nacc;
+    if (!warp_wait(&bar.recfull[c], static_cast<uint32_t>(k / nacc) & 1u, p.timeout_cycles, abort_flag)) {
       if (lane == 0 && !*abort_flag) {
         atomicOr(p.status, 2u);
         *abort_flag = 1;
@@ -504,7 +521,7 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
       publish(-1);
       return;
     }
-    if (!warp_wait(&bar.accfull[c], static_cast<uint32_t>(k >> 1) & 1u, p.timeout_cycles, abort_flag)) {
+    if (!warp_wait(&bar.accfull[c], static_cast<uint32_t>(k / nacc) & 1u, p.timeout_cycles, abort_flag)) {
       if (lane == 0 && !*abort_flag) {
         atomicOr(p.status, 4u);
         *abort_flag = 1;
@@ -518,7 +535,7 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
       if (lane < h) pm0 = p.perm[rec.out + lane];
       if (32 + lane < h) pm1 = p.perm[rec.out + 32 + lane];
     }
-    const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(c * kAccCols);
+    const uint32_t tbase = tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(c * acc_cols(bf));
     for (int n0 = 16 * hf; n0 < rec.n; n0 += 32) {
       uint32_t v[16];
       asm volatile(
@@ -527,7 +544,20 @@ __device__ void epilogue(const PanelParams& p, unsigned char* sm, const Bars& ba
             "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
           : "r"(tbase + static_cast<uint32_t>(n0))
           : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (bf) {  // + hi*lo, n columns on
+        uint32_t w[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]),
+              "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
+            : "r"(tbase + static_cast<uint32_t>(n0 + rec.n))
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = __float_as_uint(__uint_as_float(v[e]) + __uint_as_float(w[e]));
+      } else {
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      }
       // Re: D[2r][2i] - D[2r+1][2i+1]; Im: D[2r+1][2i] + D[2r][2i+1] (partner lane m ^ 1).
       float val[8];
 #pragma unroll
@@ -616,11 +646,10 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelParams p)
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kSlots; ++s) {
-      mbar_init(&bar.bfull[s], 1);
-      mbar_init(&bar.afull[s], 1);
+      mbar_init(&bar.full[s], 2);  // operand B and operand A
       mbar_init(&bar.empty[s], 1);  // MMA commit: both operands read
     }
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kAccs; ++q) {
       mbar_init(&bar.accfull[q], 1);
       mbar_init(&bar.accempty[q], kEpiWarps);
       mbar_init(&bar.recfull[q], 1);

@@ -50,7 +50,7 @@ constexpr int kPanelABytes = kPanelK * kPanelRowBytes;       // operand A of an 
 // whose consumption frees that room and the item's slot (PanelItem::room), so the copies need
 // no allocator on the device.
 constexpr int kPanelBRing = 120 * 1024;
-constexpr int kPanelSlots = 16;
+constexpr int kPanelSlots = 24;
 // Bytes of a panel row in a pass: M = 128 rows of operand A, or the compact layout of M = 64
 // (the same core-matrix pattern for rows 0-63, blocks of C * 256 bytes) for at most 32
 // right-hand sides.

@@ -44,15 +44,13 @@ size_t swizzled(int row, int k, int rows, int esz) {
          (((byte / 16) ^ (row % 8)) * 16) + byte % 16;
 }
 
-// Schedule cost of an item, in bytes streamed in the same time: its operand B, a quarter of its
-// operand A (read from L2, not HBM), but at least the bytes a CTA streams while the tensor core
-// runs the item's MMAs (measured on GB300: about 0.45 us per item of 64 panel rows in BF16x3,
-// 0.35 us in TF32, against ~45 GB/s of operator per CTA).
-constexpr int64_t kABytesDivisor = 4;
-int64_t item_cost(int mode, int64_t b_bytes, int64_t a_bytes) {
-  const int64_t mma_floor = mode == kPanelTF32 ? 16384 : 20480;
-  return std::max(b_bytes + a_bytes / kABytesDivisor, mma_floor);
-}
+// Schedule cost of an item. A CTA's time over a pass grows with the number of its items and
+// hardly with their bytes (measured on GB300 with per-CTA clock stamps, N = 32768 sphere, both
+// modes: about 7 us + 0.85 us per item, the spread of bytes per CTA explaining none of the rest):
+// the per-item path of the MMA issuer (operand waits, then the item's MMAs) sets the pace. The
+// operand-B bytes only break ties.
+constexpr int64_t kItemCost = int64_t{1} << 20;
+int64_t item_cost(int64_t b_bytes) { return kItemCost + b_bytes; }
 
 }  // namespace
 
@@ -119,7 +117,7 @@ void PanelBuilder::add_chunk(int phase, int16_t kind, int64_t out, int h, const 
       }
     }
     pack_item(cur, h, spec, q);
-    ch.cost += item_cost(mode_, panel_tile_bytes(mode_, cur.n, cur.nrows), static_cast<int64_t>(cur.nrows) * kPanelRowBytes);
+    ch.cost += item_cost(panel_tile_bytes(mode_, cur.n, cur.nrows));
     ch.items.push_back(cur);
     cur = fresh();
     spec.clear();
@@ -183,18 +181,24 @@ const char* PanelBuilder::finalize() {
   begin.assign(ncta_ + 1, 0);
   using Entry = std::pair<int64_t, int>;
   std::vector<std::vector<int>> per_cta(ncta_);
+  // Phase 0 on its own (every coupling item waits until all of Z1 is written, so the CTAs start
+  // phase 1 together); phases 1 and 2 together, phase 2 on the loads phase 1 left (its near
+  // field does not wait for Z2, so a CTA runs the two back to back).
+  std::vector<int64_t> load(ncta_, 0);
   for (int phase = 0; phase < 3; ++phase) {
     std::vector<int> ids;
     for (size_t c = 0; c < chunks_.size(); ++c)
       if (chunks_[c].phase == phase) ids.push_back(static_cast<int>(c));
     std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return chunks_[a].cost > chunks_[b].cost; });
+    if (phase < 2) load.assign(ncta_, 0);
     std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> pq;
-    for (int b = 0; b < ncta_; ++b) pq.push({0, b});
+    for (int b = 0; b < ncta_; ++b) pq.push({load[b], b});
     for (int c : ids) {
       auto [l, b] = pq.top();
       pq.pop();
       per_cta[b].push_back(c);
-      pq.push({l + chunks_[c].cost, b});
+      load[b] = l + chunks_[c].cost;
+      pq.push({load[b], b});
     }
   }
   for (int b = 0; b < ncta_; ++b) {

@@ -23,8 +23,8 @@ class PanelBuilder {
   // in operand B.
   void add_chunk(int phase, int16_t kind, int64_t out, int h, const std::vector<ColSpec>& cols);
 
-  // Assign the chunks of each phase to CTAs (longest processing time first) and lay the items
-  // out by CTA, each CTA's list phase by phase.
+  // Assign the chunks to CTAs (longest processing time first: phase 0 on its own, phases 1 and 2
+  // on shared loads) and lay the items out by CTA, each CTA's list phase by phase.
   const char* finalize();
   // Checks every address the kernel derives from the program against the panel heights
   // (src_rows: rows of XP, Z1, Z2, each a multiple of the block rows) and the output heights
