@@ -397,41 +397,45 @@ def build_models(workloads):
             for w in workloads]
 
 
-def build_ops(workloads, precision="c64"):
-    """Device ops of several operators, each built on the GPU and uploaded, its host model freed
-    before the next one is built."""
+def build_ops(workloads, precision="c64", params=None):
+    """Device ops of several operators, each built on the GPU and uploaded (packing parameters
+    `params`, None: the defaults), its host model freed before the next one is built."""
     from paper_2405_15573_gb300 import uh as U
     ops = []
     for w in workloads:
         m = U.HelmholtzModel(w.points(), w.wavenumber, w.leaf, w.eta, w.eps, w.tol_aca, device=True)
-        ops.append(m.uh_op(precision))
+        ops.append(m.uh_op(precision, params))
         m.close()
     return ops
 
 
-def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30, true_residual_sample=0):
+def serving_figures(pool_count, n_hi, rates, requests, tol=1e-6, restart=30, true_residual_sample=0, max_active=128,
+                    pass_width=2):
     """GMRES(restart) solves served from a pool of resident complex64 UH operators (uh_server):
     per arrival rate, `requests` solves with Poisson arrivals, each on a random operator of the
     pool with a seeded right-hand side. Latency = submission to completion (library clock);
     throughput = completed solves / wall time from the first submission to the last completion.
     Each rate runs max(requests, rate / 5) solves, so that at the high rates the start and the
-    drain of the queue take a small part of the wall time."""
+    drain of the queue take a small part of the wall time. Solves of one operator share their
+    Arnoldi products in passes of `pass_width` right-hand sides: 2 on the automatic packing, 4 on
+    operators packed for one CTA per SM (the four-wide stages do not fit twice on an SM)."""
     from paper_2405_15573_gb300 import inputs as I
     from paper_2405_15573_gb300 import uh as U
     pool = I.serving_pool(pool_count, n_hi=n_hi)
     t0 = time.time()
-    ops = build_ops(pool)
+    ops = build_ops(pool, params=U.PackParams(0, 0, 0, 0, 1) if pass_width == 4 else None)
     build_s = time.time() - t0
-    for o in ops:  # solves of one operator share their Arnoldi products (passes of two)
-        o.reserve(2)
-    # up to 128 solves run at once: the more of them share an operator, the more products run in
-    # shared passes
-    srv = U.Server(max_active=128, hbm_budget=48 << 30, queue_capacity=1 << 20)
+    for o in ops:
+        o.reserve(pass_width)
+    # up to max_active solves run at once: the more of them share an operator, the more products
+    # run in shared passes
+    srv = U.Server(max_active=max_active, hbm_budget=48 << 30, queue_capacity=1 << 20)
     for o, w in zip(ops, pool):  # one solve per operator before timing
         srv.wait(srv.submit(o, I.complex_normal(w.n, 7), tol=tol, restart=restart))
     out = {"pool": pool_count, "n_range": [min(w.n for w in pool), max(w.n for w in pool)],
            "operator_bytes_c64": int(sum(o.stats()["algo_bytes_matvec"] for o in ops)),
-           "build_s": round(build_s, 1), "tol": tol, "restart": restart, "rates": {}}
+           "build_s": round(build_s, 1), "tol": tol, "restart": restart, "max_active": max_active,
+           "pass_width": pass_width, "rates": {}}
     base_requests = requests
     for lam in rates:
         requests = max(base_requests, int(lam / 5))
@@ -868,6 +872,8 @@ def main():
     ap.add_argument("--n-hi", type=int, default=65536)
     ap.add_argument("--rates", default="50,100,200,500,1000,2000")
     ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--max-active", type=int, default=128, help="serving: solves running at once")
+    ap.add_argument("--pass-width", type=int, default=2, choices=[2, 4], help="serving: right-hand sides per shared pass")
     ap.add_argument("--batched", action="store_true", help="batched-operator timing only")
     ap.add_argument("--operators", type=int, default=256)
     args = ap.parse_args()
@@ -879,7 +885,8 @@ def main():
     if args.serve:
         import torch
         torch.cuda.init()
-        res = serving_figures(args.pool, args.n_hi, [float(v) for v in args.rates.split(",")], args.requests)
+        res = serving_figures(args.pool, args.n_hi, [float(v) for v in args.rates.split(",")], args.requests,
+                              max_active=args.max_active, pass_width=args.pass_width)
         print(json.dumps({"serving": res}), flush=True)
         return
     if args.profile_op:
